@@ -1,0 +1,775 @@
+/*
+ * HODLRdD CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 restatement of the HODLRdD method (Khan, Kandappan and
+ * Ambikasaran, "HODLRdD: A new black-box fast algorithm for N-body problems in
+ * d-dimensions with guaranteed error bounds"). It exists to check the GPU path:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg may load
+ * it. It shares no code, header or table with the CUDA library.
+ *
+ * What it computes (each function below cites its passage):
+ *   - the kernel matrix K(i,j) = scale * F(x_i, x_j) + diag * [i == j]
+ *     (Section "Preliminaries", kernel matrix; the log experiment's zero diagonal
+ *     in Section "HODLRdD fast matrix-vector product");
+ *   - the direct O(N^2) product y = K x, the exact result;
+ *   - the balanced 2^d tree on a bounding hyper-cube (Section "Construction of
+ *     the tree"), its levels and leaves (Algorithm 1's level rule, read with <=);
+ *   - the interaction lists from the clan / IL definitions of Table "Notations"
+ *     and the HODLRdD admissibility condition, by brute force over box pairs;
+ *   - partial-pivoted ACA of every (target, IL) block (Section "HODLRdD
+ *     algorithm", Eq. keq1 / keq2, Algorithm 1);
+ *   - the matrix-vector product of Algorithm 2, in two algebraically equal forms:
+ *     stored factors U V^T, and the paper's memory-efficient form
+ *     K(I,tau) U^-1 L^-1 K(sigma,J) with forward/back substitution.
+ *
+ * Built with -ffp-contract=off so every a*b+c rounds twice, in source order.
+ * Readings of places where the paper is silent are listed in the design notes;
+ * the ones that shape this file are stated next to the code they affect.
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+enum {
+  K_LOG = 0, K_INV_R = 1, K_MATERN32 = 2, K_GAUSS = 3, K_EXP = 4,
+  K_INV_R2_4D = 5, K_R = 6, K_SIN = 7, K_INV_SQRT1P = 8, K_COUNT = 9
+};
+
+enum { FLAG_DENSE_IF_CHEAPER = 1 };
+
+struct Kern {
+  int id;
+  double scale, diag, p0, p1;
+};
+
+// Squared Euclidean distance, summed over dimensions in order 0..d-1.
+double sqdist(const double* a, const double* b, int d) {
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double t = a[k] - b[k];
+    s = s + t * t;
+  }
+  return s;
+}
+
+// F as a function of s = r^2. Section "Preliminaries" lists F1..F8 with
+// r = |x - y|_2; the matvec experiment sets F(x,x) = 0 for log r. Reading: every
+// singular kernel (log r, 1/r, 1/r^2) is 0 at r = 0, for any pair of indices.
+double F_of_s(const Kern& k, double s) {
+  switch (k.id) {
+    case K_LOG: {
+      if (s == 0.0) return 0.0;
+      double r = std::sqrt(s);
+      return std::log(r);
+    }
+    case K_INV_R: {
+      if (s == 0.0) return 0.0;
+      double r = std::sqrt(s);
+      return 1.0 / r;
+    }
+    case K_MATERN32: {  // (1 + sqrt(3) r / l) exp(-sqrt(3) r / l), l = p0
+      double r = std::sqrt(s);
+      double a = (1.7320508075688772 * r) / k.p0;
+      return (1.0 + a) * std::exp(-a);
+    }
+    case K_GAUSS:  // exp(-r^2 / (2 h^2)), h = p0
+      return std::exp(-s / (2.0 * k.p0 * k.p0));
+    case K_EXP: {  // exp(-r / l), l = p0 (F8, Matern nu = 1/2)
+      double r = std::sqrt(s);
+      return std::exp(-r / k.p0);
+    }
+    case K_INV_R2_4D:  // 4D Laplace Green's function -1 / (4 pi^2 r^2)
+      if (s == 0.0) return 0.0;
+      return -1.0 / (39.47841760435743 * s);
+    case K_R:
+      return std::sqrt(s);
+    case K_SIN:
+      return std::sin(std::sqrt(s));
+    case K_INV_SQRT1P: {
+      double r = std::sqrt(s);
+      return 1.0 / std::sqrt(1.0 + r);
+    }
+  }
+  return 0.0;
+}
+
+struct Problem {
+  int d = 0;
+  int64_t N = 0;
+  Kern K{};
+  std::vector<double> pts;  // N x d row-major, original order
+  // K(i, j) by ORIGINAL indices (the diagonal term needs index identity).
+  double entry(int64_t i, int64_t j) const {
+    double s = sqdist(&pts[(size_t)i * d], &pts[(size_t)j * d], d);
+    double v = K.scale * F_of_s(K, s);
+    if (i == j) v = v + K.diag;
+    return v;
+  }
+};
+
+struct Block {
+  int level = 0;
+  int64_t ti = 0, sj = 0;          // target / source box index at `level`
+  int64_t I0 = 0, m = 0, J0 = 0, n = 0;  // tree-order row / column ranges
+  int rank = 0;
+  int dense = 0;                   // 1: applied exactly, no factors kept
+  int capped = 0;                  // 1: ACA reached min(m, n) without meeting tol
+  std::vector<int64_t> sigma, tau; // pivot rows / columns (block-local)
+  std::vector<double> U, V;        // m x rank and n x rank, column-major
+};
+
+struct Tree {
+  Problem P;
+  int leaf = 0, flags = 0, B = 0, kappa = 0;
+  double tol = 0.0;
+  std::vector<double> lo;
+  double side = 0.0, inv = 0.0;
+  std::vector<uint64_t> key;    // Morton key per original point
+  std::vector<int64_t> perm;    // tree position -> original index
+  std::vector<uint64_t> skey;   // keys in tree order
+  std::vector<std::vector<int64_t>> bstart;  // level -> nb + 1 offsets
+  std::vector<std::vector<uint64_t>> bkey;   // level -> box keys (ascending)
+  std::vector<std::vector<int64_t>> iloff, ilidx;  // level -> IL CSR (level 0 empty)
+  std::vector<int64_t> nearoff, nearidx;           // leaf level near CSR
+  std::vector<int64_t> blk_off;                    // level -> first block index
+  std::vector<Block> blocks;
+};
+
+// ---------------------------------------------------------------- tree ----
+// Section "Construction of the tree to build d dimensional hierarchical matrix":
+// a hyper-cube C holding all points is split 2^d-ways per level. Reading: C is
+// computed from the points, lo_k = min_i x_ik, side = max_k (max - min) scaled by
+// (1 + 2^-40) so the largest coordinate falls inside. Integer cell coordinates
+// use B = min(32, floor(63 / d)) bits per dimension; the box of a point at level
+// l is the top l bits of each coordinate.
+void bounding_cube(Tree& T) {
+  const int d = T.P.d;
+  const int64_t N = T.P.N;
+  T.lo.assign(d, 0.0);
+  std::vector<double> hi(d, 0.0);
+  for (int k = 0; k < d; ++k) {
+    double mn = T.P.pts[k], mx = T.P.pts[k];
+    for (int64_t i = 1; i < N; ++i) {
+      double v = T.P.pts[(size_t)i * d + k];
+      if (v < mn) mn = v;
+      if (v > mx) mx = v;
+    }
+    T.lo[k] = mn;
+    hi[k] = mx;
+  }
+  double ext = 0.0;
+  for (int k = 0; k < d; ++k) ext = std::max(ext, hi[k] - T.lo[k]);
+  T.side = ext > 0.0 ? ext * (1.0 + std::ldexp(1.0, -40)) : 1.0;
+  T.B = std::min(32, 63 / d);
+  T.inv = std::ldexp(1.0, T.B) / T.side;
+}
+
+// The point's cell coordinate along dimension k at the finest level B.
+uint64_t cell_coord(const Tree& T, int64_t i, int k) {
+  double t = (T.P.pts[(size_t)i * T.P.d + k] - T.lo[k]) * T.inv;
+  double f = std::floor(t);
+  uint64_t maxc = (uint64_t(1) << T.B) - 1;
+  if (f < 0.0) f = 0.0;
+  uint64_t q = (uint64_t)f;
+  return q > maxc ? maxc : q;
+}
+
+// Morton key: level digits from coarse to fine, dimension k at bit k of a digit.
+uint64_t morton(const uint64_t* q, int d, int bits) {
+  uint64_t key = 0;
+  for (int b = bits - 1; b >= 0; --b)
+    for (int k = 0; k < d; ++k) key |= ((q[k] >> b) & 1u) << (d * b + k);
+  return key;
+}
+
+void decode(uint64_t key, int d, int bits, int64_t* c) {
+  for (int k = 0; k < d; ++k) c[k] = 0;
+  for (int b = 0; b < bits; ++b)
+    for (int k = 0; k < d; ++k) c[k] |= (int64_t)((key >> (d * b + k)) & 1u) << b;
+}
+
+void build_levels(Tree& T) {
+  const int d = T.P.d;
+  const int64_t N = T.P.N;
+  T.key.resize(N);
+  std::vector<uint64_t> q(d);
+  for (int64_t i = 0; i < N; ++i) {
+    for (int k = 0; k < d; ++k) q[k] = cell_coord(T, i, k);
+    T.key[i] = morton(q.data(), d, T.B);
+  }
+  // Stable order by key; equal keys keep their original order.
+  T.perm.resize(N);
+  for (int64_t i = 0; i < N; ++i) T.perm[i] = i;
+  std::stable_sort(T.perm.begin(), T.perm.end(),
+                   [&](int64_t a, int64_t b) { return T.key[a] < T.key[b]; });
+  T.skey.resize(N);
+  for (int64_t i = 0; i < N; ++i) T.skey[i] = T.key[T.perm[i]];
+
+  // Algorithm 1: kappa = the first level whose every box holds at most
+  // leaf points (read with <=, as the tree section's "at most N_max"); capped
+  // at B, where identical points can no longer be separated.
+  T.bstart.clear();
+  T.bkey.clear();
+  for (int l = 0;; ++l) {
+    int shift = d * (T.B - l);
+    std::vector<int64_t> st;
+    std::vector<uint64_t> bk;
+    int64_t maxocc = 0;
+    for (int64_t i = 0; i < N; ++i) {
+      uint64_t bkey = (shift >= 64) ? 0 : (T.skey[i] >> shift);
+      if (i == 0 || bkey != bk.back()) {
+        if (!st.empty()) maxocc = std::max(maxocc, i - st.back());
+        st.push_back(i);
+        bk.push_back(bkey);
+      }
+    }
+    if (N > 0) maxocc = std::max(maxocc, N - st.back());
+    st.push_back(N);
+    T.bstart.push_back(st);
+    T.bkey.push_back(bk);
+    if (maxocc <= T.leaf || l == T.B) {
+      T.kappa = l;
+      break;
+    }
+  }
+}
+
+// Interaction lists, by the definitions (Table "Notations for this section"):
+//   clan(i) = siblings(i) U children(P) for P sharing a d'-hyper-surface with
+//   parent(i); IL(i) = clan(i) ∩ (vertex-sharing U far-field of i).
+// Reading: the union over P is taken for d' = 1..d-1 (and the parent itself via
+// the siblings). Taking d' = 0 as well would admit again pairs already admitted
+// at the parent's level, and Algorithm 2 would then add them twice.
+// Far-field = at least one box away (Chebyshev index distance >= 2); sharing a
+// d'-surface = Chebyshev distance 1 with d' zero offsets; a vertex = d' = 0.
+void classify(Tree& T) {
+  const int d = T.P.d;
+  T.iloff.assign(T.kappa + 1, std::vector<int64_t>(1, 0));
+  T.ilidx.assign(T.kappa + 1, std::vector<int64_t>());
+  std::vector<int64_t> ci(d), cj(d);
+  for (int l = 1; l <= T.kappa; ++l) {
+    const std::vector<uint64_t>& bk = T.bkey[l];
+    const int64_t nb = (int64_t)bk.size();
+    std::vector<int64_t> coords((size_t)nb * d);
+    for (int64_t b = 0; b < nb; ++b) decode(bk[b], d, l, &coords[(size_t)b * d]);
+    std::vector<int64_t>& off = T.iloff[l];
+    std::vector<int64_t>& idx = T.ilidx[l];
+    off.assign(nb + 1, 0);
+    idx.clear();
+    for (int64_t i = 0; i < nb; ++i) {
+      const int64_t* c_i = &coords[(size_t)i * d];
+      for (int64_t j = 0; j < nb; ++j) {
+        if (j == i) continue;
+        const int64_t* c_j = &coords[(size_t)j * d];
+        // Parent relation: same parent, or parents sharing a d' >= 1 surface.
+        bool pnear = true, pzero = false, psame = true;
+        for (int k = 0; k < d; ++k) {
+          int64_t dp = (c_j[k] >> 1) - (c_i[k] >> 1);
+          if (dp < -1 || dp > 1) pnear = false;
+          if (dp == 0) pzero = true; else psame = false;
+        }
+        if (!pnear || !(psame || pzero)) continue;
+        int64_t cheb = 0;
+        bool vertex = true;
+        for (int k = 0; k < d; ++k) {
+          int64_t dl = c_j[k] - c_i[k];
+          int64_t a = dl < 0 ? -dl : dl;
+          cheb = std::max(cheb, a);
+          if (a != 1) vertex = false;
+        }
+        if (cheb >= 2 || vertex) idx.push_back(j);
+      }
+      off[i + 1] = (int64_t)idx.size();
+    }
+  }
+  // Leaf near field (Algorithm 2's dense part): self and every leaf sharing a
+  // d' >= 1 hyper-surface, in ascending box order.
+  const int l = T.kappa;
+  const int64_t nb = (int64_t)T.bkey[l].size();
+  std::vector<int64_t> coords((size_t)nb * d);
+  for (int64_t b = 0; b < nb; ++b) decode(T.bkey[l][b], d, l, &coords[(size_t)b * d]);
+  T.nearoff.assign(nb + 1, 0);
+  T.nearidx.clear();
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int64_t j = 0; j < nb; ++j) {
+      bool zero = false;
+      int64_t cheb = 0;
+      for (int k = 0; k < d; ++k) {
+        int64_t dl = coords[(size_t)j * d + k] - coords[(size_t)i * d + k];
+        int64_t a = dl < 0 ? -dl : dl;
+        cheb = std::max(cheb, a);
+        if (dl == 0) zero = true;
+      }
+      if (cheb <= 1 && zero) T.nearidx.push_back(j);  // includes j == i
+    }
+    T.nearoff[i + 1] = (int64_t)T.nearidx.size();
+  }
+}
+
+// ----------------------------------------------------------------- ACA ----
+// Partial-pivoted ACA (the paper compresses each IL block with ACA, Eq. keq1,
+// citing Bebendorf and Tyrtyshnikov). Readings of what the paper leaves open:
+// first pivot row 0; lowest index wins ties; a residual row that is exactly zero
+// is skipped; stop after appending term k when |u_k||v_k| <= tol * ||A_k||_F
+// (the term is kept) or when k = min(m, n). ||A_k||_F^2 is updated by
+//   S += 2 sum_{q<k} (u_q . u_k)(v_q . v_k) + |u_k|^2 |v_k|^2.
+// With FLAG_DENSE_IF_CHEAPER a block whose factors would hold at least as many
+// numbers as the block itself (k (m + n) >= m n) is marked dense and applied
+// exactly; this is the library's storage rule, not the paper's.
+template <class Entry>
+void aca(const Entry& A, int64_t m, int64_t n, double tol, int flags, Block& out) {
+  out.U.clear();
+  out.V.clear();
+  out.sigma.clear();
+  out.tau.clear();
+  out.rank = 0;
+  out.dense = 0;
+  out.capped = 0;
+  const int64_t kmax = std::min(m, n);
+  std::vector<char> used(m, 0);
+  int64_t nused = 0;
+  int64_t istar = 0;
+  double S = 0.0;
+  std::vector<double> a(n), u(m);
+  int64_t k = 0;
+  while (true) {
+    // Residual row istar: a_j = A(istar, j) - sum_q u_q(istar) v_q(j).
+    for (int64_t j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int64_t q = 0; q < k; ++q) s = s + out.U[(size_t)q * m + istar] * out.V[(size_t)q * n + j];
+      a[j] = A(istar, j) - s;
+    }
+    used[istar] = 1;
+    ++nused;
+    int64_t jstar = 0;
+    double best = std::fabs(a[0]);
+    for (int64_t j = 1; j < n; ++j) {
+      double v = std::fabs(a[j]);
+      if (v > best) { best = v; jstar = j; }
+    }
+    if (best == 0.0) {  // exactly zero residual row: try the next unused row
+      if (nused == m) break;
+      istar = 0;
+      while (used[istar]) ++istar;
+      continue;
+    }
+    const double piv = a[jstar];
+    // v_k = a / a_jstar ; u_k = A(:, jstar) - sum_q v_q(jstar) u_q.
+    for (int64_t j = 0; j < n; ++j) out.V.push_back(a[j] / piv);
+    for (int64_t i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int64_t q = 0; q < k; ++q) s = s + out.V[(size_t)q * n + jstar] * out.U[(size_t)q * m + i];
+      u[i] = A(i, jstar) - s;
+    }
+    for (int64_t i = 0; i < m; ++i) out.U.push_back(u[i]);
+    out.sigma.push_back(istar);
+    out.tau.push_back(jstar);
+    const double* uk = &out.U[(size_t)k * m];
+    const double* vk = &out.V[(size_t)k * n];
+    double uu = 0.0, vv = 0.0;
+    for (int64_t i = 0; i < m; ++i) uu = uu + uk[i] * uk[i];
+    for (int64_t j = 0; j < n; ++j) vv = vv + vk[j] * vk[j];
+    double cross = 0.0;
+    for (int64_t q = 0; q < k; ++q) {
+      double du = 0.0, dv = 0.0;
+      for (int64_t i = 0; i < m; ++i) du = du + out.U[(size_t)q * m + i] * uk[i];
+      for (int64_t j = 0; j < n; ++j) dv = dv + out.V[(size_t)q * n + j] * vk[j];
+      cross = cross + du * dv;
+    }
+    S = S + 2.0 * cross + uu * vv;
+    ++k;
+    out.rank = (int)k;
+    if ((flags & FLAG_DENSE_IF_CHEAPER) && k * (m + n) >= m * n) {
+      out.dense = 1;
+      break;
+    }
+    if (std::sqrt(uu) * std::sqrt(vv) <= tol * std::sqrt(std::max(S, 0.0))) break;
+    if (k == kmax) {
+      out.capped = 1;
+      break;
+    }
+    if (nused == m) break;
+    // Next row: largest |u_k(i)| among unused rows, lowest index on ties.
+    int64_t inext = -1;
+    double ubest = -1.0;
+    for (int64_t i = 0; i < m; ++i) {
+      if (used[i]) continue;
+      double v = std::fabs(uk[i]);
+      if (v > ubest) { ubest = v; inext = i; }
+    }
+    istar = inext;
+  }
+  if (out.dense) {
+    out.U.clear();
+    out.V.clear();
+    out.sigma.clear();
+    out.tau.clear();
+    out.rank = 0;
+  }
+}
+
+void compress(Tree& T) {
+  T.blocks.clear();
+  T.blk_off.assign(T.kappa + 2, 0);
+  for (int l = 1; l <= T.kappa; ++l) {
+    T.blk_off[l] = (int64_t)T.blocks.size();
+    const int64_t nb = (int64_t)T.bkey[l].size();
+    for (int64_t i = 0; i < nb; ++i)
+      for (int64_t e = T.iloff[l][i]; e < T.iloff[l][i + 1]; ++e) {
+        Block b;
+        b.level = l;
+        b.ti = i;
+        b.sj = T.ilidx[l][e];
+        b.I0 = T.bstart[l][i];
+        b.m = T.bstart[l][i + 1] - b.I0;
+        b.J0 = T.bstart[l][b.sj];
+        b.n = T.bstart[l][b.sj + 1] - b.J0;
+        T.blocks.push_back(std::move(b));
+      }
+  }
+  T.blk_off[T.kappa + 1] = (int64_t)T.blocks.size();
+  const int64_t nblk = (int64_t)T.blocks.size();
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t b = 0; b < nblk; ++b) {
+    Block& B = T.blocks[b];
+    const int64_t* rows = &T.perm[B.I0];
+    const int64_t* cols = &T.perm[B.J0];
+    auto A = [&](int64_t i, int64_t j) { return T.P.entry(rows[i], cols[j]); };
+    aca(A, B.m, B.n, T.tol, T.flags, B);
+  }
+}
+
+// -------------------------------------------------------------- matvec ----
+// Algorithm 2 (stored-factor form): for every level and every (i, j in IL(i)),
+// b(I) += U (V^T q(J)); then at the leaves b(I) += K(I,J) q(J) for J in the
+// near list (self and the d' >= 1 neighbours). Fixed accumulation order: levels
+// ascending, IL in list order, then the near list in list order.
+void dense_add(const Tree& T, int64_t I0, int64_t m, int64_t J0, int64_t n, const double* xt, double* yt,
+               int nrhs) {
+  for (int64_t r = 0; r < m; ++r)
+    for (int c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int64_t j = 0; j < n; ++j)
+        s = s + T.P.entry(T.perm[I0 + r], T.perm[J0 + j]) * xt[(size_t)(J0 + j) * nrhs + c];
+      yt[(size_t)(I0 + r) * nrhs + c] = yt[(size_t)(I0 + r) * nrhs + c] + s;
+    }
+}
+
+void lowrank_add(const Block& B, const double* xt, double* yt, int nrhs) {
+  std::vector<double> t((size_t)B.rank);
+  for (int c = 0; c < nrhs; ++c) {
+    for (int q = 0; q < B.rank; ++q) {
+      double s = 0.0;
+      for (int64_t j = 0; j < B.n; ++j) s = s + B.V[(size_t)q * B.n + j] * xt[(size_t)(B.J0 + j) * nrhs + c];
+      t[q] = s;
+    }
+    for (int64_t r = 0; r < B.m; ++r) {
+      double s = 0.0;
+      for (int q = 0; q < B.rank; ++q) s = s + B.U[(size_t)q * B.m + r] * t[q];
+      yt[(size_t)(B.I0 + r) * nrhs + c] = yt[(size_t)(B.I0 + r) * nrhs + c] + s;
+    }
+  }
+}
+
+// The paper's memory-efficient apply (Eq. keq2 with the remark on triangular
+// solves): w = K(sigma, J) q(J); z = L^-1 w (forward); z = U^-1 z (backward,
+// unit diagonal); b(I) += K(I, tau) z. With pivots from ACA, K(sigma, tau) = L U,
+// L(l, q) = u_q(sigma_l), U(q, l) = v_q(tau_l).
+void skeleton_add(const Tree& T, const Block& B, const double* xt, double* yt, int nrhs) {
+  const int p = B.rank;
+  std::vector<double> w(p), z(p);
+  for (int c = 0; c < nrhs; ++c) {
+    for (int l = 0; l < p; ++l) {
+      double s = 0.0;
+      for (int64_t j = 0; j < B.n; ++j)
+        s = s + T.P.entry(T.perm[B.I0 + B.sigma[l]], T.perm[B.J0 + j]) * xt[(size_t)(B.J0 + j) * nrhs + c];
+      w[l] = s;
+    }
+    for (int l = 0; l < p; ++l) {  // forward substitution with L
+      double s = w[l];
+      for (int q = 0; q < l; ++q) s = s - B.U[(size_t)q * B.m + B.sigma[l]] * z[q];
+      z[l] = s / B.U[(size_t)l * B.m + B.sigma[l]];
+    }
+    for (int l = p - 1; l >= 0; --l) {  // back substitution with unit-diagonal U
+      double s = z[l];
+      for (int q = l + 1; q < p; ++q) s = s - B.V[(size_t)l * B.n + B.tau[q]] * z[q];
+      z[l] = s;
+    }
+    for (int64_t r = 0; r < B.m; ++r) {
+      double s = 0.0;
+      for (int q = 0; q < p; ++q) s = s + T.P.entry(T.perm[B.I0 + r], T.perm[B.J0 + B.tau[q]]) * z[q];
+      yt[(size_t)(B.I0 + r) * nrhs + c] = yt[(size_t)(B.I0 + r) * nrhs + c] + s;
+    }
+  }
+}
+
+void matvec(const Tree& T, const double* x, double* y, int nrhs, bool skeleton) {
+  const int64_t N = T.P.N;
+  std::vector<double> xt((size_t)N * nrhs), yt((size_t)N * nrhs, 0.0);
+  for (int64_t i = 0; i < N; ++i)
+    for (int c = 0; c < nrhs; ++c) xt[(size_t)i * nrhs + c] = x[(size_t)T.perm[i] * nrhs + c];
+  for (int l = 1; l <= T.kappa; ++l) {
+    const int64_t nb = (int64_t)T.bkey[l].size();
+    // Boxes of one level own disjoint rows, so they may run in parallel.
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nb; ++i)
+      for (int64_t e = T.iloff[l][i]; e < T.iloff[l][i + 1]; ++e) {
+        const Block& B = T.blocks[T.blk_off[l] + e];
+        if (B.dense)
+          dense_add(T, B.I0, B.m, B.J0, B.n, xt.data(), yt.data(), nrhs);
+        else if (skeleton)
+          skeleton_add(T, B, xt.data(), yt.data(), nrhs);
+        else
+          lowrank_add(B, xt.data(), yt.data(), nrhs);
+      }
+  }
+  const int l = T.kappa;
+  const int64_t nb = (int64_t)T.bkey[l].size();
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < nb; ++i)
+    for (int64_t e = T.nearoff[i]; e < T.nearoff[i + 1]; ++e) {
+      int64_t j = T.nearidx[e];
+      dense_add(T, T.bstart[l][i], T.bstart[l][i + 1] - T.bstart[l][i], T.bstart[l][j],
+                T.bstart[l][j + 1] - T.bstart[l][j], xt.data(), yt.data(), nrhs);
+    }
+  for (int64_t i = 0; i < N; ++i)
+    for (int c = 0; c < nrhs; ++c) y[(size_t)T.perm[i] * nrhs + c] = yt[(size_t)i * nrhs + c];
+}
+
+bool valid_kernel(int id, const double* prm) {
+  if (id < 0 || id >= K_COUNT) return false;
+  if ((id == K_MATERN32 || id == K_GAUSS || id == K_EXP) && !(prm[2] > 0.0)) return false;
+  return true;
+}
+
+Kern make_kern(int id, const double* prm) {
+  Kern k;
+  k.id = id;
+  k.scale = prm ? prm[0] : 1.0;
+  k.diag = prm ? prm[1] : 0.0;
+  k.p0 = prm ? prm[2] : 0.0;
+  k.p1 = prm ? prm[3] : 0.0;
+  return k;
+}
+
+}  // namespace
+
+// ================================================================ C API ====
+extern "C" {
+
+typedef struct or_tree or_tree;
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+// Direct O(N^2) sum y = K x (x, y: N x nrhs row-major, original order). Exact
+// up to FP64 rounding; the reference every HODLRdD result is measured against.
+// Rows in [r0, r1) only, so large problems can be sampled row by row.
+int or_direct_rows(const double* pts, int d, int64_t N, int kid, const double* prm, const double* x,
+                   int nrhs, int64_t r0, int64_t r1, double* y) {
+  double p4[4] = {1.0, 0.0, 0.0, 0.0};
+  if (prm) std::memcpy(p4, prm, sizeof p4);
+  if (d < 1 || N < 1 || nrhs < 1 || !valid_kernel(kid, p4) || r0 < 0 || r1 > N || r0 > r1) return 1;
+  Problem P;
+  P.d = d;
+  P.N = N;
+  P.K = make_kern(kid, p4);
+  P.pts.assign(pts, pts + (size_t)N * d);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = r0; i < r1; ++i)
+    for (int c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int64_t j = 0; j < N; ++j) s = s + P.entry(i, j) * x[(size_t)j * nrhs + c];
+      y[(size_t)(i - r0) * nrhs + c] = s;
+    }
+  return 0;
+}
+
+// Dense kernel block F(X_i, Y_j) (m x n row-major), scale applied, no diagonal.
+int or_kernel_block(const double* X, int64_t m, const double* Y, int64_t n, int d, int kid, const double* prm,
+                    double* out) {
+  double p4[4] = {1.0, 0.0, 0.0, 0.0};
+  if (prm) std::memcpy(p4, prm, sizeof p4);
+  if (!valid_kernel(kid, p4)) return 1;
+  Kern K = make_kern(kid, p4);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j)
+      out[(size_t)i * n + j] = K.scale * F_of_s(K, sqdist(X + (size_t)i * d, Y + (size_t)j * d, d));
+  return 0;
+}
+
+// ACA of an explicit dense matrix A (m x n row-major). Outputs: rank, pivots
+// (sigma, tau: length >= min(m,n)), U (m x rank) and V (n x rank) column-major,
+// each with room for min(m,n) columns. Returns 0 on success.
+int or_aca_dense(const double* A, int64_t m, int64_t n, double tol, int flags, int* rank, int* dense,
+                 int64_t* sigma, int64_t* tau, double* U, double* V) {
+  if (m < 1 || n < 1) return 1;
+  Block B;
+  auto E = [&](int64_t i, int64_t j) { return A[(size_t)i * n + j]; };
+  aca(E, m, n, tol, flags, B);
+  *rank = B.rank;
+  *dense = B.dense;
+  for (int q = 0; q < B.rank; ++q) {
+    sigma[q] = B.sigma[q];
+    tau[q] = B.tau[q];
+  }
+  std::memcpy(U, B.U.data(), sizeof(double) * B.U.size());
+  std::memcpy(V, B.V.data(), sizeof(double) * B.V.size());
+  return 0;
+}
+
+int or_build(const double* pts, int d, int64_t N, int kid, const double* prm, int leaf, double tol, int flags,
+             or_tree** out) {
+  double p4[4] = {1.0, 0.0, 0.0, 0.0};
+  if (prm) std::memcpy(p4, prm, sizeof p4);
+  if (!out || !pts || d < 1 || d > 8 || N < 1 || leaf < 1 || !(tol > 0.0) || !valid_kernel(kid, p4)) return 1;
+  for (int64_t i = 0; i < N * d; ++i)
+    if (!std::isfinite(pts[i])) return 1;
+  Tree* T = new (std::nothrow) Tree();
+  if (!T) return 2;
+  T->P.d = d;
+  T->P.N = N;
+  T->P.K = make_kern(kid, p4);
+  T->P.pts.assign(pts, pts + (size_t)N * d);
+  T->leaf = leaf;
+  T->tol = tol;
+  T->flags = flags;
+  bounding_cube(*T);
+  build_levels(*T);
+  classify(*T);
+  compress(*T);
+  *out = reinterpret_cast<or_tree*>(T);
+  return 0;
+}
+
+void or_destroy(or_tree* h) { delete reinterpret_cast<Tree*>(h); }
+
+// Sizes: [kappa, B, nblocks, nnear, total_factor_elems, n_dense, n_capped, max_rank]
+int or_info(const or_tree* h, int64_t* info) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  int64_t fe = 0, nd = 0, nc = 0, mr = 0;
+  for (const Block& b : T.blocks) {
+    fe += (int64_t)b.rank * (b.m + b.n);
+    nd += b.dense;
+    nc += b.capped;
+    mr = std::max<int64_t>(mr, b.rank);
+  }
+  info[0] = T.kappa;
+  info[1] = T.B;
+  info[2] = (int64_t)T.blocks.size();
+  info[3] = (int64_t)T.nearidx.size();
+  info[4] = fe;
+  info[5] = nd;
+  info[6] = nc;
+  info[7] = mr;
+  return 0;
+}
+
+// Bounding cube: lo[d], side, inv.
+int or_cube(const or_tree* h, double* lo, double* side_inv) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  for (int k = 0; k < T.P.d; ++k) lo[k] = T.lo[k];
+  side_inv[0] = T.side;
+  side_inv[1] = T.inv;
+  return 0;
+}
+
+int or_perm(const or_tree* h, int64_t* perm, uint64_t* skey) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  for (int64_t i = 0; i < T.P.N; ++i) {
+    perm[i] = T.perm[i];
+    skey[i] = T.skey[i];
+  }
+  return 0;
+}
+
+int64_t or_level_nboxes(const or_tree* h, int l) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  if (l < 0 || l > T.kappa) return -1;
+  return (int64_t)T.bkey[l].size();
+}
+
+int or_level(const or_tree* h, int l, int64_t* bstart, uint64_t* bkey) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  if (l < 0 || l > T.kappa) return 1;
+  const int64_t nb = (int64_t)T.bkey[l].size();
+  for (int64_t b = 0; b <= nb; ++b) bstart[b] = T.bstart[l][b];
+  for (int64_t b = 0; b < nb; ++b) bkey[b] = T.bkey[l][b];
+  return 0;
+}
+
+int64_t or_il_size(const or_tree* h, int l) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  if (l < 1 || l > T.kappa) return -1;
+  return (int64_t)T.ilidx[l].size();
+}
+
+int or_il(const or_tree* h, int l, int64_t* off, int64_t* idx) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  if (l < 1 || l > T.kappa) return 1;
+  for (size_t i = 0; i < T.iloff[l].size(); ++i) off[i] = T.iloff[l][i];
+  for (size_t i = 0; i < T.ilidx[l].size(); ++i) idx[i] = T.ilidx[l][i];
+  return 0;
+}
+
+int or_near(const or_tree* h, int64_t* off, int64_t* idx) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  for (size_t i = 0; i < T.nearoff.size(); ++i) off[i] = T.nearoff[i];
+  for (size_t i = 0; i < T.nearidx.size(); ++i) idx[i] = T.nearidx[i];
+  return 0;
+}
+
+// Per block (CSR order): [level, ti, sj, I0, m, J0, n, rank, dense, capped].
+int or_blocks(const or_tree* h, int64_t* rec) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  for (size_t b = 0; b < T.blocks.size(); ++b) {
+    const Block& B = T.blocks[b];
+    int64_t* r = rec + b * 10;
+    r[0] = B.level; r[1] = B.ti; r[2] = B.sj; r[3] = B.I0; r[4] = B.m;
+    r[5] = B.J0; r[6] = B.n; r[7] = B.rank; r[8] = B.dense; r[9] = B.capped;
+  }
+  return 0;
+}
+
+// Pivots and factors of block b: sigma/tau (rank), U (m x rank), V (n x rank).
+int or_block_factors(const or_tree* h, int64_t b, int64_t* sigma, int64_t* tau, double* U, double* V) {
+  const Tree& T = *reinterpret_cast<const Tree*>(h);
+  if (b < 0 || b >= (int64_t)T.blocks.size()) return 1;
+  const Block& B = T.blocks[b];
+  for (int q = 0; q < B.rank; ++q) {
+    sigma[q] = B.sigma[q];
+    tau[q] = B.tau[q];
+  }
+  if (U) std::memcpy(U, B.U.data(), sizeof(double) * B.U.size());
+  if (V) std::memcpy(V, B.V.data(), sizeof(double) * B.V.size());
+  return 0;
+}
+
+int or_matvec(const or_tree* h, const double* x, double* y, int nrhs) {
+  if (nrhs < 1) return 1;
+  matvec(*reinterpret_cast<const Tree*>(h), x, y, nrhs, false);
+  return 0;
+}
+
+int or_matvec_skeleton(const or_tree* h, const double* x, double* y, int nrhs) {
+  if (nrhs < 1) return 1;
+  matvec(*reinterpret_cast<const Tree*>(h), x, y, nrhs, true);
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+"""Pins for the oracle's 2^d tree and interaction lists (no GPU).
+
+Pinned by brute force and by the invariants the definitions imply:
+* each point's box at each level, computed directly with floor, equals the
+  Morton-decoded box (Section "Construction of the tree");
+* Algorithm 1's level rule: every leaf holds at most leaf points, some box one
+  level up holds more;
+* coverage: Algorithm 2 reproduces K only if every ordered pair of points falls
+  in exactly one block (an IL block at one level, or a leaf near block);
+* IL symmetry: j in IL(i) iff i in IL(j) (the admissibility condition and the clan
+  relation are symmetric);
+* d = 1 is classical HODLR: every box's IL is its sibling.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def decode(key, d, bits):
+    c = np.zeros(d, np.int64)
+    for b in range(bits):
+        for k in range(d):
+            c[k] |= ((int(key) >> (d * b + k)) & 1) << b
+    return c
+
+
+def box_of_points(T, l):
+    st, bk = T.level(l)
+    owner = np.zeros(T.N, np.int64)
+    for b in range(len(bk)):
+        owner[st[b]:st[b + 1]] = b
+    return st, bk, owner
+
+
+@pytest.mark.parametrize("d,N", [(1, 500), (2, 1500), (3, 1200), (4, 1300)])
+def test_boxes_match_floor(oracle_mod, d, N):
+    w = W.make("t", d, N, W.K_LOG, leaf=16, seed=d)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, w.leaf, 1e-6)
+    lo, side, inv = T.cube()
+    assert np.all(lo == w.points.min(axis=0))
+    assert side >= (w.points.max(axis=0) - lo).max()
+    perm, skey = T.perm()
+    assert np.array_equal(np.sort(perm), np.arange(N))
+    assert np.all(np.diff(skey.astype(np.float64)) >= 0)
+    for l in range(0, T.kappa + 1):
+        st, bk, owner = box_of_points(T, l)
+        # direct: floor((x - lo) * inv * 2^(l - B)), an exact power-of-two scaling
+        direct = np.floor((w.points[perm] - lo) * inv * 2.0 ** (l - T.B)).astype(np.int64)
+        direct = np.minimum(direct, 2 ** l - 1)
+        dec = np.array([decode(bk[b], d, l) for b in owner])
+        assert np.array_equal(direct, dec), l
+        assert len(np.unique(bk)) == len(bk) and np.all(np.diff(bk.astype(np.float64)) > 0)
+
+
+@pytest.mark.parametrize("leaf", [1, 7, 32, 100])
+def test_level_rule(oracle_mod, leaf):
+    w = W.make("t", 2, 800, W.K_LOG, leaf=leaf, seed=2)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, leaf, 1e-6)
+    st, _ = T.level(T.kappa)
+    assert np.diff(st).max() <= leaf
+    if T.kappa > 0:
+        st1, _ = T.level(T.kappa - 1)
+        assert np.diff(st1).max() > leaf
+
+
+def test_duplicates_are_stable_and_bounded(oracle_mod):
+    # 40 copies of one point cannot be separated: the tree stops at B levels and
+    # the stable sort keeps equal keys in input order.
+    rng = np.random.default_rng(0)
+    pts = np.concatenate([rng.uniform(-1, 1, (60, 2)), np.tile([[0.25, -0.5]], (40, 1))])
+    T = oracle_mod.Tree(pts, W.K_LOG, None, 8, 1e-6)
+    assert T.kappa == T.B
+    perm, skey = T.perm()
+    dup = perm[perm >= 60]
+    assert np.array_equal(dup, np.arange(60, 100))
+
+
+def coverage_matrix(T):
+    cov = np.zeros((T.N, T.N), np.int32)
+    perm, _ = T.perm()
+    for rec in T.blocks():
+        _, _, _, I0, m, J0, n = rec[:7]
+        cov[I0:I0 + m, J0:J0 + n] += 1
+    st, _ = T.level(T.kappa)
+    off, idx = T.near()
+    for i in range(len(st) - 1):
+        for e in range(off[i], off[i + 1]):
+            j = idx[e]
+            cov[st[i]:st[i + 1], st[j]:st[j + 1]] += 1
+    return cov
+
+
+@pytest.mark.parametrize("d,N,leaf,dist", [(1, 700, 9, "uniform"), (2, 1500, 20, "uniform"),
+                                           (3, 1400, 12, "uniform"), (4, 1500, 10, "uniform"),
+                                           (3, 1200, 16, "clustered"), (2, 37, 64, "uniform")])
+def test_coverage_exactly_once(oracle_mod, d, N, leaf, dist):
+    w = W.make("t", d, N, W.K_LOG, leaf=leaf, seed=11, dist=dist)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, leaf, 1e-6)
+    cov = coverage_matrix(T)
+    assert cov.min() == 1 and cov.max() == 1
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_il_symmetry_and_admissibility(oracle_mod, d):
+    w = W.make("t", d, 1500, W.K_LOG, leaf=10, seed=7)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, 10, 1e-6)
+    for l in range(1, T.kappa + 1):
+        off, idx = T.il(l)
+        _, bk = T.level(l)
+        pairs = {(i, int(idx[e])) for i in range(len(off) - 1) for e in range(off[i], off[i + 1])}
+        assert all((j, i) in pairs for (i, j) in pairs)
+        for (i, j) in pairs:
+            delta = decode(bk[j], d, l) - decode(bk[i], d, l)
+            a = np.abs(delta)
+            # HODLRdD admissibility: far (>= 1 box between) or sharing at most a vertex
+            assert a.max() >= 2 or np.all(a == 1)
+            pd = (decode(bk[j], d, l) >> 1) - (decode(bk[i], d, l) >> 1)
+            # clan: the parents coincide or share a d' >= 1 hyper-surface
+            assert np.abs(pd).max() <= 1 and (np.all(pd == 0) or np.any(pd == 0))
+        for i in range(len(off) - 1):
+            assert np.all(np.diff(idx[off[i]:off[i + 1]]) > 0)
+
+
+def test_d1_is_hodlr(oracle_mod):
+    w = W.make("t", 1, 1024, W.K_LOG, leaf=16, seed=1)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, 16, 1e-8)
+    for l in range(1, T.kappa + 1):
+        off, idx = T.il(l)
+        _, bk = T.level(l)
+        for i in range(len(off) - 1):
+            sib = int(bk[i]) ^ 1
+            expected = [j for j in range(len(bk)) if int(bk[j]) == sib]
+            assert list(idx[off[i]:off[i + 1]]) == expected
+    off, idx = T.near()
+    assert np.array_equal(idx, np.arange(len(off) - 1))  # leaf near field = self only
+
+
+def test_2d_counts_config1(oracle_mod):
+    """d=2, N=4096 uniform [-1,1]^2 (seed 0), leaf 64: level structure of the plain-FP64 workload."""
+    w = W.plain_fp64_2d()
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, w.leaf, w.tol)
+    assert T.kappa == 4
+    assert [len(T.il(l)[1]) for l in range(1, 5)] == [4, 128, 736, 3392]
+    assert T.nnear == 1216
+    # level 1 in 2D: each quadrant's only admissible sibling is the diagonal one
+    off, idx = T.il(1)
+    assert list(np.diff(off)) == [1, 1, 1, 1]
+    assert list(idx) == [3, 2, 1, 0]
