@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""HODLRdD matvec throughput on one GB300 (or N independent replicas).
+
+Workload (default): d=3, N=262144 points uniform in [-1,1]^3, F = 1/r with zero
+diagonal, leaf 64, ACA tol 1e-7, one right-hand side ~ N(0,1). One step = one
+HODLRdD matrix-vector product y = K x (gather, low-rank applies over all
+levels, on-the-fly near field, scatter) with x already in HBM. The build
+(tree, lists, ACA, packing) runs once before timing and is reported separately,
+as the paper reports initialisation and product times separately.
+
+Reported: throughput in N*nrhs per second of the headline precision form and of
+the plain FP64 form, the headline form's relative error against the FP64 form,
+the dominant kernel's roofline, end-to-end throughput through the C ABI with
+host buffers, and the CPU oracle timed on the host cores on a bounded sample.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HODLRdD matvec N·nrhs/s vs plain FP64 @rel err≤1e-6; serving p50/p99 ms"
+UNIT = "N·nrhs/s"
+ERR_BAR = 1e-6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
+    p.add_argument("--n", type=int, default=262144)
+    p.add_argument("--nrhs", type=int, default=1)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-sample-n", type=int, default=32768)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_group(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def aggregate(units: float, seconds: float, dist, device=None):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    if dist is None:
+        return units, seconds
+    import torch
+
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=device)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def workload(args, rank):
+    import workloads as W
+
+    w = W.precision_3d(N=args.n, seed=args.seed + rank)
+    if args.nrhs != 1:
+        rng = np.random.default_rng(args.seed + rank + 7)
+        w.x = rng.standard_normal((w.N, args.nrhs))
+        w.nrhs = args.nrhs
+    return w
+
+
+def workload_name(w):
+    return (f"d={w.d} N={w.N} uniform [-1,1]^{w.d}, F=1/r (zero diagonal), leaf {w.leaf}, "
+            f"tol {w.tol:g}, nrhs {w.nrhs}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def factor_bytes(h, precision):
+    """Algorithmic bytes of the packed U and V factors (incl. row padding and scales)."""
+    from paper_2209_05819_gb300 import _binding as B
+
+    rec = h.blocks()
+    p = rec[:, 7]
+    m = rec[:, 4]
+    n = rec[:, 6]
+    pad = lambda v: (v + 1) // 2 * 2
+    es = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    ub = int((p * pad(m)).sum()) * es
+    vb = int((p * pad(n)).sum()) * es
+    tr = int(p.sum())
+    scales = 4 * tr if precision in ("fp16", "bf16") else 0
+    del B
+    return ub, vb, tr, scales
+
+
+def time_steps(fn, steps, warmup, torch, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(args, rank_w):
+    """The oracle (FP64 C++), as it stands, on the host cores: HODLRdD build and
+    matvec on a smaller draw of the same point distribution."""
+    import oracle
+    import workloads as W
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    ws = W.subsample(rank_w, args.cpu_sample_n, seed=args.seed + 12345)
+    t0 = time.perf_counter()
+    T = oracle.Tree(ws.points, ws.kernel, ws.params, ws.leaf, ws.tol, dense_if_cheaper=True)
+    t_build = time.perf_counter() - t0
+    times = []
+    t_end = time.perf_counter() + 8.0
+    while len(times) < 3 or (time.perf_counter() < t_end and len(times) < 20):
+        t0 = time.perf_counter()
+        T.matvec(ws.x)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle FP64 HODLRdD on a {ws.N}-point draw of the same distribution (d={ws.d}, 1/r, "
+                      f"leaf {ws.leaf}, tol {ws.tol:g}); matvec median of {len(times)} runs; build {t_build:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    w = workload(args, 0)
+    ws = W.subsample(w, args.cpu_sample_n, seed=args.seed + 12345)
+    T = oracle.Tree(ws.points, ws.kernel, ws.params, ws.leaf, ws.tol, dense_if_cheaper=True)
+    for _ in range(args.warmup):
+        T.matvec(ws.x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        T.matvec(ws.x)
+    dt = time.perf_counter() - t0
+    value = ws.N * ws.nrhs * args.steps / dt
+    sample = (f"oracle FP64 HODLRdD matvec on a {ws.N}-point draw of the same distribution (each step one matvec "
+              f"of the sample)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(w), "sample_n": ws.N},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import build as cbuild
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_group(world, "nccl")
+    cbuild.build()
+    stream = torch.cuda.current_stream()
+    w = workload(args, rank)
+    pts = torch.from_numpy(w.points).cuda()
+    nrhs = w.nrhs
+    units = w.N * nrhs
+
+    h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision)
+    s = h.stats()
+    io = torch.float64 if args.precision == "fp64" else torch.float32
+    x = torch.from_numpy(np.ascontiguousarray(w.x.reshape(w.N, nrhs))).to(io).cuda()
+    y = torch.empty_like(x)
+
+    def step():
+        h.matvec(x, y)
+
+    # headline timing (with stage events recorded on the same stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    h.set_profiling(True)
+    launches0 = h.profile()["launches"]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    seconds = e0.elapsed_time(e1) / 1e3
+    if dist is not None:
+        dist.barrier()
+    prof = h.profile()
+    h.set_profiling(False)
+    launches = prof["launches"] - launches0
+    total_units, max_seconds = aggregate(units * args.steps, seconds, dist, device="cuda")
+    value = total_units / max_seconds
+    ms_per_step = 1e3 * max_seconds / args.steps
+
+    # plain FP64 form, and the headline form's error against it
+    fp64 = None
+    err = None
+    if not args.no_fp64:
+        if args.precision == "fp64":
+            h64, x64 = h, x
+        else:
+            h64 = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp64")
+            x64 = x.to(torch.float64)
+        y64 = torch.empty_like(x64)
+        t64 = time_steps(lambda: h64.matvec(x64, y64), max(3, args.steps // 4), args.warmup, torch, stream)
+        n64 = max(3, args.steps // 4)
+        h.matvec(x, y)
+        torch.cuda.synchronize()
+        num = torch.linalg.norm((y.to(torch.float64) - y64), dim=0)
+        den = torch.linalg.norm(y64, dim=0)
+        err = float((num / den).max().item())
+        fp64 = {"value": units * n64 / t64, "ms_per_step": 1e3 * t64 / n64, "build_ms": h64.stats()["t_build_ms"]}
+        if h64 is not h:
+            h64.close()
+
+    # end to end through the C ABI with host (pinned) buffers
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    n_e2e = max(3, args.steps // 2)
+    t_e2e = time_steps(lambda: h.matvec(xh, yh), n_e2e, 1, torch, stream)
+    e2e_units, e2e_sec = aggregate(units * n_e2e, t_e2e, dist, device="cuda")
+    io_bytes = x.element_size() * x.numel()
+
+    # roofline of the dominant kernel (bytes it must move per launch / its mean duration)
+    ub, vb, tr, scales = factor_bytes(h, args.precision)
+    acc = 8 if args.precision == "fp64" else 4
+    n_chunks = max(prof["chunks"], 1)
+    stage = {"vapply": prof["vapply_ms"] / n_chunks, "uapply": prof["uapply_ms"] / n_chunks,
+             "near": prof["near_ms"] / n_chunks, "gather": prof["gather_ms"] / n_chunks}
+    nr = min(nrhs, 8)
+    algo = {"vapply": vb + scales + tr * nr * acc + w.N * nr * acc,
+            "uapply": ub + tr * nr * acc + s["kappa"] * w.N * nr * acc}
+    dom = max(("vapply", "uapply"), key=lambda k: stage[k])
+    peak, peak_kind = measured_peaks()
+    achieved = algo[dom] / (stage[dom] / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "algorithmic_bytes": algo[dom],
+            "stage_ms": {k: round(v, 4) for k, v in stage.items()},
+            "stage_share": {k: round(v / sum(stage.values()), 4) for k, v in stage.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16+f32", "bf16": "bf16+f32"}[
+                args.precision], "data": "synthetic",
+            "config": {"workload": workload_name(w), "precision": args.precision,
+                       "factors": f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"
+                       else "fp64", "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2: {(ub + vb) / 1e9:.2f} GB of factors streamed per step"},
+            "rel_err_vs_fp64": err, "meets_err_bar": (err is not None and err <= ERR_BAR),
+            "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
+            "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
+                                                   "t_pack_ms")},
+            "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],
+                          "n_dense": s["n_dense"], "max_rank": s["max_rank"], "factor_gb": (ub + vb) / 1e9,
+                          "dense_pairs": s["dense_pairs"], "mean_rank_per_level":
+                              [round(v, 1) for v in s["mean_rank_per_level"]]},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_units / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

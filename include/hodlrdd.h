@@ -1,0 +1,247 @@
+/*
+ * hodlrdd.h -- C ABI of the GB300 HODLRdD library (libhodlrdd.so).
+ *
+ * HODLRdD (Khan, Kandappan, Ambikasaran) represents a kernel matrix
+ * K(i,j) = F(x_i, x_j) on N points in d dimensions (Section "Preliminaries",
+ * kernel matrix) hierarchically: a balanced 2^d tree (Section "Construction of
+ * the tree"), interaction lists under the HODLRdD weak admissibility condition
+ * (far-field and vertex-sharing clusters are admissible; Table "Notations" and
+ * the admissibility definition), every admissible block compressed by ACA
+ * (Eq. keq1 / keq2, Algorithm 1), and an almost-linear matrix-vector product
+ * (Algorithm 2). This library builds that representation on one GPU and applies
+ * it with hand-written CUDA kernels.
+ *
+ * Conventions for every call:
+ *  - Every function returns an int status (enum hodlrdd_status); nothing aborts.
+ *    hodlrdd_last_error() gives a human-readable detail for the calling thread.
+ *  - Pointer arguments marked "host or device" may point to host memory (pageable
+ *    or pinned) or to device memory of the current device; the library finds out
+ *    which with cudaPointerGetAttributes.
+ *  - Invalid arguments are rejected on the host before any GPU work.
+ *  - No type from CUDA or PyTorch appears here: a stream is passed as void*
+ *    (a cudaStream_t; NULL is the legacy default stream).
+ */
+#ifndef HODLRDD_H
+#define HODLRDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hodlrdd_s* hodlrdd_handle;
+
+enum hodlrdd_status {
+  HODLRDD_OK = 0,
+  HODLRDD_ERR_INVALID = 1,     /* bad argument (checked on the host) */
+  HODLRDD_ERR_OOM = 2,         /* a device or host allocation failed; nothing leaks */
+  HODLRDD_ERR_CUDA = 3,        /* a CUDA call failed; see hodlrdd_last_error() */
+  HODLRDD_ERR_UNSUPPORTED = 4, /* valid but not supported (e.g. precision/nrhs combination) */
+  HODLRDD_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  HODLRDD_ERR_NUMERIC = 6      /* non-finite values met during the build */
+};
+
+/* Kernel functions F(x, y) of r = |x - y|_2. The paper's list F1..F8 (Section
+ * "Preliminaries") plus the kernels of its experiments. Singular kernels
+ * (LOG, INV_R, INV_R2_4D) evaluate to 0 at r = 0 (the matvec experiment sets
+ * K(i,i) = 0). */
+enum hodlrdd_kernel {
+  HODLRDD_K_LOG = 0,        /* log r                                   (F2) */
+  HODLRDD_K_INV_R = 1,      /* 1 / r                                   (F1) */
+  HODLRDD_K_MATERN32 = 2,   /* (1 + sqrt(3) r / l) exp(-sqrt(3) r / l), l = p0 */
+  HODLRDD_K_GAUSS = 3,      /* exp(-r^2 / (2 h^2)), h = p0 */
+  HODLRDD_K_EXP = 4,        /* exp(-r / l), l = p0                     (F8) */
+  HODLRDD_K_INV_R2_4D = 5,  /* -1 / (4 pi^2 r^2): 4D Laplace Green's function */
+  HODLRDD_K_R = 6,          /* r                                       (F5) */
+  HODLRDD_K_SIN = 7,        /* sin r                                   (F6) */
+  HODLRDD_K_INV_SQRT1P = 8  /* 1 / sqrt(1 + r)                         (F7) */
+};
+
+/* Storage precision of the low-rank factors and arithmetic of the matvec.
+ *  FP64: factors FP64, all arithmetic FP64; x and y are double.
+ *  FP32: factors FP32, arithmetic FP32; x and y are float.
+ *  FP16 / BF16: factors 16-bit with one FP32 scale per factor column, kernel
+ *  evaluation and accumulation FP32; x and y are float.
+ * The compression itself (ACA) always runs in FP64. */
+enum hodlrdd_precision {
+  HODLRDD_PREC_FP64 = 0,
+  HODLRDD_PREC_FP32 = 1,
+  HODLRDD_PREC_FP16 = 2,
+  HODLRDD_PREC_BF16 = 3
+};
+
+typedef struct hodlrdd_options {
+  int precision;        /* enum hodlrdd_precision; default FP64 */
+  int dense_if_cheaper; /* 1 (default): an IL block whose factors would hold at least
+                           as many numbers as the block, p (m + n) >= m n, is applied
+                           exactly by evaluating the kernel on the fly (no storage).
+                           0: every IL block is applied through its ACA factors, as
+                           in Algorithm 2. */
+  int max_nrhs;         /* workspace is sized for nrhs <= max_nrhs (default 16);
+                           larger nrhs is processed in chunks */
+  int aca_max_rank;     /* cap on the ACA rank of blocks larger than 2048 rows or
+                           columns (default 1024); a block that does not converge
+                           within its cap is applied exactly instead */
+  int reserved[8];      /* set to 0 */
+} hodlrdd_options;
+
+#define HODLRDD_MAX_LEVELS 64
+
+typedef struct hodlrdd_stats {
+  int d;
+  int kappa;                 /* number of tree levels below the root (leaf level) */
+  int precision;
+  int max_rank;              /* largest ACA rank over all low-rank blocks */
+  int64_t N;
+  int64_t n_blocks;          /* IL blocks over all levels */
+  int64_t n_lowrank;         /* of which applied through factors */
+  int64_t n_dense;           /* of which applied exactly */
+  int64_t n_rank_capped;     /* of which hit aca_max_rank (applied exactly) */
+  int64_t n_near;            /* leaf near-field blocks (self + d' >= 1 neighbours) */
+  int64_t factor_elems;      /* sum over low-rank blocks of p (m + n) */
+  int64_t factor_bytes;      /* bytes of packed factors (incl. padding and scales) */
+  int64_t dense_pairs;       /* kernel evaluations per matvec and right-hand side */
+  int64_t boxes_per_level[HODLRDD_MAX_LEVELS];
+  int64_t blocks_per_level[HODLRDD_MAX_LEVELS];
+  int max_rank_per_level[HODLRDD_MAX_LEVELS];
+  double mean_rank_per_level[HODLRDD_MAX_LEVELS];
+  double t_tree_ms;          /* bounding cube, Morton keys, sort, level tables */
+  double t_classify_ms;      /* interaction and near lists */
+  double t_aca_ms;           /* both ACA passes */
+  double t_pack_ms;          /* factor packing / precision conversion, task lists */
+  double t_build_ms;         /* whole build, wall clock */
+  int64_t device_bytes;      /* device memory held by the handle */
+} hodlrdd_stats;
+
+/* Fills *opt with the defaults described above. */
+int hodlrdd_options_default(hodlrdd_options* opt);
+
+/*
+ * Builds the HODLRdD representation of K on the current CUDA device
+ * (Algorithm 1: form the 2^d tree, then compress every IL block with ACA).
+ *
+ *  points         host or device, N x d FP64, row-major (point i at points[i*d]),
+ *                 original order; finite values only (else HODLRDD_ERR_INVALID).
+ *  d              1..8.      N  >= 1, < 2^31.
+ *  kernel_id      enum hodlrdd_kernel.
+ *  kernel_params  host array of 4 doubles {scale, diag, p0, p1} or NULL for
+ *                 {1, 0, 0, 0}: K(i,j) = scale * F(x_i, x_j; p0, p1) + diag * [i == j].
+ *                 MATERN32, GAUSS, EXP need p0 > 0.
+ *  leaf_size      N_max of the paper: the tree is refined until every leaf holds at
+ *                 most leaf_size points (Algorithm 1's level rule); >= 1.
+ *  tol            ACA tolerance (relative, Frobenius estimate), > 0.
+ *  opt            NULL for defaults.
+ *  out            receives the handle.
+ *
+ * The points are copied into library-owned memory: the caller may free them on
+ * return. The call is synchronous (returns after all device work completes) and
+ * thread-safe for distinct handles. The handle owns all its device memory until
+ * hodlrdd_destroy.
+ */
+int hodlrdd_build(const double* points, int d, int64_t N, int kernel_id, const double* kernel_params,
+                  int leaf_size, double tol, hodlrdd_handle* out);
+int hodlrdd_build_ex(const double* points, int d, int64_t N, int kernel_id, const double* kernel_params,
+                     int leaf_size, double tol, const hodlrdd_options* opt, hodlrdd_handle* out);
+
+/*
+ * y = K x (Algorithm 2): per-level low-rank applies, leaf near field evaluated on
+ * the fly, all in the handle's precision.
+ *
+ *  x, y    host or device, N x nrhs row-major (column c of point i at [i*nrhs + c]),
+ *          ORIGINAL point order; double for FP64 handles, float otherwise. y is
+ *          overwritten, never accumulated. x and y must not overlap.
+ *  nrhs    >= 1.
+ *  stream  cudaStream_t (as void*); NULL = legacy default stream.
+ *
+ * With device x and y the call is asynchronous on `stream`: it only enqueues
+ * kernels and allocates nothing. With host x or y it stages through buffers the
+ * handle owns and returns after y is written (synchronous). A handle's workspace
+ * is shared: concurrent matvecs on one handle from different streams must be
+ * serialised by the caller.
+ */
+int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
+
+/* Frees the handle and all device memory it holds. NULL is accepted. */
+int hodlrdd_destroy(hodlrdd_handle h);
+
+/* Sizes, ranks and phase timings of the build (the paper reports maximum rank,
+ * memory of the representation and initialisation time). */
+int hodlrdd_get_stats(hodlrdd_handle h, hodlrdd_stats* s);
+
+/* Static description of a status code. */
+const char* hodlrdd_error_string(int status);
+/* Detail of the last failure on the calling thread (never NULL). */
+const char* hodlrdd_last_error(void);
+
+/*
+ * Stage timing of subsequent matvecs (tracing). With on = 1 every matvec records
+ * CUDA events on its own stream between its stages; on = 0 stops recording.
+ * Enabling resets the accumulated values.
+ */
+int hodlrdd_set_profiling(hodlrdd_handle h, int on);
+
+/*
+ * Accumulated stage times since profiling was enabled (synchronises with the
+ * recorded events): ms[4] = gather, V-apply, U-apply, near field + combine;
+ * *chunks = number of right-hand-side chunks timed; *launches = kernels the
+ * handle's matvecs have launched since the build (counted whether or not
+ * profiling is on). Any pointer may be NULL.
+ */
+int hodlrdd_get_profile(hodlrdd_handle h, double* ms, int64_t* chunks, int64_t* launches);
+
+/* ---------------------------------------------------------------------------
+ * Introspection: copies of the integer structure, for bit-exact checks.
+ * All output arrays are host memory sized by the caller from hodlrdd_get_stats
+ * and hodlrdd_get_level.
+ * ------------------------------------------------------------------------- */
+
+/* perm[i] = original index of the point at tree position i; keys[i] = its Morton
+ * key (B = min(32, floor(63/d)) bits per dimension, dimension k at bit k of each
+ * d-bit level digit, coarse level first). Either pointer may be NULL. */
+int hodlrdd_get_tree(hodlrdd_handle h, int64_t* perm, uint64_t* keys);
+
+/* Bounding cube: lo[d], side_inv[0] = side, side_inv[1] = 2^B / side. */
+int hodlrdd_get_cube(hodlrdd_handle h, double* lo, double* side_inv);
+
+/* Level l (0..kappa): *nboxes non-empty boxes; bstart[nboxes+1] tree-order point
+ * offsets; bkey[nboxes] box keys (the top l digits of the Morton key). Either
+ * array may be NULL (query *nboxes first). */
+int hodlrdd_get_level(hodlrdd_handle h, int l, int64_t* nboxes, int64_t* bstart, uint64_t* bkey);
+
+/* Interaction lists of level l (1..kappa): CSR off[nboxes+1], idx[off[nboxes]]
+ * (source box indices, ascending per target box). *nnz receives off[nboxes];
+ * off / idx may be NULL. */
+int hodlrdd_get_il(hodlrdd_handle h, int l, int64_t* nnz, int64_t* off, int64_t* idx);
+
+/* Leaf near lists (self and boxes sharing a d' >= 1 hyper-surface), same CSR form. */
+int hodlrdd_get_near(hodlrdd_handle h, int64_t* nnz, int64_t* off, int64_t* idx);
+
+/* Per IL block, in CSR order (levels ascending, then target, then source), 9
+ * int64: level, target box, source box, I0, m, J0, n, rank, dense. */
+int hodlrdd_get_blocks(hodlrdd_handle h, int64_t* rec);
+
+/* ACA pivots (block-local row / column indices, in pivot order) of block b;
+ * arrays of length >= rank. */
+int hodlrdd_get_pivots(hodlrdd_handle h, int64_t b, int64_t* sigma, int64_t* tau);
+
+/* FP64 copy of block b's factors as applied (after the precision conversion and
+ * scales): U m x rank, V n x rank, column-major. */
+int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V);
+
+/*
+ * Replaces every IL block's factors with caller-supplied ones (host arrays, FP64):
+ * rank[b] and dense[b] per block in CSR order; U_all / V_all hold, block after
+ * block, U_b (m x rank, column-major) and V_b (n x rank). The factors are then
+ * packed in the handle's precision exactly as after hodlrdd_build. Used to check
+ * the matvec against a reference representation independently of the ACA.
+ */
+int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t* dense, const double* U_all,
+                           const double* V_all);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HODLRDD_H */

@@ -207,9 +207,12 @@ class Tree:
 
     def blocks(self):
         """(nblocks, 10) int64: level, ti, sj, I0, m, J0, n, rank, dense, capped."""
-        rec = np.zeros(self.nblocks * 10, np.int64)
-        self._lib.or_blocks(self._h, rec)
-        return rec.reshape(self.nblocks, 10)
+        if getattr(self, "_blocks", None) is None:
+            rec = np.zeros(max(self.nblocks, 1) * 10, np.int64)
+            self._lib.or_blocks(self._h, rec)
+            self._blocks = rec[: self.nblocks * 10].reshape(self.nblocks, 10)
+            self._blocks.setflags(write=False)
+        return self._blocks
 
     def factors(self, b):
         rec = self.blocks()[b]

@@ -1,0 +1,25 @@
+"""GB300-native HODLRdD: hierarchical kernel-matrix products on one GPU.
+
+Public API (a thin ctypes layer over include/hodlrdd.h; every step runs in the
+CUDA library, there is no CPU fallback):
+
+    Handle(points, kernel, params, leaf, tol, precision=...)   build (Algorithm 1)
+    Handle.matvec(x)                                            y = K x (Algorithm 2)
+    Handle.stats()                                              ranks, sizes, phase times
+"""
+from ._binding import (  # noqa: F401
+    ERR_CUDA,
+    ERR_INVALID,
+    ERR_NUMERIC,
+    ERR_OOM,
+    ERR_TIMEOUT,
+    ERR_UNSUPPORTED,
+    OK,
+    PREC,
+    Handle,
+    HodlrddError,
+    header_functions,
+    load,
+)
+
+K_LOG, K_INV_R, K_MATERN32, K_GAUSS, K_EXP, K_INV_R2_4D, K_R, K_SIN, K_INV_SQRT1P = range(9)

@@ -1,0 +1,292 @@
+"""ctypes binding of libhodlrdd (include/hodlrdd.h): argument marshalling only.
+
+Every computation happens in the CUDA library. Arrays may be numpy arrays (host
+memory) or torch tensors (host or CUDA); torch is used for device memory and
+streams only. If the compiled library is missing this module raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libhodlrdd.so")
+HEADER = os.path.join(ROOT, "include", "hodlrdd.h")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_NUMERIC = range(7)
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+MAX_LEVELS = 64
+
+
+class HodlrddError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
+                ("aca_max_rank", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("d", C.c_int), ("kappa", C.c_int), ("precision", C.c_int), ("max_rank", C.c_int),
+        ("N", C.c_int64), ("n_blocks", C.c_int64), ("n_lowrank", C.c_int64), ("n_dense", C.c_int64),
+        ("n_rank_capped", C.c_int64), ("n_near", C.c_int64), ("factor_elems", C.c_int64),
+        ("factor_bytes", C.c_int64), ("dense_pairs", C.c_int64),
+        ("boxes_per_level", C.c_int64 * MAX_LEVELS), ("blocks_per_level", C.c_int64 * MAX_LEVELS),
+        ("max_rank_per_level", C.c_int * MAX_LEVELS), ("mean_rank_per_level", C.c_double * MAX_LEVELS),
+        ("t_tree_ms", C.c_double), ("t_classify_ms", C.c_double), ("t_aca_ms", C.c_double),
+        ("t_pack_ms", C.c_double), ("t_build_ms", C.c_double), ("device_bytes", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhodlrdd.so not found at {LIB_PATH}: run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "hodlrdd_options_default": (i32, [C.POINTER(Options)]),
+        "hodlrdd_build": (i32, [vp, i32, i64, i32, vp, i32, dbl, C.POINTER(vp)]),
+        "hodlrdd_build_ex": (i32, [vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(vp)]),
+        "hodlrdd_matvec": (i32, [vp, vp, vp, i32, vp]),
+        "hodlrdd_destroy": (i32, [vp]),
+        "hodlrdd_get_stats": (i32, [vp, C.POINTER(Stats)]),
+        "hodlrdd_error_string": (C.c_char_p, [i32]),
+        "hodlrdd_last_error": (C.c_char_p, []),
+        "hodlrdd_get_tree": (i32, [vp, vp, vp]),
+        "hodlrdd_get_cube": (i32, [vp, vp, vp]),
+        "hodlrdd_get_level": (i32, [vp, i32, C.POINTER(i64), vp, vp]),
+        "hodlrdd_get_il": (i32, [vp, i32, C.POINTER(i64), vp, vp]),
+        "hodlrdd_get_near": (i32, [vp, C.POINTER(i64), vp, vp]),
+        "hodlrdd_get_blocks": (i32, [vp, vp]),
+        "hodlrdd_get_pivots": (i32, [vp, i64, vp, vp]),
+        "hodlrdd_get_factors": (i32, [vp, i64, vp, vp]),
+        "hodlrdd_import_factors": (i32, [vp, vp, vp, vp, vp]),
+        "hodlrdd_debug_fail_alloc_after": (i32, [i64]),
+        "hodlrdd_set_profiling": (i32, [vp, i32]),
+        "hodlrdd_get_profile": (i32, [vp, vp, C.POINTER(i64), C.POINTER(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function include/hodlrdd.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(hodlrdd_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        lib = load()
+        detail = lib.hodlrdd_last_error().decode(errors="replace")
+        raise HodlrddError(status, where, detail or lib.hodlrdd_error_string(status).decode())
+
+
+def _ptr(a):
+    """(address, keepalive) of a numpy array or torch tensor (any device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)!r}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Handle:
+    """A HODLRdD representation of K on the current CUDA device."""
+
+    def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
+                 precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
+                 aca_max_rank: int = 1024):
+        lib = load()
+        if isinstance(points, np.ndarray):
+            points = np.ascontiguousarray(points, dtype=np.float64)
+        if points.ndim != 2:
+            raise ValueError("points must be N x d")
+        self.N, self.d = int(points.shape[0]), int(points.shape[1])
+        self.precision = precision
+        self.io_dtype = np.float64 if precision == "fp64" else np.float32
+        opt = Options()
+        lib.hodlrdd_options_default(C.byref(opt))
+        opt.precision = PREC[precision]
+        opt.dense_if_cheaper = 1 if dense_if_cheaper else 0
+        opt.max_nrhs = int(max_nrhs)
+        opt.aca_max_rank = int(aca_max_rank)
+        p = np.zeros(4, np.float64)
+        p[0] = 1.0
+        if params is not None:
+            v = np.asarray(params, np.float64).reshape(-1)
+            p[: min(4, v.size)] = v[:4]
+        self.params = p
+        addr, keep = _ptr(points)
+        h = C.c_void_p()
+        st = lib.hodlrdd_build_ex(addr, self.d, self.N, int(kernel), p.ctypes.data, int(leaf), float(tol),
+                                  C.byref(opt), C.byref(h))
+        _check(st, "hodlrdd_build")
+        self._h = h
+        self._lib = lib
+        self.kernel = int(kernel)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.hodlrdd_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the product ---------------------------------------------------------------
+    def matvec(self, x, y=None, stream=None):
+        """y = K x. x: (N,) or (N, nrhs), numpy (host) or torch (host / CUDA)."""
+        nrhs = 1 if x.ndim == 1 else int(x.shape[1])
+        if y is None:
+            if isinstance(x, np.ndarray):
+                y = np.empty(x.shape, dtype=self.io_dtype)
+            else:
+                y = x.new_empty(x.shape)
+        xa, kx = _ptr(x)
+        ya, ky = _ptr(y)
+        st = self._lib.hodlrdd_matvec(self._h, xa, ya, nrhs, _stream_ptr(stream))
+        _check(st, "hodlrdd_matvec")
+        return y
+
+    # -- statistics and introspection ----------------------------------------------
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.hodlrdd_get_stats(self._h, C.byref(s)), "hodlrdd_get_stats")
+        k = s.kappa
+        out = {name: getattr(s, name) for name, _ in Stats._fields_ if not name.endswith("_level")}
+        out["boxes_per_level"] = list(s.boxes_per_level[: k + 1])
+        out["blocks_per_level"] = list(s.blocks_per_level[: k + 1])
+        out["max_rank_per_level"] = list(s.max_rank_per_level[: k + 1])
+        out["mean_rank_per_level"] = list(s.mean_rank_per_level[: k + 1])
+        return out
+
+    def set_profiling(self, on: bool):
+        _check(self._lib.hodlrdd_set_profiling(self._h, 1 if on else 0), "hodlrdd_set_profiling")
+
+    def profile(self) -> dict:
+        """Accumulated stage times (ms) since profiling was enabled, and launch count."""
+        ms = np.zeros(4, np.float64)
+        chunks = C.c_int64()
+        launches = C.c_int64()
+        _check(self._lib.hodlrdd_get_profile(self._h, ms.ctypes.data, C.byref(chunks), C.byref(launches)),
+               "hodlrdd_get_profile")
+        return {"gather_ms": ms[0], "vapply_ms": ms[1], "uapply_ms": ms[2], "near_ms": ms[3],
+                "chunks": chunks.value, "launches": launches.value}
+
+    def tree(self):
+        perm = np.zeros(self.N, np.int64)
+        keys = np.zeros(self.N, np.uint64)
+        _check(self._lib.hodlrdd_get_tree(self._h, perm.ctypes.data, keys.ctypes.data), "hodlrdd_get_tree")
+        return perm, keys
+
+    def cube(self):
+        lo = np.zeros(self.d, np.float64)
+        si = np.zeros(2, np.float64)
+        _check(self._lib.hodlrdd_get_cube(self._h, lo.ctypes.data, si.ctypes.data), "hodlrdd_get_cube")
+        return lo, float(si[0]), float(si[1])
+
+    def level(self, l):
+        nb = C.c_int64()
+        _check(self._lib.hodlrdd_get_level(self._h, int(l), C.byref(nb), None, None), "hodlrdd_get_level")
+        st = np.zeros(nb.value + 1, np.int64)
+        bk = np.zeros(nb.value, np.uint64)
+        _check(self._lib.hodlrdd_get_level(self._h, int(l), C.byref(nb), st.ctypes.data, bk.ctypes.data),
+               "hodlrdd_get_level")
+        return st, bk
+
+    def il(self, l):
+        nb = C.c_int64()
+        self._lib.hodlrdd_get_level(self._h, int(l), C.byref(nb), None, None)
+        nnz = C.c_int64()
+        _check(self._lib.hodlrdd_get_il(self._h, int(l), C.byref(nnz), None, None), "hodlrdd_get_il")
+        off = np.zeros(nb.value + 1, np.int64)
+        idx = np.zeros(nnz.value, np.int64)
+        _check(self._lib.hodlrdd_get_il(self._h, int(l), C.byref(nnz), off.ctypes.data, idx.ctypes.data),
+               "hodlrdd_get_il")
+        return off, idx
+
+    def near(self):
+        s = self.stats()
+        nb = s["boxes_per_level"][s["kappa"]]
+        nnz = C.c_int64()
+        off = np.zeros(nb + 1, np.int64)
+        idx = np.zeros(s["n_near"], np.int64)
+        _check(self._lib.hodlrdd_get_near(self._h, C.byref(nnz), off.ctypes.data, idx.ctypes.data),
+               "hodlrdd_get_near")
+        return off, idx
+
+    def blocks(self):
+        """(n_blocks, 9) int64: level, target, source, I0, m, J0, n, rank, dense."""
+        nb = self.stats()["n_blocks"]
+        rec = np.zeros(max(nb, 1) * 9, np.int64)
+        _check(self._lib.hodlrdd_get_blocks(self._h, rec.ctypes.data), "hodlrdd_get_blocks")
+        return rec[: nb * 9].reshape(nb, 9)
+
+    def pivots(self, b, rank):
+        sig = np.zeros(max(rank, 1), np.int64)
+        tau = np.zeros(max(rank, 1), np.int64)
+        _check(self._lib.hodlrdd_get_pivots(self._h, int(b), sig.ctypes.data, tau.ctypes.data),
+               "hodlrdd_get_pivots")
+        return sig[:rank], tau[:rank]
+
+    def factors(self, b, m, n, rank):
+        U = np.zeros(max(m * rank, 1), np.float64)
+        V = np.zeros(max(n * rank, 1), np.float64)
+        _check(self._lib.hodlrdd_get_factors(self._h, int(b), U.ctypes.data, V.ctypes.data), "hodlrdd_get_factors")
+        return U[: m * rank].reshape(rank, m).T, V[: n * rank].reshape(rank, n).T
+
+    def import_factors(self, ranks, dense, U_all, V_all):
+        r = np.ascontiguousarray(ranks, np.int32)
+        dn = np.ascontiguousarray(dense, np.int32)
+        U = np.ascontiguousarray(U_all, np.float64)
+        V = np.ascontiguousarray(V_all, np.float64)
+        _check(self._lib.hodlrdd_import_factors(self._h, r.ctypes.data, dn.ctypes.data, U.ctypes.data,
+                                                V.ctypes.data), "hodlrdd_import_factors")
+
+
+def debug_fail_alloc_after(k: int):
+    load().hodlrdd_debug_fail_alloc_after(int(k))

@@ -1,0 +1,292 @@
+// Internal declarations shared by the translation units of libhodlrdd.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/hodlrdd.h"
+
+namespace hd {
+
+// ------------------------------------------------------------------ errors ----
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define HD_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return ::hd::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HD_TRY(call)                 \
+  do {                               \
+    int s_ = (call);                 \
+    if (s_ != HODLRDD_OK) return s_; \
+  } while (0)
+
+// Test hook: make the k-th device allocation from now fail (k < 0: never).
+void debug_fail_alloc_after(int64_t k);
+int dev_alloc(void** p, size_t bytes);
+
+// Owning device buffer. Frees on destruction; never copied.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return HODLRDD_OK;
+    void* q = nullptr;
+    int s = dev_alloc(&q, count * sizeof(T));
+    if (s != HODLRDD_OK) return s;
+    p = static_cast<T*>(q);
+    n = count;
+    return HODLRDD_OK;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+template <class T>
+int upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t st) {
+  HD_TRY(d.alloc(h.size()));
+  if (!h.empty()) HD_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return HODLRDD_OK;
+}
+
+template <class T>
+int download(std::vector<T>& h, const T* d, size_t n, cudaStream_t st) {
+  h.resize(n);
+  if (n) HD_CUDA(cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+  return HODLRDD_OK;
+}
+
+// ------------------------------------------------------------------ kernel ----
+struct KernelSpec {
+  int id;
+  double scale, diag, p0, p1;
+};
+
+constexpr int kMaxDim = 8;
+constexpr int kPadRows = 2;  // factor columns are padded to a multiple of this many rows
+
+__host__ __device__ inline int64_t pad_rows(int64_t m) { return (m + kPadRows - 1) / kPadRows * kPadRows; }
+
+// Squared distance and F(s) in FP64 with a fixed operation order. The file
+// that evaluates entries for the compression is compiled with contraction off,
+// so these round exactly like a plain CPU evaluation of the same formulas.
+__device__ __forceinline__ double f64_of_s(int id, double s, double p0) {
+  switch (id) {
+    case HODLRDD_K_LOG:
+      return s == 0.0 ? 0.0 : log(sqrt(s));
+    case HODLRDD_K_INV_R:
+      return s == 0.0 ? 0.0 : 1.0 / sqrt(s);
+    case HODLRDD_K_MATERN32: {
+      double a = (1.7320508075688772 * sqrt(s)) / p0;
+      return (1.0 + a) * exp(-a);
+    }
+    case HODLRDD_K_GAUSS:
+      return exp(-s / (2.0 * p0 * p0));
+    case HODLRDD_K_EXP:
+      return exp(-sqrt(s) / p0);
+    case HODLRDD_K_INV_R2_4D:
+      return s == 0.0 ? 0.0 : -1.0 / (39.47841760435743 * s);
+    case HODLRDD_K_R:
+      return sqrt(s);
+    case HODLRDD_K_SIN:
+      return sin(sqrt(s));
+    case HODLRDD_K_INV_SQRT1P:
+      return 1.0 / sqrt(1.0 + sqrt(s));
+  }
+  return 0.0;
+}
+
+// FP32 evaluation for the mixed-precision near field. `c` is a per-kernel
+// precomputed constant (see kernel_const32).
+__device__ __forceinline__ float f32_of_s(int id, float s, float c) {
+  switch (id) {
+    case HODLRDD_K_LOG:
+      return s == 0.0f ? 0.0f : 0.5f * logf(s);
+    case HODLRDD_K_INV_R:
+      return s == 0.0f ? 0.0f : rsqrtf(s);
+    case HODLRDD_K_MATERN32: {
+      float a = c * sqrtf(s);
+      return (1.0f + a) * expf(-a);
+    }
+    case HODLRDD_K_GAUSS:
+      return expf(-c * s);
+    case HODLRDD_K_EXP:
+      return expf(-c * sqrtf(s));
+    case HODLRDD_K_INV_R2_4D:
+      return s == 0.0f ? 0.0f : c / s;
+    case HODLRDD_K_R:
+      return sqrtf(s);
+    case HODLRDD_K_SIN:
+      return sinf(sqrtf(s));
+    case HODLRDD_K_INV_SQRT1P:
+      return rsqrtf(1.0f + sqrtf(s));
+  }
+  return 0.0f;
+}
+
+// FP64 evaluation for the FP64 matvec near field: same formulas, contraction
+// allowed (this is not used where bitwise agreement with the oracle matters).
+__device__ __forceinline__ double f64fast_of_s(int id, double s, double c) {
+  switch (id) {
+    case HODLRDD_K_LOG:
+      return s == 0.0 ? 0.0 : 0.5 * log(s);
+    case HODLRDD_K_INV_R:
+      return s == 0.0 ? 0.0 : rsqrt(s);
+    case HODLRDD_K_MATERN32: {
+      double a = c * sqrt(s);
+      return (1.0 + a) * exp(-a);
+    }
+    case HODLRDD_K_GAUSS:
+      return exp(-c * s);
+    case HODLRDD_K_EXP:
+      return exp(-c * sqrt(s));
+    case HODLRDD_K_INV_R2_4D:
+      return s == 0.0 ? 0.0 : c / s;
+    case HODLRDD_K_R:
+      return sqrt(s);
+    case HODLRDD_K_SIN:
+      return sin(sqrt(s));
+    case HODLRDD_K_INV_SQRT1P:
+      return rsqrt(1.0 + sqrt(s));
+  }
+  return 0.0;
+}
+
+// The constant folded into the matvec evaluators above.
+inline double kernel_const(const KernelSpec& k) {
+  switch (k.id) {
+    case HODLRDD_K_MATERN32: return 1.7320508075688772 / k.p0;
+    case HODLRDD_K_GAUSS: return 1.0 / (2.0 * k.p0 * k.p0);
+    case HODLRDD_K_EXP: return 1.0 / k.p0;
+    case HODLRDD_K_INV_R2_4D: return -1.0 / 39.47841760435743;
+    default: return 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ handle ----
+struct Level {
+  int64_t nb = 0;
+  std::vector<int32_t> h_bstart;  // nb + 1
+  std::vector<uint64_t> h_bkey;   // nb
+  std::vector<int32_t> h_iloff;   // nb + 1 (levels >= 1)
+  std::vector<int32_t> h_ilidx;
+  DevBuf<int32_t> bstart;
+  DevBuf<uint64_t> bkey;
+  DevBuf<int32_t> cfirst;  // nb + 1: first child box at level l + 1
+  DevBuf<int32_t> bid;     // per tree-order point: its box at this level (build only)
+  DevBuf<int32_t> iloff, ilidx;
+};
+
+// Per-precision packed factors and everything the matvec launches read.
+struct Plan {
+  int64_t n_vitems = 0, n_uitems = 0, n_nitems = 0;
+  DevBuf<int4> vitems;    // {block, k0, kc, 0}
+  DevBuf<int4> uitems;    // {blk_begin, blk_end, row_start, nrows}; ylev row = level-major
+  DevBuf<int32_t> ulevel; // level of each U item
+  DevBuf<int4> nitems;    // leaf boxes: {I0, m, near_begin, near_end}
+  DevBuf<int32_t> near_src;  // extended near list: source leaf box index per entry
+  int64_t n_near_src = 0;
+  int max_vn = 0;
+};
+
+}  // namespace hd
+
+struct hodlrdd_s {
+  // problem
+  int d = 0;
+  int64_t N = 0;
+  hd::KernelSpec K{};
+  int leaf = 0;
+  double tol = 0.0;
+  hodlrdd_options opt{};
+  int device = 0;
+  cudaStream_t st = nullptr;  // the handle's own stream (build, staging)
+
+  // tree
+  int B = 0, kappa = 0;
+  double lo[hd::kMaxDim] = {0};
+  double side = 0.0, inv = 0.0;
+  std::vector<int32_t> h_perm;
+  std::vector<uint64_t> h_skey;
+  hd::DevBuf<int32_t> perm;    // tree position -> original index
+  hd::DevBuf<uint64_t> skey;
+  hd::DevBuf<double> pts64;    // SoA d x N, tree order
+  hd::DevBuf<float> pts32;     // SoA d x N, tree order
+  std::vector<hd::Level> lv;   // levels 0..kappa
+  std::vector<int32_t> h_nearoff, h_nearidx;
+  hd::DevBuf<int32_t> nearoff, nearidx;
+
+  // blocks (CSR order over levels 1..kappa)
+  int64_t nblk = 0;
+  std::vector<int32_t> h_blevel, h_bti, h_bsj, h_bI0, h_bm, h_bJ0, h_bn, h_rank, h_dense;
+  std::vector<int64_t> h_blk_off;  // level -> first block (size kappa + 2)
+  hd::DevBuf<int32_t> bI0, bm, bJ0, bn, rank, dense;
+  hd::DevBuf<int64_t> uoff, voff, toff;  // packed factor offsets (elements); t / pivot offsets
+  hd::DevBuf<int32_t> piv_sigma, piv_tau;  // by toff
+  int64_t total_rank = 0, n_rank_capped = 0;
+
+  // factors in the handle's precision
+  hd::DevBuf<char> U, V;       // packed factor storage
+  hd::DevBuf<float> su, sv;    // per-column scales (16-bit precisions)
+  int64_t factor_elems = 0, factor_bytes = 0, dense_pairs = 0;
+  hd::Plan plan;
+
+  // matvec workspace (right-hand sides are processed in chunks of at most 8)
+  hd::DevBuf<char> xt, tbuf, ylev, xstage, ystage;
+
+  // tracing: events between matvec stages, resolved by hodlrdd_get_profile
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::vector<cudaEvent_t>> ev_pending;  // per chunk: 5 events
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_chunks = 0;
+  int64_t launches = 0;
+
+  // stats
+  hodlrdd_stats stats{};
+};
+
+namespace hd {
+// Build stages (tree.cu, aca.cu, apply.cu).
+int build_tree(hodlrdd_s* h, const double* dpts);
+int build_lists(hodlrdd_s* h);
+int build_blocks(hodlrdd_s* h);
+int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<int64_t>& uoff64,
+            std::vector<int64_t>& voff64);
+int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
+                 const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64);
+int build_plan(hodlrdd_s* h);
+int alloc_workspace(hodlrdd_s* h);
+int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
+int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
+size_t elem_size(int precision);
+}  // namespace hd
