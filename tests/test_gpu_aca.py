@@ -25,7 +25,14 @@ def env():
     return torch, oracle, hd
 
 
-def compare(T, h, check_factors=True, max_factor_checks=400):
+def compare(T, h, exact, max_factor_checks=400):
+    """Fraction of blocks with identical rank, dense flag and pivots.
+
+    For those blocks the factors are compared: bit-identical when every kernel
+    value is correctly rounded on both sides (exact), else through the product
+    U V^T (late ACA terms divide rounding-level residuals by small pivots, so
+    ulp differences between CUDA's and the host's log / exp show up in v_k
+    entries of negligible weight)."""
     bo = T.blocks()
     bg = h.blocks()
     checked = 0
@@ -42,12 +49,14 @@ def compare(T, h, check_factors=True, max_factor_checks=400):
         sg, tg = h.pivots(b, rg)
         if np.array_equal(so, sg) and np.array_equal(to, tg):
             same += 1
-            if check_factors and checked < max_factor_checks:
+            if checked < max_factor_checks:
                 checked += 1
                 Ug, Vg = h.factors(b, int(bo[b, 4]), int(bo[b, 6]), rg)
-                scale = max(np.abs(Uo).max(), 1e-300)
-                assert np.abs(Ug - Uo).max() <= 1e-12 * scale
-                assert np.abs(Vg - Vo).max() <= 1e-12
+                if exact:
+                    assert np.array_equal(Ug, Uo) and np.array_equal(Vg, Vo)
+                else:
+                    Ao = Uo @ Vo.T
+                    assert np.linalg.norm(Ug @ Vg.T - Ao) <= 1e-12 * np.linalg.norm(Ao)
     return same / max(len(bo), 1)
 
 
@@ -67,7 +76,7 @@ def test_ranks_and_pivots_match_oracle(env, d, N, kernel, params, leaf, tol, exa
     w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), leaf, tol, 1, seed=d * 7 + 1)
     T = oracle.Tree(w.points, w.kernel, w.params, leaf, tol, dense_if_cheaper=dense_if_cheaper)
     h = gpu_handle(hd, w, dense_if_cheaper=dense_if_cheaper)
-    frac = compare(T, h)
+    frac = compare(T, h, exact)
     assert frac == 1.0 if exact else frac >= 0.99
     s = h.stats()
     assert s["n_rank_capped"] == 0
