@@ -39,7 +39,7 @@ ERR_BAR = 1e-6
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
@@ -167,21 +167,11 @@ def measured_peaks():
 
 
 def factor_bytes(h, precision):
-    """Algorithmic bytes of the packed U and V factors (incl. row padding and scales)."""
-    from paper_2209_05819_gb300 import _binding as B
-
-    rec = h.blocks()
-    p = rec[:, 7]
-    m = rec[:, 4]
-    n = rec[:, 6]
-    pad = lambda v: (v + 1) // 2 * 2
-    es = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
-    ub = int((p * pad(m)).sum()) * es
-    vb = int((p * pad(n)).sum()) * es
-    tr = int(p.sum())
-    scales = 4 * tr if precision in ("fp16", "bf16") else 0
-    del B
-    return ub, vb, tr, scales
+    """Algorithmic bytes of the packed U and V streams (incl. alignment pads) and scales."""
+    s = h.stats()
+    tr = int(s["total_rank"])
+    scales = 8 * tr if precision in ("fp16", "bf16") else 0
+    return int(s["factor_bytes_u"]), int(s["factor_bytes_v"]), tr, scales
 
 
 def time_steps(fn, steps, warmup, torch, stream):
@@ -305,6 +295,7 @@ def main():
         dist.barrier()
     prof = h.profile()
     h.set_profiling(False)
+    h.sync()  # raises if a bounded device-side wait expired during the timed steps
     launches = prof["launches"] - launches0
     total_units, max_seconds = aggregate(units * args.steps, seconds, dist, device="cuda")
     value = total_units / max_seconds

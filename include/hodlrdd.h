@@ -113,6 +113,9 @@ typedef struct hodlrdd_stats {
   double t_pack_ms;          /* factor packing / precision conversion, task lists */
   double t_build_ms;         /* whole build, wall clock */
   int64_t device_bytes;      /* device memory held by the handle */
+  int64_t factor_bytes_u;    /* bytes of the packed U stream (rows per level and box) */
+  int64_t factor_bytes_v;    /* bytes of the packed V stream (columns per block) */
+  int64_t total_rank;        /* sum of ranks: length of the t vector of the V-apply */
 } hodlrdd_stats;
 
 /* Fills *opt with the defaults described above. */
@@ -162,6 +165,14 @@ int hodlrdd_build_ex(const double* points, int d, int64_t N, int kernel_id, cons
  * serialised by the caller.
  */
 int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
+
+/*
+ * Waits for all device work (cudaDeviceSynchronize) and reports failures the
+ * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
+ * their bounded waits expired (the y of that matvec is then invalid). Clears the
+ * recorded failure. Failure detection for callers that keep matvecs asynchronous.
+ */
+int hodlrdd_sync(hodlrdd_handle h);
 
 /* Frees the handle and all device memory it holds. NULL is accepted. */
 int hodlrdd_destroy(hodlrdd_handle h);

@@ -44,6 +44,7 @@ class Stats(C.Structure):
         ("max_rank_per_level", C.c_int * MAX_LEVELS), ("mean_rank_per_level", C.c_double * MAX_LEVELS),
         ("t_tree_ms", C.c_double), ("t_classify_ms", C.c_double), ("t_aca_ms", C.c_double),
         ("t_pack_ms", C.c_double), ("t_build_ms", C.c_double), ("device_bytes", C.c_int64),
+        ("factor_bytes_u", C.c_int64), ("factor_bytes_v", C.c_int64), ("total_rank", C.c_int64),
     ]
 
 
@@ -80,6 +81,7 @@ def load():
         "hodlrdd_import_factors": (i32, [vp, vp, vp, vp, vp]),
         "hodlrdd_debug_fail_alloc_after": (i32, [i64]),
         "hodlrdd_set_profiling": (i32, [vp, i32]),
+        "hodlrdd_sync": (i32, [vp]),
         "hodlrdd_get_profile": (i32, [vp, vp, C.POINTER(i64), C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +205,10 @@ class Handle:
         out["max_rank_per_level"] = list(s.max_rank_per_level[: k + 1])
         out["mean_rank_per_level"] = list(s.mean_rank_per_level[: k + 1])
         return out
+
+    def sync(self):
+        """Wait for the device; raise if a matvec kernel recorded a failed bounded wait."""
+        _check(self._lib.hodlrdd_sync(self._h), "hodlrdd_sync")
 
     def set_profiling(self, on: bool):
         _check(self._lib.hodlrdd_set_profiling(self._h, 1 if on else 0), "hodlrdd_set_profiling")

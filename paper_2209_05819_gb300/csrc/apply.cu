@@ -1,23 +1,30 @@
 // Factor packing (a6) and the HODLRdD matrix-vector product (a7 - a10).
 //
 // Algorithm 2 in GPU form, for a chunk of NR right-hand sides:
-//   a7  gather    x_t[i] = x[perm[i]]                         (tree order)
-//   a8  V-apply   t_b = V_b^T x_t(J_b) for every low-rank IL block b
-//       U-apply   ylev[l](I) = sum_{b in IL(box)} U_b t_b, one owner warp per
-//                 (level, target box, 64-row slice); IL blocks flagged dense at
-//                 coarse levels are evaluated on the fly here
-//   a9  near      per leaf box: sum over the near list (self and d' >= 1
-//                 neighbours) and the leaf-level dense IL blocks, K(I,J) x_t(J)
-//                 evaluated on the fly from the point coordinates, never stored
-//   a10 combine   y[perm[i]] = sum_l ylev[l][i] + near(i)
-// Every output row has exactly one writer per stage and a fixed summation
-// order, so results are bitwise reproducible and no atomics touch y.
+//   a7  gather    x_t[i] = x[perm[i]]                          (tree order)
+//   a8  V-apply   t_b[k] = V_b[:,k] . x_t(J_b)  for every low-rank IL block
+//       U-apply   y_l(i) = U_box(i)[r,:] . t_box  for every level l and box
+//   a9  dense     K(I,J) x_t(J) evaluated on the fly: IL blocks flagged dense at
+//                 coarse levels, then per leaf box the near field (self and d' >= 1
+//                 neighbours) and the leaf-level dense IL blocks
+//   a10 combine   y[perm[i]] = sum_l y_l(i) + near(i)
 //
-// Factor layout: block b's U_b (m x p) and V_b (n x p) are column-major with the
-// row count padded to an even number (2-element vector loads), blocks in CSR
-// order. 16-bit factors carry one FP32 scale per column (a power of two, so
-// scaling is exact); the V-apply folds both scales of column k into t_b[k].
+// Both low-rank applies are the same operation: dot products of contiguous
+// factor segments with a vector. V is stored column by column; U is stored per
+// (level, box) row-major over the concatenated columns of the box's IL blocks,
+// so a box's rows read one contiguous t vector. Each factor array is a stream
+// of 16-byte aligned segments, consumed by one persistent CTA per SM: a
+// producer lane moves 32 KB stages with cp.async.bulk into a shared-memory ring
+// guarded by mbarriers; consumer warps split every stage into lane teams sized
+// to the segment length and reduce with shuffles. Every output has one writer
+// and a fixed summation order (bitwise reproducible, no atomics on results).
+// All waits are bounded; on timeout the kernel records an error and returns.
+//
+// 16-bit factors carry one power-of-two FP32 scale per column (exact
+// rescaling); the V-apply folds the U and V scales of column k into t_b[k].
 #include <algorithm>
+#include <climits>
+#include <cmath>
 
 #include "internal.cuh"
 
@@ -33,307 +40,452 @@ size_t elem_size(int precision) {
 
 namespace {
 
-template <class F> struct Fac;
+constexpr int kStageBytes = 32768;
+constexpr int kStages = 4;
+constexpr int kConsumerWarps = 8;
+constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
+constexpr int kGuard = 16;                        // zero elements around xt and t (per rhs)
+constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at GB300 clocks
+
+enum { ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_DRAIN = 3 };
+
+// ---------------------------------------------------------- element types ----
+template <class T> struct Fac;
 template <> struct Fac<double> {
   using acc = double;
+  static constexpr int E = 2;  // elements per 16-byte chunk
   static constexpr bool scaled = false;
   __device__ static double from(double v) { return v; }
   __host__ static double to_host(double v) { return v; }
-  __device__ static void load2(const double* p, double& a, double& b) {
-    double2 v = *reinterpret_cast<const double2*>(p);
-    a = v.x; b = v.y;
+  __device__ static void chunk(const void* p, double (&v)[2]) {
+    double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
   }
 };
 template <> struct Fac<float> {
   using acc = float;
+  static constexpr int E = 4;
   static constexpr bool scaled = false;
   __device__ static float from(double v) { return (float)v; }
   __host__ static double to_host(float v) { return v; }
-  __device__ static void load2(const float* p, float& a, float& b) {
-    float2 v = *reinterpret_cast<const float2*>(p);
-    a = v.x; b = v.y;
+  __device__ static void chunk(const void* p, float (&v)[4]) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
 };
 template <> struct Fac<__half> {
   using acc = float;
+  static constexpr int E = 8;
   static constexpr bool scaled = true;
   __device__ static __half from(double v) { return __float2half_rn((float)v); }
   __host__ static double to_host(__half v) { return (double)__half2float(v); }
-  __device__ static void load2(const __half* p, float& a, float& b) {
-    float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
-    a = v.x; b = v.y;
+  __device__ static void chunk(const void* p, float (&v)[8]) {
+    uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __half2* hh = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __half22float2(hh[i]);
+      v[2 * i] = f.x; v[2 * i + 1] = f.y;
+    }
   }
 };
 template <> struct Fac<__nv_bfloat16> {
   using acc = float;
+  static constexpr int E = 8;
   static constexpr bool scaled = true;
   __device__ static __nv_bfloat16 from(double v) { return __float2bfloat16_rn((float)v); }
   __host__ static double to_host(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-  __device__ static void load2(const __nv_bfloat16* p, float& a, float& b) {
-    float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-    a = v.x; b = v.y;
+  __device__ static void chunk(const void* p, float (&v)[8]) {
+    uint4 q = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 f = __bfloat1622float2(hh[i]);
+      v[2 * i] = f.x; v[2 * i + 1] = f.y;
+    }
   }
 };
 
-constexpr int kWarpsPerCta = 8;
-
-// ---------------------------------------------------------------- packing ----
-// One CTA per block, one warp per factor column. 16-bit: column scale = the
-// smallest power of two >= max |entry| (exact rescaling), entries stored / scale.
-template <class F>
-__global__ void k_pack(int64_t nblk, const int32_t* __restrict__ rank, const int32_t* __restrict__ bm,
-                       const int32_t* __restrict__ bn, const double* __restrict__ U64,
-                       const double* __restrict__ V64, const int64_t* __restrict__ uoff64,
-                       const int64_t* __restrict__ voff64, const int64_t* __restrict__ uoff,
-                       const int64_t* __restrict__ voff, const int64_t* __restrict__ toff, F* __restrict__ U,
-                       F* __restrict__ V, float* __restrict__ su, float* __restrict__ sv) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int p = rank[b];
-    if (p == 0) continue;
-    for (int side = 0; side < 2; ++side) {
-      const int64_t rows = side == 0 ? bm[b] : bn[b];
-      const int64_t ld = pad_rows(rows);
-      const double* src = side == 0 ? U64 + uoff64[b] : V64 + voff64[b];
-      F* dst = side == 0 ? U + uoff[b] : V + voff[b];
-      float* sc = side == 0 ? su : sv;
-      for (int k = w; k < p; k += nw) {
-        const double* col = src + (int64_t)k * rows;
-        double scale = 1.0;
-        if (Fac<F>::scaled) {
-          double mx = 0.0;
-          for (int64_t i = lane; i < rows; i += 32) mx = fmax(mx, fabs(col[i]));
-          for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          int e = 0;
-          if (mx > 0.0) {
-            frexp(mx, &e);  // mx = f * 2^e with f in [0.5, 1)
-          }
-          scale = mx > 0.0 ? ldexp(1.0, e) : 1.0;
-          if (lane == 0) sc[toff[b] + k] = (float)scale;
-        }
-        const double inv = 1.0 / scale;
-        for (int64_t i = lane; i < ld; i += 32) dst[(int64_t)k * ld + i] = Fac<F>::from(i < rows ? col[i] * inv : 0.0);
-      }
+// E * NR consecutive vector values (16-byte aligned) into registers.
+template <class Acc, int E, int NR>
+__device__ __forceinline__ void load_vec(const Acc* __restrict__ p, Acc (&v)[E * NR]) {
+  constexpr int PER = 16 / sizeof(Acc);
+#pragma unroll
+  for (int i = 0; i < E * NR; i += PER) {
+    if constexpr (sizeof(Acc) == 4) {
+      float4 q = *reinterpret_cast<const float4*>(p + i);
+      v[i] = q.x; v[i + 1] = q.y; v[i + 2] = q.z; v[i + 3] = q.w;
+    } else {
+      double2 q = *reinterpret_cast<const double2*>(p + i);
+      v[i] = q.x; v[i + 1] = q.y;
     }
   }
 }
 
-// ----------------------------------------------------------------- matvec ----
-template <class Acc, class IO, int NR>
-__global__ void k_gather(const IO* __restrict__ x, const int32_t* __restrict__ perm, int64_t N, int ldx, int c0,
-                         Acc* __restrict__ xt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const IO* src = x + (int64_t)perm[i] * ldx + c0;
+// ------------------------------------------------------------- mbarriers ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false (and the error word set) if
+// it has not completed within kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void consumer_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
+}
+
+// ------------------------------------------------------ segmented dot ----
+// Stage kinds (decided on the host): "short" stages hold whole segments of at
+// most kLongChunks 16-byte chunks from up to kGmax groups and are processed by
+// lane teams of Stage::ts lanes over a flat list of the stage's segments;
+// "long" stages (ts = 0) hold whole longer segments of one group, each shared
+// by all consumer warps; "piece" stages hold part of a segment longer than a
+// stage. The vector slice of every group that fits kVecBytes is bulk-copied
+// next to the factor data (one right-hand side).
+constexpr int kLongChunks = 512;
+constexpr int kVecBytes = 20480;
+constexpr int kGmax = 32;
+struct SlotMeta {
+  Stage st;
+  SegGroup g[kGmax];
+  int32_t voff[kGmax];      // byte offset of group i's vector slice in the slot, -1 if not staged
+  int32_t sbeg[kGmax + 1];  // first stage-local segment of group i
+  int32_t gpos[kGmax];      // element offset of group i's first segment in the stage
+  int32_t s0[kGmax];        // index within group i of its first segment in the stage
+};
+constexpr int kMetaBytes = (int)((sizeof(SlotMeta) + 127) / 128 * 128);
+constexpr int kSlotBytes = kStageBytes + kVecBytes + kMetaBytes;
+
+template <class T, int NR>
+__device__ __forceinline__ void write_out(int64_t o, const typename Fac<T>::acc (&acc)[NR],
+                                          typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
+                                          const float* __restrict__ sb) {
+  using Acc = typename Fac<T>::acc;
+  const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) xt[i * NR + r] = (Acc)src[r];
+  for (int r = 0; r < NR; ++r) out[o * NR + r] = acc[r] * sc;
+}
+
+template <class T, int NR>
+__device__ __forceinline__ void dot_chunk(const char* fp, const typename Fac<T>::acc* vp,
+                                          typename Fac<T>::acc (&acc)[NR]) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  Acc f[E];
+  Fac<T>::chunk(fp, f);
+  Acc v[E * NR];
+  load_vec<Acc, E, NR>(vp, v);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] += f[e] * v[e * NR + r];
+}
+
+// Short stage: teams of TS lanes take the stage's segments round-robin across
+// group boundaries, SU segments in flight per team; a lane covers chunks
+// tl, tl + TS, ... of its segment. Shuffle reduction within the team.
+template <class T, int NR>
+__device__ __forceinline__ void consume_short(const SlotMeta* meta, const char* base,
+                                              const typename Fac<T>::acc* __restrict__ vec,
+                                              typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
+                                              const float* __restrict__ sb, int cw, int lane) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  constexpr int SU = NR == 1 ? 4 : 2;
+  const int TS = meta->st.pad;
+  const int S = meta->st.nseg;
+  const int per_warp = 32 / TS;
+  const int nteams = kConsumerWarps * per_warp;
+  const int team = cw * per_warp + lane / TS;
+  const int tl = lane % TS;
+  int gi = 0;
+  for (int b0 = 0; b0 < S; b0 += nteams * SU) {
+    Acc acc[SU][NR];
+    int64_t oidx[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[u][r] = Acc(0);
+      oidx[u] = -1;
+      const int q = b0 + u * nteams + team;
+      if (q < S) {
+        while (q >= meta->sbeg[gi + 1]) ++gi;
+        const SegGroup& G = meta->g[gi];
+        const int j = q - meta->sbeg[gi];
+        const int C = G.L / E;
+        const char* sp = base + ((int64_t)meta->gpos[gi] + (int64_t)j * G.L) * sizeof(T);
+        const int vo = meta->voff[gi];
+        const Acc* vsrc = vo >= 0 ? reinterpret_cast<const Acc*>(base + kStageBytes + vo) : vec + (int64_t)G.vec * NR;
+#pragma unroll 4
+        for (int c = tl; c < C; c += TS) dot_chunk<T, NR>(sp + (size_t)c * 16, vsrc + (int64_t)c * E * NR, acc[u]);
+        oidx[u] = (int64_t)G.out0 + meta->s0[gi] + j;
+      }
+    }
+    for (int o = TS >> 1; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < SU; ++u)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[u][r] += __shfl_xor_sync(0xffffffffu, acc[u][r], o);
+    if (tl == 0) {
+#pragma unroll
+      for (int u = 0; u < SU; ++u)
+        if (oidx[u] >= 0) write_out<T, NR>(oidx[u], acc[u], out, sa, sb);
+    }
   }
 }
 
-// Sum 32 per-lane partial values across the warp; lane l ends with the total of
-// value index l (butterfly halving: 31 shuffles for 32 sums).
-template <class Acc>
-__device__ __forceinline__ Acc transpose_reduce(Acc (&v)[32]) {
-  const int lane = threadIdx.x & 31;
+// Long stage: all consumer warps share one segment at a time; warp sums meet in
+// double-buffered shared memory (one consumer barrier per segment).
+template <class T, int NR>
+__device__ __forceinline__ void consume_long(const SlotMeta* meta, const char* base,
+                                             const typename Fac<T>::acc* __restrict__ vec,
+                                             typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
+                                             const float* __restrict__ sb, int cw, int lane,
+                                             typename Fac<T>::acc* part, int& pbuf) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  const SegGroup& G = meta->g[0];
+  const int C = G.L / E;
+  const int vo = meta->voff[0];
+  const Acc* vsrc = vo >= 0 ? reinterpret_cast<const Acc*>(base + kStageBytes + vo) : vec + (int64_t)G.vec * NR;
+  const int ct = cw * 32 + lane;
+  for (int j = 0; j < meta->st.nseg; ++j) {
+    const char* sp = base + (int64_t)j * G.L * sizeof(T);
+    Acc acc[NR];
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      Acc send = upper ? v[i] : v[i + off];
-      Acc keep = upper ? v[i + off] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
-// t_b[k] = sv_k su_k sum_j V_b[j, k] x_t[J0 + j]   for the columns of one item.
-// Item = {block, k0, kc}: up to 32 columns; processed CW = 32 / NR at a time.
-template <class F, int NR>
-__global__ void __launch_bounds__(256) k_vapply(const int4* __restrict__ items, int64_t nitems,
-                                                const F* __restrict__ V, const int64_t* __restrict__ voff,
-                                                const int32_t* __restrict__ bJ0, const int32_t* __restrict__ bn,
-                                                const int64_t* __restrict__ toff, const float* __restrict__ su,
-                                                const float* __restrict__ sv,
-                                                const typename Fac<F>::acc* __restrict__ xt,
-                                                typename Fac<F>::acc* __restrict__ t) {
-  using Acc = typename Fac<F>::acc;
-  constexpr int CW = 32 / NR;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = warp; it < nitems; it += nwarps) {
-    const int4 item = items[it];
-    const int b = item.x;
-    const int J0 = bJ0[b], n = bn[b];
-    const int64_t ld = pad_rows(n);
-    const F* Vb = V + voff[b];
-    for (int c0 = item.y; c0 < item.y + item.z; c0 += CW) {
-      const int kc = min(CW, item.y + item.z - c0);
-      Acc acc[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] = Acc(0);
-      for (int j = 2 * lane; j < n; j += 64) {
-        Acc x0[NR], x1[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          x0[r] = xt[(int64_t)(J0 + j) * NR + r];
-          x1[r] = (j + 1 < n) ? xt[(int64_t)(J0 + j + 1) * NR + r] : Acc(0);
-        }
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-          if (c < kc) {
-            Acc a, bb;
-            Fac<F>::load2(Vb + (int64_t)(c0 + c) * ld + j, a, bb);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[c * NR + r] += a * x0[r] + bb * x1[r];
-          }
-        }
-      }
-      Acc tot = transpose_reduce(acc);
-      const int c = lane / NR, r = lane % NR;
-      if (c < kc) {
-        const int64_t col = toff[b] + c0 + c;
-        if (Fac<F>::scaled) tot *= (Acc)(sv[col] * su[col]);
-        t[col * NR + r] = tot;
-      }
-    }
-  }
-}
-
-// ylev[l](rows) = sum over the IL blocks of the target box (low-rank: U_b t_b;
-// dense at coarse levels: K(I,J) x_t(J) on the fly). One warp per item, 2 rows
-// per lane. Item = {blk_begin, blk_end, row_start, nrows}; ulevel = level.
-template <class F, int NR, bool FP64EVAL>
-__global__ void __launch_bounds__(256) k_uapply(const int4* __restrict__ items, const int32_t* __restrict__ ulevel,
-                                                int64_t nitems, int kappa, const F* __restrict__ U,
-                                                const int64_t* __restrict__ uoff, const int32_t* __restrict__ rank,
-                                                const int32_t* __restrict__ dense, const int32_t* __restrict__ bI0,
-                                                const int32_t* __restrict__ bm, const int32_t* __restrict__ bJ0,
-                                                const int32_t* __restrict__ bn,
-                                                const int64_t* __restrict__ toff, const typename Fac<F>::acc* __restrict__ t,
-                                                const typename Fac<F>::acc* __restrict__ xt, const void* __restrict__ pts,
-                                                int64_t N, int d, int kid, double kc_const, double kscale,
-                                                typename Fac<F>::acc* __restrict__ ylev) {
-  using Acc = typename Fac<F>::acc;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = warp; it < nitems; it += nwarps) {
-    const int4 item = items[it];
-    const int l = ulevel[it];
-    const int row0 = item.z + 2 * lane;
-    const bool v0 = 2 * lane < item.w, v1 = 2 * lane + 1 < item.w;
-    Acc acc0[NR], acc1[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) { acc0[r] = Acc(0); acc1[r] = Acc(0); }
-    for (int b = item.x; b < item.y; ++b) {
-      if (dense[b]) {
-        if (l == kappa) continue;  // leaf-level dense blocks belong to the near stage
-        // on-the-fly K(I,J) x_t(J) for this lane's two rows
-        const int J0 = bJ0[b], n = bn[b];
-        Acc s0[NR], s1[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) { s0[r] = Acc(0); s1[r] = Acc(0); }
-        if (FP64EVAL) {
-          const double* P = static_cast<const double*>(pts);
-          double xa[kMaxDim], xb[kMaxDim];
-          for (int c = 0; c < d; ++c) {
-            xa[c] = v0 ? P[(int64_t)c * N + row0] : 0.0;
-            xb[c] = v1 ? P[(int64_t)c * N + row0 + 1] : 0.0;
-          }
-          for (int j = J0; j < J0 + n; ++j) {
-            double sa = 0.0, sb = 0.0;
-            for (int c = 0; c < d; ++c) {
-              double pj = P[(int64_t)c * N + j];
-              double da = xa[c] - pj, db = xb[c] - pj;
-              sa += da * da;
-              sb += db * db;
-            }
-            double fa = f64fast_of_s(kid, sa, kc_const), fb = f64fast_of_s(kid, sb, kc_const);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              Acc xv = xt[(int64_t)j * NR + r];
-              s0[r] += (Acc)fa * xv;
-              s1[r] += (Acc)fb * xv;
-            }
-          }
-        } else {
-          const float* P = static_cast<const float*>(pts);
-          float xa[kMaxDim], xb[kMaxDim];
-          for (int c = 0; c < d; ++c) {
-            xa[c] = v0 ? P[(int64_t)c * N + row0] : 0.f;
-            xb[c] = v1 ? P[(int64_t)c * N + row0 + 1] : 0.f;
-          }
-          const float kcf = (float)kc_const;
-          for (int j = J0; j < J0 + n; ++j) {
-            float sa = 0.f, sb = 0.f;
-            for (int c = 0; c < d; ++c) {
-              float pj = P[(int64_t)c * N + j];
-              float da = xa[c] - pj, db = xb[c] - pj;
-              sa += da * da;
-              sb += db * db;
-            }
-            float fa = f32_of_s(kid, sa, kcf), fb = f32_of_s(kid, sb, kcf);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-              Acc xv = xt[(int64_t)j * NR + r];
-              s0[r] += (Acc)fa * xv;
-              s1[r] += (Acc)fb * xv;
-            }
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          acc0[r] += (Acc)kscale * s0[r];
-          acc1[r] += (Acc)kscale * s1[r];
-        }
-        continue;
-      }
-      const int p = rank[b];
-      if (p == 0) continue;
-      const F* Ub = U + uoff[b];
-      const int64_t ldU = pad_rows((int64_t)bm[b]);  // column stride: padded target-box height
-      const int64_t rl = (int64_t)(row0 - bI0[b]);
-      const Acc* tb = t + toff[b] * NR;
-      if (v0) {
-        for (int k = 0; k < p; ++k) {
-          Acc a, bb;
-          Fac<F>::load2(Ub + (int64_t)k * ldU + rl, a, bb);
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            Acc tv = tb[k * NR + r];
-            acc0[r] += a * tv;
-            acc1[r] += bb * tv;
-          }
-        }
-      }
-    }
-    const int64_t yrow = (int64_t)(l - 1) * N + row0;
+    for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
+#pragma unroll 4
+    for (int c = ct; c < C; c += kConsumerWarps * 32) dot_chunk<T, NR>(sp + (size_t)c * 16, vsrc + (int64_t)c * E * NR, acc);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (v0) ylev[yrow * NR + r] = acc0[r];
-      if (v1) ylev[(yrow + 1) * NR + r] = acc1[r];
+      Acc a = acc[r];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) part[(pbuf * kConsumerWarps + cw) * NR + r] = a;
     }
+    consumer_bar();
+    if (cw == 0 && lane == 0) {
+      Acc tot[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        tot[r] = Acc(0);
+        for (int w = 0; w < kConsumerWarps; ++w) tot[r] += part[(pbuf * kConsumerWarps + w) * NR + r];
+      }
+      write_out<T, NR>((int64_t)G.out0 + meta->st.s + j, tot, out, sa, sb);
+    }
+    pbuf ^= 1;
   }
 }
 
-// Near field and final combination for one leaf box per warp. Rows are handled
-// G at a time with 32 / G source stripes; stripes are summed by shuffles.
-template <class Acc, class IO, int NR, bool FP64EVAL>
-__global__ void __launch_bounds__(256) k_near(const int4* __restrict__ items, int64_t nitems,
-                                              const int32_t* __restrict__ near_src,
-                                              const int32_t* __restrict__ leaf_start, const Acc* __restrict__ xt,
-                                              const void* __restrict__ pts, int64_t N, int d, int kid,
-                                              double kc_const, double kscale, double kdiag,
-                                              const Acc* __restrict__ ylev, int kappa,
-                                              const int32_t* __restrict__ perm, IO* __restrict__ y, int ldy, int c0) {
+// out[out0 + s] = scale(out0 + s) * sum_e F[seg s][e] vec[vec + e]  (x NR columns)
+//
+// Warp 0 produces: per stage it waits for the slot to drain, writes the stage's
+// metadata (group descriptors, per-group segment and element prefixes, vector
+// slice offsets) into the slot, and issues the bulk copies of the factor data
+// and of the staged vector slices, all completing on the slot's `full`
+// barrier. Consumer warps read only shared memory on their critical path.
+template <class T, int NR>
+__global__ void __launch_bounds__(kSegThreads, 1)
+    k_segdot(const T* __restrict__ F, const SegGroup* __restrict__ groups, const Stage* __restrict__ stages,
+             const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ vec,
+             typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa, const float* __restrict__ sb,
+             int32_t* __restrict__ err) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  constexpr int PIECE = kStageBytes / (int)sizeof(T);
+  constexpr bool STAGE_VEC = NR == 1;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ Acc part[2][kConsumerWarps][NR];  // cross-warp partials, double-buffered
+  int pbuf = 0;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    int issued = 0;
+    bool ok = true;
+    for (int q = q0; q < q1; ++q, ++issued) {
+      const int slot = issued % kStages;
+      const int use = issued / kStages;
+      if (use > 0) {
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, w, 0)) {
+          ok = false;
+          break;
+        }
+      }
+      char* base = smem + (size_t)slot * kSlotBytes;
+      SlotMeta* meta = reinterpret_cast<SlotMeta*>(base + kStageBytes + kVecBytes);
+      const Stage st = stages[q];
+      const bool in = lane < st.ng;
+      SegGroup G{};
+      if (in) G = groups[st.g + lane];
+      // segments of group `lane` in this stage
+      const int avail = in ? G.cnt - (lane == 0 ? st.s : 0) : 0;
+      int sc_avail = avail;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, sc_avail, o);
+        if (lane >= o) sc_avail += t;
+      }
+      const int before = sc_avail - avail;
+      const int take = in ? max(0, min(avail, st.nseg - before)) : 0;
+      int sc_take = take, sc_pos = take * G.L;
+      const int vb = (in && STAGE_VEC && st.piece < 0 && G.L * (int)sizeof(Acc) <= kVecBytes) ? G.L * (int)sizeof(Acc)
+                                                                                          : 0;
+      int sc_vb = vb;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, sc_take, o);
+        const int b = __shfl_up_sync(0xffffffffu, sc_pos, o);
+        const int c = __shfl_up_sync(0xffffffffu, sc_vb, o);
+        if (lane >= o) {
+          sc_take += a;
+          sc_pos += b;
+          sc_vb += c;
+        }
+      }
+      const int vtotal = __shfl_sync(0xffffffffu, sc_vb, 31);
+      const int voff = sc_vb - vb;
+      if (in) {
+        meta->g[lane] = G;
+        meta->voff[lane] = vb > 0 ? voff : -1;
+        meta->sbeg[lane] = sc_take - take;
+        meta->gpos[lane] = sc_pos - take * G.L;
+        meta->s0[lane] = lane == 0 ? st.s : 0;
+        if (lane == st.ng - 1) meta->sbeg[lane + 1] = sc_take;
+      }
+      if (lane == 0) meta->st = st;
+      __threadfence_block();
+      __syncwarp();
+      const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
+      if (lane == 0) mbar_expect_tx(&full[slot], fbytes + (uint32_t)vtotal);
+      __syncwarp();
+      if (lane == 0) bulk_g2s(base, F + st.off, fbytes, &full[slot]);
+      if (vb > 0) bulk_g2s(base + kStageBytes + voff, vec + G.vec, (uint32_t)vb, &full[slot]);
+    }
+    if (!ok && lane == 0) {
+      // drain: copies already issued must land before the CTA's smem goes away
+      for (int k = max(0, issued - kStages); k < issued; ++k)
+        mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
+    }
+    return;
+  }
+
+  // consumers
+  const int cw = warp - 1;
+  Acc lacc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) lacc[r] = Acc(0);
+  for (int q = q0; q < q1; ++q) {
+    const int i = q - q0;
+    const int slot = i % kStages;
+    if (!mbar_wait(&full[slot], (i / kStages) & 1, err, ERR_WAIT_FULL)) return;
+    const char* base = smem + (size_t)slot * kSlotBytes;
+    const SlotMeta* meta = reinterpret_cast<const SlotMeta*>(base + kStageBytes + kVecBytes);
+    const Stage& st = meta->st;
+    if (st.piece < 0) {
+      if (st.pad > 0)
+        consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
+      else
+        consume_long<T, NR>(meta, base, vec, out, sa, sb, cw, lane, &part[0][0][0], pbuf);
+    } else {
+      // one piece of a long segment: all consumer warps share it; per-lane
+      // partials persist across pieces and are combined after the last one
+      const SegGroup& G = meta->g[0];
+      const int C = st.nelem / E;
+      const int64_t vbase = (int64_t)G.vec + (int64_t)st.piece * PIECE;
+      for (int c = cw * 32 + lane; c < C; c += kConsumerWarps * 32)
+        dot_chunk<T, NR>(base + (size_t)c * 16, vec + (vbase + (int64_t)c * E) * NR, lacc);
+      if (st.last) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          Acc a = lacc[r];
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (lane == 0) part[pbuf][cw][r] = a;
+          lacc[r] = Acc(0);
+        }
+        consumer_bar();
+        if (cw == 0 && lane == 0) {
+          Acc tot[NR];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            tot[r] = Acc(0);
+            for (int w = 0; w < kConsumerWarps; ++w) tot[r] += part[pbuf][w][r];
+          }
+          write_out<T, NR>((int64_t)G.out0 + st.s, tot, out, sa, sb);
+        }
+        pbuf ^= 1;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
+  }
+}
+
+// ------------------------------------------------------------- dense ----
+// One warp per task (target rows [I0, I0+m) at one level). Rows are handled G
+// at a time with 32 / G source stripes. Box-relative FP32 coordinates:
+// x_i - x_j = (rel_i - rel_j) + (c_I - c_J) h, where the box offset is exact in
+// FP32, so differences keep full FP32 accuracy at the box scale. The FP64 form
+// uses the global FP64 coordinates.
+template <class Acc, class IO, int NR, int D, bool F64, bool FINAL>
+__global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
+                                               const int2* __restrict__ srcs, const float* __restrict__ soff,
+                                               const float* __restrict__ rel, const double* __restrict__ p64,
+                                               int64_t N, int d_rt, int kid, double kc, double kscale, double kdiag,
+                                               const Acc* __restrict__ xt, Acc* __restrict__ ylev_l,
+                                               const Acc* __restrict__ ylev, int kappa,
+                                               const int32_t* __restrict__ perm, IO* __restrict__ y, int ldy,
+                                               int c0) {
+  const int d = D > 0 ? D : d_rt;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = warp; it < nitems; it += nwarps) {
-    const int4 item = items[it];
-    const int I0 = item.x, m = item.y;
+  const float kcf = (float)kc;
+  for (int64_t it = t0 + warp; it < t1; it += nwarps) {
+    const int4 task = tasks[it];
+    const int I0 = task.x, m = task.y;
     int G = 1;
     while (G < m && G < 32) G <<= 1;
     const int S = 32 / G;
@@ -344,39 +496,36 @@ __global__ void __launch_bounds__(256) k_near(const int4* __restrict__ items, in
       Acc acc[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
-      if (FP64EVAL) {
-        const double* P = static_cast<const double*>(pts);
-        double xr[kMaxDim];
-        for (int c = 0; c < d; ++c) xr[c] = valid ? P[(int64_t)c * N + row] : 0.0;
-        for (int e = item.z; e < item.w; ++e) {
-          const int src = near_src[e];
-          const int J0 = leaf_start[src], J1 = leaf_start[src + 1];
-          for (int j = J0 + stripe; j < J1; j += S) {
+      if constexpr (F64) {
+        double xr[D > 0 ? D : kMaxDim];
+        for (int k = 0; k < d; ++k) xr[k] = valid ? p64[(int64_t)k * N + row] : 0.0;
+        for (int e = task.z; e < task.w; ++e) {
+          const int2 sj = srcs[e];
+          for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
             double s = 0.0;
-            for (int c = 0; c < d; ++c) {
-              double dd = xr[c] - P[(int64_t)c * N + j];
-              s += dd * dd;
+            for (int k = 0; k < d; ++k) {
+              double t = xr[k] - p64[(int64_t)k * N + j];
+              s = fma(t, t, s);
             }
-            double f = f64fast_of_s(kid, s, kc_const);
+            const double f = f64fast_of_s(kid, s, kc);
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
           }
         }
       } else {
-        const float* P = static_cast<const float*>(pts);
-        const float kcf = (float)kc_const;
-        float xr[kMaxDim];
-        for (int c = 0; c < d; ++c) xr[c] = valid ? P[(int64_t)c * N + row] : 0.f;
-        for (int e = item.z; e < item.w; ++e) {
-          const int src = near_src[e];
-          const int J0 = leaf_start[src], J1 = leaf_start[src + 1];
-          for (int j = J0 + stripe; j < J1; j += S) {
+        float xr[D > 0 ? D : kMaxDim];
+        for (int k = 0; k < d; ++k) xr[k] = valid ? rel[(int64_t)k * N + row] : 0.f;
+        for (int e = task.z; e < task.w; ++e) {
+          const int2 sj = srcs[e];
+          float off[D > 0 ? D : kMaxDim];
+          for (int k = 0; k < d; ++k) off[k] = soff[(int64_t)e * d + k];
+          for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
             float s = 0.f;
-            for (int c = 0; c < d; ++c) {
-              float dd = xr[c] - P[(int64_t)c * N + j];
-              s += dd * dd;
+            for (int k = 0; k < d; ++k) {
+              float t = (xr[k] - rel[(int64_t)k * N + j]) + off[k];
+              s = fmaf(t, t, s);
             }
-            float f = f32_of_s(kid, s, kcf);
+            const float f = f32_of_s(kid, s, kcf);
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
           }
@@ -386,47 +535,340 @@ __global__ void __launch_bounds__(256) k_near(const int4* __restrict__ items, in
       for (int r = 0; r < NR; ++r)
         for (int o = G; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
       if (stripe == 0 && valid) {
-        const int64_t orow = perm[row];
+        if constexpr (FINAL) {
+          const int64_t orow = perm[row];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          Acc tot = (Acc)kscale * acc[r] + (Acc)kdiag * xt[(int64_t)row * NR + r];
-          for (int l = 1; l <= kappa; ++l) tot += ylev[((int64_t)(l - 1) * N + row) * NR + r];
-          y[orow * ldy + c0 + r] = (IO)tot;
+          for (int r = 0; r < NR; ++r) {
+            Acc tot = (Acc)kscale * acc[r] + (Acc)kdiag * xt[(int64_t)row * NR + r];
+            for (int l = 1; l <= kappa; ++l) tot += ylev[((int64_t)(l - 1) * N + row) * NR + r];
+            y[orow * ldy + c0 + r] = (IO)tot;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < NR; ++r) ylev_l[(int64_t)row * NR + r] += (Acc)kscale * acc[r];
         }
       }
     }
   }
 }
 
-int grid_warps(int64_t items, int dev_sms) {
-  int64_t ctas = (items + kWarpsPerCta - 1) / kWarpsPerCta;
-  int64_t cap = (int64_t)dev_sms * 8;
+template <class Acc, class IO, int NR>
+__global__ void k_gather(const IO* __restrict__ x, const int32_t* __restrict__ perm, int64_t N, int ldx, int c0,
+                         Acc* __restrict__ xt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const IO* src = x + (int64_t)perm[i] * ldx + c0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) xt[i * NR + r] = (Acc)src[r];
+  }
+}
+
+// ---------------------------------------------------------------- packing ----
+// Column source offsets in the FP64 ACA output: colU[c] / colV[c] for global
+// column c = toff[b] + k.
+__global__ void k_colmap(int64_t nblk, const int32_t* __restrict__ rank, const int32_t* __restrict__ bm,
+                         const int32_t* __restrict__ bn, const int64_t* __restrict__ toff,
+                         const int64_t* __restrict__ uoff64, const int64_t* __restrict__ voff64,
+                         int64_t* __restrict__ colU, int64_t* __restrict__ colV) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < rank[b]; ++k) {
+      colU[toff[b] + k] = uoff64[b] + (int64_t)k * bm[b];
+      colV[toff[b] + k] = voff64[b] + (int64_t)k * bn[b];
+    }
+}
+
+// One warp per column: power-of-two scale >= max |entry| (16-bit), else 1.
+__global__ void k_colscale(int64_t ncol, const int64_t* __restrict__ colU, const int64_t* __restrict__ colV,
+                           const int32_t* __restrict__ colrows_u, const int32_t* __restrict__ colrows_v,
+                           const double* __restrict__ U64, const double* __restrict__ V64, int scaled,
+                           float* __restrict__ su, float* __restrict__ sv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncol; c += nw) {
+    for (int side = 0; side < 2; ++side) {
+      const double* col = side == 0 ? U64 + colU[c] : V64 + colV[c];
+      const int rows = side == 0 ? colrows_u[c] : colrows_v[c];
+      double mx = 0.0;
+      if (scaled)
+        for (int i = lane; i < rows; i += 32) mx = fmax(mx, fabs(col[i]));
+      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int e = 0;
+      if (mx > 0.0) frexp(mx, &e);
+      const float sc = mx > 0.0 ? (float)ldexp(1.0, e) : 1.0f;
+      if (lane == 0) (side == 0 ? su : sv)[c] = sc;
+    }
+  }
+}
+
+// V stream: one CTA per group (= block); segment k = column k, lead pad a.
+template <class T>
+__global__ void k_packV(int64_t ngroups, const SegGroup* __restrict__ groups, const int32_t* __restrict__ lead,
+                        const int32_t* __restrict__ nrows, const int64_t* __restrict__ colV,
+                        const double* __restrict__ V64, const float* __restrict__ sv, T* __restrict__ out) {
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const SegGroup G = groups[g];
+    const int a = lead[g], n = nrows[g];
+    for (int k = 0; k < G.cnt; ++k) {
+      const int64_t c = (int64_t)G.out0 + k;
+      const double* col = V64 + colV[c];
+      const double inv = 1.0 / (double)sv[c];
+      T* dst = out + G.off + (int64_t)k * G.L;
+      for (int e = threadIdx.x; e < G.L; e += blockDim.x)
+        dst[e] = Fac<T>::from((e >= a && e < a + n) ? col[e - a] * inv : 0.0);
+    }
+  }
+}
+
+// U stream: one CTA per group (= level, box); segment r = row r of the box,
+// element e = lead pad a + concatenated column q (global column tfirst + q).
+template <class T>
+__global__ void k_packU(int64_t ngroups, const SegGroup* __restrict__ groups, const int32_t* __restrict__ lead,
+                        const int32_t* __restrict__ ncols, const int64_t* __restrict__ tfirst,
+                        const int64_t* __restrict__ colU, const double* __restrict__ U64,
+                        const float* __restrict__ su, T* __restrict__ out) {
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const SegGroup G = groups[g];
+    const int a = lead[g], P = ncols[g];
+    const int64_t c0 = tfirst[g];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)G.cnt * G.L; idx += blockDim.x) {
+      const int r = (int)(idx / G.L), e = (int)(idx % G.L);
+      const int q = e - a;
+      double v = 0.0;
+      if (q >= 0 && q < P) v = U64[colU[c0 + q] + r] / (double)su[c0 + q];
+      out[G.off + idx] = Fac<T>::from(v);
+    }
+  }
+}
+
+// Box-relative FP32 coordinates at level l: rel = x - (lo + c_box * h).
+__global__ void k_relcoords(const double* __restrict__ p64, int64_t N, int d, int l,
+                            const int32_t* __restrict__ bstart, const uint64_t* __restrict__ bkey, int64_t nb,
+                            const double* __restrict__ lo, double h, float* __restrict__ rel) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = 0, b = nb;  // last box with bstart <= i
+    while (b - a > 1) {
+      int64_t mid = (a + b) >> 1;
+      if (bstart[mid] <= i) a = mid; else b = mid;
+    }
+    const uint64_t key = bkey[a];
+    for (int k = 0; k < d; ++k) {
+      int64_t c = 0;
+      for (int bit = 0; bit < l; ++bit) c |= (int64_t)((key >> (d * bit + k)) & 1u) << bit;
+      rel[(int64_t)k * N + i] = (float)(p64[(int64_t)k * N + i] - (lo[k] + (double)c * h));
+    }
+  }
+}
+
+int grid_warps(int64_t items, int sms) {
+  int64_t ctas = (items + 7) / 8;
+  int64_t cap = (int64_t)sms * 8;
   if (ctas > cap) ctas = cap;
   if (ctas < 1) ctas = 1;
   return (int)ctas;
 }
 
-template <class F>
-int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, const DevBuf<int64_t>& du64,
-               const DevBuf<int64_t>& dv64, const DevBuf<int64_t>& duoff, const DevBuf<int64_t>& dvoff,
-               int64_t uelems, int64_t velems) {
-  HD_TRY(h->U.alloc(std::max<int64_t>(uelems, 1) * sizeof(F)));
-  HD_TRY(h->V.alloc(std::max<int64_t>(velems, 1) * sizeof(F)));
-  if (Fac<F>::scaled) {
-    HD_TRY(h->su.alloc(std::max<int64_t>(h->total_rank, 1)));
-    HD_TRY(h->sv.alloc(std::max<int64_t>(h->total_rank, 1)));
-  } else {
-    h->su.release();
-    h->sv.release();
+// Stage schedule of a stream: whole segments packed into stages of at most
+// kStageBytes; segments longer than a stage become pieces. CTA ranges are
+// balanced by bytes and never cut a long segment.
+void schedule(Stream& S, size_t esize, size_t vsize, int E, int ctas) {
+  const int64_t cap = kStageBytes / (int64_t)esize;
+  S.h_stages.clear();
+  Stage cur{0, 0, -1, 0, 0, -1, 0, 0, 0};
+  int64_t cur_vbytes = 0, cur_group = -1, cur_maxc = 0;
+  auto flush = [&]() {
+    if (cur.nseg > 0) {
+      if (cur.pad != 0) {  // short stage: team size = power of two >= max chunks, at most a warp
+        int ts = 1;
+        while (ts < cur_maxc && ts < 32) ts <<= 1;
+        cur.pad = ts;
+      }
+      S.h_stages.push_back(cur);
+    }
+    cur = Stage{0, 0, -1, 0, 0, -1, 0, 0, 0};
+    cur_vbytes = 0;
+    cur_group = -1;
+    cur_maxc = 0;
+  };
+  for (int64_t g = 0; g < (int64_t)S.h_groups.size(); ++g) {
+    const SegGroup& G = S.h_groups[g];
+    const int64_t C = G.L / E;
+    if (G.L > cap) {  // pieces
+      flush();
+      for (int s = 0; s < G.cnt; ++s)
+        for (int64_t p0 = 0, piece = 0; p0 < G.L; p0 += cap, ++piece) {
+          const int64_t len = std::min<int64_t>(cap, G.L - p0);
+          S.h_stages.push_back(Stage{G.off + (int64_t)s * G.L + p0, (int32_t)len, (int32_t)g, s, 0,
+                                     (int32_t)piece, p0 + len >= G.L ? 1 : 0, 1, 0});
+        }
+      continue;
+    }
+    if (C > kLongChunks) {  // long stages: whole segments of this group only
+      flush();
+      for (int s = 0; s < G.cnt; ++s) {
+        if (cur.nseg > 0 && cur.nelem + G.L > cap) flush();
+        if (cur.nseg == 0) cur = Stage{G.off + (int64_t)s * G.L, 0, (int32_t)g, s, 0, -1, 0, 1, 0};
+        cur.nelem += G.L;
+        cur.nseg += 1;
+      }
+      flush();
+      continue;
+    }
+    const int64_t vb = G.L * (int64_t)vsize <= kVecBytes ? G.L * (int64_t)vsize : 0;
+    for (int s = 0; s < G.cnt; ++s) {
+      const bool new_group = cur_group != g;
+      if (cur.nseg > 0 &&
+          (cur.nelem + G.L > cap || (new_group && (cur.ng + 1 > kGmax || cur_vbytes + vb > kVecBytes))))
+        flush();
+      if (cur.nseg == 0) {
+        cur.off = G.off + (int64_t)s * G.L;
+        cur.g = (int32_t)g;
+        cur.s = s;
+        cur.pad = 1;  // marks a short stage; the team size is set at flush
+      }
+      if (cur_group != g) {
+        cur.ng += 1;
+        cur_vbytes += vb;
+        cur_group = g;
+        cur_maxc = std::max(cur_maxc, C);
+      }
+      cur.nelem += G.L;
+      cur.nseg += 1;
+    }
   }
-  if (h->nblk > 0) {
-    int g = (int)std::min<int64_t>(h->nblk, 152 * 32);
-    k_pack<F><<<g, 256, 0, h->st>>>(h->nblk, h->rank.p, h->bm.p, h->bn.p, U64.p, V64.p, du64.p, dv64.p, duoff.p,
-                                    dvoff.p, h->toff.p, reinterpret_cast<F*>(h->U.p), reinterpret_cast<F*>(h->V.p),
-                                    h->su.p, h->sv.p);
+  flush();
+  // balance CTAs by bytes, cutting only between whole segments
+  int64_t total = 0;
+  for (const Stage& st : S.h_stages) total += st.nelem;
+  S.h_cta.assign(1, 0);
+  int64_t acc = 0;
+  const int64_t target = std::max<int64_t>(1, (total + ctas - 1) / ctas);
+  for (size_t q = 0; q < S.h_stages.size(); ++q) {
+    acc += S.h_stages[q].nelem;
+    const bool cut_ok = S.h_stages[q].piece < 0 || S.h_stages[q].last;
+    if (cut_ok && acc >= target * (int64_t)S.h_cta.size() && (int)S.h_cta.size() < ctas)
+      S.h_cta.push_back((int32_t)(q + 1));
+  }
+  if (S.h_cta.back() != (int32_t)S.h_stages.size()) S.h_cta.push_back((int32_t)S.h_stages.size());
+  S.ctas = (int)S.h_cta.size() - 1;
+}
+
+template <class T>
+int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
+               const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64) {
+  cudaStream_t st = h->st;
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  const int A1 = 16 / (int)sizeof(Acc);  // vector alignment in elements
+  const int64_t nblk = h->nblk;
+  Plan& P = h->plan;
+  auto roundE = [&](int64_t v) { return (v + E - 1) / E * E; };
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+
+  // V groups: one per low-rank block
+  P.vs.h_groups.clear();
+  P.h_vgroup.assign(nblk, -1);
+  std::vector<int32_t> vlead, vrows;
+  int64_t off = 0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int p = h->h_rank[b];
+    if (p == 0) continue;
+    const int a = (int)(h->h_bJ0[b] % A1);
+    const int64_t L = roundE(a + h->h_bn[b]);
+    P.h_vgroup[b] = (int64_t)P.vs.h_groups.size();
+    P.vs.h_groups.push_back(SegGroup{off, (int32_t)L, p, h->h_bJ0[b] - a, (int32_t)h->h_toff[b]});
+    vlead.push_back(a);
+    vrows.push_back(h->h_bn[b]);
+    off += L * p;
+  }
+  P.vs.elems = off;
+  // U groups: one per (level, box) with low-rank blocks
+  P.us.h_groups.clear();
+  P.h_ugroup.assign(nblk, -1);
+  P.h_ucol.assign(nblk, 0);
+  std::vector<int32_t> ulead, ucols;
+  std::vector<int64_t> utfirst;
+  off = 0;
+  for (int l = 1; l <= h->kappa; ++l) {
+    const Level& L = h->lv[l];
+    for (int64_t i = 0; i < L.nb; ++i) {
+      const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
+      int64_t Pi = 0, tf = -1;
+      for (int64_t b = b0; b < b1; ++b)
+        if (h->h_rank[b] > 0) {
+          if (tf < 0) tf = h->h_toff[b];
+          P.h_ugroup[b] = (int64_t)P.us.h_groups.size();
+          P.h_ucol[b] = (int32_t)Pi;
+          Pi += h->h_rank[b];
+        }
+      if (Pi == 0) continue;
+      const int a = (int)(tf % A1);
+      const int64_t Lr = roundE(a + Pi);
+      const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
+      P.us.h_groups.push_back(
+          SegGroup{off, (int32_t)Lr, m, (int32_t)(tf - a), (int32_t)((int64_t)(l - 1) * h->N + I0)});
+      ulead.push_back(a);
+      ucols.push_back((int32_t)Pi);
+      utfirst.push_back(tf);
+      off += Lr * m;
+    }
+  }
+  P.us.elems = off;
+  if ((int64_t)h->total_rank + 2 * kGuard >= INT32_MAX || (int64_t)h->kappa * h->N >= INT32_MAX) {
+    set_error("problem too large for 32-bit vector indices");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
+  schedule(P.vs, sizeof(T), sizeof(Acc), E, sms);
+  schedule(P.us, sizeof(T), sizeof(Acc), E, sms);
+
+  // column maps, scales, packing
+  const int64_t ncol = h->total_rank;
+  DevBuf<int64_t> colU, colV, du64, dv64, dutfirst;
+  DevBuf<int32_t> crows_u, crows_v, dvlead, dvrows, dulead, ducols;
+  std::vector<int32_t> hcru(std::max<int64_t>(ncol, 1)), hcrv(std::max<int64_t>(ncol, 1));
+  for (int64_t b = 0; b < nblk; ++b)
+    for (int k = 0; k < h->h_rank[b]; ++k) {
+      hcru[h->h_toff[b] + k] = h->h_bm[b];
+      hcrv[h->h_toff[b] + k] = h->h_bn[b];
+    }
+  HD_TRY(colU.alloc(std::max<int64_t>(ncol, 1)));
+  HD_TRY(colV.alloc(std::max<int64_t>(ncol, 1)));
+  HD_TRY(upload(du64, uoff64, st));
+  HD_TRY(upload(dv64, voff64, st));
+  HD_TRY(upload(crows_u, hcru, st));
+  HD_TRY(upload(crows_v, hcrv, st));
+  HD_TRY(upload(dvlead, vlead, st));
+  HD_TRY(upload(dvrows, vrows, st));
+  HD_TRY(upload(dulead, ulead, st));
+  HD_TRY(upload(ducols, ucols, st));
+  HD_TRY(upload(dutfirst, utfirst, st));
+  HD_TRY(h->su.alloc(std::max<int64_t>(ncol, 1)));
+  HD_TRY(h->sv.alloc(std::max<int64_t>(ncol, 1)));
+  HD_TRY(P.vs.data.alloc((size_t)std::max<int64_t>(P.vs.elems, E) * sizeof(T)));
+  HD_TRY(P.us.data.alloc((size_t)std::max<int64_t>(P.us.elems, E) * sizeof(T)));
+  HD_TRY(upload(P.vs.groups, P.vs.h_groups, st));
+  HD_TRY(upload(P.us.groups, P.us.h_groups, st));
+  HD_TRY(upload(P.vs.stages, P.vs.h_stages, st));
+  HD_TRY(upload(P.us.stages, P.us.h_stages, st));
+  HD_TRY(upload(P.vs.cta, P.vs.h_cta, st));
+  HD_TRY(upload(P.us.cta, P.us.h_cta, st));
+  if (ncol > 0) {
+    k_colmap<<<(int)std::min<int64_t>((nblk + 255) / 256, 4096), 256, 0, st>>>(
+        nblk, h->rank.p, h->bm.p, h->bn.p, h->toff.p, du64.p, dv64.p, colU.p, colV.p);
+    k_colscale<<<grid_warps(ncol, sms), 256, 0, st>>>(ncol, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p,
+                                                      Fac<T>::scaled ? 1 : 0, h->su.p, h->sv.p);
+    const int64_t nvg = (int64_t)P.vs.h_groups.size(), nug = (int64_t)P.us.h_groups.size();
+    if (nvg)
+      k_packV<T><<<(int)std::min<int64_t>(nvg, sms * 16), 256, 0, st>>>(
+          nvg, P.vs.groups.p, dvlead.p, dvrows.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(P.vs.data.p));
+    if (nug)
+      k_packU<T><<<(int)std::min<int64_t>(nug, sms * 16), 256, 0, st>>>(
+          nug, P.us.groups.p, dulead.p, ducols.p, dutfirst.p, colU.p, U64.p, h->su.p,
+          reinterpret_cast<T*>(P.us.data.p));
     HD_CUDA(cudaGetLastError());
   }
-  HD_CUDA(cudaStreamSynchronize(h->st));
+  HD_CUDA(cudaStreamSynchronize(st));
+  h->factor_bytes = (P.vs.elems + P.us.elems) * (int64_t)sizeof(T) + (Fac<T>::scaled ? 2 * ncol * 4 : 0);
   return HODLRDD_OK;
 }
 
@@ -434,98 +876,128 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
 
 int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
                  const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64) {
-  const int64_t nblk = h->nblk;
-  std::vector<int64_t> uoff(nblk + 1, 0), voff(nblk + 1, 0);
+  h->h_toff.assign(h->nblk + 1, 0);
   h->factor_elems = 0;
-  for (int64_t b = 0; b < nblk; ++b) {
-    const int64_t p = h->h_rank[b];
-    uoff[b + 1] = uoff[b] + p * pad_rows(h->h_bm[b]);
-    voff[b + 1] = voff[b] + p * pad_rows(h->h_bn[b]);
-    h->factor_elems += p * (h->h_bm[b] + h->h_bn[b]);
+  for (int64_t b = 0; b < h->nblk; ++b) {
+    h->h_toff[b + 1] = h->h_toff[b] + h->h_rank[b];
+    h->factor_elems += (int64_t)h->h_rank[b] * (h->h_bm[b] + h->h_bn[b]);
   }
-  DevBuf<int64_t> du64, dv64;
-  HD_TRY(upload(du64, uoff64, h->st));
-  HD_TRY(upload(dv64, voff64, h->st));
-  HD_TRY(upload(h->uoff, uoff, h->st));
-  HD_TRY(upload(h->voff, voff, h->st));
-  HD_CUDA(cudaStreamSynchronize(h->st));
-  const int64_t ue = uoff[nblk], ve = voff[nblk];
-  int rc;
   switch (h->opt.precision) {
-    case HODLRDD_PREC_FP64: rc = pack_typed<double>(h, U64, V64, du64, dv64, h->uoff, h->voff, ue, ve); break;
-    case HODLRDD_PREC_FP32: rc = pack_typed<float>(h, U64, V64, du64, dv64, h->uoff, h->voff, ue, ve); break;
-    case HODLRDD_PREC_FP16: rc = pack_typed<__half>(h, U64, V64, du64, dv64, h->uoff, h->voff, ue, ve); break;
-    default: rc = pack_typed<__nv_bfloat16>(h, U64, V64, du64, dv64, h->uoff, h->voff, ue, ve); break;
+    case HODLRDD_PREC_FP64: return pack_typed<double>(h, U64, V64, uoff64, voff64);
+    case HODLRDD_PREC_FP32: return pack_typed<float>(h, U64, V64, uoff64, voff64);
+    case HODLRDD_PREC_FP16: return pack_typed<__half>(h, U64, V64, uoff64, voff64);
+    default: return pack_typed<__nv_bfloat16>(h, U64, V64, uoff64, voff64);
   }
-  if (rc != HODLRDD_OK) return rc;
-  h->factor_bytes = (ue + ve) * (int64_t)elem_size(h->opt.precision) +
-                    (h->opt.precision >= HODLRDD_PREC_FP16 ? 2 * h->total_rank * 4 : 0);
-  return HODLRDD_OK;
 }
 
+// Dense task lists (near field and dense-flagged IL blocks) and the per-level
+// box-relative coordinates they read.
 int build_plan(hodlrdd_s* h) {
   Plan& P = h->plan;
-  const int64_t nblk = h->nblk;
-  std::vector<int4> vitems;
-  for (int64_t b = 0; b < nblk; ++b)
-    for (int k0 = 0; k0 < h->h_rank[b]; k0 += 32)
-      vitems.push_back(make_int4((int)b, k0, std::min(32, h->h_rank[b] - k0), 0));
-  std::stable_sort(vitems.begin(), vitems.end(),
-                   [&](const int4& a, const int4& c) { return h->h_bn[a.x] > h->h_bn[c.x]; });
-  std::vector<int4> uitems;
-  std::vector<int32_t> ulevel;
-  for (int l = 1; l <= h->kappa; ++l) {
-    const Level& L = h->lv[l];
-    for (int64_t i = 0; i < L.nb; ++i) {
-      const int32_t b0 = (int32_t)(h->h_blk_off[l] + L.h_iloff[i]);
-      const int32_t b1 = (int32_t)(h->h_blk_off[l] + L.h_iloff[i + 1]);
-      bool work = false;
-      for (int32_t b = b0; b < b1 && !work; ++b)
-        work = h->h_rank[b] > 0 || (h->h_dense[b] && l < h->kappa);
-      if (!work) continue;
-      const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
-      for (int32_t r = 0; r < m; r += 64) {
-        uitems.push_back(make_int4(b0, b1, I0 + r, std::min(64, m - r)));
-        ulevel.push_back(l);
-      }
-    }
+  const int d = h->d;
+  const bool f64 = h->opt.precision == HODLRDD_PREC_FP64;
+  std::vector<int4> tasks;
+  std::vector<int2> srcs;
+  std::vector<float> soff;
+  // reference side of level-l boxes rounded to 20 significant bits, so that
+  // (c_I - c_J) h is exact in FP32 for |c_I - c_J| < 16
+  P.h_box.assign(h->kappa + 1, 0.0);
+  for (int l = 0; l <= h->kappa; ++l) {
+    int e = 0;
+    double m = std::frexp(std::ldexp(h->side, -l), &e);
+    P.h_box[l] = std::ldexp(std::nearbyint(std::ldexp(m, 20)), e - 20);
   }
-  // near list per leaf box: self + d' >= 1 neighbours, then dense leaf-level IL blocks
-  const Level& Lk = h->lv[h->kappa];
-  std::vector<int4> nitems;
-  std::vector<int32_t> near_src;
-  h->dense_pairs = 0;
-  for (int64_t i = 0; i < Lk.nb; ++i) {
-    const int32_t I0 = Lk.h_bstart[i], m = Lk.h_bstart[i + 1] - I0;
-    const int32_t e0 = (int32_t)near_src.size();
-    for (int32_t e = h->h_nearoff[i]; e < h->h_nearoff[i + 1]; ++e) {
-      int32_t j = h->h_nearidx[e];
-      near_src.push_back(j);
-      h->dense_pairs += (int64_t)m * (Lk.h_bstart[j + 1] - Lk.h_bstart[j]);
+  auto coords = [&](int l, int64_t b, int64_t* c) {
+    const uint64_t key = h->lv[l].h_bkey[b];
+    for (int k = 0; k < d; ++k) {
+      c[k] = 0;
+      for (int bit = 0; bit < l; ++bit) c[k] |= (int64_t)((key >> (d * bit + k)) & 1u) << bit;
     }
-    if (h->kappa >= 1) {
-      const int64_t b0 = h->h_blk_off[h->kappa] + Lk.h_iloff[i], b1 = h->h_blk_off[h->kappa] + Lk.h_iloff[i + 1];
+  };
+  auto add_src = [&](int l, int64_t I, int64_t J) {
+    const Level& L = h->lv[l];
+    srcs.push_back(make_int2(L.h_bstart[J], L.h_bstart[J + 1] - L.h_bstart[J]));
+    int64_t cI[kMaxDim], cJ[kMaxDim];
+    coords(l, I, cI);
+    coords(l, J, cJ);
+    for (int k = 0; k < d; ++k) soff.push_back((float)((double)(cI[k] - cJ[k]) * P.h_box[l]));
+  };
+  h->dense_pairs = 0;
+  P.coarse.clear();
+  std::vector<char> need_rel(h->kappa + 1, 0);
+  for (int l = 1; l < h->kappa; ++l) {
+    const Level& L = h->lv[l];
+    DenseLevel DL;
+    DL.level = l;
+    DL.t0 = (int64_t)tasks.size();
+    for (int64_t i = 0; i < L.nb; ++i) {
+      const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
+      const int32_t s0 = (int32_t)srcs.size();
       for (int64_t b = b0; b < b1; ++b)
         if (h->h_dense[b]) {
-          near_src.push_back(h->h_bsj[b]);
-          h->dense_pairs += (int64_t)m * h->h_bn[b];
+          add_src(l, i, h->h_bsj[b]);
+          h->dense_pairs += (int64_t)h->h_bm[b] * h->h_bn[b];
         }
+      const int32_t s1 = (int32_t)srcs.size();
+      if (s1 == s0) continue;
+      const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
+      for (int32_t r = 0; r < m; r += 32) tasks.push_back(make_int4(I0 + r, std::min(32, m - r), s0, s1));
     }
-    nitems.push_back(make_int4(I0, m, e0, (int32_t)near_src.size()));
+    DL.t1 = (int64_t)tasks.size();
+    if (DL.t1 > DL.t0) {
+      P.coarse.push_back(DL);
+      need_rel[l] = 1;
+    }
   }
-  for (int64_t b = 0; b < nblk; ++b)
-    if (h->h_dense[b] && h->h_blevel[b] < h->kappa) h->dense_pairs += (int64_t)h->h_bm[b] * h->h_bn[b];
-  std::vector<int4> nsorted = nitems;
+  {
+    const int l = h->kappa;
+    const Level& L = h->lv[l];
+    P.leaf.level = l;
+    P.leaf.t0 = (int64_t)tasks.size();
+    for (int64_t i = 0; i < L.nb; ++i) {
+      const int32_t s0 = (int32_t)srcs.size();
+      const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
+      for (int32_t e = h->h_nearoff[i]; e < h->h_nearoff[i + 1]; ++e) {
+        add_src(l, i, h->h_nearidx[e]);
+        h->dense_pairs += (int64_t)m * srcs.back().y;
+      }
+      if (l >= 1) {
+        const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
+        for (int64_t b = b0; b < b1; ++b)
+          if (h->h_dense[b]) {
+            add_src(l, i, h->h_bsj[b]);
+            h->dense_pairs += (int64_t)m * h->h_bn[b];
+          }
+      }
+      tasks.push_back(make_int4(I0, m, s0, (int32_t)srcs.size()));
+    }
+    P.leaf.t1 = (int64_t)tasks.size();
+    need_rel[l] = 1;
+  }
+  if ((int64_t)srcs.size() >= INT32_MAX) {
+    set_error("dense source list too long");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
   cudaStream_t st = h->st;
-  P.n_vitems = (int64_t)vitems.size();
-  P.n_uitems = (int64_t)uitems.size();
-  P.n_nitems = (int64_t)nsorted.size();
-  P.n_near_src = (int64_t)near_src.size();
-  HD_TRY(upload(P.vitems, vitems, st));
-  HD_TRY(upload(P.uitems, uitems, st));
-  HD_TRY(upload(P.ulevel, ulevel, st));
-  HD_TRY(upload(P.nitems, nsorted, st));
-  HD_TRY(upload(P.near_src, near_src, st));
+  HD_TRY(upload(P.tasks, tasks, st));
+  HD_TRY(upload(P.srcs, srcs, st));
+  HD_TRY(upload(P.soff, soff, st));
+  P.rel.clear();
+  P.rel.resize(h->kappa + 1);
+  if (!f64) {
+    std::vector<double> hlo(h->lo, h->lo + d);
+    DevBuf<double> dlo;
+    HD_TRY(upload(dlo, hlo, st));
+    for (int l = 0; l <= h->kappa; ++l) {
+      if (!need_rel[l]) continue;
+      HD_TRY(P.rel[l].alloc((size_t)h->N * d));
+      const Level& L = h->lv[l];
+      k_relcoords<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(
+          h->pts64.p, h->N, d, l, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[l], P.rel[l].p);
+      HD_CUDA(cudaGetLastError());
+    }
+    HD_CUDA(cudaStreamSynchronize(st));
+  }
   HD_CUDA(cudaStreamSynchronize(st));
   return HODLRDD_OK;
 }
@@ -533,9 +1005,14 @@ int build_plan(hodlrdd_s* h) {
 int alloc_workspace(hodlrdd_s* h) {
   const int nr = 8;
   const size_t acc = h->opt.precision == HODLRDD_PREC_FP64 ? 8 : 4;
-  HD_TRY(h->xt.alloc((size_t)h->N * nr * acc));
-  HD_TRY(h->tbuf.alloc((size_t)std::max<int64_t>(h->total_rank, 1) * nr * acc));
+  HD_TRY(h->xt.alloc(((size_t)h->N + 2 * kGuard) * nr * acc));
+  HD_TRY(h->tbuf.alloc(((size_t)h->total_rank + 2 * kGuard) * nr * acc));
   HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * nr * acc));
+  HD_TRY(h->err.alloc(1));
+  HD_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes(), h->st));
+  HD_CUDA(cudaMemsetAsync(h->tbuf.p, 0, h->tbuf.bytes(), h->st));
+  HD_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->st));
+  HD_CUDA(cudaStreamSynchronize(h->st));
   return HODLRDD_OK;
 }
 
@@ -556,65 +1033,99 @@ int chunk_events(hodlrdd_s* h, cudaEvent_t* ev) {
   return HODLRDD_OK;
 }
 
-template <class F, class IO, int NR>
+template <class Acc, class IO, int NR, int D, bool F64>
+int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl, IO* y, int ldy, int c0) {
+  const Plan& P = h->plan;
+  const double kc = kernel_const(h->K);
+  for (const DenseLevel& DL : P.coarse) {
+    const float* rel = F64 ? nullptr : P.rel[DL.level].p;
+    k_dense<Acc, IO, NR, D, F64, false><<<grid_warps(DL.t1 - DL.t0, sms), 256, 0, st>>>(
+        P.tasks.p, DL.t0, DL.t1, P.srcs.p, P.soff.p, rel, h->pts64.p, h->N, h->d, h->K.id, kc, h->K.scale,
+        h->K.diag, xt, yl + (int64_t)(DL.level - 1) * h->N * NR, yl, h->kappa, h->perm.p, y, ldy, c0);
+    h->launches += 1;
+  }
+  const float* rel = F64 ? nullptr : P.rel[h->kappa].p;
+  k_dense<Acc, IO, NR, D, F64, true><<<grid_warps(P.leaf.t1 - P.leaf.t0, sms), 256, 0, st>>>(
+      P.tasks.p, P.leaf.t0, P.leaf.t1, P.srcs.p, P.soff.p, rel, h->pts64.p, h->N, h->d, h->K.id, kc, h->K.scale,
+      h->K.diag, xt, nullptr, yl, h->kappa, h->perm.p, y, ldy, c0);
+  h->launches += 1;
+  HD_CUDA(cudaGetLastError());
+  return HODLRDD_OK;
+}
+
+template <class T, class IO, int NR>
 int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t st) {
-  using Acc = typename Fac<F>::acc;
-  constexpr bool F64 = std::is_same<F, double>::value;
+  using Acc = typename Fac<T>::acc;
+  constexpr bool F64 = std::is_same<T, double>::value;
   const Plan& P = h->plan;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  Acc* xt = reinterpret_cast<Acc*>(h->xt.p);
-  Acc* t = reinterpret_cast<Acc*>(h->tbuf.p);
+  Acc* xt = reinterpret_cast<Acc*>(h->xt.p) + (size_t)kGuard * NR;
+  Acc* t = reinterpret_cast<Acc*>(h->tbuf.p) + (size_t)kGuard * NR;
   Acc* yl = reinterpret_cast<Acc*>(h->ylev.p);
-  const void* pts = F64 ? (const void*)h->pts64.p : (const void*)h->pts32.p;
-  const double kc = kernel_const(h->K);
   cudaEvent_t ev[5];
   const bool prof = h->profiling;
   if (prof) {
     HD_TRY(chunk_events(h, ev));
     HD_CUDA(cudaEventRecord(ev[0], st));
   }
-  k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N, ldx,
-                                                                                              c0, xt);
+  k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
+                                                                                              ldx, c0, xt);
   h->launches += 1;
   if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
+  const size_t smem = (size_t)kStages * kSlotBytes;
   if (h->kappa >= 1) {
     HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)h->kappa * h->N * NR * sizeof(Acc), st));
-    if (P.n_vitems > 0) {
-      k_vapply<F, NR><<<grid_warps(P.n_vitems, sms), 32 * kWarpsPerCta, 0, st>>>(
-          P.vitems.p, P.n_vitems, reinterpret_cast<const F*>(h->V.p), h->voff.p, h->bJ0.p, h->bn.p, h->toff.p,
-          h->su.p, h->sv.p, xt, t);
+    if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
+      k_segdot<T, NR><<<P.vs.ctas, kSegThreads, smem, st>>>(
+          reinterpret_cast<const T*>(P.vs.data.p), P.vs.groups.p, P.vs.stages.p, P.vs.cta.p, xt, t,
+          Fac<T>::scaled ? h->sv.p : nullptr, Fac<T>::scaled ? h->su.p : nullptr, h->err.p);
       h->launches += 1;
     }
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
-  if (h->kappa >= 1) {
-    if (P.n_uitems > 0) {
-      k_uapply<F, NR, F64><<<grid_warps(P.n_uitems, sms), 32 * kWarpsPerCta, 0, st>>>(
-          P.uitems.p, P.ulevel.p, P.n_uitems, h->kappa, reinterpret_cast<const F*>(h->U.p), h->uoff.p, h->rank.p,
-          h->dense.p, h->bI0.p, h->bm.p, h->bJ0.p, h->bn.p, h->toff.p, t, xt, pts, h->N, h->d, h->K.id, kc, h->K.scale, yl);
-      h->launches += 1;
-    }
+  if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
+    k_segdot<T, NR><<<P.us.ctas, kSegThreads, smem, st>>>(reinterpret_cast<const T*>(P.us.data.p), P.us.groups.p,
+                                                          P.us.stages.p, P.us.cta.p, t, yl, nullptr, nullptr,
+                                                          h->err.p);
+    h->launches += 1;
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
-  k_near<Acc, IO, NR, F64><<<grid_warps(P.n_nitems, sms), 32 * kWarpsPerCta, 0, st>>>(
-      P.nitems.p, P.n_nitems, P.near_src.p, h->lv[h->kappa].bstart.p, xt, pts, h->N, h->d, h->K.id, kc, h->K.scale,
-      h->K.diag, yl, h->kappa, h->perm.p, y, ldx, c0);
-  h->launches += 1;
-  HD_CUDA(cudaGetLastError());
+  switch (h->d) {
+    case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+    case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+    case 3: HD_TRY((launch_dense<Acc, IO, NR, 3, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+    case 4: HD_TRY((launch_dense<Acc, IO, NR, 4, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+    default: HD_TRY((launch_dense<Acc, IO, NR, 0, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+  }
   if (prof) HD_CUDA(cudaEventRecord(ev[4], st));
+  HD_CUDA(cudaGetLastError());
   return HODLRDD_OK;
 }
 
-template <class F, class IO>
+template <class T>
+int set_smem_attr() {
+  static bool done = false;
+  if (done) return HODLRDD_OK;
+  const int smem = kStages * kSlotBytes;
+  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  done = true;
+  return HODLRDD_OK;
+}
+
+template <class T, class IO>
 int matvec_typed(hodlrdd_s* h, const IO* x, IO* y, int nrhs, cudaStream_t st) {
+  HD_TRY(set_smem_attr<T>());
   int c0 = 0;
   while (c0 < nrhs) {
     const int rem = nrhs - c0;
-    if (rem >= 8) { HD_TRY((matvec_chunk<F, IO, 8>(h, x, y, nrhs, c0, st))); c0 += 8; }
-    else if (rem >= 4) { HD_TRY((matvec_chunk<F, IO, 4>(h, x, y, nrhs, c0, st))); c0 += 4; }
-    else if (rem >= 2) { HD_TRY((matvec_chunk<F, IO, 2>(h, x, y, nrhs, c0, st))); c0 += 2; }
-    else { HD_TRY((matvec_chunk<F, IO, 1>(h, x, y, nrhs, c0, st))); c0 += 1; }
+    if (rem >= 8) { HD_TRY((matvec_chunk<T, IO, 8>(h, x, y, nrhs, c0, st))); c0 += 8; }
+    else if (rem >= 4) { HD_TRY((matvec_chunk<T, IO, 4>(h, x, y, nrhs, c0, st))); c0 += 4; }
+    else if (rem >= 2) { HD_TRY((matvec_chunk<T, IO, 2>(h, x, y, nrhs, c0, st))); c0 += 2; }
+    else { HD_TRY((matvec_chunk<T, IO, 1>(h, x, y, nrhs, c0, st))); c0 += 1; }
   }
   return HODLRDD_OK;
 }
@@ -635,28 +1146,34 @@ int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t s
 }
 
 namespace {
-template <class F>
+template <class T>
 int unpack_typed(hodlrdd_s* h, int64_t b, double* U, double* V) {
   const int p = h->h_rank[b];
   if (p == 0) return HODLRDD_OK;
-  std::vector<int64_t> uo(2), vo(2), to(1);
-  HD_CUDA(cudaMemcpy(uo.data(), h->uoff.p + b, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
-  HD_CUDA(cudaMemcpy(vo.data(), h->voff.p + b, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
-  HD_CUDA(cudaMemcpy(to.data(), h->toff.p + b, sizeof(int64_t), cudaMemcpyDeviceToHost));
-  for (int side = 0; side < 2; ++side) {
-    const int64_t rows = side == 0 ? h->h_bm[b] : h->h_bn[b];
-    const int64_t ld = pad_rows(rows);
-    std::vector<F> buf((size_t)ld * p);
-    const F* src = reinterpret_cast<const F*>(side == 0 ? h->U.p : h->V.p) + (side == 0 ? uo[0] : vo[0]);
-    HD_CUDA(cudaMemcpy(buf.data(), src, buf.size() * sizeof(F), cudaMemcpyDeviceToHost));
-    std::vector<float> sc(p, 1.0f);
-    if (Fac<F>::scaled)
-      HD_CUDA(cudaMemcpy(sc.data(), (side == 0 ? h->su.p : h->sv.p) + to[0], p * sizeof(float),
-                         cudaMemcpyDeviceToHost));
-    double* out = side == 0 ? U : V;
-    if (!out) continue;
+  const Plan& P = h->plan;
+  const int64_t c0 = h->h_toff[b];
+  std::vector<float> su(p, 1.0f), sv(p, 1.0f);
+  HD_CUDA(cudaMemcpy(su.data(), h->su.p + c0, p * sizeof(float), cudaMemcpyDeviceToHost));
+  HD_CUDA(cudaMemcpy(sv.data(), h->sv.p + c0, p * sizeof(float), cudaMemcpyDeviceToHost));
+  const int m = h->h_bm[b], n = h->h_bn[b];
+  if (V) {
+    const SegGroup& G = P.vs.h_groups[P.h_vgroup[b]];
+    const int a = h->h_bJ0[b] - G.vec;  // lead pad
+    std::vector<T> buf((size_t)G.L * G.cnt);
+    HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.vs.data.p) + G.off, buf.size() * sizeof(T),
+                       cudaMemcpyDeviceToHost));
     for (int k = 0; k < p; ++k)
-      for (int64_t i = 0; i < rows; ++i) out[k * rows + i] = Fac<F>::to_host(buf[k * ld + i]) * (double)sc[k];
+      for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = Fac<T>::to_host(buf[(size_t)k * G.L + a + j]) * sv[k];
+  }
+  if (U) {
+    const SegGroup& G = P.us.h_groups[P.h_ugroup[b]];
+    // element e of a row holds global t column G.vec + e
+    const int64_t e0 = h->h_toff[b] - (int64_t)G.vec;
+    std::vector<T> buf((size_t)G.L * G.cnt);
+    HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.us.data.p) + G.off, buf.size() * sizeof(T),
+                       cudaMemcpyDeviceToHost));
+    for (int k = 0; k < p; ++k)
+      for (int r = 0; r < m; ++r) U[(size_t)k * m + r] = Fac<T>::to_host(buf[(size_t)r * G.L + e0 + k]) * su[k];
   }
   return HODLRDD_OK;
 }
@@ -669,6 +1186,14 @@ int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V) {
     case HODLRDD_PREC_FP16: return unpack_typed<__half>(h, b, U, V);
     default: return unpack_typed<__nv_bfloat16>(h, b, U, V);
   }
+}
+
+int read_error_word(hodlrdd_s* h, int32_t* code) {
+  *code = 0;
+  if (!h->err.p) return HODLRDD_OK;
+  HD_CUDA(cudaDeviceSynchronize());
+  HD_CUDA(cudaMemcpy(code, h->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return HODLRDD_OK;
 }
 
 }  // namespace hd

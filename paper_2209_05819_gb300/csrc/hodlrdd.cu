@@ -114,15 +114,23 @@ void fill_stats(hodlrdd_s* h) {
   s.factor_elems = h->factor_elems;
   s.factor_bytes = h->factor_bytes;
   s.dense_pairs = h->dense_pairs;
+  const Plan& P = h->plan;
   int64_t bytes = (int64_t)(h->perm.bytes() + h->skey.bytes() + h->pts64.bytes() + h->pts32.bytes() +
                             h->nearoff.bytes() + h->nearidx.bytes() + h->bI0.bytes() + h->bm.bytes() +
-                            h->bJ0.bytes() + h->bn.bytes() + h->rank.bytes() + h->dense.bytes() + h->uoff.bytes() +
-                            h->voff.bytes() + h->toff.bytes() + h->piv_sigma.bytes() + h->piv_tau.bytes() +
-                            h->U.bytes() + h->V.bytes() + h->su.bytes() + h->sv.bytes() + h->xt.bytes() +
-                            h->tbuf.bytes() + h->ylev.bytes() + h->xstage.bytes() + h->ystage.bytes());
+                            h->bJ0.bytes() + h->bn.bytes() + h->rank.bytes() + h->dense.bytes() + h->toff.bytes() +
+                            h->piv_sigma.bytes() + h->piv_tau.bytes() + h->su.bytes() + h->sv.bytes() +
+                            h->xt.bytes() + h->tbuf.bytes() + h->ylev.bytes() + h->xstage.bytes() +
+                            h->ystage.bytes() + P.vs.data.bytes() + P.us.data.bytes() + P.vs.groups.bytes() +
+                            P.us.groups.bytes() + P.vs.stages.bytes() + P.us.stages.bytes() + P.tasks.bytes() +
+                            P.srcs.bytes() + P.soff.bytes());
+  for (auto& r : P.rel) bytes += (int64_t)r.bytes();
   for (auto& L : h->lv)
     bytes += (int64_t)(L.bstart.bytes() + L.bkey.bytes() + L.cfirst.bytes() + L.iloff.bytes() + L.ilidx.bytes());
   s.device_bytes = bytes;
+  const int64_t es = (int64_t)elem_size(h->opt.precision);
+  s.factor_bytes_u = P.us.elems * es;
+  s.factor_bytes_v = P.vs.elems * es;
+  s.total_rank = h->total_rank;
 }
 
 int validate_build(const double* points, int d, int64_t N, int kernel_id, const double* prm, int leaf, double tol,
@@ -428,6 +436,21 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
   HD_TRY(alloc_workspace(h));
   HD_CUDA(cudaStreamSynchronize(h->st));
   fill_stats(h);
+  return HODLRDD_OK;
+}
+
+int hodlrdd_sync(hodlrdd_handle h) {
+  if (!h) return HODLRDD_ERR_INVALID;
+  int32_t code = 0;
+  HD_TRY(read_error_word(h, &code));
+  if (code != 0) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "a bounded device-side wait expired (code %d); the matvec output is invalid",
+                  code);
+    set_error(buf);
+    HD_CUDA(cudaMemset(h->err.p, 0, sizeof(int32_t)));
+    return HODLRDD_ERR_TIMEOUT;
+  }
   return HODLRDD_OK;
 }
 

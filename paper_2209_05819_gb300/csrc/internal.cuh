@@ -206,16 +206,66 @@ struct Level {
   DevBuf<int32_t> iloff, ilidx;
 };
 
-// Per-precision packed factors and everything the matvec launches read.
+// A run of `cnt` segments of equal padded length L, contiguous in a factor
+// stream. Segment s holds the factor row / column whose dot product with
+// vec[vec + e] (e < L) is written to out[out0 + s]. The first elements are a
+// zero lead pad that aligns vec + e to 16 bytes; the tail is zero padded.
+struct SegGroup {
+  int64_t off;   // element offset of segment 0 in the stream
+  int32_t L;     // padded segment length in elements (a multiple of 16 bytes)
+  int32_t cnt;   // segments in the run
+  int32_t vec;   // vector index of element 0 (vector offset minus lead pad)
+  int32_t out0;  // output index of segment 0
+};
+
+// One bulk copy into the shared-memory ring: whole segments (piece < 0) or
+// one piece of a segment longer than a stage.
+struct Stage {
+  int64_t off;    // element offset in the stream
+  int32_t nelem;  // elements copied
+  int32_t g;      // group of the first segment
+  int32_t s;      // index of the first segment within the group
+  int32_t nseg;   // whole segments (piece < 0)
+  int32_t piece;  // piece of a long segment, or -1
+  int32_t last;   // 1 on a long segment's last piece
+  int32_t ng;     // groups touched by the stage (g .. g + ng - 1)
+  int32_t pad;
+};
+
+// A factor stream with its stage schedule: stages [cta[c], cta[c+1]) belong to
+// persistent CTA c; a long segment never straddles two CTAs.
+struct Stream {
+  DevBuf<char> data;
+  int64_t elems = 0;
+  std::vector<SegGroup> h_groups;
+  std::vector<Stage> h_stages;
+  std::vector<int32_t> h_cta;
+  DevBuf<SegGroup> groups;
+  DevBuf<Stage> stages;
+  DevBuf<int32_t> cta;
+  int ctas = 0;
+};
+
+// On-the-fly dense work: per task a target row range and a list of source
+// boxes at the same level; `soff` holds, per source, the exact FP32 offset
+// (c_I - c_J) h between the boxes' reference corners.
+struct DenseLevel {
+  int level = 0;
+  int64_t t0 = 0, t1 = 0;  // task range
+};
+
 struct Plan {
-  int64_t n_vitems = 0, n_uitems = 0, n_nitems = 0;
-  DevBuf<int4> vitems;    // {block, k0, kc, 0}
-  DevBuf<int4> uitems;    // {blk_begin, blk_end, row_start, nrows}; ylev row = level-major
-  DevBuf<int32_t> ulevel; // level of each U item
-  DevBuf<int4> nitems;    // leaf boxes: {I0, m, near_begin, near_end}
-  DevBuf<int32_t> near_src;  // extended near list: source leaf box index per entry
-  int64_t n_near_src = 0;
-  int max_vn = 0;
+  Stream vs, us;                   // V columns; U rows per (level, box)
+  std::vector<int64_t> h_vgroup;   // block -> V group (or -1)
+  std::vector<int64_t> h_ugroup;   // block -> U group (or -1)
+  std::vector<int32_t> h_ucol;     // block -> first column within its box row
+  DevBuf<int4> tasks;              // {I0, m, src_begin, src_end}
+  DevBuf<int2> srcs;               // {J0, n}
+  DevBuf<float> soff;              // d per source
+  std::vector<DenseLevel> coarse;  // dense IL blocks above the leaf level
+  DenseLevel leaf;                 // near field + leaf-level dense IL blocks
+  std::vector<DevBuf<float>> rel;  // per level (index l): SoA d x N box-relative FP32 coordinates
+  std::vector<double> h_box;       // per level: reference side h'_l (20 significant bits)
 };
 
 }  // namespace hd
@@ -250,18 +300,20 @@ struct hodlrdd_s {
   std::vector<int32_t> h_blevel, h_bti, h_bsj, h_bI0, h_bm, h_bJ0, h_bn, h_rank, h_dense;
   std::vector<int64_t> h_blk_off;  // level -> first block (size kappa + 2)
   hd::DevBuf<int32_t> bI0, bm, bJ0, bn, rank, dense;
-  hd::DevBuf<int64_t> uoff, voff, toff;  // packed factor offsets (elements); t / pivot offsets
+  hd::DevBuf<int64_t> toff;               // first t column / pivot of each block
+  std::vector<int64_t> h_toff;
   hd::DevBuf<int32_t> piv_sigma, piv_tau;  // by toff
   int64_t total_rank = 0, n_rank_capped = 0;
 
-  // factors in the handle's precision
-  hd::DevBuf<char> U, V;       // packed factor storage
-  hd::DevBuf<float> su, sv;    // per-column scales (16-bit precisions)
+  // factors in the handle's precision (plan.vs / plan.us hold the streams)
+  hd::DevBuf<float> su, sv;    // per-column scales (16-bit precisions; 1 otherwise)
   int64_t factor_elems = 0, factor_bytes = 0, dense_pairs = 0;
   hd::Plan plan;
 
-  // matvec workspace (right-hand sides are processed in chunks of at most 8)
+  // matvec workspace (right-hand sides are processed in chunks of at most 8);
+  // xt and tbuf carry zero guards of kGuard elements on both sides
   hd::DevBuf<char> xt, tbuf, ylev, xstage, ystage;
+  hd::DevBuf<int32_t> err;     // device error word of bounded waits
 
   // tracing: events between matvec stages, resolved by hodlrdd_get_profile
   bool profiling = false;
@@ -288,5 +340,6 @@ int build_plan(hodlrdd_s* h);
 int alloc_workspace(hodlrdd_s* h);
 int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
+int read_error_word(hodlrdd_s* h, int32_t* code);
 size_t elem_size(int precision);
 }  // namespace hd
