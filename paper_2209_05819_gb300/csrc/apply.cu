@@ -44,6 +44,7 @@ constexpr int kStageBytes = 32768;
 constexpr int kStages = 4;
 constexpr int kConsumerWarps = 8;
 constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
+constexpr int kPanelRows = 512;                // rows per U panel
 constexpr int kGuard = 16;                        // zero elements around xt and t (per rhs)
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at GB300 clocks
 
@@ -175,7 +176,8 @@ __device__ __forceinline__ void consumer_bar() {
 // by all consumer warps; "piece" stages hold part of a segment longer than a
 // stage. The vector slice of every group that fits kVecBytes is bulk-copied
 // next to the factor data (one right-hand side).
-constexpr int kLongChunks = 512;
+constexpr int kLongChunks = 512;  // longer segments: all consumer warps share each one
+constexpr int kBatchChunks = 64;  // shorter segments: batched transpose-reduction (one right-hand side)
 constexpr int kVecBytes = 20480;
 constexpr int kGmax = 32;
 struct SlotMeta {
@@ -185,6 +187,7 @@ struct SlotMeta {
   int32_t sbeg[kGmax + 1];  // first stage-local segment of group i
   int32_t gpos[kGmax];      // element offset of group i's first segment in the stage
   int32_t s0[kGmax];        // index within group i of its first segment in the stage
+  int32_t ubeg[kGmax + 1];  // batched V-apply: first work unit (W columns) of group i
 };
 constexpr int kMetaBytes = (int)((sizeof(SlotMeta) + 127) / 128 * 128);
 constexpr int kSlotBytes = kStageBytes + kVecBytes + kMetaBytes;
@@ -309,6 +312,183 @@ __device__ __forceinline__ void consume_long(const SlotMeta* meta, const char* b
   }
 }
 
+// Producer warp of the segment streams: per stage it waits for the slot to
+// drain, writes the stage's metadata (group descriptors, per-group segment,
+// element and work-unit prefixes, vector slice offsets) into the slot and
+// issues the bulk copies of the factor data and of the staged vector slices,
+// all completing on the slot's `full` barrier.
+template <class T, int NR>
+__device__ void produce_segment_stages(const T* __restrict__ F, const SegGroup* __restrict__ groups,
+                                       const Stage* __restrict__ stages, int q0, int q1,
+                                       const typename Fac<T>::acc* __restrict__ vec, char* smem, uint64_t* full,
+                                       uint64_t* empty, int32_t* err, int lane) {
+  using Acc = typename Fac<T>::acc;
+  constexpr bool STAGE_VEC = NR == 1;
+  int issued = 0;
+  bool ok = true;
+  for (int q = q0; q < q1; ++q, ++issued) {
+    const int slot = issued % kStages;
+    const int use = issued / kStages;
+    if (use > 0) {
+      int w = 1;
+      if (lane == 0) w = mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, w, 0)) {
+        ok = false;
+        break;
+      }
+    }
+    char* base = smem + (size_t)slot * kSlotBytes;
+    SlotMeta* meta = reinterpret_cast<SlotMeta*>(base + kStageBytes + kVecBytes);
+    const Stage st = stages[q];
+    const bool in = lane < st.ng;
+    SegGroup G{};
+    if (in) G = groups[st.g + lane];
+    // segments of group `lane` in this stage
+    const int avail = in ? G.cnt - (lane == 0 ? st.s : 0) : 0;
+    int sc_avail = avail;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, sc_avail, o);
+      if (lane >= o) sc_avail += t;
+    }
+    const int before = sc_avail - avail;
+    const int take = in ? max(0, min(avail, st.nseg - before)) : 0;
+    const int W = st.pad > 0 ? st.pad : 1;
+    const int units = (take + W - 1) / W;
+    int sc_take = take, sc_pos = take * G.L, sc_units = units;
+    const int vb =
+        (in && STAGE_VEC && st.piece < 0 && G.L * (int)sizeof(Acc) <= kVecBytes) ? G.L * (int)sizeof(Acc) : 0;
+    int sc_vb = vb;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(0xffffffffu, sc_take, o);
+      const int b = __shfl_up_sync(0xffffffffu, sc_pos, o);
+      const int c = __shfl_up_sync(0xffffffffu, sc_vb, o);
+      const int d = __shfl_up_sync(0xffffffffu, sc_units, o);
+      if (lane >= o) {
+        sc_take += a;
+        sc_pos += b;
+        sc_vb += c;
+        sc_units += d;
+      }
+    }
+    const int vtotal = __shfl_sync(0xffffffffu, sc_vb, 31);
+    const int voff = sc_vb - vb;
+    if (in) {
+      meta->g[lane] = G;
+      meta->voff[lane] = vb > 0 ? voff : -1;
+      meta->sbeg[lane] = sc_take - take;
+      meta->gpos[lane] = sc_pos - take * G.L;
+      meta->s0[lane] = lane == 0 ? st.s : 0;
+      meta->ubeg[lane] = sc_units - units;
+      if (lane == st.ng - 1) {
+        meta->sbeg[lane + 1] = sc_take;
+        meta->ubeg[lane + 1] = sc_units;
+      }
+    }
+    if (lane == 0) meta->st = st;
+    __threadfence_block();
+    __syncwarp();
+    const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
+    if (lane == 0) mbar_expect_tx(&full[slot], fbytes + (uint32_t)vtotal);
+    __syncwarp();
+    if (lane == 0) bulk_g2s(base, F + st.off, fbytes, &full[slot]);
+    if (vb > 0) bulk_g2s(base + kStageBytes + voff, vec + G.vec, (uint32_t)vb, &full[slot]);
+  }
+  if (!ok && lane == 0) {
+    // drain: copies already issued must land before the CTA's smem goes away
+    for (int k = max(0, issued - kStages); k < issued; ++k)
+      mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
+  }
+}
+
+// Sum W per-lane partial values across a team of W lanes (W a power of two,
+// teams aligned within the warp); lane i of the team ends with the total of
+// value i. Butterfly halving: W - 1 shuffles for W sums.
+template <class Acc, int W>
+__device__ __forceinline__ Acc transpose_reduce(Acc (&v)[32], int tl) {
+#pragma unroll
+  for (int off = W / 2; off >= 1; off >>= 1) {
+    const bool upper = (tl & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const Acc send = upper ? v[i] : v[i + off];
+      const Acc keep = upper ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+// Batched V-apply of a short stage (one right-hand side): a work unit is W
+// consecutive columns of one block. The W lanes of a team own fixed row chunks
+// tl, tl + W, ... (up to KMAX), keep the matching x chunks in registers, and
+// accumulate all W columns before one transpose reduction, so each column costs
+// one shared-memory load per chunk and (W - 1) / W shuffles.
+template <class T, int W, int KMAX>
+__device__ __forceinline__ void consume_vbatch(const SlotMeta* meta, const char* base,
+                                               typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
+                                               const float* __restrict__ sb, int cw, int lane) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  constexpr int PER_WARP = 32 / W;
+  constexpr int NTEAMS = kConsumerWarps * PER_WARP;
+  const int tl = lane % W;
+  const int ng = meta->st.ng;
+  const int nunits = meta->ubeg[ng];
+  int gi = 0;
+  for (int u0 = cw * PER_WARP; u0 < nunits; u0 += NTEAMS) {
+    const int u = u0 + lane / W;
+    const bool valid = u < nunits;
+    Acc acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = Acc(0);
+    int ncols = 0;
+    int64_t o0 = 0;
+    if (valid) {
+      while (u >= meta->ubeg[gi + 1]) ++gi;
+      const SegGroup& G = meta->g[gi];
+      const int C = G.L / E;
+      const int j0 = (u - meta->ubeg[gi]) * W;
+      const int take = meta->sbeg[gi + 1] - meta->sbeg[gi];
+      ncols = min(W, take - j0);
+      o0 = (int64_t)G.out0 + meta->s0[gi] + j0;
+      const Acc* xs = reinterpret_cast<const Acc*>(base + kStageBytes + meta->voff[gi]);
+      Acc xr[KMAX][E];
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        const int c = tl + k * W;
+        if (c < C) {
+          load_vec<Acc, E, 1>(xs + (int64_t)c * E, xr[k]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) xr[k][e] = Acc(0);
+        }
+      }
+      const char* cp = base + ((int64_t)meta->gpos[gi] + (int64_t)j0 * G.L) * sizeof(T);
+#pragma unroll
+      for (int jj = 0; jj < W; ++jj) {
+        if (jj < ncols) {
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k) {
+            const int c = tl + k * W;
+            if (c < C) {
+              Acc f[E];
+              Fac<T>::chunk(cp + ((int64_t)jj * G.L + (int64_t)c * E) * sizeof(T), f);
+#pragma unroll
+              for (int e = 0; e < E; ++e) acc[jj] += f[e] * xr[k][e];
+            }
+          }
+        }
+      }
+    }
+    const Acc tot = transpose_reduce<Acc, W>(acc, tl);
+    if (valid && tl < ncols) {
+      const int64_t o = o0 + tl;
+      const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
+      out[o] = tot * sc;
+    }
+  }
+}
+
 // out[out0 + s] = scale(out0 + s) * sum_e F[seg s][e] vec[vec + e]  (x NR columns)
 //
 // Warp 0 produces: per stage it waits for the slot to drain, writes the stage's
@@ -343,72 +523,7 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   __syncthreads();
 
   if (warp == 0) {
-    int issued = 0;
-    bool ok = true;
-    for (int q = q0; q < q1; ++q, ++issued) {
-      const int slot = issued % kStages;
-      const int use = issued / kStages;
-      if (use > 0) {
-        int w = 1;
-        if (lane == 0) w = mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY) ? 1 : 0;
-        if (!__shfl_sync(0xffffffffu, w, 0)) {
-          ok = false;
-          break;
-        }
-      }
-      char* base = smem + (size_t)slot * kSlotBytes;
-      SlotMeta* meta = reinterpret_cast<SlotMeta*>(base + kStageBytes + kVecBytes);
-      const Stage st = stages[q];
-      const bool in = lane < st.ng;
-      SegGroup G{};
-      if (in) G = groups[st.g + lane];
-      // segments of group `lane` in this stage
-      const int avail = in ? G.cnt - (lane == 0 ? st.s : 0) : 0;
-      int sc_avail = avail;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, sc_avail, o);
-        if (lane >= o) sc_avail += t;
-      }
-      const int before = sc_avail - avail;
-      const int take = in ? max(0, min(avail, st.nseg - before)) : 0;
-      int sc_take = take, sc_pos = take * G.L;
-      const int vb = (in && STAGE_VEC && st.piece < 0 && G.L * (int)sizeof(Acc) <= kVecBytes) ? G.L * (int)sizeof(Acc)
-                                                                                          : 0;
-      int sc_vb = vb;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int a = __shfl_up_sync(0xffffffffu, sc_take, o);
-        const int b = __shfl_up_sync(0xffffffffu, sc_pos, o);
-        const int c = __shfl_up_sync(0xffffffffu, sc_vb, o);
-        if (lane >= o) {
-          sc_take += a;
-          sc_pos += b;
-          sc_vb += c;
-        }
-      }
-      const int vtotal = __shfl_sync(0xffffffffu, sc_vb, 31);
-      const int voff = sc_vb - vb;
-      if (in) {
-        meta->g[lane] = G;
-        meta->voff[lane] = vb > 0 ? voff : -1;
-        meta->sbeg[lane] = sc_take - take;
-        meta->gpos[lane] = sc_pos - take * G.L;
-        meta->s0[lane] = lane == 0 ? st.s : 0;
-        if (lane == st.ng - 1) meta->sbeg[lane + 1] = sc_take;
-      }
-      if (lane == 0) meta->st = st;
-      __threadfence_block();
-      __syncwarp();
-      const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
-      if (lane == 0) mbar_expect_tx(&full[slot], fbytes + (uint32_t)vtotal);
-      __syncwarp();
-      if (lane == 0) bulk_g2s(base, F + st.off, fbytes, &full[slot]);
-      if (vb > 0) bulk_g2s(base + kStageBytes + voff, vec + G.vec, (uint32_t)vb, &full[slot]);
-    }
-    if (!ok && lane == 0) {
-      // drain: copies already issued must land before the CTA's smem goes away
-      for (int k = max(0, issued - kStages); k < issued; ++k)
-        mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
-    }
+    produce_segment_stages<T, NR>(F, groups, stages, q0, q1, vec, smem, full, empty, err, lane);
     return;
   }
 
@@ -425,9 +540,23 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     const SlotMeta* meta = reinterpret_cast<const SlotMeta*>(base + kStageBytes + kVecBytes);
     const Stage& st = meta->st;
     if (st.piece < 0) {
-      if (st.pad > 0)
-        consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
-      else
+      if (st.pad > 0) {
+        if constexpr (NR == 1) {
+          if (st.last > 0) {
+            switch (st.pad * 8 + st.last) {  // (W, KMAX) chosen on the host
+#define HD_VB(W, K) case W * 8 + K: consume_vbatch<T, W, K>(meta, base, out, sa, sb, cw, lane); break;
+              HD_VB(1, 1) HD_VB(2, 1) HD_VB(2, 2) HD_VB(4, 1) HD_VB(4, 2) HD_VB(4, 4) HD_VB(8, 1) HD_VB(8, 2)
+              HD_VB(8, 4) HD_VB(16, 1) HD_VB(16, 2) HD_VB(16, 4) HD_VB(1, 2) HD_VB(1, 4) HD_VB(2, 4)
+#undef HD_VB
+              default: consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane); break;
+            }
+          } else {
+            consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
+          }
+        } else {
+          consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
+        }
+      } else
         consume_long<T, NR>(meta, base, vec, out, sa, sb, cw, lane, &part[0][0][0], pbuf);
     } else {
       // one piece of a long segment: all consumer warps share it; per-lane
@@ -461,6 +590,148 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[slot]);
   }
+}
+
+// ----------------------------------------------------- U-apply (columns) ----
+// y_l(rows of a panel) = sum_k U[:, k] t[tfirst + k]. Threads own fixed row
+// chunks of the panel (chunk = 16 bytes of a column) and, when the panel is
+// short, one of CG column groups; they stream the panel's columns through the
+// same bulk-copy ring and accumulate in registers across stages. No reduction
+// is needed except, once per panel, across the CG column groups.
+constexpr int kUSlotBytes = kStageBytes + 128;  // factor columns + {Stage, Panel}
+struct USlotMeta {
+  Stage st;
+  Panel P;
+};
+
+template <class T, int NR>
+__global__ void __launch_bounds__(kSegThreads, 1)
+    k_ucols(const T* __restrict__ F, const Panel* __restrict__ panels, const Stage* __restrict__ stages,
+            const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ t,
+            typename Fac<T>::acc* __restrict__ ylev, int32_t* __restrict__ err) {
+  using Acc = typename Fac<T>::acc;
+  constexpr int E = Fac<T>::E;
+  constexpr int NT = kConsumerWarps * 32;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)kStages * kUSlotBytes);  // NT * E * NR
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    if (lane != 0) return;
+    int issued = 0;
+    bool ok = true;
+    for (int q = q0; q < q1; ++q, ++issued) {
+      const int slot = issued % kStages;
+      const int use = issued / kStages;
+      if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY)) {
+        ok = false;
+        break;
+      }
+      char* base = smem + (size_t)slot * kUSlotBytes;
+      USlotMeta* meta = reinterpret_cast<USlotMeta*>(base + kStageBytes);
+      const Stage st = stages[q];
+      meta->st = st;
+      meta->P = panels[st.g];
+      __threadfence_block();
+      const uint32_t bytes = (uint32_t)st.nelem * sizeof(T);
+      mbar_expect_tx(&full[slot], bytes);
+      bulk_g2s(base, F + st.off, bytes, &full[slot]);
+    }
+    if (!ok) {
+      for (int k = max(0, issued - kStages); k < issued; ++k)
+        mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
+    }
+    return;
+  }
+
+  const int ct = (warp - 1) * 32 + lane;
+  Acc acc[E][NR];
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[e][r] = Acc(0);
+  for (int q = q0; q < q1; ++q) {
+    const int i = q - q0;
+    const int slot = i % kStages;
+    if (!mbar_wait(&full[slot], (i / kStages) & 1, err, ERR_WAIT_FULL)) return;
+    const char* base = smem + (size_t)slot * kUSlotBytes;
+    const USlotMeta* meta = reinterpret_cast<const USlotMeta*>(base + kStageBytes);
+    const Stage st = meta->st;
+    const Panel P = meta->P;
+    const int RC = P.ld / E;
+    int RCP = 1;
+    while (RCP < RC) RCP <<= 1;
+    const int CG = NT / RCP;
+    const int rc = ct % RCP, cg = ct / RCP;
+    if (st.ng) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[e][r] = Acc(0);
+    }
+    if (rc < RC) {
+      const Acc* tp = t + ((int64_t)P.tfirst + st.s) * NR;
+#pragma unroll 4
+      for (int k = cg; k < st.nseg; k += CG) {
+        Acc f[E];
+        Fac<T>::chunk(base + ((int64_t)k * P.ld + (int64_t)rc * E) * sizeof(T), f);
+        Acc tk[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tk[r] = tp[(int64_t)k * NR + r];
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[e][r] += f[e] * tk[r];
+      }
+    }
+    if (st.last) {
+      if (CG > 1) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) red[((int64_t)ct * E + e) * NR + r] = acc[e][r];
+        consumer_bar();
+        if (cg == 0 && rc < RC) {
+          for (int g = 1; g < CG; ++g)
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+#pragma unroll
+              for (int r = 0; r < NR; ++r) acc[e][r] += red[((int64_t)(g * RCP + rc) * E + e) * NR + r];
+        }
+        consumer_bar();
+      }
+      if (cg == 0 && rc < RC) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int row = rc * E + e;
+          if (row < P.R) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) ylev[((int64_t)P.out0 + row) * NR + r] = acc[e][r];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
+  }
+}
+
+// Dynamic shared memory of k_ucols: the ring plus the cross-group reduction buffer.
+template <class T, int NR>
+constexpr size_t usmem() {
+  return (size_t)kStages * kUSlotBytes +
+         (size_t)kConsumerWarps * 32 * Fac<T>::E * NR * sizeof(typename Fac<T>::acc);
 }
 
 // ------------------------------------------------------------- dense ----
@@ -619,23 +890,20 @@ __global__ void k_packV(int64_t ngroups, const SegGroup* __restrict__ groups, co
   }
 }
 
-// U stream: one CTA per group (= level, box); segment r = row r of the box,
-// element e = lead pad a + concatenated column q (global column tfirst + q).
+// U stream: one CTA per panel; element (r, k) of the column-major panel is row
+// r0 + r of global column tfirst + k, divided by its scale (zero below R).
 template <class T>
-__global__ void k_packU(int64_t ngroups, const SegGroup* __restrict__ groups, const int32_t* __restrict__ lead,
-                        const int32_t* __restrict__ ncols, const int64_t* __restrict__ tfirst,
+__global__ void k_packU(int64_t npanels, const Panel* __restrict__ panels, const int32_t* __restrict__ prow0,
                         const int64_t* __restrict__ colU, const double* __restrict__ U64,
                         const float* __restrict__ su, T* __restrict__ out) {
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const SegGroup G = groups[g];
-    const int a = lead[g], P = ncols[g];
-    const int64_t c0 = tfirst[g];
-    for (int64_t idx = threadIdx.x; idx < (int64_t)G.cnt * G.L; idx += blockDim.x) {
-      const int r = (int)(idx / G.L), e = (int)(idx % G.L);
-      const int q = e - a;
-      double v = 0.0;
-      if (q >= 0 && q < P) v = U64[colU[c0 + q] + r] / (double)su[c0 + q];
-      out[G.off + idx] = Fac<T>::from(v);
+  for (int64_t p = blockIdx.x; p < npanels; p += gridDim.x) {
+    const Panel Pn = panels[p];
+    const int r0 = prow0[p];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)Pn.P * Pn.ld; idx += blockDim.x) {
+      const int k = (int)(idx / Pn.ld), r = (int)(idx % Pn.ld);
+      const int64_t c = (int64_t)Pn.tfirst + k;
+      const double v = r < Pn.R ? U64[colU[c] + r0 + r] / (double)su[c] : 0.0;
+      out[Pn.off + idx] = Fac<T>::from(v);
     }
   }
 }
@@ -677,10 +945,22 @@ void schedule(Stream& S, size_t esize, size_t vsize, int E, int ctas) {
   int64_t cur_vbytes = 0, cur_group = -1, cur_maxc = 0;
   auto flush = [&]() {
     if (cur.nseg > 0) {
-      if (cur.pad != 0) {  // short stage: team size = power of two >= max chunks, at most a warp
-        int ts = 1;
-        while (ts < cur_maxc && ts < 32) ts <<= 1;
-        cur.pad = ts;
+      if (cur.pad != 0) {
+        if (cur_maxc < kBatchChunks) {
+          // batched: W lanes own up to KMAX = 4 chunks each (W, KMAX powers of two)
+          int64_t w = 1;
+          while (w * 4 < cur_maxc) w <<= 1;
+          int64_t k = 1;
+          while (w * k < cur_maxc) k <<= 1;
+          cur.pad = (int32_t)w;
+          cur.last = (int32_t)k;
+        } else {
+          // one team of TS lanes per segment
+          int ts = 1;
+          while (ts < cur_maxc && ts < 32) ts <<= 1;
+          cur.pad = ts;
+          cur.last = 0;
+        }
       }
       S.h_stages.push_back(cur);
     }
@@ -752,6 +1032,33 @@ void schedule(Stream& S, size_t esize, size_t vsize, int E, int ctas) {
   S.ctas = (int)S.h_cta.size() - 1;
 }
 
+// Stage schedule of the U panels: whole columns of one panel per stage; CTA
+// ranges are balanced by bytes and cut only at panel boundaries.
+void schedule_panels(Stream& S, size_t esize, int ctas) {
+  S.h_stages.clear();
+  for (int64_t p = 0; p < (int64_t)S.h_panels.size(); ++p) {
+    const Panel& Pn = S.h_panels[p];
+    const int per = std::max<int>(1, (int)(kStageBytes / ((int64_t)Pn.ld * (int64_t)esize)));
+    for (int k0 = 0; k0 < Pn.P; k0 += per) {
+      const int nc = std::min(per, Pn.P - k0);
+      S.h_stages.push_back(Stage{Pn.off + (int64_t)k0 * Pn.ld, (int32_t)((int64_t)nc * Pn.ld), (int32_t)p, k0, nc,
+                                 -1, k0 + nc >= Pn.P ? 1 : 0, k0 == 0 ? 1 : 0, 0});
+    }
+  }
+  int64_t total = 0;
+  for (const Stage& st : S.h_stages) total += st.nelem;
+  S.h_cta.assign(1, 0);
+  int64_t acc = 0;
+  const int64_t target = std::max<int64_t>(1, (total + ctas - 1) / ctas);
+  for (size_t q = 0; q < S.h_stages.size(); ++q) {
+    acc += S.h_stages[q].nelem;
+    if (S.h_stages[q].last && acc >= target * (int64_t)S.h_cta.size() && (int)S.h_cta.size() < ctas)
+      S.h_cta.push_back((int32_t)(q + 1));
+  }
+  if (S.h_cta.back() != (int32_t)S.h_stages.size()) S.h_cta.push_back((int32_t)S.h_stages.size());
+  S.ctas = (int)S.h_cta.size() - 1;
+}
+
 template <class T>
 int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
                const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64) {
@@ -782,12 +1089,12 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
     off += L * p;
   }
   P.vs.elems = off;
-  // U groups: one per (level, box) with low-rank blocks
-  P.us.h_groups.clear();
+  // U panels: per (level, box) with low-rank blocks, rows in panels of at most
+  // kPanelRows, column-major over the box's concatenated IL columns
+  P.us.h_panels.clear();
   P.h_ugroup.assign(nblk, -1);
   P.h_ucol.assign(nblk, 0);
-  std::vector<int32_t> ulead, ucols;
-  std::vector<int64_t> utfirst;
+  std::vector<int32_t> prow0;
   off = 0;
   for (int l = 1; l <= h->kappa; ++l) {
     const Level& L = h->lv[l];
@@ -797,20 +1104,20 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
       for (int64_t b = b0; b < b1; ++b)
         if (h->h_rank[b] > 0) {
           if (tf < 0) tf = h->h_toff[b];
-          P.h_ugroup[b] = (int64_t)P.us.h_groups.size();
+          P.h_ugroup[b] = (int64_t)P.us.h_panels.size();
           P.h_ucol[b] = (int32_t)Pi;
           Pi += h->h_rank[b];
         }
       if (Pi == 0) continue;
-      const int a = (int)(tf % A1);
-      const int64_t Lr = roundE(a + Pi);
       const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
-      P.us.h_groups.push_back(
-          SegGroup{off, (int32_t)Lr, m, (int32_t)(tf - a), (int32_t)((int64_t)(l - 1) * h->N + I0)});
-      ulead.push_back(a);
-      ucols.push_back((int32_t)Pi);
-      utfirst.push_back(tf);
-      off += Lr * m;
+      for (int32_t r0 = 0; r0 < m; r0 += kPanelRows) {
+        const int32_t R = std::min(kPanelRows, m - r0);
+        const int64_t ld = roundE(R);
+        P.us.h_panels.push_back(Panel{off, (int32_t)ld, R, (int32_t)Pi, (int32_t)tf,
+                                      (int32_t)((int64_t)(l - 1) * h->N + I0 + r0), 0});
+        prow0.push_back(r0);
+        off += ld * Pi;
+      }
     }
   }
   P.us.elems = off;
@@ -819,12 +1126,12 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
     return HODLRDD_ERR_UNSUPPORTED;
   }
   schedule(P.vs, sizeof(T), sizeof(Acc), E, sms);
-  schedule(P.us, sizeof(T), sizeof(Acc), E, sms);
+  schedule_panels(P.us, sizeof(T), sms);
 
   // column maps, scales, packing
   const int64_t ncol = h->total_rank;
-  DevBuf<int64_t> colU, colV, du64, dv64, dutfirst;
-  DevBuf<int32_t> crows_u, crows_v, dvlead, dvrows, dulead, ducols;
+  DevBuf<int64_t> colU, colV, du64, dv64;
+  DevBuf<int32_t> crows_u, crows_v, dvlead, dvrows, dprow0;
   std::vector<int32_t> hcru(std::max<int64_t>(ncol, 1)), hcrv(std::max<int64_t>(ncol, 1));
   for (int64_t b = 0; b < nblk; ++b)
     for (int k = 0; k < h->h_rank[b]; ++k) {
@@ -839,15 +1146,13 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
   HD_TRY(upload(crows_v, hcrv, st));
   HD_TRY(upload(dvlead, vlead, st));
   HD_TRY(upload(dvrows, vrows, st));
-  HD_TRY(upload(dulead, ulead, st));
-  HD_TRY(upload(ducols, ucols, st));
-  HD_TRY(upload(dutfirst, utfirst, st));
+  HD_TRY(upload(dprow0, prow0, st));
   HD_TRY(h->su.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(h->sv.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(P.vs.data.alloc((size_t)std::max<int64_t>(P.vs.elems, E) * sizeof(T)));
   HD_TRY(P.us.data.alloc((size_t)std::max<int64_t>(P.us.elems, E) * sizeof(T)));
   HD_TRY(upload(P.vs.groups, P.vs.h_groups, st));
-  HD_TRY(upload(P.us.groups, P.us.h_groups, st));
+  HD_TRY(upload(P.us.panels, P.us.h_panels, st));
   HD_TRY(upload(P.vs.stages, P.vs.h_stages, st));
   HD_TRY(upload(P.us.stages, P.us.h_stages, st));
   HD_TRY(upload(P.vs.cta, P.vs.h_cta, st));
@@ -857,14 +1162,13 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
         nblk, h->rank.p, h->bm.p, h->bn.p, h->toff.p, du64.p, dv64.p, colU.p, colV.p);
     k_colscale<<<grid_warps(ncol, sms), 256, 0, st>>>(ncol, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p,
                                                       Fac<T>::scaled ? 1 : 0, h->su.p, h->sv.p);
-    const int64_t nvg = (int64_t)P.vs.h_groups.size(), nug = (int64_t)P.us.h_groups.size();
+    const int64_t nvg = (int64_t)P.vs.h_groups.size(), nup = (int64_t)P.us.h_panels.size();
     if (nvg)
       k_packV<T><<<(int)std::min<int64_t>(nvg, sms * 16), 256, 0, st>>>(
           nvg, P.vs.groups.p, dvlead.p, dvrows.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(P.vs.data.p));
-    if (nug)
-      k_packU<T><<<(int)std::min<int64_t>(nug, sms * 16), 256, 0, st>>>(
-          nug, P.us.groups.p, dulead.p, ducols.p, dutfirst.p, colU.p, U64.p, h->su.p,
-          reinterpret_cast<T*>(P.us.data.p));
+    if (nup)
+      k_packU<T><<<(int)std::min<int64_t>(nup, sms * 16), 256, 0, st>>>(nup, P.us.panels.p, dprow0.p, colU.p, U64.p,
+                                                                        h->su.p, reinterpret_cast<T*>(P.us.data.p));
     HD_CUDA(cudaGetLastError());
   }
   HD_CUDA(cudaStreamSynchronize(st));
@@ -1085,9 +1389,9 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
   if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
-    k_segdot<T, NR><<<P.us.ctas, kSegThreads, smem, st>>>(reinterpret_cast<const T*>(P.us.data.p), P.us.groups.p,
-                                                          P.us.stages.p, P.us.cta.p, t, yl, nullptr, nullptr,
-                                                          h->err.p);
+    k_ucols<T, NR><<<P.us.ctas, kSegThreads, usmem<T, NR>(), st>>>(reinterpret_cast<const T*>(P.us.data.p),
+                                                                 P.us.panels.p, P.us.stages.p, P.us.cta.p, t, yl,
+                                                                 h->err.p);
     h->launches += 1;
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
@@ -1112,6 +1416,10 @@ int set_smem_attr() {
   HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 1>()));
+  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 2>()));
+  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 4>()));
+  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 8>()));
   done = true;
   return HODLRDD_OK;
 }
@@ -1166,14 +1474,16 @@ int unpack_typed(hodlrdd_s* h, int64_t b, double* U, double* V) {
       for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = Fac<T>::to_host(buf[(size_t)k * G.L + a + j]) * sv[k];
   }
   if (U) {
-    const SegGroup& G = P.us.h_groups[P.h_ugroup[b]];
-    // element e of a row holds global t column G.vec + e
-    const int64_t e0 = h->h_toff[b] - (int64_t)G.vec;
-    std::vector<T> buf((size_t)G.L * G.cnt);
-    HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.us.data.p) + G.off, buf.size() * sizeof(T),
-                       cudaMemcpyDeviceToHost));
-    for (int k = 0; k < p; ++k)
-      for (int r = 0; r < m; ++r) U[(size_t)k * m + r] = Fac<T>::to_host(buf[(size_t)r * G.L + e0 + k]) * su[k];
+    // the box's panels are consecutive; the block's columns start at h_ucol[b]
+    for (int r0 = 0; r0 < m; r0 += kPanelRows) {
+      const Panel& Pn = P.us.h_panels[P.h_ugroup[b] + r0 / kPanelRows];
+      std::vector<T> buf((size_t)Pn.ld * p);
+      HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.us.data.p) + Pn.off + (int64_t)P.h_ucol[b] * Pn.ld,
+                         buf.size() * sizeof(T), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < p; ++k)
+        for (int r = 0; r < Pn.R; ++r)
+          U[(size_t)k * m + r0 + r] = Fac<T>::to_host(buf[(size_t)k * Pn.ld + r]) * su[k];
+    }
   }
   return HODLRDD_OK;
 }

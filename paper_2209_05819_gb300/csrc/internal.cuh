@@ -232,15 +232,33 @@ struct Stage {
   int32_t pad;
 };
 
+// A row panel of one box's U at one level: rows [r0, r0 + R) of the box times
+// the P concatenated columns of its low-rank IL blocks, column-major with
+// leading dimension ld (R rounded up to 16 bytes). Column k multiplies
+// t[tfirst + k]; row r accumulates into ylev index out0 + r.
+struct Panel {
+  int64_t off;   // element offset in the stream
+  int32_t ld;
+  int32_t R;
+  int32_t P;
+  int32_t tfirst;
+  int32_t out0;
+  int32_t pad;
+};
+
 // A factor stream with its stage schedule: stages [cta[c], cta[c+1]) belong to
-// persistent CTA c; a long segment never straddles two CTAs.
+// persistent CTA c; a long segment or a U panel never straddles two CTAs.
+// For the U stream a Stage covers columns [s, s + nseg) of panel g; `last`
+// marks the panel's final stage and `ng` its first.
 struct Stream {
   DevBuf<char> data;
   int64_t elems = 0;
   std::vector<SegGroup> h_groups;
+  std::vector<Panel> h_panels;
   std::vector<Stage> h_stages;
   std::vector<int32_t> h_cta;
   DevBuf<SegGroup> groups;
+  DevBuf<Panel> panels;
   DevBuf<Stage> stages;
   DevBuf<int32_t> cta;
   int ctas = 0;
@@ -257,8 +275,8 @@ struct DenseLevel {
 struct Plan {
   Stream vs, us;                   // V columns; U rows per (level, box)
   std::vector<int64_t> h_vgroup;   // block -> V group (or -1)
-  std::vector<int64_t> h_ugroup;   // block -> U group (or -1)
-  std::vector<int32_t> h_ucol;     // block -> first column within its box row
+  std::vector<int64_t> h_ugroup;   // block -> first U panel of its (level, box) (or -1)
+  std::vector<int32_t> h_ucol;     // block -> first column within its box's panels
   DevBuf<int4> tasks;              // {I0, m, src_begin, src_end}
   DevBuf<int2> srcs;               // {J0, n}
   DevBuf<float> soff;              // d per source
