@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kStageBytes = 32768;
 constexpr int kStages = 4;
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 16;
 constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
 constexpr int kPanelRows = 512;                // rows per U panel
 constexpr int kGuard = 16;                        // zero elements around xt and t (per rhs)
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   constexpr int NT = kConsumerWarps * 32;
   extern __shared__ __align__(128) char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)kStages * kUSlotBytes);  // NT * E * NR
+  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)kStages * kUSlotBytes);  // NT * 8
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
@@ -656,11 +656,16 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   }
 
   const int ct = (warp - 1) * 32 + lane;
-  Acc acc[E][NR];
+  // FP32 factors: compensated (Kahan) accumulation over the long column loops
+  constexpr bool KAHAN = std::is_same<T, float>::value;
+  Acc acc[E][NR], cmp[E][NR];
 #pragma unroll
   for (int e = 0; e < E; ++e)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[e][r] = Acc(0);
+    for (int r = 0; r < NR; ++r) {
+      acc[e][r] = Acc(0);
+      cmp[e][r] = Acc(0);
+    }
   for (int q = q0; q < q1; ++q) {
     const int i = q - q0;
     const int slot = i % kStages;
@@ -678,7 +683,10 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 #pragma unroll
       for (int e = 0; e < E; ++e)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[e][r] = Acc(0);
+        for (int r = 0; r < NR; ++r) {
+          acc[e][r] = Acc(0);
+          cmp[e][r] = Acc(0);
+        }
     }
     if (rc < RC) {
       const Acc* tp = t + ((int64_t)P.tfirst + st.s) * NR;
@@ -692,24 +700,41 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 #pragma unroll
         for (int e = 0; e < E; ++e)
 #pragma unroll
-          for (int r = 0; r < NR; ++r) acc[e][r] += f[e] * tk[r];
+          for (int r = 0; r < NR; ++r) {
+            if constexpr (KAHAN) {
+              const Acc y = f[e] * tk[r] - cmp[e][r];
+              const Acc s2 = acc[e][r] + y;
+              cmp[e][r] = (s2 - acc[e][r]) - y;
+              acc[e][r] = s2;
+            } else {
+              acc[e][r] += f[e] * tk[r];
+            }
+          }
       }
     }
     if (st.last) {
-      if (CG > 1) {
+      if constexpr (KAHAN) {
 #pragma unroll
         for (int e = 0; e < E; ++e)
 #pragma unroll
-          for (int r = 0; r < NR; ++r) red[((int64_t)ct * E + e) * NR + r] = acc[e][r];
-        consumer_bar();
-        if (cg == 0 && rc < RC) {
-          for (int g = 1; g < CG; ++g)
+          for (int r = 0; r < NR; ++r) acc[e][r] -= cmp[e][r];
+      }
+      if (CG > 1) {
+        // sum the CG column groups, 8 components per pass through `red`
 #pragma unroll
-            for (int e = 0; e < E; ++e)
+        for (int q0c = 0; q0c < E * NR; q0c += 8) {
 #pragma unroll
-              for (int r = 0; r < NR; ++r) acc[e][r] += red[((int64_t)(g * RCP + rc) * E + e) * NR + r];
+          for (int c = 0; c < 8; ++c)
+            if (q0c + c < E * NR) red[(int64_t)ct * 8 + c] = acc[(q0c + c) / NR][(q0c + c) % NR];
+          consumer_bar();
+          if (cg == 0 && rc < RC) {
+            for (int g = 1; g < CG; ++g)
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                if (q0c + c < E * NR) acc[(q0c + c) / NR][(q0c + c) % NR] += red[(int64_t)(g * RCP + rc) * 8 + c];
+          }
+          consumer_bar();
         }
-        consumer_bar();
       }
       if (cg == 0 && rc < RC) {
 #pragma unroll
@@ -730,8 +755,7 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 // Dynamic shared memory of k_ucols: the ring plus the cross-group reduction buffer.
 template <class T, int NR>
 constexpr size_t usmem() {
-  return (size_t)kStages * kUSlotBytes +
-         (size_t)kConsumerWarps * 32 * Fac<T>::E * NR * sizeof(typename Fac<T>::acc);
+  return (size_t)kStages * kUSlotBytes + (size_t)kConsumerWarps * 32 * 8 * sizeof(typename Fac<T>::acc);
 }
 
 // ------------------------------------------------------------- dense ----
@@ -821,6 +845,109 @@ __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, i
       }
     }
   }
+}
+
+// Packed near field / dense blocks (FP32, d <= 3, one right-hand side): a
+// point is one float4 (box-relative coordinates, x_t in .w); a source box is an
+// int4 {J0, n} and its exact box offset; the kernel function is a template
+// parameter so the pair loop has no branch on it.
+template <int KID>
+__device__ __forceinline__ float f32k(float s, float c) {
+  if constexpr (KID == HODLRDD_K_LOG) return s == 0.0f ? 0.0f : 0.5f * logf(s);
+  else if constexpr (KID == HODLRDD_K_INV_R) return s == 0.0f ? 0.0f : rsqrtf(s);
+  else if constexpr (KID == HODLRDD_K_MATERN32) {
+    const float a = c * sqrtf(s);
+    return (1.0f + a) * expf(-a);
+  } else if constexpr (KID == HODLRDD_K_GAUSS) return expf(-c * s);
+  else if constexpr (KID == HODLRDD_K_EXP) return expf(-c * sqrtf(s));
+  else if constexpr (KID == HODLRDD_K_INV_R2_4D) return s == 0.0f ? 0.0f : c / s;
+  else if constexpr (KID == HODLRDD_K_R) return sqrtf(s);
+  else if constexpr (KID == HODLRDD_K_SIN) return sinf(sqrtf(s));
+  else return rsqrtf(1.0f + sqrtf(s));
+}
+
+template <int D, int KID, bool FINAL>
+__global__ void __launch_bounds__(256) k_dense4(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
+                                                const int4* __restrict__ srcs, const float4* __restrict__ soff,
+                                                const float4* __restrict__ P, int64_t N, float kc, float kscale,
+                                                float kdiag, float* __restrict__ ylev_l,
+                                                const float* __restrict__ ylev, int kappa,
+                                                const int32_t* __restrict__ perm, float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = t0 + warp; it < t1; it += nwarps) {
+    const int4 task = tasks[it];
+    const int I0 = task.x, m = task.y;
+    int G = 1;
+    while (G < m && G < 32) G <<= 1;
+    const int S = 32 / G;
+    const int gi = lane % G, stripe = lane / G;
+    for (int g0 = 0; g0 < m; g0 += G) {
+      const int row = I0 + g0 + gi;
+      const bool valid = g0 + gi < m;
+      const float4 xr = valid ? P[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float acc0 = 0.f, acc1 = 0.f;
+      for (int e = task.z; e < task.w; ++e) {
+        const int4 sj = srcs[e];
+        const float4 of = soff[e];
+        const int j1 = sj.x + sj.y;
+        int j = sj.x + stripe;
+        for (; j + S < j1; j += 2 * S) {  // two independent pairs in flight
+          const float4 p0 = P[j], p1 = P[j + S];
+          float s0 = 0.f, s1 = 0.f, t;
+          t = (xr.x - p0.x) + of.x; s0 = fmaf(t, t, s0);
+          t = (xr.x - p1.x) + of.x; s1 = fmaf(t, t, s1);
+          if (D > 1) {
+            t = (xr.y - p0.y) + of.y; s0 = fmaf(t, t, s0);
+            t = (xr.y - p1.y) + of.y; s1 = fmaf(t, t, s1);
+          }
+          if (D > 2) {
+            t = (xr.z - p0.z) + of.z; s0 = fmaf(t, t, s0);
+            t = (xr.z - p1.z) + of.z; s1 = fmaf(t, t, s1);
+          }
+          acc0 = fmaf(f32k<KID>(s0, kc), p0.w, acc0);
+          acc1 = fmaf(f32k<KID>(s1, kc), p1.w, acc1);
+        }
+        if (j < j1) {
+          const float4 p0 = P[j];
+          float s0 = 0.f, t;
+          t = (xr.x - p0.x) + of.x; s0 = fmaf(t, t, s0);
+          if (D > 1) { t = (xr.y - p0.y) + of.y; s0 = fmaf(t, t, s0); }
+          if (D > 2) { t = (xr.z - p0.z) + of.z; s0 = fmaf(t, t, s0); }
+          acc0 = fmaf(f32k<KID>(s0, kc), p0.w, acc0);
+        }
+      }
+      float acc = acc0 + acc1;
+      for (int o = G; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (stripe == 0 && valid) {
+        if constexpr (FINAL) {
+          float tot = kscale * acc + kdiag * xr.w;
+          for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
+          y[perm[row]] = tot;
+        } else {
+          ylev_l[row] += kscale * acc;
+        }
+      }
+    }
+  }
+}
+
+// One right-hand side with packed points: x_t[i] and the .w lane of every
+// packed level array.
+template <class IO>
+__global__ void k_gather_pack(const IO* __restrict__ x, const int32_t* __restrict__ perm, int64_t N, int ldx,
+                              int c0, float* __restrict__ xt, float4* const* __restrict__ packs, int npacks) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (float)x[(int64_t)perm[i] * ldx + c0];
+    xt[i] = v;
+    for (int k = 0; k < npacks; ++k) packs[k][i].w = v;
+  }
+}
+
+__global__ void k_pack_rel4(const float* __restrict__ rel, int64_t N, int d, float4* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float4(rel[i], d > 1 ? rel[N + i] : 0.f, d > 2 ? rel[2 * N + i] : 0.f, 0.f);
 }
 
 template <class Acc, class IO, int NR>
@@ -1300,6 +1427,31 @@ int build_plan(hodlrdd_s* h) {
           h->pts64.p, h->N, d, l, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[l], P.rel[l].p);
       HD_CUDA(cudaGetLastError());
     }
+    if (d <= 3) {
+      P.rel4.clear();
+      P.rel4.resize(h->kappa + 1);
+      std::vector<int32_t> lvls;
+      std::vector<float4*> ptrs;
+      for (int l = 0; l <= h->kappa; ++l) {
+        if (!need_rel[l]) continue;
+        HD_TRY(P.rel4[l].alloc(h->N));
+        k_pack_rel4<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(P.rel[l].p, h->N, d,
+                                                                                         P.rel4[l].p);
+        HD_CUDA(cudaGetLastError());
+        lvls.push_back(l);
+        ptrs.push_back(P.rel4[l].p);
+      }
+      HD_TRY(upload(P.rel4_levels, lvls, st));
+      HD_TRY(upload(P.rel4_ptrs, ptrs, st));
+      std::vector<int4> s4(srcs.size());
+      std::vector<float4> o4(srcs.size());
+      for (size_t e = 0; e < srcs.size(); ++e) {
+        s4[e] = make_int4(srcs[e].x, srcs[e].y, 0, 0);
+        o4[e] = make_float4(soff[e * d], d > 1 ? soff[e * d + 1] : 0.f, d > 2 ? soff[e * d + 2] : 0.f, 0.f);
+      }
+      HD_TRY(upload(P.srcs4, s4, st));
+      HD_TRY(upload(P.soff4, o4, st));
+    }
     HD_CUDA(cudaStreamSynchronize(st));
   }
   HD_CUDA(cudaStreamSynchronize(st));
@@ -1357,6 +1509,59 @@ int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl,
   return HODLRDD_OK;
 }
 
+template <int D, int KID>
+void launch_dense4_k(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, float* y) {
+  const Plan& P = h->plan;
+  const float kc = (float)kernel_const(h->K);
+  for (const DenseLevel& DL : P.coarse) {
+    k_dense4<D, KID, false><<<grid_warps(DL.t1 - DL.t0, sms), 256, 0, st>>>(
+        P.tasks.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.rel4[DL.level].p, h->N, kc, (float)h->K.scale,
+        (float)h->K.diag, yl + (int64_t)(DL.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
+    h->launches += 1;
+  }
+  k_dense4<D, KID, true><<<grid_warps(P.leaf.t1 - P.leaf.t0, sms), 256, 0, st>>>(
+      P.tasks.p, P.leaf.t0, P.leaf.t1, P.srcs4.p, P.soff4.p, P.rel4[h->kappa].p, h->N, kc, (float)h->K.scale,
+      (float)h->K.diag, nullptr, yl, h->kappa, h->perm.p, y);
+  h->launches += 1;
+}
+
+template <int D>
+void launch_dense4_d(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, float* y) {
+  switch (h->K.id) {
+    case HODLRDD_K_LOG: launch_dense4_k<D, HODLRDD_K_LOG>(h, st, sms, yl, y); break;
+    case HODLRDD_K_INV_R: launch_dense4_k<D, HODLRDD_K_INV_R>(h, st, sms, yl, y); break;
+    case HODLRDD_K_MATERN32: launch_dense4_k<D, HODLRDD_K_MATERN32>(h, st, sms, yl, y); break;
+    case HODLRDD_K_GAUSS: launch_dense4_k<D, HODLRDD_K_GAUSS>(h, st, sms, yl, y); break;
+    case HODLRDD_K_EXP: launch_dense4_k<D, HODLRDD_K_EXP>(h, st, sms, yl, y); break;
+    case HODLRDD_K_INV_R2_4D: launch_dense4_k<D, HODLRDD_K_INV_R2_4D>(h, st, sms, yl, y); break;
+    case HODLRDD_K_R: launch_dense4_k<D, HODLRDD_K_R>(h, st, sms, yl, y); break;
+    case HODLRDD_K_SIN: launch_dense4_k<D, HODLRDD_K_SIN>(h, st, sms, yl, y); break;
+    default: launch_dense4_k<D, HODLRDD_K_INV_SQRT1P>(h, st, sms, yl, y); break;
+  }
+}
+
+// Packed dense / near-field launches (FP32, d <= 3, one right-hand side, y of
+// type float with leading dimension 1).
+template <class IO>
+int launch_dense4(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, IO* y, int ldy, int c0) {
+  if constexpr (!std::is_same<IO, float>::value) {
+    set_error("packed near field needs float output");
+    return HODLRDD_ERR_UNSUPPORTED;
+  } else {
+    if (ldy != 1 || c0 != 0) {
+      set_error("packed near field is for one right-hand side");
+      return HODLRDD_ERR_UNSUPPORTED;
+    }
+    switch (h->d) {
+      case 1: launch_dense4_d<1>(h, st, sms, yl, y); break;
+      case 2: launch_dense4_d<2>(h, st, sms, yl, y); break;
+      default: launch_dense4_d<3>(h, st, sms, yl, y); break;
+    }
+    HD_CUDA(cudaGetLastError());
+    return HODLRDD_OK;
+  }
+}
+
 template <class T, class IO, int NR>
 int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t st) {
   using Acc = typename Fac<T>::acc;
@@ -1373,8 +1578,15 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     HD_TRY(chunk_events(h, ev));
     HD_CUDA(cudaEventRecord(ev[0], st));
   }
-  k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
-                                                                                              ldx, c0, xt);
+  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.rel4_ptrs.n > 0;
+  if (packed) {
+    if constexpr (NR == 1 && !F64)
+      k_gather_pack<IO><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(
+          x, h->perm.p, h->N, ldx, c0, reinterpret_cast<float*>(xt), P.rel4_ptrs.p, (int)P.rel4_ptrs.n);
+  } else {
+    k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
+                                                                                                ldx, c0, xt);
+  }
   h->launches += 1;
   if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
   const size_t smem = (size_t)kStages * kSlotBytes;
@@ -1395,7 +1607,9 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     h->launches += 1;
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
-  switch (h->d) {
+  if (packed) {
+    if constexpr (NR == 1 && !F64) HD_TRY((launch_dense4<IO>(h, st, sms, yl, y, ldx, c0)));
+  } else switch (h->d) {
     case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
     case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
     case 3: HD_TRY((launch_dense<Acc, IO, NR, 3, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;

@@ -283,6 +283,14 @@ struct Plan {
   std::vector<DenseLevel> coarse;  // dense IL blocks above the leaf level
   DenseLevel leaf;                 // near field + leaf-level dense IL blocks
   std::vector<DevBuf<float>> rel;  // per level (index l): SoA d x N box-relative FP32 coordinates
+  // packed form for d <= 3 and one right-hand side: per level a float4 per point
+  // (box-relative coordinates, x_t of the current matvec in .w) and per source a
+  // {J0, n} int4 and an offset float4
+  std::vector<DevBuf<float4>> rel4;
+  DevBuf<int4> srcs4;
+  DevBuf<float4> soff4;
+  DevBuf<int32_t> rel4_levels;     // levels holding a packed array (device copy for the gather)
+  DevBuf<float4*> rel4_ptrs;
   std::vector<double> h_box;       // per level: reference side h'_l (20 significant bits)
 };
 

@@ -178,3 +178,33 @@ def test_injected_allocation_failure_is_clean(env):
     assert abs(free1 - free0) < (64 << 20)
     h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol)  # still usable
     assert h.stats()["n_blocks"] > 0
+
+
+PACKED_CASES = [
+    (1, 3000, W.K_EXP, (1, 0, 1.0, 0), 16, 1e-9),
+    (2, 4096, W.K_LOG, None, 64, 1e-8),
+    (2, 3000, W.K_R, None, 25, 1e-9),
+    (2, 3000, W.K_SIN, None, 25, 1e-9),
+    (3, 9000, W.K_INV_R, None, 32, 1e-8),
+    (3, 5000, W.K_GAUSS, (1, 1e-3, 0.5, 0), 32, 1e-6),
+    (3, 5000, W.K_MATERN32, (1, 0, 0.2, 0), 40, 1e-7),
+    (3, 4000, W.K_INV_R2_4D, None, 30, 1e-8),
+    (3, 3000, W.K_INV_SQRT1P, None, 25, 1e-9),
+]
+
+
+@pytest.mark.parametrize("d,N,kernel,params,leaf,tol", PACKED_CASES)
+def test_fp32_single_rhs_packed_near_field(env, d, N, kernel, params, leaf, tol):
+    """One right-hand side in FP32 uses packed box-relative points and a
+    kernel-specialised pair loop; it must agree with the FP64 form and with the
+    general (two right-hand sides) FP32 path."""
+    torch, oracle, hd = env
+    w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), leaf, tol, nrhs=2, seed=N + 5 * d)
+    h64 = gpu_handle(hd, w)
+    h32 = gpu_handle(hd, w, precision="fp32")
+    y64 = gpu_matvec(h64, w.x[:, :1])
+    y1 = gpu_matvec(h32, w.x[:, :1])
+    y2 = gpu_matvec(h32, w.x)
+    h32.sync()
+    assert relerr(y1, y64) <= MIXED_BOUND["fp32"]
+    assert relerr(y1, y2[:, :1]) <= 1e-6
