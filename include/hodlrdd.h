@@ -167,6 +167,31 @@ int hodlrdd_build_ex(const double* points, int d, int64_t N, int kernel_id, cons
 int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
 
 /*
+ * y = K x exactly as hodlrdd_matvec computes it (same kernels, same result), for
+ * callers that must not allocate device memory: a serving loop whose device
+ * memory another allocator reserved up front, or a loop that cannot take the
+ * synchronisation a cudaMalloc/cudaFree may bring. The paper has no counterpart;
+ * it is a library addition.
+ *
+ * Host x or y pass through one fixed scratch array in the library's static device
+ * memory (16 MiB per device) instead of buffers the handle grows: this call runs
+ * no cudaMalloc, cudaFree or allocating library. The staged bytes,
+ * round_up(N*nrhs*esize, 256) for a host x plus N*nrhs*esize for a host y (esize
+ * 8 for FP64 handles, else 4), must be <= 16 MiB, else HODLRDD_ERR_INVALID with
+ * the sizes in hodlrdd_last_error() and nothing enqueued. Nothing in the scratch
+ * has to start at zero. Device x and y need no scratch.
+ *
+ * The first call on a device does set-up (it looks up the scratch's device
+ * address, which also loads this part of the library's device code): make it
+ * before any stream capture. Profiling must be off (HODLRDD_ERR_INVALID
+ * otherwise). Arguments, layout and synchronisation as hodlrdd_matvec. All calls
+ * on one device share the one scratch: two calls in flight at the same time on
+ * the same device (from several threads, or one thread's asynchronous work on
+ * other streams) race on it and must be serialised by the caller.
+ */
+int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
+
+/*
  * Waits for all device work (cudaDeviceSynchronize) and reports failures the
  * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
  * their bounded waits expired (the y of that matvec is then invalid). Clears the

@@ -66,6 +66,7 @@ def load():
         "hodlrdd_build": (i32, [vp, i32, i64, i32, vp, i32, dbl, C.POINTER(vp)]),
         "hodlrdd_build_ex": (i32, [vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(vp)]),
         "hodlrdd_matvec": (i32, [vp, vp, vp, i32, vp]),
+        "hodlrdd_matvec_noalloc": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_destroy": (i32, [vp]),
         "hodlrdd_get_stats": (i32, [vp, C.POINTER(Stats)]),
         "hodlrdd_error_string": (C.c_char_p, [i32]),
@@ -192,6 +193,21 @@ class Handle:
         ya, ky = _ptr(y)
         st = self._lib.hodlrdd_matvec(self._h, xa, ya, nrhs, _stream_ptr(stream))
         _check(st, "hodlrdd_matvec")
+        return y
+
+    def matvec_noalloc(self, x, y=None, stream=None):
+        """y = K x through hodlrdd_matvec_noalloc: host buffers are staged in the
+        library's fixed static device scratch, never in newly allocated memory."""
+        nrhs = 1 if x.ndim == 1 else int(x.shape[1])
+        if y is None:
+            if isinstance(x, np.ndarray):
+                y = np.empty(x.shape, dtype=self.io_dtype)
+            else:
+                y = x.new_empty(x.shape)
+        xa, kx = _ptr(x)
+        ya, ky = _ptr(y)
+        st = self._lib.hodlrdd_matvec_noalloc(self._h, xa, ya, nrhs, _stream_ptr(stream))
+        _check(st, "hodlrdd_matvec_noalloc")
         return y
 
     # -- statistics and introspection ----------------------------------------------

@@ -24,6 +24,7 @@ SOURCES = {
     "tree.cu": ["--fmad=false"],
     "aca.cu": ["--fmad=false"],
     "apply.cu": [],
+    "noalloc.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]
