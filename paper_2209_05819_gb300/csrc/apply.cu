@@ -41,7 +41,6 @@ size_t elem_size(int precision) {
 namespace {
 
 constexpr int kStageBytes = 32768;
-constexpr int kStages = 4;
 constexpr int kConsumerWarps = 16;
 constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
 constexpr int kPanelRows = 512;                // rows per U panel
@@ -107,22 +106,6 @@ template <> struct Fac<__nv_bfloat16> {
   }
 };
 
-// E * NR consecutive vector values (16-byte aligned) into registers.
-template <class Acc, int E, int NR>
-__device__ __forceinline__ void load_vec(const Acc* __restrict__ p, Acc (&v)[E * NR]) {
-  constexpr int PER = 16 / sizeof(Acc);
-#pragma unroll
-  for (int i = 0; i < E * NR; i += PER) {
-    if constexpr (sizeof(Acc) == 4) {
-      float4 q = *reinterpret_cast<const float4*>(p + i);
-      v[i] = q.x; v[i + 1] = q.y; v[i + 2] = q.z; v[i + 3] = q.w;
-    } else {
-      double2 q = *reinterpret_cast<const double2*>(p + i);
-      v[i] = q.x; v[i + 1] = q.y;
-    }
-  }
-}
-
 // ------------------------------------------------------------- mbarriers ----
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -164,462 +147,122 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// L2 policy for data read exactly once per matvec (the factor streams): evict
+// it first, so the vectors and descriptors the kernels reuse stay resident.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s_once(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Stage descriptors reach a producer warp 32 at a time (lane i holds one), one
+// batch ahead of use, so no stage waits on a descriptor load.
+struct StageRegs {
+  int2 w[5];
+};
+static_assert(sizeof(Stage) == 40, "Stage is five 8-byte words");
+__device__ __forceinline__ void load_stage_regs(StageRegs& r, const Stage* __restrict__ s, int q, int q1) {
+  if (q < q1) {
+    const int2* p = reinterpret_cast<const int2*>(s + q);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.w[k] = __ldg(p + k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.w[k] = make_int2(0, 0);
+  }
+}
+// Stage k (0 <= k < 64) of the batches a (k < 32) and b (k >= 32), to every
+// lane; k is warp-uniform.
+__device__ __forceinline__ Stage pick_stage(const StageRegs& a, const StageRegs& b, int k) {
+  int2 w[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int x = k < 32 ? a.w[i].x : b.w[i].x, y = k < 32 ? a.w[i].y : b.w[i].y;
+    w[i] = make_int2(__shfl_sync(0xffffffffu, x, k & 31), __shfl_sync(0xffffffffu, y, k & 31));
+  }
+  Stage st;
+  memcpy(&st, w, sizeof st);
+  return st;
+}
+
 __device__ __forceinline__ void consumer_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
 }
 
-// ------------------------------------------------------ segmented dot ----
-// Stage kinds (decided on the host): "short" stages hold whole segments of at
-// most kLongChunks 16-byte chunks from up to kGmax groups and are processed by
-// lane teams of Stage::ts lanes over a flat list of the stage's segments;
-// "long" stages (ts = 0) hold whole longer segments of one group, each shared
-// by all consumer warps; "piece" stages hold part of a segment longer than a
-// stage. The vector slice of every group that fits kVecBytes is bulk-copied
-// next to the factor data (one right-hand side).
-constexpr int kLongChunks = 512;  // longer segments: all consumer warps share each one
-constexpr int kBatchChunks = 64;  // shorter segments: batched transpose-reduction (one right-hand side)
-constexpr int kVecBytes = 20480;
-constexpr int kGmax = 32;
-struct SlotMeta {
-  Stage st;
-  SegGroup g[kGmax];
-  int32_t voff[kGmax];      // byte offset of group i's vector slice in the slot, -1 if not staged
-  int32_t sbeg[kGmax + 1];  // first stage-local segment of group i
-  int32_t gpos[kGmax];      // element offset of group i's first segment in the stage
-  int32_t s0[kGmax];        // index within group i of its first segment in the stage
-  int32_t ubeg[kGmax + 1];  // batched V-apply: first work unit (W columns) of group i
-};
-constexpr int kMetaBytes = (int)((sizeof(SlotMeta) + 127) / 128 * 128);
-constexpr int kSlotBytes = kStageBytes + kVecBytes + kMetaBytes;
-
-template <class T, int NR>
-__device__ __forceinline__ void write_out(int64_t o, const typename Fac<T>::acc (&acc)[NR],
-                                          typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
-                                          const float* __restrict__ sb) {
-  using Acc = typename Fac<T>::acc;
-  const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
-#pragma unroll
-  for (int r = 0; r < NR; ++r) out[o * NR + r] = acc[r] * sc;
-}
-
-template <class T, int NR>
-__device__ __forceinline__ void dot_chunk(const char* fp, const typename Fac<T>::acc* vp,
-                                          typename Fac<T>::acc (&acc)[NR]) {
-  using Acc = typename Fac<T>::acc;
-  constexpr int E = Fac<T>::E;
-  Acc f[E];
-  Fac<T>::chunk(fp, f);
-  Acc v[E * NR];
-  load_vec<Acc, E, NR>(vp, v);
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] += f[e] * v[e * NR + r];
-}
-
-// Short stage: teams of TS lanes take the stage's segments round-robin across
-// group boundaries, SU segments in flight per team; a lane covers chunks
-// tl, tl + TS, ... of its segment. Shuffle reduction within the team.
-template <class T, int NR>
-__device__ __forceinline__ void consume_short(const SlotMeta* meta, const char* base,
-                                              const typename Fac<T>::acc* __restrict__ vec,
-                                              typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
-                                              const float* __restrict__ sb, int cw, int lane) {
-  using Acc = typename Fac<T>::acc;
-  constexpr int E = Fac<T>::E;
-  constexpr int SU = NR == 1 ? 4 : 2;
-  const int TS = meta->st.pad;
-  const int S = meta->st.nseg;
-  const int per_warp = 32 / TS;
-  const int nteams = kConsumerWarps * per_warp;
-  const int team = cw * per_warp + lane / TS;
-  const int tl = lane % TS;
-  int gi = 0;
-  for (int b0 = 0; b0 < S; b0 += nteams * SU) {
-    Acc acc[SU][NR];
-    int64_t oidx[SU];
-#pragma unroll
-    for (int u = 0; u < SU; ++u) {
-#pragma unroll
-      for (int r = 0; r < NR; ++r) acc[u][r] = Acc(0);
-      oidx[u] = -1;
-      const int q = b0 + u * nteams + team;
-      if (q < S) {
-        while (q >= meta->sbeg[gi + 1]) ++gi;
-        const SegGroup& G = meta->g[gi];
-        const int j = q - meta->sbeg[gi];
-        const int C = G.L / E;
-        const char* sp = base + ((int64_t)meta->gpos[gi] + (int64_t)j * G.L) * sizeof(T);
-        const int vo = meta->voff[gi];
-        const Acc* vsrc = vo >= 0 ? reinterpret_cast<const Acc*>(base + kStageBytes + vo) : vec + (int64_t)G.vec * NR;
-#pragma unroll 4
-        for (int c = tl; c < C; c += TS) dot_chunk<T, NR>(sp + (size_t)c * 16, vsrc + (int64_t)c * E * NR, acc[u]);
-        oidx[u] = (int64_t)G.out0 + meta->s0[gi] + j;
-      }
-    }
-    for (int o = TS >> 1; o > 0; o >>= 1)
-#pragma unroll
-      for (int u = 0; u < SU; ++u)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[u][r] += __shfl_xor_sync(0xffffffffu, acc[u][r], o);
-    if (tl == 0) {
-#pragma unroll
-      for (int u = 0; u < SU; ++u)
-        if (oidx[u] >= 0) write_out<T, NR>(oidx[u], acc[u], out, sa, sb);
-    }
-  }
-}
-
-// Long stage: all consumer warps share one segment at a time; warp sums meet in
-// double-buffered shared memory (one consumer barrier per segment).
-template <class T, int NR>
-__device__ __forceinline__ void consume_long(const SlotMeta* meta, const char* base,
-                                             const typename Fac<T>::acc* __restrict__ vec,
-                                             typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
-                                             const float* __restrict__ sb, int cw, int lane,
-                                             typename Fac<T>::acc* part, int& pbuf) {
-  using Acc = typename Fac<T>::acc;
-  constexpr int E = Fac<T>::E;
-  const SegGroup& G = meta->g[0];
-  const int C = G.L / E;
-  const int vo = meta->voff[0];
-  const Acc* vsrc = vo >= 0 ? reinterpret_cast<const Acc*>(base + kStageBytes + vo) : vec + (int64_t)G.vec * NR;
-  const int ct = cw * 32 + lane;
-  for (int j = 0; j < meta->st.nseg; ++j) {
-    const char* sp = base + (int64_t)j * G.L * sizeof(T);
-    Acc acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
-#pragma unroll 4
-    for (int c = ct; c < C; c += kConsumerWarps * 32) dot_chunk<T, NR>(sp + (size_t)c * 16, vsrc + (int64_t)c * E * NR, acc);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      Acc a = acc[r];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) part[(pbuf * kConsumerWarps + cw) * NR + r] = a;
-    }
-    consumer_bar();
-    if (cw == 0 && lane == 0) {
-      Acc tot[NR];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        tot[r] = Acc(0);
-        for (int w = 0; w < kConsumerWarps; ++w) tot[r] += part[(pbuf * kConsumerWarps + w) * NR + r];
-      }
-      write_out<T, NR>((int64_t)G.out0 + meta->st.s + j, tot, out, sa, sb);
-    }
-    pbuf ^= 1;
-  }
-}
-
-// Producer warp of the segment streams: per stage it waits for the slot to
-// drain, writes the stage's metadata (group descriptors, per-group segment,
-// element and work-unit prefixes, vector slice offsets) into the slot and
-// issues the bulk copies of the factor data and of the staged vector slices,
-// all completing on the slot's `full` barrier.
-template <class T, int NR>
-__device__ void produce_segment_stages(const T* __restrict__ F, const SegGroup* __restrict__ groups,
-                                       const Stage* __restrict__ stages, int q0, int q1,
-                                       const typename Fac<T>::acc* __restrict__ vec, char* smem, uint64_t* full,
-                                       uint64_t* empty, int32_t* err, int lane) {
-  using Acc = typename Fac<T>::acc;
-  constexpr bool STAGE_VEC = NR == 1;
-  int issued = 0;
-  bool ok = true;
-  for (int q = q0; q < q1; ++q, ++issued) {
-    const int slot = issued % kStages;
-    const int use = issued / kStages;
-    if (use > 0) {
-      int w = 1;
-      if (lane == 0) w = mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, w, 0)) {
-        ok = false;
-        break;
-      }
-    }
-    char* base = smem + (size_t)slot * kSlotBytes;
-    SlotMeta* meta = reinterpret_cast<SlotMeta*>(base + kStageBytes + kVecBytes);
-    const Stage st = stages[q];
-    const bool in = lane < st.ng;
-    SegGroup G{};
-    if (in) G = groups[st.g + lane];
-    // segments of group `lane` in this stage
-    const int avail = in ? G.cnt - (lane == 0 ? st.s : 0) : 0;
-    int sc_avail = avail;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, sc_avail, o);
-      if (lane >= o) sc_avail += t;
-    }
-    const int before = sc_avail - avail;
-    const int take = in ? max(0, min(avail, st.nseg - before)) : 0;
-    const int W = st.pad > 0 ? st.pad : 1;
-    const int units = (take + W - 1) / W;
-    int sc_take = take, sc_pos = take * G.L, sc_units = units;
-    const int vb =
-        (in && STAGE_VEC && st.piece < 0 && G.L * (int)sizeof(Acc) <= kVecBytes) ? G.L * (int)sizeof(Acc) : 0;
-    int sc_vb = vb;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int a = __shfl_up_sync(0xffffffffu, sc_take, o);
-      const int b = __shfl_up_sync(0xffffffffu, sc_pos, o);
-      const int c = __shfl_up_sync(0xffffffffu, sc_vb, o);
-      const int d = __shfl_up_sync(0xffffffffu, sc_units, o);
-      if (lane >= o) {
-        sc_take += a;
-        sc_pos += b;
-        sc_vb += c;
-        sc_units += d;
-      }
-    }
-    const int vtotal = __shfl_sync(0xffffffffu, sc_vb, 31);
-    const int voff = sc_vb - vb;
-    if (in) {
-      meta->g[lane] = G;
-      meta->voff[lane] = vb > 0 ? voff : -1;
-      meta->sbeg[lane] = sc_take - take;
-      meta->gpos[lane] = sc_pos - take * G.L;
-      meta->s0[lane] = lane == 0 ? st.s : 0;
-      meta->ubeg[lane] = sc_units - units;
-      if (lane == st.ng - 1) {
-        meta->sbeg[lane + 1] = sc_take;
-        meta->ubeg[lane + 1] = sc_units;
-      }
-    }
-    if (lane == 0) meta->st = st;
-    __threadfence_block();
-    __syncwarp();
-    const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
-    if (lane == 0) mbar_expect_tx(&full[slot], fbytes + (uint32_t)vtotal);
-    __syncwarp();
-    if (lane == 0) bulk_g2s(base, F + st.off, fbytes, &full[slot]);
-    if (vb > 0) bulk_g2s(base + kStageBytes + voff, vec + G.vec, (uint32_t)vb, &full[slot]);
-  }
-  if (!ok && lane == 0) {
-    // drain: copies already issued must land before the CTA's smem goes away
-    for (int k = max(0, issued - kStages); k < issued; ++k)
-      mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
-  }
-}
-
-// Sum W per-lane partial values across a team of W lanes (W a power of two,
-// teams aligned within the warp); lane i of the team ends with the total of
-// value i. Butterfly halving: W - 1 shuffles for W sums.
-template <class Acc, int W>
-__device__ __forceinline__ Acc transpose_reduce(Acc (&v)[32], int tl) {
-#pragma unroll
-  for (int off = W / 2; off >= 1; off >>= 1) {
-    const bool upper = (tl & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      const Acc send = upper ? v[i] : v[i + off];
-      const Acc keep = upper ? v[i + off] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
-// Batched V-apply of a short stage (one right-hand side): a work unit is W
-// consecutive columns of one block. The W lanes of a team own fixed row chunks
-// tl, tl + W, ... (up to KMAX), keep the matching x chunks in registers, and
-// accumulate all W columns before one transpose reduction, so each column costs
-// one shared-memory load per chunk and (W - 1) / W shuffles.
-template <class T, int W, int KMAX>
-__device__ __forceinline__ void consume_vbatch(const SlotMeta* meta, const char* base,
-                                               typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa,
-                                               const float* __restrict__ sb, int cw, int lane) {
-  using Acc = typename Fac<T>::acc;
-  constexpr int E = Fac<T>::E;
-  constexpr int PER_WARP = 32 / W;
-  constexpr int NTEAMS = kConsumerWarps * PER_WARP;
-  const int tl = lane % W;
-  const int ng = meta->st.ng;
-  const int nunits = meta->ubeg[ng];
-  int gi = 0;
-  for (int u0 = cw * PER_WARP; u0 < nunits; u0 += NTEAMS) {
-    const int u = u0 + lane / W;
-    const bool valid = u < nunits;
-    Acc acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = Acc(0);
-    int ncols = 0;
-    int64_t o0 = 0;
-    if (valid) {
-      while (u >= meta->ubeg[gi + 1]) ++gi;
-      const SegGroup& G = meta->g[gi];
-      const int C = G.L / E;
-      const int j0 = (u - meta->ubeg[gi]) * W;
-      const int take = meta->sbeg[gi + 1] - meta->sbeg[gi];
-      ncols = min(W, take - j0);
-      o0 = (int64_t)G.out0 + meta->s0[gi] + j0;
-      const Acc* xs = reinterpret_cast<const Acc*>(base + kStageBytes + meta->voff[gi]);
-      Acc xr[KMAX][E];
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        const int c = tl + k * W;
-        if (c < C) {
-          load_vec<Acc, E, 1>(xs + (int64_t)c * E, xr[k]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < E; ++e) xr[k][e] = Acc(0);
-        }
-      }
-      const char* cp = base + ((int64_t)meta->gpos[gi] + (int64_t)j0 * G.L) * sizeof(T);
-#pragma unroll
-      for (int jj = 0; jj < W; ++jj) {
-        if (jj < ncols) {
-#pragma unroll
-          for (int k = 0; k < KMAX; ++k) {
-            const int c = tl + k * W;
-            if (c < C) {
-              Acc f[E];
-              Fac<T>::chunk(cp + ((int64_t)jj * G.L + (int64_t)c * E) * sizeof(T), f);
-#pragma unroll
-              for (int e = 0; e < E; ++e) acc[jj] += f[e] * xr[k][e];
-            }
-          }
-        }
-      }
-    }
-    const Acc tot = transpose_reduce<Acc, W>(acc, tl);
-    if (valid && tl < ncols) {
-      const int64_t o = o0 + tl;
-      const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
-      out[o] = tot * sc;
-    }
-  }
-}
-
-// out[out0 + s] = scale(out0 + s) * sum_e F[seg s][e] vec[vec + e]  (x NR columns)
+// ------------------------------------------------------------- panel apply ----
+// Both low-rank applies are the same operation on a "panel": a matrix stored
+// as P consecutive lines of ld elements (ld a multiple of 16 bytes), and
+//   out[w] = sum_k line_k[w] * s_k      for w < R,
+// where s_k is the vector value of line k (NR right-hand sides).
+//   U-apply: a panel is rows [r0, r0 + R) of one box's U at one level, stored
+//            column-major over the concatenated columns of the box's low-rank
+//            IL blocks; line k = column k, s_k = t[vfirst + k], outputs are the
+//            contiguous ylev rows out0 + w.
+//   V-apply: a panel is up to kPanelWidth consecutive columns of the
+//            concatenated V factors of all low-rank IL blocks that share one
+//            source box J, stored row-major; line k = source point J0 + k,
+//            s_k = x_t[vfirst + k], output w is t[map[out0 + w]].
+// Threads own fixed 16-byte chunks of a line (rc) and a residue class of lines
+// (cg), so no reduction happens until the panel ends. Long panels are cut into
+// sub-panels of at most kSplitBytes so that CTAs get balanced work; a cut
+// panel writes per-sub-panel partial sums that k_combine adds in order.
 //
-// Warp 0 produces: per stage it waits for the slot to drain, writes the stage's
-// metadata (group descriptors, per-group segment and element prefixes, vector
-// slice offsets) into the slot, and issues the bulk copies of the factor data
-// and of the staged vector slices, all completing on the slot's `full`
-// barrier. Consumer warps read only shared memory on their critical path.
+// Per stage the producer bulk-copies the lines and their vector values into
+// the slot (the values with a lead pad to keep the copy 16-byte aligned), so
+// the consumers read only shared memory.
+constexpr int kMaxLines = 256;      // lines per stage (bounds the staged vector values)
+constexpr int kPanelWidth = 512;    // outputs per panel
+constexpr int kMetaBytes = 128;     // {Stage, Panel, lead pad}
+constexpr int kDynSmemMax = 232448 - 1024;
+
 template <class T, int NR>
-__global__ void __launch_bounds__(kSegThreads, 1)
-    k_segdot(const T* __restrict__ F, const SegGroup* __restrict__ groups, const Stage* __restrict__ stages,
-             const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ vec,
-             typename Fac<T>::acc* __restrict__ out, const float* __restrict__ sa, const float* __restrict__ sb,
-             int32_t* __restrict__ err) {
+struct PanelCfg {
   using Acc = typename Fac<T>::acc;
-  constexpr int E = Fac<T>::E;
-  constexpr int PIECE = kStageBytes / (int)sizeof(T);
-  constexpr bool STAGE_VEC = NR == 1;
-  extern __shared__ __align__(128) char smem[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  __shared__ Acc part[2][kConsumerWarps][NR];  // cross-warp partials, double-buffered
-  int pbuf = 0;
+  static constexpr int kScal = kMaxLines * NR * (int)sizeof(Acc) + 16;
+  static constexpr int kSlot = kStageBytes + kScal + kMetaBytes;
+  static constexpr int kRed = kConsumerWarps * 32 * 8 * (int)sizeof(Acc);
+  static constexpr int kFit = (kDynSmemMax - kRed) / kSlot;
+  static constexpr int kStagesN = kFit < 6 ? kFit : 6;
+  static constexpr size_t kSmem = (size_t)kStagesN * kSlot + kRed;
+  static_assert(kStagesN >= 3, "panel ring needs at least three slots");
+};
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  if (warp == 0) {
-    produce_segment_stages<T, NR>(F, groups, stages, q0, q1, vec, smem, full, empty, err, lane);
-    return;
-  }
-
-  // consumers
-  const int cw = warp - 1;
-  Acc lacc[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) lacc[r] = Acc(0);
-  for (int q = q0; q < q1; ++q) {
-    const int i = q - q0;
-    const int slot = i % kStages;
-    if (!mbar_wait(&full[slot], (i / kStages) & 1, err, ERR_WAIT_FULL)) return;
-    const char* base = smem + (size_t)slot * kSlotBytes;
-    const SlotMeta* meta = reinterpret_cast<const SlotMeta*>(base + kStageBytes + kVecBytes);
-    const Stage& st = meta->st;
-    if (st.piece < 0) {
-      if (st.pad > 0) {
-        if constexpr (NR == 1) {
-          if (st.last > 0) {
-            switch (st.pad * 8 + st.last) {  // (W, KMAX) chosen on the host
-#define HD_VB(W, K) case W * 8 + K: consume_vbatch<T, W, K>(meta, base, out, sa, sb, cw, lane); break;
-              HD_VB(1, 1) HD_VB(2, 1) HD_VB(2, 2) HD_VB(4, 1) HD_VB(4, 2) HD_VB(4, 4) HD_VB(8, 1) HD_VB(8, 2)
-              HD_VB(8, 4) HD_VB(16, 1) HD_VB(16, 2) HD_VB(16, 4) HD_VB(1, 2) HD_VB(1, 4) HD_VB(2, 4)
-#undef HD_VB
-              default: consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane); break;
-            }
-          } else {
-            consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
-          }
-        } else {
-          consume_short<T, NR>(meta, base, vec, out, sa, sb, cw, lane);
-        }
-      } else
-        consume_long<T, NR>(meta, base, vec, out, sa, sb, cw, lane, &part[0][0][0], pbuf);
-    } else {
-      // one piece of a long segment: all consumer warps share it; per-lane
-      // partials persist across pieces and are combined after the last one
-      const SegGroup& G = meta->g[0];
-      const int C = st.nelem / E;
-      const int64_t vbase = (int64_t)G.vec + (int64_t)st.piece * PIECE;
-      for (int c = cw * 32 + lane; c < C; c += kConsumerWarps * 32)
-        dot_chunk<T, NR>(base + (size_t)c * 16, vec + (vbase + (int64_t)c * E) * NR, lacc);
-      if (st.last) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          Acc a = lacc[r];
-          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          if (lane == 0) part[pbuf][cw][r] = a;
-          lacc[r] = Acc(0);
-        }
-        consumer_bar();
-        if (cw == 0 && lane == 0) {
-          Acc tot[NR];
-#pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            tot[r] = Acc(0);
-            for (int w = 0; w < kConsumerWarps; ++w) tot[r] += part[pbuf][w][r];
-          }
-          write_out<T, NR>((int64_t)G.out0 + st.s, tot, out, sa, sb);
-        }
-        pbuf ^= 1;
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[slot]);
-  }
-}
-
-// ----------------------------------------------------- U-apply (columns) ----
-// y_l(rows of a panel) = sum_k U[:, k] t[tfirst + k]. Threads own fixed row
-// chunks of the panel (chunk = 16 bytes of a column) and, when the panel is
-// short, one of CG column groups; they stream the panel's columns through the
-// same bulk-copy ring and accumulate in registers across stages. No reduction
-// is needed except, once per panel, across the CG column groups.
-constexpr int kUSlotBytes = kStageBytes + 128;  // factor columns + {Stage, Panel}
-struct USlotMeta {
+struct PanelMeta {
   Stage st;
   Panel P;
+  int32_t lead;  // elements of lead pad before the first staged vector value
 };
+static_assert(sizeof(PanelMeta) <= kMetaBytes, "panel metadata exceeds its slot area");
 
-template <class T, int NR>
+template <class T, int NR, bool VMODE>
 __global__ void __launch_bounds__(kSegThreads, 1)
-    k_ucols(const T* __restrict__ F, const Panel* __restrict__ panels, const Stage* __restrict__ stages,
-            const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ t,
-            typename Fac<T>::acc* __restrict__ ylev, int32_t* __restrict__ err) {
+    k_panel(const T* __restrict__ F, const Panel* __restrict__ panels, const Stage* __restrict__ stages,
+            const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ vec,
+            typename Fac<T>::acc* __restrict__ out, const int32_t* __restrict__ map, const float* __restrict__ sa,
+            const float* __restrict__ sb, typename Fac<T>::acc* __restrict__ part, int32_t* __restrict__ err) {
   using Acc = typename Fac<T>::acc;
+  using C = PanelCfg<T, NR>;
   constexpr int E = Fac<T>::E;
+  constexpr int NS = C::kStagesN;
   constexpr int NT = kConsumerWarps * 32;
+  constexpr int A1 = 16 / (int)sizeof(Acc);  // vector elements per 16 bytes
   extern __shared__ __align__(128) char smem[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)kStages * kUSlotBytes);  // NT * 8
+  __shared__ __align__(8) uint64_t full[NS], empty[NS];
+  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)NS * C::kSlot);  // NT * 8
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
     }
@@ -628,36 +271,72 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   __syncthreads();
 
   if (warp == 0) {
-    if (lane != 0) return;
+    // producer: stage descriptors a batch ahead, panel records one stage ahead
+    // (registers) and eight ahead (L2)
+    const uint64_t once = l2_evict_first();
     int issued = 0;
     bool ok = true;
+    StageRegs ca, cb;
+    load_stage_regs(ca, stages, q0 + lane, q1);
+    load_stage_regs(cb, stages, q0 + 32 + lane, q1);
+    Stage st_next = pick_stage(ca, cb, 0);
+    Panel P_next{};
+    if (q0 < q1) P_next = panels[st_next.g];
     for (int q = q0; q < q1; ++q, ++issued) {
-      const int slot = issued % kStages;
-      const int use = issued / kStages;
-      if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY)) {
-        ok = false;
-        break;
+      const int k = issued & 31;
+      const Stage st = st_next;
+      const Panel Pq = P_next;
+      if (q + 1 < q1) {
+        st_next = pick_stage(ca, cb, k + 1);
+        P_next = panels[st_next.g];
       }
-      char* base = smem + (size_t)slot * kUSlotBytes;
-      USlotMeta* meta = reinterpret_cast<USlotMeta*>(base + kStageBytes);
-      const Stage st = stages[q];
-      meta->st = st;
-      meta->P = panels[st.g];
-      __threadfence_block();
-      const uint32_t bytes = (uint32_t)st.nelem * sizeof(T);
-      mbar_expect_tx(&full[slot], bytes);
-      bulk_g2s(base, F + st.off, bytes, &full[slot]);
+      if (q + 8 < q1) {
+        const Stage sp = pick_stage(ca, cb, k + 8);
+        if (lane == 0) prefetch_l2(panels + sp.g);
+      }
+      if (k == 31) {
+        ca = cb;
+        load_stage_regs(cb, stages, q + 33 + lane, q1);
+      }
+      const int slot = issued % NS;
+      const int use = issued / NS;
+      if (use > 0) {
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&empty[slot], (use - 1) & 1, err, ERR_WAIT_EMPTY) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, w, 0)) {
+          ok = false;
+          break;
+        }
+      }
+      if (lane == 0) {
+        char* base = smem + (size_t)slot * C::kSlot;
+        PanelMeta* meta = reinterpret_cast<PanelMeta*>(base + kStageBytes + C::kScal);
+        const int64_t v0 = ((int64_t)Pq.vfirst + st.s) * NR;
+        const int a = (int)(v0 % A1);
+        meta->st = st;
+        meta->P = Pq;
+        meta->lead = a;
+        __threadfence_block();
+        const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
+        const uint32_t sbytes = (uint32_t)(((a + st.nseg * NR) * (int)sizeof(Acc) + 15) & ~15);
+        mbar_expect_tx(&full[slot], fbytes + sbytes);
+        bulk_g2s_once(base, F + st.off, fbytes, &full[slot], once);
+        bulk_g2s(base + kStageBytes, vec + (v0 - a), sbytes, &full[slot]);
+      }
+      __syncwarp();
     }
-    if (!ok) {
-      for (int k = max(0, issued - kStages); k < issued; ++k)
-        mbar_wait(&full[k % kStages], (k / kStages) & 1, err, ERR_WAIT_DRAIN);
+    if (!ok && lane == 0) {
+      // drain: copies already issued must land before the CTA's smem goes away
+      for (int k = max(0, issued - NS); k < issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, err, ERR_WAIT_DRAIN);
     }
     return;
   }
 
-  const int ct = (warp - 1) * 32 + lane;
-  // FP32 factors: compensated (Kahan) accumulation over the long column loops
-  constexpr bool KAHAN = std::is_same<T, float>::value;
+  const int cw = warp - 1;
+  const int ct = cw * 32 + lane;
+  // FP32 with one or two right-hand sides: compensated (Kahan) accumulation
+  // of the per-stage sums; otherwise plain accumulation (register budget)
+  constexpr bool KAHAN = std::is_same<T, float>::value && NR <= 2;
   Acc acc[E][NR], cmp[E][NR];
 #pragma unroll
   for (int e = 0; e < E; ++e)
@@ -668,12 +347,13 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     }
   for (int q = q0; q < q1; ++q) {
     const int i = q - q0;
-    const int slot = i % kStages;
-    if (!mbar_wait(&full[slot], (i / kStages) & 1, err, ERR_WAIT_FULL)) return;
-    const char* base = smem + (size_t)slot * kUSlotBytes;
-    const USlotMeta* meta = reinterpret_cast<const USlotMeta*>(base + kStageBytes);
+    const int slot = i % NS;
+    if (!mbar_wait(&full[slot], (i / NS) & 1, err, ERR_WAIT_FULL)) return;
+    const char* base = smem + (size_t)slot * C::kSlot;
+    const PanelMeta* meta = reinterpret_cast<const PanelMeta*>(base + kStageBytes + C::kScal);
     const Stage st = meta->st;
     const Panel P = meta->P;
+    const Acc* sv = reinterpret_cast<const Acc*>(base + kStageBytes) + meta->lead;
     const int RC = P.ld / E;
     int RCP = 1;
     while (RCP < RC) RCP <<= 1;
@@ -689,27 +369,40 @@ __global__ void __launch_bounds__(kSegThreads, 1)
         }
     }
     if (rc < RC) {
-      const Acc* tp = t + ((int64_t)P.tfirst + st.s) * NR;
-#pragma unroll 4
-      for (int k = cg; k < st.nseg; k += CG) {
-        Acc f[E];
-        Fac<T>::chunk(base + ((int64_t)k * P.ld + (int64_t)rc * E) * sizeof(T), f);
-        Acc tk[NR];
+      if constexpr (KAHAN) {
+        Acc sum[E][NR];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) tk[r] = tp[(int64_t)k * NR + r];
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) sum[e][r] = Acc(0);
+#pragma unroll 4
+        for (int k = cg; k < st.nseg; k += CG) {
+          Acc f[E];
+          Fac<T>::chunk(base + ((int64_t)k * P.ld + (int64_t)rc * E) * sizeof(T), f);
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sum[e][r] += f[e] * sv[k * NR + r];
+        }
 #pragma unroll
         for (int e = 0; e < E; ++e)
 #pragma unroll
           for (int r = 0; r < NR; ++r) {
-            if constexpr (KAHAN) {
-              const Acc y = f[e] * tk[r] - cmp[e][r];
-              const Acc s2 = acc[e][r] + y;
-              cmp[e][r] = (s2 - acc[e][r]) - y;
-              acc[e][r] = s2;
-            } else {
-              acc[e][r] += f[e] * tk[r];
-            }
+            const Acc y = sum[e][r] - cmp[e][r];
+            const Acc s2 = acc[e][r] + y;
+            cmp[e][r] = (s2 - acc[e][r]) - y;
+            acc[e][r] = s2;
           }
+      } else {
+#pragma unroll 4
+        for (int k = cg; k < st.nseg; k += CG) {
+          Acc f[E];
+          Fac<T>::chunk(base + ((int64_t)k * P.ld + (int64_t)rc * E) * sizeof(T), f);
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[e][r] += f[e] * sv[k * NR + r];
+        }
       }
     }
     if (st.last) {
@@ -719,30 +412,52 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 #pragma unroll
           for (int r = 0; r < NR; ++r) acc[e][r] -= cmp[e][r];
       }
-      if (CG > 1) {
-        // sum the CG column groups, 8 components per pass through `red`
+      // sum the CG line classes: lanes of one warp first, then across warps
+      for (int o = 16; o >= RCP; o >>= 1)
 #pragma unroll
-        for (int q0c = 0; q0c < E * NR; q0c += 8) {
+        for (int e = 0; e < E; ++e)
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (q0c + c < E * NR) red[(int64_t)ct * 8 + c] = acc[(q0c + c) / NR][(q0c + c) % NR];
+          for (int r = 0; r < NR; ++r) acc[e][r] += __shfl_xor_sync(0xffffffffu, acc[e][r], o);
+      const int WG = RCP > 32 ? RCP / 32 : 1;  // warps per line class
+      const int NG = kConsumerWarps / WG;      // line classes left after the warp step
+      const int sub = cw % WG, g = cw / WG;
+      const bool holds = lane < (RCP < 32 ? RCP : 32);
+      if (NG > 1) {
+#pragma unroll
+        for (int c0 = 0; c0 < E * NR; c0 += 8) {
+          if (holds)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c0 + c < E * NR) red[(int64_t)ct * 8 + c] = acc[(c0 + c) / NR][(c0 + c) % NR];
           consumer_bar();
-          if (cg == 0 && rc < RC) {
-            for (int g = 1; g < CG; ++g)
+          if (g == 0 && holds) {
+            for (int gg = 1; gg < NG; ++gg)
 #pragma unroll
               for (int c = 0; c < 8; ++c)
-                if (q0c + c < E * NR) acc[(q0c + c) / NR][(q0c + c) % NR] += red[(int64_t)(g * RCP + rc) * 8 + c];
+                if (c0 + c < E * NR)
+                  acc[(c0 + c) / NR][(c0 + c) % NR] += red[(int64_t)((gg * WG + sub) * 32 + lane) * 8 + c];
           }
           consumer_bar();
         }
       }
-      if (cg == 0 && rc < RC) {
+      const int orc = sub * 32 + lane;  // chunk held after the reduction
+      if (g == 0 && holds && orc < RC) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int row = rc * E + e;
-          if (row < P.R) {
+          const int w = orc * E + e;
+          if (w < P.R) {
+            if (P.part >= 0) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) ylev[((int64_t)P.out0 + row) * NR + r] = acc[e][r];
+              for (int r = 0; r < NR; ++r) part[((int64_t)P.part + w) * NR + r] = acc[e][r];
+            } else if constexpr (VMODE) {
+              const int64_t o = map[(int64_t)P.out0 + w];
+              const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
+#pragma unroll
+              for (int r = 0; r < NR; ++r) out[o * NR + r] = acc[e][r] * sc;
+            } else {
+#pragma unroll
+              for (int r = 0; r < NR; ++r) out[((int64_t)P.out0 + w) * NR + r] = acc[e][r];
+            }
           }
         }
       }
@@ -752,10 +467,25 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   }
 }
 
-// Dynamic shared memory of k_ucols: the ring plus the cross-group reduction buffer.
-template <class T, int NR>
-constexpr size_t usmem() {
-  return (size_t)kStages * kUSlotBytes + (size_t)kConsumerWarps * 32 * 8 * sizeof(typename Fac<T>::acc);
+// Sums of cut panels: out = sum over the sub-panels' partials, in sub-panel
+// order; V outputs go through the column map and the column scales.
+template <class Acc, int NR, bool VMODE>
+__global__ void __launch_bounds__(256) k_combine(const Split* __restrict__ splits, const Acc* __restrict__ part,
+                                                  Acc* __restrict__ out, const int32_t* __restrict__ map,
+                                                  const float* __restrict__ sa, const float* __restrict__ sb) {
+  const Split S = splits[blockIdx.x];
+  for (int idx = threadIdx.x; idx < S.R * NR; idx += blockDim.x) {
+    const int w = idx / NR, r = idx % NR;
+    Acc v = Acc(0);
+    for (int s = 0; s < S.nsplit; ++s) v += part[((int64_t)S.part + (int64_t)s * S.R + w) * NR + r];
+    if constexpr (VMODE) {
+      const int64_t o = map[(int64_t)S.out0 + w];
+      const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
+      out[o * NR + r] = v * sc;
+    } else {
+      out[((int64_t)S.out0 + w) * NR + r] = v;
+    }
+  }
 }
 
 // ------------------------------------------------------------- dense ----
@@ -998,40 +728,55 @@ __global__ void k_colscale(int64_t ncol, const int64_t* __restrict__ colU, const
   }
 }
 
-// V stream: one CTA per group (= block); segment k = column k, lead pad a.
+// U panels: one CTA per whole panel; element (k, w) is row r0 + w of global
+// column c0 + k, divided by the column's scale (zero for w >= R).
 template <class T>
-__global__ void k_packV(int64_t ngroups, const SegGroup* __restrict__ groups, const int32_t* __restrict__ lead,
-                        const int32_t* __restrict__ nrows, const int64_t* __restrict__ colV,
-                        const double* __restrict__ V64, const float* __restrict__ sv, T* __restrict__ out) {
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const SegGroup G = groups[g];
-    const int a = lead[g], n = nrows[g];
-    for (int k = 0; k < G.cnt; ++k) {
-      const int64_t c = (int64_t)G.out0 + k;
-      const double* col = V64 + colV[c];
-      const double inv = 1.0 / (double)sv[c];
-      T* dst = out + G.off + (int64_t)k * G.L;
-      for (int e = threadIdx.x; e < G.L; e += blockDim.x)
-        dst[e] = Fac<T>::from((e >= a && e < a + n) ? col[e - a] * inv : 0.0);
+__global__ void k_packU(int64_t npan, const LPanel* __restrict__ lp, const int32_t* __restrict__ prow0,
+                        const int32_t* __restrict__ pcol0, const int64_t* __restrict__ colU,
+                        const double* __restrict__ U64, const float* __restrict__ su, T* __restrict__ out) {
+  for (int64_t p = blockIdx.x; p < npan; p += gridDim.x) {
+    const LPanel L = lp[p];
+    const int r0 = prow0[p], c0 = pcol0[p];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)L.lines * L.ld; idx += blockDim.x) {
+      const int k = (int)(idx / L.ld), w = (int)(idx % L.ld);
+      const int64_t c = (int64_t)c0 + k;
+      const double v = w < L.R ? U64[colU[c] + r0 + w] / (double)su[c] : 0.0;
+      out[L.off + idx] = Fac<T>::from(v);
     }
   }
 }
 
-// U stream: one CTA per panel; element (r, k) of the column-major panel is row
-// r0 + r of global column tfirst + k, divided by its scale (zero below R).
+// V panels: one CTA per whole panel; element (k, w) is row k of global column
+// map[m0 + w], divided by its scale. 32 x 32 tiles through shared memory keep
+// both the column reads and the row writes contiguous.
 template <class T>
-__global__ void k_packU(int64_t npanels, const Panel* __restrict__ panels, const int32_t* __restrict__ prow0,
-                        const int64_t* __restrict__ colU, const double* __restrict__ U64,
-                        const float* __restrict__ su, T* __restrict__ out) {
-  for (int64_t p = blockIdx.x; p < npanels; p += gridDim.x) {
-    const Panel Pn = panels[p];
-    const int r0 = prow0[p];
-    for (int64_t idx = threadIdx.x; idx < (int64_t)Pn.P * Pn.ld; idx += blockDim.x) {
-      const int k = (int)(idx / Pn.ld), r = (int)(idx % Pn.ld);
-      const int64_t c = (int64_t)Pn.tfirst + k;
-      const double v = r < Pn.R ? U64[colU[c] + r0 + r] / (double)su[c] : 0.0;
-      out[Pn.off + idx] = Fac<T>::from(v);
-    }
+__global__ void __launch_bounds__(256) k_packV(int64_t npan, const LPanel* __restrict__ lp,
+                                               const int32_t* __restrict__ pm0, const int32_t* __restrict__ map,
+                                               const int64_t* __restrict__ colV, const double* __restrict__ V64,
+                                               const float* __restrict__ sv, T* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t p = blockIdx.x; p < npan; p += gridDim.x) {
+    const LPanel L = lp[p];
+    const int m0 = pm0[p];
+    for (int k0 = 0; k0 < L.lines; k0 += 32)
+      for (int w0 = 0; w0 < L.ld; w0 += 32) {
+        for (int ww = warp; ww < 32; ww += 8) {
+          const int w = w0 + ww, k = k0 + lane;
+          double v = 0.0;
+          if (w < L.R && k < L.lines) {
+            const int64_t c = map[m0 + w];
+            v = V64[colV[c] + k] / (double)sv[c];
+          }
+          tile[ww][lane] = v;
+        }
+        __syncthreads();
+        for (int kk = warp; kk < 32; kk += 8) {
+          const int k = k0 + kk, w = w0 + lane;
+          if (k < L.lines && w < L.ld) out[L.off + (int64_t)k * L.ld + w] = Fac<T>::from(tile[lane][kk]);
+        }
+        __syncthreads();
+      }
   }
 }
 
@@ -1062,114 +807,42 @@ int grid_warps(int64_t items, int sms) {
   return (int)ctas;
 }
 
-// Stage schedule of a stream: whole segments packed into stages of at most
-// kStageBytes; segments longer than a stage become pieces. CTA ranges are
-// balanced by bytes and never cut a long segment.
-void schedule(Stream& S, size_t esize, size_t vsize, int E, int ctas) {
-  const int64_t cap = kStageBytes / (int64_t)esize;
-  S.h_stages.clear();
-  Stage cur{0, 0, -1, 0, 0, -1, 0, 0, 0};
-  int64_t cur_vbytes = 0, cur_group = -1, cur_maxc = 0;
-  auto flush = [&]() {
-    if (cur.nseg > 0) {
-      if (cur.pad != 0) {
-        if (cur_maxc < kBatchChunks) {
-          // batched: W lanes own up to KMAX = 4 chunks each (W, KMAX powers of two)
-          int64_t w = 1;
-          while (w * 4 < cur_maxc) w <<= 1;
-          int64_t k = 1;
-          while (w * k < cur_maxc) k <<= 1;
-          cur.pad = (int32_t)w;
-          cur.last = (int32_t)k;
-        } else {
-          // one team of TS lanes per segment
-          int ts = 1;
-          while (ts < cur_maxc && ts < 32) ts <<= 1;
-          cur.pad = ts;
-          cur.last = 0;
-        }
-      }
-      S.h_stages.push_back(cur);
-    }
-    cur = Stage{0, 0, -1, 0, 0, -1, 0, 0, 0};
-    cur_vbytes = 0;
-    cur_group = -1;
-    cur_maxc = 0;
-  };
-  for (int64_t g = 0; g < (int64_t)S.h_groups.size(); ++g) {
-    const SegGroup& G = S.h_groups[g];
-    const int64_t C = G.L / E;
-    if (G.L > cap) {  // pieces
-      flush();
-      for (int s = 0; s < G.cnt; ++s)
-        for (int64_t p0 = 0, piece = 0; p0 < G.L; p0 += cap, ++piece) {
-          const int64_t len = std::min<int64_t>(cap, G.L - p0);
-          S.h_stages.push_back(Stage{G.off + (int64_t)s * G.L + p0, (int32_t)len, (int32_t)g, s, 0,
-                                     (int32_t)piece, p0 + len >= G.L ? 1 : 0, 1, 0});
-        }
-      continue;
-    }
-    if (C > kLongChunks) {  // long stages: whole segments of this group only
-      flush();
-      for (int s = 0; s < G.cnt; ++s) {
-        if (cur.nseg > 0 && cur.nelem + G.L > cap) flush();
-        if (cur.nseg == 0) cur = Stage{G.off + (int64_t)s * G.L, 0, (int32_t)g, s, 0, -1, 0, 1, 0};
-        cur.nelem += G.L;
-        cur.nseg += 1;
-      }
-      flush();
-      continue;
-    }
-    const int64_t vb = G.L * (int64_t)vsize <= kVecBytes ? G.L * (int64_t)vsize : 0;
-    for (int s = 0; s < G.cnt; ++s) {
-      const bool new_group = cur_group != g;
-      if (cur.nseg > 0 &&
-          (cur.nelem + G.L > cap || (new_group && (cur.ng + 1 > kGmax || cur_vbytes + vb > kVecBytes))))
-        flush();
-      if (cur.nseg == 0) {
-        cur.off = G.off + (int64_t)s * G.L;
-        cur.g = (int32_t)g;
-        cur.s = s;
-        cur.pad = 1;  // marks a short stage; the team size is set at flush
-      }
-      if (cur_group != g) {
-        cur.ng += 1;
-        cur_vbytes += vb;
-        cur_group = g;
-        cur_maxc = std::max(cur_maxc, C);
-      }
-      cur.nelem += G.L;
-      cur.nseg += 1;
-    }
-  }
-  flush();
-  // balance CTAs by bytes, cutting only between whole segments
-  int64_t total = 0;
-  for (const Stage& st : S.h_stages) total += st.nelem;
-  S.h_cta.assign(1, 0);
-  int64_t acc = 0;
-  const int64_t target = std::max<int64_t>(1, (total + ctas - 1) / ctas);
-  for (size_t q = 0; q < S.h_stages.size(); ++q) {
-    acc += S.h_stages[q].nelem;
-    const bool cut_ok = S.h_stages[q].piece < 0 || S.h_stages[q].last;
-    if (cut_ok && acc >= target * (int64_t)S.h_cta.size() && (int)S.h_cta.size() < ctas)
-      S.h_cta.push_back((int32_t)(q + 1));
-  }
-  if (S.h_cta.back() != (int32_t)S.h_stages.size()) S.h_cta.push_back((int32_t)S.h_stages.size());
-  S.ctas = (int)S.h_cta.size() - 1;
-}
+// Sub-panels, partial-sum splits and stages of a stream whose whole panels
+// (h_lp, with per-panel vector and output origins) are set. A panel longer than
+// kSplitBytes is cut into nearly equal sub-panels whose sums k_combine adds; a
+// stage holds up to kMaxLines whole lines and at most kStageBytes. CTA ranges
+// are balanced by bytes and cut only between sub-panels.
+constexpr int64_t kSplitBytes = 1 << 20;
 
-// Stage schedule of the U panels: whole columns of one panel per stage; CTA
-// ranges are balanced by bytes and cut only at panel boundaries.
-void schedule_panels(Stream& S, size_t esize, int ctas) {
+void schedule_stream(Stream& S, const std::vector<int32_t>& vfirst, const std::vector<int32_t>& out0,
+                     size_t esize, int ctas) {
+  S.h_panels.clear();
   S.h_stages.clear();
-  for (int64_t p = 0; p < (int64_t)S.h_panels.size(); ++p) {
-    const Panel& Pn = S.h_panels[p];
-    const int per = std::max<int>(1, (int)(kStageBytes / ((int64_t)Pn.ld * (int64_t)esize)));
-    for (int k0 = 0; k0 < Pn.P; k0 += per) {
-      const int nc = std::min(per, Pn.P - k0);
-      S.h_stages.push_back(Stage{Pn.off + (int64_t)k0 * Pn.ld, (int32_t)((int64_t)nc * Pn.ld), (int32_t)p, k0, nc,
-                                 -1, k0 + nc >= Pn.P ? 1 : 0, k0 == 0 ? 1 : 0, 0});
+  S.h_splits.clear();
+  S.part_rows = 0;
+  for (size_t p = 0; p < S.h_lp.size(); ++p) {
+    const LPanel& L = S.h_lp[p];
+    const int64_t line_bytes = (int64_t)L.ld * (int64_t)esize;
+    const int64_t maxl = std::max<int64_t>(1, kSplitBytes / line_bytes);
+    const int nsplit = (int)std::max<int64_t>(1, (L.lines + maxl - 1) / maxl);
+    const int per_split = (L.lines + nsplit - 1) / nsplit;
+    int32_t pbase = -1;
+    if (nsplit > 1) {
+      pbase = (int32_t)S.part_rows;
+      S.h_splits.push_back(Split{pbase, nsplit, L.R, out0[p]});
+      S.part_rows += (int64_t)nsplit * L.R;
+    }
+    const int per_stage = (int)std::min<int64_t>(kMaxLines, std::max<int64_t>(1, kStageBytes / line_bytes));
+    for (int s = 0, k0 = 0; k0 < L.lines; ++s, k0 += per_split) {
+      const int k1 = std::min(L.lines, k0 + per_split);
+      const int g = (int)S.h_panels.size();
+      S.h_panels.push_back(Panel{L.off + (int64_t)k0 * L.ld, L.ld, L.R, k1 - k0, vfirst[p] + k0, out0[p],
+                                 nsplit > 1 ? pbase + s * L.R : -1});
+      for (int k = 0; k < k1 - k0; k += per_stage) {
+        const int n = std::min(per_stage, k1 - k0 - k);
+        S.h_stages.push_back(Stage{L.off + (int64_t)(k0 + k) * L.ld, n * L.ld, g, k, n, -1,
+                                   k + n >= k1 - k0 ? 1 : 0, k == 0 ? 1 : 0, 0});
+      }
     }
   }
   int64_t total = 0;
@@ -1186,42 +859,72 @@ void schedule_panels(Stream& S, size_t esize, int ctas) {
   S.ctas = (int)S.h_cta.size() - 1;
 }
 
+int upload_stream(Stream& S, cudaStream_t st) {
+  HD_TRY(upload(S.panels, S.h_panels, st));
+  HD_TRY(upload(S.stages, S.h_stages, st));
+  HD_TRY(upload(S.cta, S.h_cta, st));
+  HD_TRY(upload(S.splits, S.h_splits, st));
+  return HODLRDD_OK;
+}
+
 template <class T>
 int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
                const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64) {
   cudaStream_t st = h->st;
-  using Acc = typename Fac<T>::acc;
   constexpr int E = Fac<T>::E;
-  const int A1 = 16 / (int)sizeof(Acc);  // vector alignment in elements
   const int64_t nblk = h->nblk;
   Plan& P = h->plan;
   auto roundE = [&](int64_t v) { return (v + E - 1) / E * E; };
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if ((int64_t)h->total_rank + 2 * kGuard >= INT32_MAX || (int64_t)h->kappa * h->N >= INT32_MAX) {
+    set_error("problem too large for 32-bit vector indices");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
 
-  // V groups: one per low-rank block
-  P.vs.h_groups.clear();
-  P.h_vgroup.assign(nblk, -1);
-  std::vector<int32_t> vlead, vrows;
+  // V panels: per level and source box, the concatenated columns of its
+  // low-rank IL blocks (in block order) in row-major panels of at most
+  // kPanelWidth columns; line k = source point J0 + k
+  P.vs.h_lp.clear();
+  P.h_vpanel.assign(nblk, -1);
+  P.h_vcol.assign(nblk, 0);
+  std::vector<int32_t> hmap, vfirst_v, out0_v;
+  hmap.reserve((size_t)h->total_rank);
   int64_t off = 0;
-  for (int64_t b = 0; b < nblk; ++b) {
-    const int p = h->h_rank[b];
-    if (p == 0) continue;
-    const int a = (int)(h->h_bJ0[b] % A1);
-    const int64_t L = roundE(a + h->h_bn[b]);
-    P.h_vgroup[b] = (int64_t)P.vs.h_groups.size();
-    P.vs.h_groups.push_back(SegGroup{off, (int32_t)L, p, h->h_bJ0[b] - a, (int32_t)h->h_toff[b]});
-    vlead.push_back(a);
-    vrows.push_back(h->h_bn[b]);
-    off += L * p;
+  for (int l = 1; l <= h->kappa; ++l) {
+    std::vector<int64_t> bs;
+    for (int64_t b = h->h_blk_off[l]; b < h->h_blk_off[l + 1]; ++b)
+      if (h->h_rank[b] > 0) bs.push_back(b);
+    std::stable_sort(bs.begin(), bs.end(), [&](int64_t a, int64_t b) { return h->h_bJ0[a] < h->h_bJ0[b]; });
+    for (size_t i = 0; i < bs.size();) {
+      size_t j = i;
+      const int32_t J0 = h->h_bJ0[bs[i]], n = h->h_bn[bs[i]];
+      const int64_t first = (int64_t)P.vs.h_lp.size(), m0 = (int64_t)hmap.size();
+      for (; j < bs.size() && h->h_bJ0[bs[j]] == J0; ++j) {
+        const int64_t b = bs[j];
+        P.h_vpanel[b] = first;
+        P.h_vcol[b] = (int32_t)((int64_t)hmap.size() - m0);
+        for (int k = 0; k < h->h_rank[b]; ++k) hmap.push_back((int32_t)(h->h_toff[b] + k));
+      }
+      const int64_t Q = (int64_t)hmap.size() - m0;
+      for (int64_t c0 = 0; c0 < Q; c0 += kPanelWidth) {
+        const int32_t R = (int32_t)std::min<int64_t>(kPanelWidth, Q - c0);
+        const int32_t ld = (int32_t)roundE(R);
+        P.vs.h_lp.push_back(LPanel{off, ld, R, n});
+        vfirst_v.push_back(J0);
+        out0_v.push_back((int32_t)(m0 + c0));
+        off += (int64_t)ld * n;
+      }
+      i = j;
+    }
   }
   P.vs.elems = off;
   // U panels: per (level, box) with low-rank blocks, rows in panels of at most
   // kPanelRows, column-major over the box's concatenated IL columns
-  P.us.h_panels.clear();
+  P.us.h_lp.clear();
   P.h_ugroup.assign(nblk, -1);
   P.h_ucol.assign(nblk, 0);
-  std::vector<int32_t> prow0;
+  std::vector<int32_t> prow0, vfirst_u, out0_u;
   off = 0;
   for (int l = 1; l <= h->kappa; ++l) {
     const Level& L = h->lv[l];
@@ -1231,7 +934,7 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
       for (int64_t b = b0; b < b1; ++b)
         if (h->h_rank[b] > 0) {
           if (tf < 0) tf = h->h_toff[b];
-          P.h_ugroup[b] = (int64_t)P.us.h_panels.size();
+          P.h_ugroup[b] = (int64_t)P.us.h_lp.size();
           P.h_ucol[b] = (int32_t)Pi;
           Pi += h->h_rank[b];
         }
@@ -1239,26 +942,24 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
       const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
       for (int32_t r0 = 0; r0 < m; r0 += kPanelRows) {
         const int32_t R = std::min(kPanelRows, m - r0);
-        const int64_t ld = roundE(R);
-        P.us.h_panels.push_back(Panel{off, (int32_t)ld, R, (int32_t)Pi, (int32_t)tf,
-                                      (int32_t)((int64_t)(l - 1) * h->N + I0 + r0), 0});
+        const int32_t ld = (int32_t)roundE(R);
+        P.us.h_lp.push_back(LPanel{off, ld, R, (int32_t)Pi});
         prow0.push_back(r0);
-        off += ld * Pi;
+        vfirst_u.push_back((int32_t)tf);
+        out0_u.push_back((int32_t)((int64_t)(l - 1) * h->N + I0 + r0));
+        off += (int64_t)ld * Pi;
       }
     }
   }
   P.us.elems = off;
-  if ((int64_t)h->total_rank + 2 * kGuard >= INT32_MAX || (int64_t)h->kappa * h->N >= INT32_MAX) {
-    set_error("problem too large for 32-bit vector indices");
-    return HODLRDD_ERR_UNSUPPORTED;
-  }
-  schedule(P.vs, sizeof(T), sizeof(Acc), E, sms);
-  schedule_panels(P.us, sizeof(T), sms);
+  schedule_stream(P.vs, vfirst_v, out0_v, sizeof(T), sms);
+  schedule_stream(P.us, vfirst_u, out0_u, sizeof(T), sms);
 
   // column maps, scales, packing
   const int64_t ncol = h->total_rank;
   DevBuf<int64_t> colU, colV, du64, dv64;
-  DevBuf<int32_t> crows_u, crows_v, dvlead, dvrows, dprow0;
+  DevBuf<int32_t> crows_u, crows_v, dprow0, dpcol0, dvm0;
+  DevBuf<LPanel> dvlp, dulp;
   std::vector<int32_t> hcru(std::max<int64_t>(ncol, 1)), hcrv(std::max<int64_t>(ncol, 1));
   for (int64_t b = 0; b < nblk; ++b)
     for (int k = 0; k < h->h_rank[b]; ++k) {
@@ -1271,31 +972,30 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
   HD_TRY(upload(dv64, voff64, st));
   HD_TRY(upload(crows_u, hcru, st));
   HD_TRY(upload(crows_v, hcrv, st));
-  HD_TRY(upload(dvlead, vlead, st));
-  HD_TRY(upload(dvrows, vrows, st));
   HD_TRY(upload(dprow0, prow0, st));
+  HD_TRY(upload(dpcol0, vfirst_u, st));
+  HD_TRY(upload(dvm0, out0_v, st));
+  HD_TRY(upload(dvlp, P.vs.h_lp, st));
+  HD_TRY(upload(dulp, P.us.h_lp, st));
+  HD_TRY(upload(P.vmap, hmap, st));
   HD_TRY(h->su.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(h->sv.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(P.vs.data.alloc((size_t)std::max<int64_t>(P.vs.elems, E) * sizeof(T)));
   HD_TRY(P.us.data.alloc((size_t)std::max<int64_t>(P.us.elems, E) * sizeof(T)));
-  HD_TRY(upload(P.vs.groups, P.vs.h_groups, st));
-  HD_TRY(upload(P.us.panels, P.us.h_panels, st));
-  HD_TRY(upload(P.vs.stages, P.vs.h_stages, st));
-  HD_TRY(upload(P.us.stages, P.us.h_stages, st));
-  HD_TRY(upload(P.vs.cta, P.vs.h_cta, st));
-  HD_TRY(upload(P.us.cta, P.us.h_cta, st));
+  HD_TRY(upload_stream(P.vs, st));
+  HD_TRY(upload_stream(P.us, st));
   if (ncol > 0) {
     k_colmap<<<(int)std::min<int64_t>((nblk + 255) / 256, 4096), 256, 0, st>>>(
         nblk, h->rank.p, h->bm.p, h->bn.p, h->toff.p, du64.p, dv64.p, colU.p, colV.p);
     k_colscale<<<grid_warps(ncol, sms), 256, 0, st>>>(ncol, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p,
                                                       Fac<T>::scaled ? 1 : 0, h->su.p, h->sv.p);
-    const int64_t nvg = (int64_t)P.vs.h_groups.size(), nup = (int64_t)P.us.h_panels.size();
-    if (nvg)
-      k_packV<T><<<(int)std::min<int64_t>(nvg, sms * 16), 256, 0, st>>>(
-          nvg, P.vs.groups.p, dvlead.p, dvrows.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(P.vs.data.p));
+    const int64_t nvp = (int64_t)P.vs.h_lp.size(), nup = (int64_t)P.us.h_lp.size();
+    if (nvp)
+      k_packV<T><<<(int)std::min<int64_t>(nvp, sms * 16), 256, 0, st>>>(
+          nvp, dvlp.p, dvm0.p, P.vmap.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(P.vs.data.p));
     if (nup)
-      k_packU<T><<<(int)std::min<int64_t>(nup, sms * 16), 256, 0, st>>>(nup, P.us.panels.p, dprow0.p, colU.p, U64.p,
-                                                                        h->su.p, reinterpret_cast<T*>(P.us.data.p));
+      k_packU<T><<<(int)std::min<int64_t>(nup, sms * 16), 256, 0, st>>>(
+          nup, dulp.p, dprow0.p, dpcol0.p, colU.p, U64.p, h->su.p, reinterpret_cast<T*>(P.us.data.p));
     HD_CUDA(cudaGetLastError());
   }
   HD_CUDA(cudaStreamSynchronize(st));
@@ -1464,6 +1164,8 @@ int alloc_workspace(hodlrdd_s* h) {
   HD_TRY(h->xt.alloc(((size_t)h->N + 2 * kGuard) * nr * acc));
   HD_TRY(h->tbuf.alloc(((size_t)h->total_rank + 2 * kGuard) * nr * acc));
   HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * nr * acc));
+  const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1});
+  HD_TRY(h->pbuf.alloc((size_t)prows * nr * acc));
   HD_TRY(h->err.alloc(1));
   HD_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes(), h->st));
   HD_CUDA(cudaMemsetAsync(h->tbuf.p, 0, h->tbuf.bytes(), h->st));
@@ -1589,22 +1291,34 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   h->launches += 1;
   if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
-  const size_t smem = (size_t)kStages * kSlotBytes;
+  using C = PanelCfg<T, NR>;
+  const float* sa = Fac<T>::scaled ? h->sv.p : nullptr;
+  const float* sb = Fac<T>::scaled ? h->su.p : nullptr;
+  Acc* pb = reinterpret_cast<Acc*>(h->pbuf.p);
   if (h->kappa >= 1) {
     HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)h->kappa * h->N * NR * sizeof(Acc), st));
     if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
-      k_segdot<T, NR><<<P.vs.ctas, kSegThreads, smem, st>>>(
-          reinterpret_cast<const T*>(P.vs.data.p), P.vs.groups.p, P.vs.stages.p, P.vs.cta.p, xt, t,
-          Fac<T>::scaled ? h->sv.p : nullptr, Fac<T>::scaled ? h->su.p : nullptr, h->err.p);
+      k_panel<T, NR, true><<<P.vs.ctas, kSegThreads, C::kSmem, st>>>(
+          reinterpret_cast<const T*>(P.vs.data.p), P.vs.panels.p, P.vs.stages.p, P.vs.cta.p, xt, t, P.vmap.p, sa, sb,
+          pb, h->err.p);
       h->launches += 1;
+      if (!P.vs.h_splits.empty()) {
+        k_combine<Acc, NR, true><<<(int)P.vs.h_splits.size(), 256, 0, st>>>(P.vs.splits.p, pb, t, P.vmap.p, sa, sb);
+        h->launches += 1;
+      }
     }
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
   if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
-    k_ucols<T, NR><<<P.us.ctas, kSegThreads, usmem<T, NR>(), st>>>(reinterpret_cast<const T*>(P.us.data.p),
-                                                                 P.us.panels.p, P.us.stages.p, P.us.cta.p, t, yl,
-                                                                 h->err.p);
+    k_panel<T, NR, false><<<P.us.ctas, kSegThreads, C::kSmem, st>>>(
+        reinterpret_cast<const T*>(P.us.data.p), P.us.panels.p, P.us.stages.p, P.us.cta.p, t, yl, nullptr, nullptr,
+        nullptr, pb, h->err.p);
     h->launches += 1;
+    if (!P.us.h_splits.empty()) {
+      k_combine<Acc, NR, false><<<(int)P.us.h_splits.size(), 256, 0, st>>>(P.us.splits.p, pb, yl, nullptr, nullptr,
+                                                                             nullptr);
+      h->launches += 1;
+    }
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
@@ -1621,19 +1335,22 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   return HODLRDD_OK;
 }
 
+template <class T, int NR>
+int set_smem_attr_nr() {
+  const int smem = (int)PanelCfg<T, NR>::kSmem;
+  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return HODLRDD_OK;
+}
+
 template <class T>
 int set_smem_attr() {
   static bool done = false;
   if (done) return HODLRDD_OK;
-  const int smem = kStages * kSlotBytes;
-  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  HD_CUDA(cudaFuncSetAttribute(k_segdot<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 1>()));
-  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 2>()));
-  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 4>()));
-  HD_CUDA(cudaFuncSetAttribute(k_ucols<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem<T, 8>()));
+  HD_TRY((set_smem_attr_nr<T, 1>()));
+  HD_TRY((set_smem_attr_nr<T, 2>()));
+  HD_TRY((set_smem_attr_nr<T, 4>()));
+  HD_TRY((set_smem_attr_nr<T, 8>()));
   done = true;
   return HODLRDD_OK;
 }
@@ -1679,18 +1396,20 @@ int unpack_typed(hodlrdd_s* h, int64_t b, double* U, double* V) {
   HD_CUDA(cudaMemcpy(sv.data(), h->sv.p + c0, p * sizeof(float), cudaMemcpyDeviceToHost));
   const int m = h->h_bm[b], n = h->h_bn[b];
   if (V) {
-    const SegGroup& G = P.vs.h_groups[P.h_vgroup[b]];
-    const int a = h->h_bJ0[b] - G.vec;  // lead pad
-    std::vector<T> buf((size_t)G.L * G.cnt);
-    HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.vs.data.p) + G.off, buf.size() * sizeof(T),
-                       cudaMemcpyDeviceToHost));
-    for (int k = 0; k < p; ++k)
-      for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = Fac<T>::to_host(buf[(size_t)k * G.L + a + j]) * sv[k];
+    // column k of the block is column h_vcol + k of its source box's panels
+    for (int k = 0; k < p; ++k) {
+      const int64_t pos = (int64_t)P.h_vcol[b] + k;
+      const LPanel& L = P.vs.h_lp[P.h_vpanel[b] + pos / kPanelWidth];
+      std::vector<T> buf(n);
+      HD_CUDA(cudaMemcpy2D(buf.data(), sizeof(T), reinterpret_cast<const T*>(P.vs.data.p) + L.off + pos % kPanelWidth,
+                           (size_t)L.ld * sizeof(T), sizeof(T), n, cudaMemcpyDeviceToHost));
+      for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = Fac<T>::to_host(buf[j]) * sv[k];
+    }
   }
   if (U) {
     // the box's panels are consecutive; the block's columns start at h_ucol[b]
     for (int r0 = 0; r0 < m; r0 += kPanelRows) {
-      const Panel& Pn = P.us.h_panels[P.h_ugroup[b] + r0 / kPanelRows];
+      const LPanel& Pn = P.us.h_lp[P.h_ugroup[b] + r0 / kPanelRows];
       std::vector<T> buf((size_t)Pn.ld * p);
       HD_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const T*>(P.us.data.p) + Pn.off + (int64_t)P.h_ucol[b] * Pn.ld,
                          buf.size() * sizeof(T), cudaMemcpyDeviceToHost));

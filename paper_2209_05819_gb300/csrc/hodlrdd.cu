@@ -120,9 +120,11 @@ void fill_stats(hodlrdd_s* h) {
                             h->bJ0.bytes() + h->bn.bytes() + h->rank.bytes() + h->dense.bytes() + h->toff.bytes() +
                             h->piv_sigma.bytes() + h->piv_tau.bytes() + h->su.bytes() + h->sv.bytes() +
                             h->xt.bytes() + h->tbuf.bytes() + h->ylev.bytes() + h->xstage.bytes() +
-                            h->ystage.bytes() + P.vs.data.bytes() + P.us.data.bytes() + P.vs.groups.bytes() +
-                            P.us.groups.bytes() + P.vs.stages.bytes() + P.us.stages.bytes() + P.tasks.bytes() +
-                            P.srcs.bytes() + P.soff.bytes());
+                            h->ystage.bytes() + P.vs.data.bytes() + P.us.data.bytes() + P.vs.panels.bytes() +
+                            P.us.panels.bytes() + P.vs.stages.bytes() + P.us.stages.bytes() + P.vs.splits.bytes() +
+                            P.us.splits.bytes() + P.vmap.bytes() + h->pbuf.bytes() + P.tasks.bytes() +
+                            P.srcs.bytes() + P.soff.bytes() + P.srcs4.bytes() + P.soff4.bytes());
+  for (auto& r : P.rel4) bytes += (int64_t)r.bytes();
   for (auto& r : P.rel) bytes += (int64_t)r.bytes();
   for (auto& L : h->lv)
     bytes += (int64_t)(L.bstart.bytes() + L.bkey.bytes() + L.cfirst.bytes() + L.iloff.bytes() + L.ilidx.bytes());

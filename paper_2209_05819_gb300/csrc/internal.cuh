@@ -210,57 +210,67 @@ struct Level {
 // stream. Segment s holds the factor row / column whose dot product with
 // vec[vec + e] (e < L) is written to out[out0 + s]. The first elements are a
 // zero lead pad that aligns vec + e to 16 bytes; the tail is zero padded.
-struct SegGroup {
-  int64_t off;   // element offset of segment 0 in the stream
-  int32_t L;     // padded segment length in elements (a multiple of 16 bytes)
-  int32_t cnt;   // segments in the run
-  int32_t vec;   // vector index of element 0 (vector offset minus lead pad)
-  int32_t out0;  // output index of segment 0
-};
-
-// One bulk copy into the shared-memory ring: whole segments (piece < 0) or
-// one piece of a segment longer than a stage.
+// One bulk copy into the shared-memory ring: lines [s, s + nseg) of sub-panel
+// g. `ng` marks the sub-panel's first stage and `last` its final one.
 struct Stage {
   int64_t off;    // element offset in the stream
   int32_t nelem;  // elements copied
-  int32_t g;      // group of the first segment
-  int32_t s;      // index of the first segment within the group
-  int32_t nseg;   // whole segments (piece < 0)
-  int32_t piece;  // piece of a long segment, or -1
-  int32_t last;   // 1 on a long segment's last piece
-  int32_t ng;     // groups touched by the stage (g .. g + ng - 1)
+  int32_t g;      // sub-panel
+  int32_t s;      // first line within the sub-panel
+  int32_t nseg;   // lines
+  int32_t piece;  // unused (-1)
+  int32_t last;   // 1 on the sub-panel's final stage
+  int32_t ng;     // 1 on the sub-panel's first stage
   int32_t pad;
 };
 
-// A row panel of one box's U at one level: rows [r0, r0 + R) of the box times
-// the P concatenated columns of its low-rank IL blocks, column-major with
-// leading dimension ld (R rounded up to 16 bytes). Column k multiplies
-// t[tfirst + k]; row r accumulates into ylev index out0 + r.
+// A sub-panel of a factor stream: P consecutive lines of ld elements (ld a
+// multiple of 16 bytes) whose R leading elements are live. Line k multiplies
+// the vector value at index vfirst + k. Outputs w < R go to output row out0 + w
+// (U-apply) or to t[map[out0 + w]] (V-apply), or, when the panel was cut into
+// several sub-panels, to the partial-sum rows part + w.
 struct Panel {
-  int64_t off;   // element offset in the stream
+  int64_t off;     // element offset of line 0 in the stream
   int32_t ld;
   int32_t R;
   int32_t P;
-  int32_t tfirst;
+  int32_t vfirst;
   int32_t out0;
-  int32_t pad;
+  int32_t part;    // -1: direct output
+};
+
+// A panel cut into nsplit sub-panels: output w = sum_s partial row part + s R + w.
+struct Split {
+  int32_t part;
+  int32_t nsplit;
+  int32_t R;
+  int32_t out0;
+};
+
+// A whole panel as stored (host side, for unpacking): element (k, w) at
+// off + k ld + w.
+struct LPanel {
+  int64_t off;
+  int32_t ld;
+  int32_t R;
+  int32_t lines;
 };
 
 // A factor stream with its stage schedule: stages [cta[c], cta[c+1]) belong to
-// persistent CTA c; a long segment or a U panel never straddles two CTAs.
-// For the U stream a Stage covers columns [s, s + nseg) of panel g; `last`
-// marks the panel's final stage and `ng` its first.
+// persistent CTA c; a sub-panel never straddles two CTAs.
 struct Stream {
   DevBuf<char> data;
   int64_t elems = 0;
-  std::vector<SegGroup> h_groups;
-  std::vector<Panel> h_panels;
+  std::vector<LPanel> h_lp;     // whole panels
+  std::vector<Panel> h_panels;  // sub-panels
   std::vector<Stage> h_stages;
   std::vector<int32_t> h_cta;
-  DevBuf<SegGroup> groups;
+  std::vector<Split> h_splits;
+  int64_t part_rows = 0;        // partial-sum rows of the cut panels
   DevBuf<Panel> panels;
   DevBuf<Stage> stages;
   DevBuf<int32_t> cta;
+  DevBuf<Split> splits;
   int ctas = 0;
 };
 
@@ -273,10 +283,12 @@ struct DenseLevel {
 };
 
 struct Plan {
-  Stream vs, us;                   // V columns; U rows per (level, box)
-  std::vector<int64_t> h_vgroup;   // block -> V group (or -1)
-  std::vector<int64_t> h_ugroup;   // block -> first U panel of its (level, box) (or -1)
-  std::vector<int32_t> h_ucol;     // block -> first column within its box's panels
+  Stream vs, us;                   // V per (level, source box); U per (level, target box)
+  DevBuf<int32_t> vmap;            // V panel outputs -> t index
+  std::vector<int64_t> h_vpanel;   // block -> first whole V panel of its source box (or -1)
+  std::vector<int32_t> h_vcol;     // block -> first column within its source box's V panels
+  std::vector<int64_t> h_ugroup;   // block -> first whole U panel of its (level, box) (or -1)
+  std::vector<int32_t> h_ucol;     // block -> first column within its box's U panels
   DevBuf<int4> tasks;              // {I0, m, src_begin, src_end}
   DevBuf<int2> srcs;               // {J0, n}
   DevBuf<float> soff;              // d per source
@@ -339,6 +351,7 @@ struct hodlrdd_s {
   // matvec workspace (right-hand sides are processed in chunks of at most 8);
   // xt and tbuf carry zero guards of kGuard elements on both sides
   hd::DevBuf<char> xt, tbuf, ylev, xstage, ystage;
+  hd::DevBuf<char> pbuf;       // partial sums of cut panels
   hd::DevBuf<int32_t> err;     // device error word of bounded waits
 
   // tracing: events between matvec stages, resolved by hodlrdd_get_profile
