@@ -79,12 +79,19 @@ typedef struct hodlrdd_options {
                            exactly by evaluating the kernel on the fly (no storage).
                            0: every IL block is applied through its ACA factors, as
                            in Algorithm 2. */
-  int max_nrhs;         /* workspace is sized for nrhs <= max_nrhs (default 16);
-                           larger nrhs is processed in chunks */
+  int max_nrhs;         /* >= 1 (default 8). Right-hand sides are processed in chunks
+                           of at most 8 through a workspace sized at build; any nrhs
+                           is accepted */
   int aca_max_rank;     /* cap on the ACA rank of blocks larger than 2048 rows or
                            columns (default 1024); a block that does not converge
                            within its cap is applied exactly instead */
-  int reserved[8];      /* set to 0 */
+  int near_mode;        /* leaf-level dense work of the packed path (FP32/FP16/BF16,
+                           d <= 3, one right-hand side): 0 (default) chooses by work,
+                           1 = one tile per parent box over the children of the
+                           parent and of its neighbours sharing a d' >= 1 face (low-rank
+                           leaf IL blocks inside the tile are subtracted), 2 = one task
+                           per leaf box over its near and dense IL lists */
+  int reserved[7];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64
@@ -113,8 +120,8 @@ typedef struct hodlrdd_stats {
   double t_pack_ms;          /* factor packing / precision conversion, task lists */
   double t_build_ms;         /* whole build, wall clock */
   int64_t device_bytes;      /* device memory held by the handle */
-  int64_t factor_bytes_u;    /* bytes of the packed U stream (rows per level and box) */
-  int64_t factor_bytes_v;    /* bytes of the packed V stream (columns per block) */
+  int64_t factor_bytes_u;    /* bytes of the U panels (per level and target box) */
+  int64_t factor_bytes_v;    /* bytes of the V panels (per level and source box) */
   int64_t total_rank;        /* sum of ranks: length of the t vector of the V-apply */
 } hodlrdd_stats;
 

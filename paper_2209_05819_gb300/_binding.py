@@ -31,7 +31,7 @@ class HodlrddError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
-                ("aca_max_rank", C.c_int), ("reserved", C.c_int * 8)]
+                ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Stats(C.Structure):
@@ -138,7 +138,7 @@ class Handle:
 
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
-                 aca_max_rank: int = 1024):
+                 aca_max_rank: int = 1024, near_mode: int = 0):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -153,6 +153,7 @@ class Handle:
         opt.dense_if_cheaper = 1 if dense_if_cheaper else 0
         opt.max_nrhs = int(max_nrhs)
         opt.aca_max_rank = int(aca_max_rank)
+        opt.near_mode = int(near_mode)
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:

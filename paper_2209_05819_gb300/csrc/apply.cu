@@ -345,6 +345,10 @@ __global__ void __launch_bounds__(kSegThreads, 1)
       acc[e][r] = Acc(0);
       cmp[e][r] = Acc(0);
     }
+  // V-apply writers (line class 0) fetch their output indices and scales when
+  // a panel starts, so the panel's end does not wait on them
+  int32_t oidx[VMODE ? E : 1];
+  Acc oscl[VMODE ? E : 1];
   for (int q = q0; q < q1; ++q) {
     const int i = q - q0;
     const int slot = i % NS;
@@ -367,6 +371,16 @@ __global__ void __launch_bounds__(kSegThreads, 1)
           acc[e][r] = Acc(0);
           cmp[e][r] = Acc(0);
         }
+      if constexpr (VMODE) {
+        if (cg == 0 && rc < RC && P.part < 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int w = rc * E + e;
+            oidx[e] = w < P.R ? map[(int64_t)P.out0 + w] : 0;
+            oscl[e] = (sa && w < P.R) ? (Acc)(sa[oidx[e]] * sb[oidx[e]]) : Acc(1);
+          }
+        }
+      }
     }
     if (rc < RC) {
       if constexpr (KAHAN) {
@@ -450,10 +464,8 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 #pragma unroll
               for (int r = 0; r < NR; ++r) part[((int64_t)P.part + w) * NR + r] = acc[e][r];
             } else if constexpr (VMODE) {
-              const int64_t o = map[(int64_t)P.out0 + w];
-              const Acc sc = sa ? (Acc)(sa[o] * sb[o]) : Acc(1);
 #pragma unroll
-              for (int r = 0; r < NR; ++r) out[o * NR + r] = acc[e][r] * sc;
+              for (int r = 0; r < NR; ++r) out[(int64_t)oidx[e] * NR + r] = acc[e][r] * oscl[e];
             } else {
 #pragma unroll
               for (int r = 0; r < NR; ++r) out[((int64_t)P.out0 + w) * NR + r] = acc[e][r];
@@ -596,88 +608,145 @@ __device__ __forceinline__ float f32k(float s, float c) {
   else return rsqrtf(1.0f + sqrtf(s));
 }
 
+// Packed dense work (FP32, d <= 3, one right-hand side), one CTA per task.
+// A task is up to kTileRows target rows [I0, I0 + m) of one box I at level l
+// and a list of source ranges J. Coordinates are box-relative at level l and
+// kept as FP32 pairs hi + lo (split from FP64 at build); a source is moved into
+// I's frame by the exact FP32 offset (c_J - c_I) h_l with an error-free sum, so
+// x_i - x_j = (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy of the
+// distance itself. Sources are staged through shared memory in chunks planned
+// on the host (entry .z = position in the chunk, .w on a chunk's first entry =
+// the entry after the chunk); then G target rows times S source stripes sweep
+// the chunk.
+//   FINAL:  y[perm[i]] = scale * sum + diag * x_i + sum over levels of y_l(i)
+//   else:   ylev_l[i] += scale * sum
+constexpr int kTileThreads = 256;
+constexpr int kTileRows = 256;
+constexpr int kTileCap = 1024;
+
+// a + b = s + e exactly (Knuth's two-sum).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+template <int D>
+__device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, const float4& sh, const float4& sl) {
+  float t = (th.x - sh.x) + (tl.x - sl.x);
+  float s = t * t;
+  if (D > 1) {
+    t = (th.y - sh.y) + (tl.y - sl.y);
+    s = fmaf(t, t, s);
+  }
+  if (D > 2) {
+    t = (th.z - sh.z) + (tl.z - sl.z);
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
 template <int D, int KID, bool FINAL>
-__global__ void __launch_bounds__(256) k_dense4(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
-                                                const int4* __restrict__ srcs, const float4* __restrict__ soff,
-                                                const float4* __restrict__ P, int64_t N, float kc, float kscale,
-                                                float kdiag, float* __restrict__ ylev_l,
-                                                const float* __restrict__ ylev, int kappa,
-                                                const int32_t* __restrict__ perm, float* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = t0 + warp; it < t1; it += nwarps) {
-    const int4 task = tasks[it];
-    const int I0 = task.x, m = task.y;
+__global__ void __launch_bounds__(kTileThreads) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
+                                                      const int4* __restrict__ srcs, const float4* __restrict__ soff,
+                                                      const float4* __restrict__ Hi, const float4* __restrict__ Lo,
+                                                      const float* __restrict__ xt, int64_t N, float kc,
+                                                      float kscale, float kdiag, float* __restrict__ ylev_l,
+                                                      const float* __restrict__ ylev, int kappa,
+                                                      const int32_t* __restrict__ perm, float* __restrict__ y) {
+  __shared__ float4 shi[kTileCap];  // hi coordinates in the task's frame, x_j in .w
+  __shared__ float4 slo[kTileCap];  // lo coordinates
+  __shared__ float red[kTileThreads];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
+    const int4 T = tasks[it];
     int G = 1;
-    while (G < m && G < 32) G <<= 1;
-    const int S = 32 / G;
-    const int gi = lane % G, stripe = lane / G;
-    for (int g0 = 0; g0 < m; g0 += G) {
-      const int row = I0 + g0 + gi;
-      const bool valid = g0 + gi < m;
-      const float4 xr = valid ? P[row] : make_float4(0.f, 0.f, 0.f, 0.f);
-      float acc0 = 0.f, acc1 = 0.f;
-      for (int e = task.z; e < task.w; ++e) {
-        const int4 sj = srcs[e];
-        const float4 of = soff[e];
-        const int j1 = sj.x + sj.y;
-        int j = sj.x + stripe;
-        for (; j + S < j1; j += 2 * S) {  // two independent pairs in flight
-          const float4 p0 = P[j], p1 = P[j + S];
-          float s0 = 0.f, s1 = 0.f, t;
-          t = (xr.x - p0.x) + of.x; s0 = fmaf(t, t, s0);
-          t = (xr.x - p1.x) + of.x; s1 = fmaf(t, t, s1);
-          if (D > 1) {
-            t = (xr.y - p0.y) + of.y; s0 = fmaf(t, t, s0);
-            t = (xr.y - p1.y) + of.y; s1 = fmaf(t, t, s1);
-          }
-          if (D > 2) {
-            t = (xr.z - p0.z) + of.z; s0 = fmaf(t, t, s0);
-            t = (xr.z - p1.z) + of.z; s1 = fmaf(t, t, s1);
-          }
-          acc0 = fmaf(f32k<KID>(s0, kc), p0.w, acc0);
-          acc1 = fmaf(f32k<KID>(s1, kc), p1.w, acc1);
-        }
-        if (j < j1) {
-          const float4 p0 = P[j];
-          float s0 = 0.f, t;
-          t = (xr.x - p0.x) + of.x; s0 = fmaf(t, t, s0);
-          if (D > 1) { t = (xr.y - p0.y) + of.y; s0 = fmaf(t, t, s0); }
-          if (D > 2) { t = (xr.z - p0.z) + of.z; s0 = fmaf(t, t, s0); }
-          acc0 = fmaf(f32k<KID>(s0, kc), p0.w, acc0);
+    while (G < T.y) G <<= 1;
+    const int S = kTileThreads / G;
+    const int gi = tid % G, stripe = tid / G;
+    const bool valid = gi < T.y;
+    const int row = T.x + gi;
+    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+    float xw = 0.f;
+    if (valid) {
+      th = Hi[row];
+      tl = Lo[row];
+      xw = xt[row];
+    }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int e = T.z; e < T.w;) {
+      const int e1 = srcs[e].w;
+      __syncthreads();  // the previous chunk has been consumed
+      for (int b = e + warp; b < e1; b += kTileThreads / 32) {
+        const int4 sj = srcs[b];
+        const float4 of = soff[b];
+        for (int k = lane; k < sj.y; k += 32) {
+          const float4 h = Hi[sj.x + k], l = Lo[sj.x + k];
+          float ex, ey, ez;
+          const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
+          shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
+          slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
         }
       }
-      float acc = acc0 + acc1;
-      for (int o = G; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (stripe == 0 && valid) {
-        if constexpr (FINAL) {
-          float tot = kscale * acc + kdiag * xr.w;
-          for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
-          y[perm[row]] = tot;
-        } else {
-          ylev_l[row] += kscale * acc;
-        }
+      const int4 lastb = srcs[e1 - 1];
+      const int n = lastb.z + lastb.y;
+      __syncthreads();
+      int f = stripe;
+      for (; f + 3 * S < n; f += 4 * S) {
+        const float4 h0 = shi[f], h1 = shi[f + S], h2 = shi[f + 2 * S], h3 = shi[f + 3 * S];
+        const float4 l0 = slo[f], l1 = slo[f + S], l2 = slo[f + 2 * S], l3 = slo[f + 3 * S];
+        a0 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h0, l0), kc), h0.w, a0);
+        a1 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h1, l1), kc), h1.w, a1);
+        a2 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h2, l2), kc), h2.w, a2);
+        a3 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h3, l3), kc), h3.w, a3);
+      }
+      for (; f < n; f += S) {
+        const float4 h0 = shi[f], l0 = slo[f];
+        a0 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h0, l0), kc), h0.w, a0);
+      }
+      e = e1;
+    }
+    red[tid] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (stripe == 0 && valid) {
+      float acc = 0.f;
+      for (int s = 0; s < S; ++s) acc += red[s * G + gi];
+      if constexpr (FINAL) {
+        float tot = kscale * acc + kdiag * xw;
+        for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
+        y[perm[row]] = tot;
+      } else {
+        ylev_l[row] += kscale * acc;
       }
     }
+    __syncthreads();  // red and the staging arrays are reused by the next task
   }
 }
 
-// One right-hand side with packed points: x_t[i] and the .w lane of every
-// packed level array.
-template <class IO>
-__global__ void k_gather_pack(const IO* __restrict__ x, const int32_t* __restrict__ perm, int64_t N, int ldx,
-                              int c0, float* __restrict__ xt, float4* const* __restrict__ packs, int npacks) {
+// Box-relative coordinates at level l as FP32 pairs: x - (lo + c_box h) = hi + lo
+// (the difference formed in FP64).
+__global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int l, const int32_t* __restrict__ bstart,
+                          const uint64_t* __restrict__ bkey, int64_t nb, const double* __restrict__ lo, double h,
+                          float4* __restrict__ Hi, float4* __restrict__ Lo) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = (float)x[(int64_t)perm[i] * ldx + c0];
-    xt[i] = v;
-    for (int k = 0; k < npacks; ++k) packs[k][i].w = v;
+    int64_t a = 0, b = nb;  // last box with bstart <= i
+    while (b - a > 1) {
+      const int64_t mid = (a + b) >> 1;
+      if (bstart[mid] <= i) a = mid; else b = mid;
+    }
+    const uint64_t key = bkey[a];
+    float hv[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < d && k < 3; ++k) {
+      int64_t c = 0;
+      for (int bit = 0; bit < l; ++bit) c |= (int64_t)((key >> (d * bit + k)) & 1u) << bit;
+      const double v = p64[(int64_t)k * N + i] - (lo[k] + (double)c * h);
+      hv[k] = __double2float_rn(v);
+      lv[k] = __double2float_rn(v - (double)hv[k]);
+    }
+    Hi[i] = make_float4(hv[0], hv[1], hv[2], 0.f);
+    Lo[i] = make_float4(lv[0], lv[1], lv[2], 0.f);
   }
-}
-
-__global__ void k_pack_rel4(const float* __restrict__ rel, int64_t N, int d, float4* __restrict__ out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = make_float4(rel[i], d > 1 ? rel[N + i] : 0.f, d > 2 ? rel[2 * N + i] : 0.f, 0.f);
 }
 
 template <class Acc, class IO, int NR>
@@ -1109,6 +1178,159 @@ int build_plan(hodlrdd_s* h) {
     set_error("dense source list too long");
     return HODLRDD_ERR_UNSUPPORTED;
   }
+  // Packed plan (FP32 arithmetic, d <= 3, one right-hand side): one CTA per
+  // task of at most kTileRows rows; sources staged in chunks of kTileCap points.
+  std::vector<int4> t4, s4;
+  std::vector<float4> o4;                  // per source entry: (c_J - c_I) h_l
+  std::vector<char> need4(h->kappa + 1, 0);
+  std::vector<std::pair<int2, float4>> sl; // current task's sources: {J0, n}, offset
+  P.packed_pairs = 0;
+  auto add_task = [&](int32_t I0, int32_t m) {
+    int64_t nsrc = 0;
+    for (auto& so : sl) nsrc += so.first.y;
+    for (int32_t r0 = 0; r0 < m; r0 += kTileRows) {
+      const int32_t s0 = (int32_t)s4.size();
+      int32_t first = s0, pos = 0;
+      for (auto& so : sl)
+        for (int32_t p0 = 0; p0 < so.first.y; p0 += kTileCap) {
+          const int32_t np = std::min(kTileCap, so.first.y - p0);
+          if (pos + np > kTileCap) {
+            s4[first].w = (int32_t)s4.size();
+            first = (int32_t)s4.size();
+            pos = 0;
+          }
+          s4.push_back(make_int4(so.first.x + p0, np, pos, 0));
+          o4.push_back(so.second);
+          pos += np;
+        }
+      if ((int32_t)s4.size() > first) s4[first].w = (int32_t)s4.size();
+      const int32_t mr = std::min(kTileRows, m - r0);
+      t4.push_back(make_int4(I0 + r0, mr, s0, (int32_t)s4.size()));
+      P.packed_pairs += (int64_t)mr * nsrc;
+    }
+  };
+  auto box_src = [&](int l, int64_t I, int64_t J) {  // source box J in target box I's frame
+    const Level& L = h->lv[l];
+    int64_t cI[kMaxDim], cJ[kMaxDim];
+    coords(l, I, cI);
+    coords(l, J, cJ);
+    float v[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < d && k < 3; ++k) v[k] = (float)((double)(cJ[k] - cI[k]) * P.h_box[l]);
+    sl.push_back({make_int2(L.h_bstart[J], L.h_bstart[J + 1] - L.h_bstart[J]), make_float4(v[0], v[1], v[2], 0.f)});
+    need4[l] = 1;
+  };
+  P.coarse4.clear();
+  if (!f64 && d <= 3) {
+    for (int l = 1; l < h->kappa; ++l) {
+      const Level& L = h->lv[l];
+      DenseLevel DL;
+      DL.level = l;
+      DL.t0 = (int64_t)t4.size();
+      for (int64_t i = 0; i < L.nb; ++i) {
+        sl.clear();
+        const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
+        for (int64_t b = b0; b < b1; ++b)
+          if (h->h_dense[b]) box_src(l, i, h->h_bsj[b]);
+        if (!sl.empty()) add_task(L.h_bstart[i], L.h_bstart[i + 1] - L.h_bstart[i]);
+      }
+      DL.t1 = (int64_t)t4.size();
+      if (DL.t1 > DL.t0) P.coarse4.push_back(DL);
+    }
+    // leaf level: tiles per parent box, or lists per leaf box, by work
+    const int lk = h->kappa;
+    const Level& LK = h->lv[lk];
+    int64_t list_pairs = 0, excl_pairs = 0, tile_pairs = 0;
+    for (int64_t i = 0; i < LK.nb; ++i) {
+      const int64_t m = LK.h_bstart[i + 1] - LK.h_bstart[i];
+      for (int32_t e = h->h_nearoff[i]; e < h->h_nearoff[i + 1]; ++e) {
+        const int64_t J = h->h_nearidx[e];
+        list_pairs += m * (LK.h_bstart[J + 1] - LK.h_bstart[J]);
+      }
+      if (lk >= 1) {
+        const int64_t b0 = h->h_blk_off[lk] + LK.h_iloff[i], b1 = h->h_blk_off[lk] + LK.h_iloff[i + 1];
+        for (int64_t b = b0; b < b1; ++b) (h->h_dense[b] ? list_pairs : excl_pairs) += m * h->h_bn[b];
+      }
+    }
+    // neighbours of parent boxes sharing a d' >= 1 face, and the box itself
+    std::vector<std::vector<int64_t>> nbr;
+    if (lk >= 1) {
+      const int lp = lk - 1;
+      const Level& LP = h->lv[lp];
+      nbr.resize(LP.nb);
+      const int64_t side = int64_t(1) << lp;
+      int64_t nd = 1;
+      for (int k = 0; k < d; ++k) nd *= 3;
+      for (int64_t pb = 0; pb < LP.nb; ++pb) {
+        int64_t c[kMaxDim], q[kMaxDim];
+        coords(lp, pb, c);
+        for (int64_t code = 0; code < nd; ++code) {
+          int64_t t = code;
+          bool inside = true, some_zero = false;
+          for (int k = 0; k < d; ++k) {
+            const int64_t delta = t % 3 - 1;
+            t /= 3;
+            q[k] = c[k] + delta;
+            some_zero |= delta == 0;
+            inside &= q[k] >= 0 && q[k] < side;
+          }
+          if (!inside || !some_zero) continue;
+          uint64_t key = 0;
+          for (int bit = 0; bit < lp; ++bit)
+            for (int k = 0; k < d; ++k) key |= (uint64_t)((q[k] >> bit) & 1) << (d * bit + k);
+          const auto it = std::lower_bound(LP.h_bkey.begin(), LP.h_bkey.begin() + LP.nb, key);
+          if (it != LP.h_bkey.begin() + LP.nb && *it == key) nbr[pb].push_back(it - LP.h_bkey.begin());
+        }
+        std::sort(nbr[pb].begin(), nbr[pb].end());
+        int64_t nsrc = 0;
+        for (int64_t qb : nbr[pb]) nsrc += LP.h_bstart[qb + 1] - LP.h_bstart[qb];
+        tile_pairs += (int64_t)(LP.h_bstart[pb + 1] - LP.h_bstart[pb]) * nsrc;
+      }
+    }
+    const int mode = h->opt.near_mode;
+    P.tiles = lk >= 1 && (mode == 1 || (mode == 0 && (double)(tile_pairs + excl_pairs) <= 1.25 * (double)list_pairs));
+    if (P.tiles) {
+      // subtract the low-rank (or zero-rank) leaf IL blocks the tiles include
+      P.excl4.level = lk;
+      P.excl4.t0 = (int64_t)t4.size();
+      for (int64_t i = 0; i < LK.nb; ++i) {
+        sl.clear();
+        const int64_t b0 = h->h_blk_off[lk] + LK.h_iloff[i], b1 = h->h_blk_off[lk] + LK.h_iloff[i + 1];
+        for (int64_t b = b0; b < b1; ++b)
+          if (!h->h_dense[b]) box_src(lk, i, h->h_bsj[b]);
+        if (!sl.empty()) add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
+      }
+      P.excl4.t1 = (int64_t)t4.size();
+      const int lp = lk - 1;
+      const Level& LP = h->lv[lp];
+      P.leaf4.level = lp;
+      P.leaf4.t0 = (int64_t)t4.size();
+      for (int64_t pb = 0; pb < LP.nb; ++pb) {
+        sl.clear();
+        for (int64_t qb : nbr[pb]) box_src(lp, pb, qb);
+        add_task(LP.h_bstart[pb], LP.h_bstart[pb + 1] - LP.h_bstart[pb]);
+      }
+      P.leaf4.t1 = (int64_t)t4.size();
+    } else {
+      P.excl4 = DenseLevel{lk, 0, 0};
+      P.leaf4.level = lk;
+      P.leaf4.t0 = (int64_t)t4.size();
+      for (int64_t i = 0; i < LK.nb; ++i) {
+        sl.clear();
+        for (int32_t e = h->h_nearoff[i]; e < h->h_nearoff[i + 1]; ++e) box_src(lk, i, h->h_nearidx[e]);
+        if (lk >= 1) {
+          const int64_t b0 = h->h_blk_off[lk] + LK.h_iloff[i], b1 = h->h_blk_off[lk] + LK.h_iloff[i + 1];
+          for (int64_t b = b0; b < b1; ++b)
+            if (h->h_dense[b]) box_src(lk, i, h->h_bsj[b]);
+        }
+        add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
+      }
+      P.leaf4.t1 = (int64_t)t4.size();
+    }
+    if ((int64_t)s4.size() >= INT32_MAX) {
+      set_error("packed source list too long");
+      return HODLRDD_ERR_UNSUPPORTED;
+    }
+  }
   cudaStream_t st = h->st;
   HD_TRY(upload(P.tasks, tasks, st));
   HD_TRY(upload(P.srcs, srcs, st));
@@ -1128,27 +1350,20 @@ int build_plan(hodlrdd_s* h) {
       HD_CUDA(cudaGetLastError());
     }
     if (d <= 3) {
-      P.rel4.clear();
-      P.rel4.resize(h->kappa + 1);
-      std::vector<int32_t> lvls;
-      std::vector<float4*> ptrs;
+      P.hi4.clear();
+      P.lo4.clear();
+      P.hi4.resize(h->kappa + 1);
+      P.lo4.resize(h->kappa + 1);
       for (int l = 0; l <= h->kappa; ++l) {
-        if (!need_rel[l]) continue;
-        HD_TRY(P.rel4[l].alloc(h->N));
-        k_pack_rel4<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(P.rel[l].p, h->N, d,
-                                                                                         P.rel4[l].p);
+        if (!need4[l]) continue;
+        HD_TRY(P.hi4[l].alloc(h->N));
+        HD_TRY(P.lo4[l].alloc(h->N));
+        const Level& L = h->lv[l];
+        k_relhilo<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(
+            h->pts64.p, h->N, d, l, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[l], P.hi4[l].p, P.lo4[l].p);
         HD_CUDA(cudaGetLastError());
-        lvls.push_back(l);
-        ptrs.push_back(P.rel4[l].p);
       }
-      HD_TRY(upload(P.rel4_levels, lvls, st));
-      HD_TRY(upload(P.rel4_ptrs, ptrs, st));
-      std::vector<int4> s4(srcs.size());
-      std::vector<float4> o4(srcs.size());
-      for (size_t e = 0; e < srcs.size(); ++e) {
-        s4[e] = make_int4(srcs[e].x, srcs[e].y, 0, 0);
-        o4[e] = make_float4(soff[e * d], d > 1 ? soff[e * d + 1] : 0.f, d > 2 ? soff[e * d + 2] : 0.f, 0.f);
-      }
+      HD_TRY(upload(P.tasks4, t4, st));
       HD_TRY(upload(P.srcs4, s4, st));
       HD_TRY(upload(P.soff4, o4, st));
     }
@@ -1212,40 +1427,52 @@ int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl,
 }
 
 template <int D, int KID>
-void launch_dense4_k(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, float* y) {
+void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, float* y) {
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
-  for (const DenseLevel& DL : P.coarse) {
-    k_dense4<D, KID, false><<<grid_warps(DL.t1 - DL.t0, sms), 256, 0, st>>>(
-        P.tasks.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.rel4[DL.level].p, h->N, kc, (float)h->K.scale,
-        (float)h->K.diag, yl + (int64_t)(DL.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
+  const float ks = (float)h->K.scale, kd = (float)h->K.diag;
+  const int cap = sms * 6;  // resident tile CTAs per SM (shared memory bound)
+  auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, cap)); };
+  for (const DenseLevel& DL : P.coarse4) {
+    k_tile<D, KID, false><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(
+        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, h->N, kc, ks, kd,
+        yl + (int64_t)(DL.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
     h->launches += 1;
   }
-  k_dense4<D, KID, true><<<grid_warps(P.leaf.t1 - P.leaf.t0, sms), 256, 0, st>>>(
-      P.tasks.p, P.leaf.t0, P.leaf.t1, P.srcs4.p, P.soff4.p, P.rel4[h->kappa].p, h->N, kc, (float)h->K.scale,
-      (float)h->K.diag, nullptr, yl, h->kappa, h->perm.p, y);
+  if (P.excl4.t1 > P.excl4.t0) {
+    // low-rank leaf blocks that the parent tiles also evaluate: subtract them
+    k_tile<D, KID, false><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
+        P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p,
+        xt, h->N, kc, -ks, kd,
+        yl + (int64_t)(P.excl4.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
+    h->launches += 1;
+  }
+  k_tile<D, KID, true><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
+      P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
+      h->N, kc, ks, kd, nullptr,
+      yl, h->kappa, h->perm.p, y);
   h->launches += 1;
 }
 
 template <int D>
-void launch_dense4_d(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, float* y) {
+void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, float* y) {
   switch (h->K.id) {
-    case HODLRDD_K_LOG: launch_dense4_k<D, HODLRDD_K_LOG>(h, st, sms, yl, y); break;
-    case HODLRDD_K_INV_R: launch_dense4_k<D, HODLRDD_K_INV_R>(h, st, sms, yl, y); break;
-    case HODLRDD_K_MATERN32: launch_dense4_k<D, HODLRDD_K_MATERN32>(h, st, sms, yl, y); break;
-    case HODLRDD_K_GAUSS: launch_dense4_k<D, HODLRDD_K_GAUSS>(h, st, sms, yl, y); break;
-    case HODLRDD_K_EXP: launch_dense4_k<D, HODLRDD_K_EXP>(h, st, sms, yl, y); break;
-    case HODLRDD_K_INV_R2_4D: launch_dense4_k<D, HODLRDD_K_INV_R2_4D>(h, st, sms, yl, y); break;
-    case HODLRDD_K_R: launch_dense4_k<D, HODLRDD_K_R>(h, st, sms, yl, y); break;
-    case HODLRDD_K_SIN: launch_dense4_k<D, HODLRDD_K_SIN>(h, st, sms, yl, y); break;
-    default: launch_dense4_k<D, HODLRDD_K_INV_SQRT1P>(h, st, sms, yl, y); break;
+    case HODLRDD_K_LOG: launch_tiles_k<D, HODLRDD_K_LOG>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_INV_R: launch_tiles_k<D, HODLRDD_K_INV_R>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_MATERN32: launch_tiles_k<D, HODLRDD_K_MATERN32>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_GAUSS: launch_tiles_k<D, HODLRDD_K_GAUSS>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_EXP: launch_tiles_k<D, HODLRDD_K_EXP>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_INV_R2_4D: launch_tiles_k<D, HODLRDD_K_INV_R2_4D>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_R: launch_tiles_k<D, HODLRDD_K_R>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_SIN: launch_tiles_k<D, HODLRDD_K_SIN>(h, st, sms, xt, yl, y); break;
+    default: launch_tiles_k<D, HODLRDD_K_INV_SQRT1P>(h, st, sms, xt, yl, y); break;
   }
 }
 
 // Packed dense / near-field launches (FP32, d <= 3, one right-hand side, y of
 // type float with leading dimension 1).
 template <class IO>
-int launch_dense4(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, IO* y, int ldy, int c0) {
+int launch_tiles(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, IO* y, int ldy, int c0) {
   if constexpr (!std::is_same<IO, float>::value) {
     set_error("packed near field needs float output");
     return HODLRDD_ERR_UNSUPPORTED;
@@ -1255,9 +1482,9 @@ int launch_dense4(hodlrdd_s* h, cudaStream_t st, int sms, float* yl, IO* y, int 
       return HODLRDD_ERR_UNSUPPORTED;
     }
     switch (h->d) {
-      case 1: launch_dense4_d<1>(h, st, sms, yl, y); break;
-      case 2: launch_dense4_d<2>(h, st, sms, yl, y); break;
-      default: launch_dense4_d<3>(h, st, sms, yl, y); break;
+      case 1: launch_tiles_d<1>(h, st, sms, xt, yl, y); break;
+      case 2: launch_tiles_d<2>(h, st, sms, xt, yl, y); break;
+      default: launch_tiles_d<3>(h, st, sms, xt, yl, y); break;
     }
     HD_CUDA(cudaGetLastError());
     return HODLRDD_OK;
@@ -1280,15 +1507,9 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     HD_TRY(chunk_events(h, ev));
     HD_CUDA(cudaEventRecord(ev[0], st));
   }
-  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.rel4_ptrs.n > 0;
-  if (packed) {
-    if constexpr (NR == 1 && !F64)
-      k_gather_pack<IO><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(
-          x, h->perm.p, h->N, ldx, c0, reinterpret_cast<float*>(xt), P.rel4_ptrs.p, (int)P.rel4_ptrs.n);
-  } else {
-    k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
-                                                                                                ldx, c0, xt);
-  }
+  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
+  k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
+                                                                                              ldx, c0, xt);
   h->launches += 1;
   if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
   using C = PanelCfg<T, NR>;
@@ -1322,7 +1543,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
-    if constexpr (NR == 1 && !F64) HD_TRY((launch_dense4<IO>(h, st, sms, yl, y, ldx, c0)));
+    if constexpr (NR == 1 && !F64)
+      HD_TRY((launch_tiles<IO>(h, st, sms, reinterpret_cast<const float*>(xt), yl, y, ldx, c0)));
   } else switch (h->d) {
     case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
     case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;

@@ -123,8 +123,10 @@ void fill_stats(hodlrdd_s* h) {
                             h->ystage.bytes() + P.vs.data.bytes() + P.us.data.bytes() + P.vs.panels.bytes() +
                             P.us.panels.bytes() + P.vs.stages.bytes() + P.us.stages.bytes() + P.vs.splits.bytes() +
                             P.us.splits.bytes() + P.vmap.bytes() + h->pbuf.bytes() + P.tasks.bytes() +
-                            P.srcs.bytes() + P.soff.bytes() + P.srcs4.bytes() + P.soff4.bytes());
-  for (auto& r : P.rel4) bytes += (int64_t)r.bytes();
+                            P.srcs.bytes() + P.soff.bytes() + P.tasks4.bytes() + P.srcs4.bytes() +
+                            P.soff4.bytes());
+  for (auto& a : P.hi4) bytes += (int64_t)a.bytes();
+  for (auto& a : P.lo4) bytes += (int64_t)a.bytes();
   for (auto& r : P.rel) bytes += (int64_t)r.bytes();
   for (auto& L : h->lv)
     bytes += (int64_t)(L.bstart.bytes() + L.bkey.bytes() + L.cfirst.bytes() + L.iloff.bytes() + L.ilidx.bytes());
@@ -146,6 +148,7 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (!kernel_ok(kernel_id, prm)) { set_error("hodlrdd_build: unknown kernel or invalid kernel parameters"); return HODLRDD_ERR_INVALID; }
   if (o.precision < HODLRDD_PREC_FP64 || o.precision > HODLRDD_PREC_BF16) { set_error("hodlrdd_build: unknown precision"); return HODLRDD_ERR_INVALID; }
   if (o.max_nrhs < 1 || o.aca_max_rank < 1) { set_error("hodlrdd_build: max_nrhs and aca_max_rank must be >= 1"); return HODLRDD_ERR_INVALID; }
+  if (o.near_mode < 0 || o.near_mode > 2) { set_error("hodlrdd_build: near_mode must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
   return HODLRDD_OK;
 }
 

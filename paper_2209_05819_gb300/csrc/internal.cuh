@@ -206,10 +206,6 @@ struct Level {
   DevBuf<int32_t> iloff, ilidx;
 };
 
-// A run of `cnt` segments of equal padded length L, contiguous in a factor
-// stream. Segment s holds the factor row / column whose dot product with
-// vec[vec + e] (e < L) is written to out[out0 + s]. The first elements are a
-// zero lead pad that aligns vec + e to 16 bytes; the tail is zero padded.
 // One bulk copy into the shared-memory ring: lines [s, s + nseg) of sub-panel
 // g. `ng` marks the sub-panel's first stage and `last` its final one.
 struct Stage {
@@ -295,14 +291,17 @@ struct Plan {
   std::vector<DenseLevel> coarse;  // dense IL blocks above the leaf level
   DenseLevel leaf;                 // near field + leaf-level dense IL blocks
   std::vector<DevBuf<float>> rel;  // per level (index l): SoA d x N box-relative FP32 coordinates
-  // packed form for d <= 3 and one right-hand side: per level a float4 per point
-  // (box-relative coordinates, x_t of the current matvec in .w) and per source a
-  // {J0, n} int4 and an offset float4
-  std::vector<DevBuf<float4>> rel4;
-  DevBuf<int4> srcs4;
-  DevBuf<float4> soff4;
-  DevBuf<int32_t> rel4_levels;     // levels holding a packed array (device copy for the gather)
-  DevBuf<float4*> rel4_ptrs;
+  // packed form (FP32 arithmetic, d <= 3, one right-hand side): CTA tasks over
+  // box-relative coordinates kept as FP32 hi + lo pairs per level
+  DevBuf<int4> tasks4;             // {I0, m, src_begin, src_end}, m <= 256
+  DevBuf<int4> srcs4;              // {J0, n, position in its staging chunk, chunk end on a chunk's first entry}
+  DevBuf<float4> soff4;            // per source: (c_J - c_I) h_l, exact in FP32
+  std::vector<DevBuf<float4>> hi4, lo4;  // per level (where used)
+  std::vector<DenseLevel> coarse4; // dense IL blocks above the leaf level
+  DenseLevel leaf4;                // final pass: per parent box (tiles) or per leaf box (lists)
+  DenseLevel excl4;                // tiles only: low-rank leaf IL blocks to subtract (level kappa)
+  bool tiles = false;              // leaf4 runs over parent tiles at level kappa - 1
+  int64_t packed_pairs = 0;        // kernel evaluations of the packed path
   std::vector<double> h_box;       // per level: reference side h'_l (20 significant bits)
 };
 
