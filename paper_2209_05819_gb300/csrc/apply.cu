@@ -593,19 +593,34 @@ __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, i
 // point is one float4 (box-relative coordinates, x_t in .w); a source box is an
 // int4 {J0, n} and its exact box offset; the kernel function is a template
 // parameter so the pair loop has no branch on it.
+// Hardware reciprocal (square root) approximations, PTX rsqrt / rcp
+// .approx.ftz (relative error below 2^-22); the packed path treats squared
+// distances below the smallest normal FP32 number as coincident points.
+__device__ __forceinline__ float rsqrt_hw(float s) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  return r;
+}
+__device__ __forceinline__ float rcp_hw(float s) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  return r;
+}
+constexpr float kTinySq = 1.17549435e-38f;  // smallest normal FP32 number
+
 template <int KID>
 __device__ __forceinline__ float f32k(float s, float c) {
   if constexpr (KID == HODLRDD_K_LOG) return s == 0.0f ? 0.0f : 0.5f * logf(s);
-  else if constexpr (KID == HODLRDD_K_INV_R) return s == 0.0f ? 0.0f : rsqrtf(s);
+  else if constexpr (KID == HODLRDD_K_INV_R) return s < kTinySq ? 0.0f : rsqrt_hw(s);
   else if constexpr (KID == HODLRDD_K_MATERN32) {
     const float a = c * sqrtf(s);
     return (1.0f + a) * expf(-a);
   } else if constexpr (KID == HODLRDD_K_GAUSS) return expf(-c * s);
   else if constexpr (KID == HODLRDD_K_EXP) return expf(-c * sqrtf(s));
-  else if constexpr (KID == HODLRDD_K_INV_R2_4D) return s == 0.0f ? 0.0f : c / s;
+  else if constexpr (KID == HODLRDD_K_INV_R2_4D) return s < kTinySq ? 0.0f : c * rcp_hw(s);
   else if constexpr (KID == HODLRDD_K_R) return sqrtf(s);
   else if constexpr (KID == HODLRDD_K_SIN) return sinf(sqrtf(s));
-  else return rsqrtf(1.0f + sqrtf(s));
+  else return rsqrt_hw(1.0f + sqrtf(s));
 }
 
 // Packed dense work (FP32, d <= 3, one right-hand side), one CTA per task.
@@ -616,8 +631,8 @@ __device__ __forceinline__ float f32k(float s, float c) {
 // x_i - x_j = (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy of the
 // distance itself. Sources are staged through shared memory in chunks planned
 // on the host (entry .z = position in the chunk, .w on a chunk's first entry =
-// the entry after the chunk); then G target rows times S source stripes sweep
-// the chunk.
+// the entry after the chunk); then threads holding two target rows each sweep
+// the chunk in S source stripes.
 //   FINAL:  y[perm[i]] = scale * sum + diag * x_i + sum over levels of y_l(i)
 //   else:   ylev_l[i] += scale * sum
 constexpr int kTileThreads = 256;
@@ -648,7 +663,7 @@ __device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, con
 }
 
 template <int D, int KID, bool FINAL>
-__global__ void __launch_bounds__(kTileThreads) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
+__global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                       const int4* __restrict__ srcs, const float4* __restrict__ soff,
                                                       const float4* __restrict__ Hi, const float4* __restrict__ Lo,
                                                       const float* __restrict__ xt, int64_t N, float kc,
@@ -657,24 +672,30 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const int4* __restrict__ 
                                                       const int32_t* __restrict__ perm, float* __restrict__ y) {
   __shared__ float4 shi[kTileCap];  // hi coordinates in the task's frame, x_j in .w
   __shared__ float4 slo[kTileCap];  // lo coordinates
-  __shared__ float red[kTileThreads];
+  __shared__ float red[kTileThreads], red2[kTileThreads];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
     const int4 T = tasks[it];
+    // each thread holds two target rows, gi and gi + G
     int G = 1;
-    while (G < T.y) G <<= 1;
+    while (2 * G < T.y) G <<= 1;
     const int S = kTileThreads / G;
     const int gi = tid % G, stripe = tid / G;
-    const bool valid = gi < T.y;
-    const int row = T.x + gi;
-    float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
-    float xw = 0.f;
-    if (valid) {
-      th = Hi[row];
-      tl = Lo[row];
-      xw = xt[row];
+    const bool va = gi < T.y, vb = gi + G < T.y;
+    const int ra = T.x + gi, rb = T.x + gi + G;
+    float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
+    float xa = 0.f, xb = 0.f;
+    if (va) {
+      tha = Hi[ra];
+      tla = Lo[ra];
+      xa = xt[ra];
     }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (vb) {
+      thb = Hi[rb];
+      tlb = Lo[rb];
+      xb = xt[rb];
+    }
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
     for (int e = T.z; e < T.w;) {
       const int e1 = srcs[e].w;
       __syncthreads();  // the previous chunk has been consumed
@@ -693,31 +714,42 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(const int4* __restrict__ 
       const int n = lastb.z + lastb.y;
       __syncthreads();
       int f = stripe;
-      for (; f + 3 * S < n; f += 4 * S) {
-        const float4 h0 = shi[f], h1 = shi[f + S], h2 = shi[f + 2 * S], h3 = shi[f + 3 * S];
-        const float4 l0 = slo[f], l1 = slo[f + S], l2 = slo[f + 2 * S], l3 = slo[f + 3 * S];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h0, l0), kc), h0.w, a0);
-        a1 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h1, l1), kc), h1.w, a1);
-        a2 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h2, l2), kc), h2.w, a2);
-        a3 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h3, l3), kc), h3.w, a3);
+      for (; f + S < n; f += 2 * S) {
+        const float4 h0 = shi[f], l0 = slo[f], h1 = shi[f + S], l1 = slo[f + S];
+        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+        a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
+        b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
       }
-      for (; f < n; f += S) {
+      if (f < n) {
         const float4 h0 = shi[f], l0 = slo[f];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(th, tl, h0, l0), kc), h0.w, a0);
+        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
       }
       e = e1;
     }
-    red[tid] = (a0 + a1) + (a2 + a3);
+    red[tid] = a0 + a1;
+    red2[tid] = b0 + b1;
     __syncthreads();
-    if (stripe == 0 && valid) {
-      float acc = 0.f;
-      for (int s = 0; s < S; ++s) acc += red[s * G + gi];
-      if constexpr (FINAL) {
-        float tot = kscale * acc + kdiag * xw;
-        for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
-        y[perm[row]] = tot;
-      } else {
-        ylev_l[row] += kscale * acc;
+    if (stripe == 0) {
+      float acc_a = 0.f, acc_b = 0.f;
+      for (int s = 0; s < S; ++s) {
+        acc_a += red[s * G + gi];
+        acc_b += red2[s * G + gi];
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const bool v = q == 0 ? va : vb;
+        if (!v) continue;
+        const int row = q == 0 ? ra : rb;
+        const float acc = q == 0 ? acc_a : acc_b;
+        if constexpr (FINAL) {
+          float tot = kscale * acc + kdiag * (q == 0 ? xa : xb);
+          for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
+          y[perm[row]] = tot;
+        } else {
+          ylev_l[row] += kscale * acc;
+        }
       }
     }
     __syncthreads();  // red and the staging arrays are reused by the next task
@@ -1431,8 +1463,8 @@ void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, flo
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
   const float ks = (float)h->K.scale, kd = (float)h->K.diag;
-  const int cap = sms * 6;  // resident tile CTAs per SM (shared memory bound)
-  auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, cap)); };
+  // one CTA per task (the hardware scheduler balances tasks of unequal size)
+  auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
   for (const DenseLevel& DL : P.coarse4) {
     k_tile<D, KID, false><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(
         P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, h->N, kc, ks, kd,
