@@ -207,7 +207,7 @@ __device__ __forceinline__ void consumer_bar() {
 //            column-major over the concatenated columns of the box's low-rank
 //            IL blocks; line k = column k, s_k = t[vfirst + k], outputs are the
 //            contiguous ylev rows out0 + w.
-//   V-apply: a panel is up to kPanelWidth consecutive columns of the
+//   V-apply: a panel is up to vpanel_width<T>() consecutive columns of the
 //            concatenated V factors of all low-rank IL blocks that share one
 //            source box J, stored row-major; line k = source point J0 + k,
 //            s_k = x_t[vfirst + k], output w is t[map[out0 + w]].
@@ -220,7 +220,12 @@ __device__ __forceinline__ void consumer_bar() {
 // the slot (the values with a lead pad to keep the copy 16-byte aligned), so
 // the consumers read only shared memory.
 constexpr int kMaxLines = 256;      // lines per stage (bounds the staged vector values)
-constexpr int kPanelWidth = 512;    // outputs per panel
+// V panels are one 16-byte chunk per consumer thread wide, so each thread
+// owns its columns over all rows and a panel needs no cross-thread reduction.
+template <class T>
+constexpr int vpanel_width() {
+  return kConsumerWarps * 32 * Fac<T>::E;
+}
 constexpr int kMetaBytes = 128;     // {Stage, Panel, lead pad}
 constexpr int kDynSmemMax = 232448 - 1024;
 
@@ -985,7 +990,7 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
 
   // V panels: per level and source box, the concatenated columns of its
   // low-rank IL blocks (in block order) in row-major panels of at most
-  // kPanelWidth columns; line k = source point J0 + k
+  // vpanel_width<T>() columns; line k = source point J0 + k
   P.vs.h_lp.clear();
   P.h_vpanel.assign(nblk, -1);
   P.h_vcol.assign(nblk, 0);
@@ -1008,8 +1013,8 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
         for (int k = 0; k < h->h_rank[b]; ++k) hmap.push_back((int32_t)(h->h_toff[b] + k));
       }
       const int64_t Q = (int64_t)hmap.size() - m0;
-      for (int64_t c0 = 0; c0 < Q; c0 += kPanelWidth) {
-        const int32_t R = (int32_t)std::min<int64_t>(kPanelWidth, Q - c0);
+      for (int64_t c0 = 0; c0 < Q; c0 += vpanel_width<T>()) {
+        const int32_t R = (int32_t)std::min<int64_t>(vpanel_width<T>(), Q - c0);
         const int32_t ld = (int32_t)roundE(R);
         P.vs.h_lp.push_back(LPanel{off, ld, R, n});
         vfirst_v.push_back(J0);
@@ -1653,9 +1658,9 @@ int unpack_typed(hodlrdd_s* h, int64_t b, double* U, double* V) {
     // column k of the block is column h_vcol + k of its source box's panels
     for (int k = 0; k < p; ++k) {
       const int64_t pos = (int64_t)P.h_vcol[b] + k;
-      const LPanel& L = P.vs.h_lp[P.h_vpanel[b] + pos / kPanelWidth];
+      const LPanel& L = P.vs.h_lp[P.h_vpanel[b] + pos / vpanel_width<T>()];
       std::vector<T> buf(n);
-      HD_CUDA(cudaMemcpy2D(buf.data(), sizeof(T), reinterpret_cast<const T*>(P.vs.data.p) + L.off + pos % kPanelWidth,
+      HD_CUDA(cudaMemcpy2D(buf.data(), sizeof(T), reinterpret_cast<const T*>(P.vs.data.p) + L.off + pos % vpanel_width<T>(),
                            (size_t)L.ld * sizeof(T), sizeof(T), n, cudaMemcpyDeviceToHost));
       for (int j = 0; j < n; ++j) V[(size_t)k * n + j] = Fac<T>::to_host(buf[j]) * sv[k];
     }
