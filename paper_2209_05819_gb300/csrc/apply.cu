@@ -485,14 +485,20 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 }
 
 // Sums of cut panels: out = sum over the sub-panels' partials, in sub-panel
-// order; V outputs go through the column map and the column scales.
+// order; V outputs go through the column map and the column scales. One CTA
+// per (split, block of kCombineRows outputs) work item.
+constexpr int kCombineRows = 256;
+
 template <class Acc, int NR, bool VMODE>
-__global__ void __launch_bounds__(256) k_combine(const Split* __restrict__ splits, const Acc* __restrict__ part,
-                                                  Acc* __restrict__ out, const int32_t* __restrict__ map,
-                                                  const float* __restrict__ sa, const float* __restrict__ sb) {
-  const Split S = splits[blockIdx.x];
-  for (int idx = threadIdx.x; idx < S.R * NR; idx += blockDim.x) {
-    const int w = idx / NR, r = idx % NR;
+__global__ void __launch_bounds__(256) k_combine(const Split* __restrict__ splits, const int2* __restrict__ work,
+                                                  const Acc* __restrict__ part, Acc* __restrict__ out,
+                                                  const int32_t* __restrict__ map, const float* __restrict__ sa,
+                                                  const float* __restrict__ sb) {
+  const int2 wk = work[blockIdx.x];
+  const Split S = splits[wk.x];
+  const int w1 = min(S.R, wk.y + kCombineRows);
+  for (int idx = threadIdx.x; idx < (w1 - wk.y) * NR; idx += blockDim.x) {
+    const int w = wk.y + idx / NR, r = idx % NR;
     Acc v = Acc(0);
     for (int s = 0; s < S.nsplit; ++s) v += part[((int64_t)S.part + (int64_t)s * S.R + w) * NR + r];
     if constexpr (VMODE) {
@@ -951,6 +957,9 @@ void schedule_stream(Stream& S, const std::vector<int32_t>& vfirst, const std::v
       }
     }
   }
+  S.h_cwork.clear();
+  for (size_t i = 0; i < S.h_splits.size(); ++i)
+    for (int w0 = 0; w0 < S.h_splits[i].R; w0 += kCombineRows) S.h_cwork.push_back(make_int2((int)i, w0));
   int64_t total = 0;
   for (const Stage& st : S.h_stages) total += st.nelem;
   S.h_cta.assign(1, 0);
@@ -970,6 +979,7 @@ int upload_stream(Stream& S, cudaStream_t st) {
   HD_TRY(upload(S.stages, S.h_stages, st));
   HD_TRY(upload(S.cta, S.h_cta, st));
   HD_TRY(upload(S.splits, S.h_splits, st));
+  HD_TRY(upload(S.cwork, S.h_cwork, st));
   return HODLRDD_OK;
 }
 
@@ -1561,7 +1571,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
           pb, h->err.p);
       h->launches += 1;
       if (!P.vs.h_splits.empty()) {
-        k_combine<Acc, NR, true><<<(int)P.vs.h_splits.size(), 256, 0, st>>>(P.vs.splits.p, pb, t, P.vmap.p, sa, sb);
+        k_combine<Acc, NR, true><<<(int)P.vs.h_cwork.size(), 256, 0, st>>>(P.vs.splits.p, P.vs.cwork.p, pb, t,
+                                                                             P.vmap.p, sa, sb);
         h->launches += 1;
       }
     }
@@ -1573,8 +1584,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
         nullptr, pb, h->err.p);
     h->launches += 1;
     if (!P.us.h_splits.empty()) {
-      k_combine<Acc, NR, false><<<(int)P.us.h_splits.size(), 256, 0, st>>>(P.us.splits.p, pb, yl, nullptr, nullptr,
-                                                                             nullptr);
+      k_combine<Acc, NR, false><<<(int)P.us.h_cwork.size(), 256, 0, st>>>(P.us.splits.p, P.us.cwork.p, pb, yl,
+                                                                              nullptr, nullptr, nullptr);
       h->launches += 1;
     }
   }

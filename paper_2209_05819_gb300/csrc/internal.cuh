@@ -262,11 +262,13 @@ struct Stream {
   std::vector<Stage> h_stages;
   std::vector<int32_t> h_cta;
   std::vector<Split> h_splits;
+  std::vector<int2> h_cwork;    // combine work items {split, first output}
   int64_t part_rows = 0;        // partial-sum rows of the cut panels
   DevBuf<Panel> panels;
   DevBuf<Stage> stages;
   DevBuf<int32_t> cta;
   DevBuf<Split> splits;
+  DevBuf<int2> cwork;
   int ctas = 0;
 };
 
