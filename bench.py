@@ -235,9 +235,23 @@ def cpu_baseline(args, rank_w):
         T.matvec(ws.x)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
-    return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+    # the same oracle on one core, and its direct O(N^2) sum on a row sample
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    T.matvec(ws.x)
+    t1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    nrow = min(ws.N, 1024)
+    t0 = time.perf_counter()
+    oracle.direct(ws.points, ws.kernel, ws.params, ws.x, (0, nrow))
+    t_dir = (time.perf_counter() - t0) * ws.N / nrow
+    extra = {"single_core_value": ws.N * ws.nrhs / t1, "direct_value": ws.N * ws.nrhs / t_dir,
+             "machine": f"{os.uname().machine}, {cores} threads"}
+    return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle", **extra,
             "sample": f"oracle FP64 HODLRdD on a {ws.N}-point draw of the same distribution (d={ws.d}, 1/r, "
-                      f"leaf {ws.leaf}, tol {ws.tol:g}); matvec median of {len(times)} runs; build {t_build:.1f} s"}
+                      f"leaf {ws.leaf}, tol {ws.tol:g}); matvec median of {len(times)} runs; build {t_build:.1f} s; "
+                      f"single_core_value: one matvec on one thread; direct_value: the oracle's direct sum on "
+                      f"{nrow} rows scaled to all rows"}
 
 
 def run_reference(args):
@@ -349,6 +363,19 @@ def main():
         if h64 is not h:
             h64.close()
 
+    # the direct O(N^2) product on the GPU (FP32, on the fly): comparator
+    direct = None
+    if args.precision != "fp64" and w.d <= 3 and nrhs == 1:
+        xd = x.reshape(-1)
+        yd = torch.empty_like(xd)
+        n_d = 3
+        t_d = time_steps(lambda: h.direct(xd, yd), n_d, 1, torch, stream)
+        h.matvec(x, y)
+        torch.cuda.synchronize()
+        e_d = float((torch.linalg.norm(y.reshape(-1).double() - yd.double()) / torch.linalg.norm(yd.double())).item())
+        direct = {"ms_per_step": 1e3 * t_d / n_d, "value": units * n_d / t_d,
+                  "pair_evals_per_s": float(w.N) * w.N * n_d / t_d, "rel_err_hodlrdd_vs_direct": e_d}
+
     # end to end through the C ABI with host (pinned) buffers
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -392,6 +419,7 @@ def main():
                        "l2": f"inputs larger than L2: {(ub + vb) / 1e9:.2f} GB of factors streamed per step"},
             "rel_err_vs_fp64": err, "meets_err_bar": (err is not None and err <= ERR_BAR),
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
+            "direct_gpu": direct,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
                                                    "t_pack_ms")},
             "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],

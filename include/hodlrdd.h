@@ -199,6 +199,23 @@ int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* str
 int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
 
 /*
+ * y = K x by direct summation over all N^2 pairs, K(i,j) = scale * F(x_i, x_j) +
+ * diag * [i == j] (the kernel matrix of Section "Preliminaries"; the product
+ * HODLRdD approximates), evaluated on the fly in FP32: a comparator for the
+ * hierarchical product, not part of Algorithm 2.
+ *
+ *  x, y    device, N floats each, ORIGINAL point order; y is overwritten. They
+ *          must not overlap. One right-hand side.
+ *  h       a handle of precision FP32, FP16 or BF16 with d <= 3, else
+ *          HODLRDD_ERR_UNSUPPORTED; host pointers give HODLRDD_ERR_INVALID.
+ *
+ * Asynchronous on `stream`; uses the handle's matvec workspace (serialise with
+ * matvecs on other streams). The first call allocates 32 N bytes of
+ * cube-relative coordinates, kept until hodlrdd_destroy.
+ */
+int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream);
+
+/*
  * Waits for all device work (cudaDeviceSynchronize) and reports failures the
  * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
  * their bounded waits expired (the y of that matvec is then invalid). Clears the

@@ -67,6 +67,7 @@ def load():
         "hodlrdd_build_ex": (i32, [vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(vp)]),
         "hodlrdd_matvec": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_matvec_noalloc": (i32, [vp, vp, vp, i32, vp]),
+        "hodlrdd_direct": (i32, [vp, vp, vp, vp]),
         "hodlrdd_destroy": (i32, [vp]),
         "hodlrdd_get_stats": (i32, [vp, C.POINTER(Stats)]),
         "hodlrdd_error_string": (C.c_char_p, [i32]),
@@ -194,6 +195,15 @@ class Handle:
         ya, ky = _ptr(y)
         st = self._lib.hodlrdd_matvec(self._h, xa, ya, nrhs, _stream_ptr(stream))
         _check(st, "hodlrdd_matvec")
+        return y
+
+    def direct(self, x, y=None, stream=None):
+        """y = K x by direct O(N^2) summation on the GPU (FP32; x a CUDA tensor, one column)."""
+        if y is None:
+            y = x.new_empty(x.shape)
+        xa, kx = _ptr(x)
+        ya, ky = _ptr(y)
+        _check(self._lib.hodlrdd_direct(self._h, xa, ya, _stream_ptr(stream)), "hodlrdd_direct")
         return y
 
     def matvec_noalloc(self, x, y=None, stream=None):

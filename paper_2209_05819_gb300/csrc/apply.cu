@@ -767,6 +767,72 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
   }
 }
 
+// Direct on-the-fly product y = K x over all N^2 pairs (FP32 arithmetic, d <=
+// 3, one right-hand side): the exact-by-definition comparator of the HODLRdD
+// product. Coordinates relative to the bounding cube's corner as FP32 hi + lo
+// pairs; each CTA holds 2 x kDirectThreads targets and streams every source
+// through shared memory; sums are compensated.
+constexpr int kDirectThreads = 128;
+
+template <int D, int KID>
+__global__ void __launch_bounds__(kDirectThreads) k_direct(const float4* __restrict__ Hi,
+                                                          const float4* __restrict__ Lo,
+                                                          const float* __restrict__ xt, int64_t N, float kc,
+                                                          float kscale, float kdiag,
+                                                          const int32_t* __restrict__ perm, float* __restrict__ y) {
+  __shared__ float4 shi[kTileCap];
+  __shared__ float4 slo[kTileCap];
+  const int tid = threadIdx.x;
+  const int64_t ra = (int64_t)blockIdx.x * 2 * kDirectThreads + tid, rb = ra + kDirectThreads;
+  float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
+  if (ra < N) {
+    tha = Hi[ra];
+    tla = Lo[ra];
+  }
+  if (rb < N) {
+    thb = Hi[rb];
+    tlb = Lo[rb];
+  }
+  // compensated (Kahan) sums: N terms per target
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, ca0 = 0.f, ca1 = 0.f, cb0 = 0.f, cb1 = 0.f;
+  auto kadd = [](float& sum, float& comp, float term) {
+    const float yv = term - comp;
+    const float t = sum + yv;
+    comp = (t - sum) - yv;
+    sum = t;
+  };
+  for (int64_t c0 = 0; c0 < N; c0 += kTileCap) {
+    const int n = N - c0 < kTileCap ? (int)(N - c0) : kTileCap;
+    __syncthreads();  // the previous chunk has been consumed
+    for (int k = tid; k < n; k += kDirectThreads) {
+      float4 h = Hi[c0 + k];
+      h.w = xt[c0 + k];
+      shi[k] = h;
+      slo[k] = Lo[c0 + k];
+    }
+    __syncthreads();
+    int f = 0;
+    for (; f + 1 < n; f += 2) {
+      const float4 h0 = shi[f], l0 = slo[f], h1 = shi[f + 1], l1 = slo[f + 1];
+      kadd(a0, ca0, f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc) * h0.w);
+      kadd(b0, cb0, f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc) * h0.w);
+      kadd(a1, ca1, f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc) * h1.w);
+      kadd(b1, cb1, f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc) * h1.w);
+    }
+    if (f < n) {
+      const float4 h0 = shi[f], l0 = slo[f];
+      kadd(a0, ca0, f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc) * h0.w);
+      kadd(b0, cb0, f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc) * h0.w);
+    }
+  }
+  a0 -= ca0;
+  a1 -= ca1;
+  b0 -= cb0;
+  b1 -= cb1;
+  if (ra < N) y[perm[ra]] = kscale * (a0 + a1) + kdiag * xt[ra];
+  if (rb < N) y[perm[rb]] = kscale * (b0 + b1) + kdiag * xt[rb];
+}
+
 // Box-relative coordinates at level l as FP32 pairs: x - (lo + c_box h) = hi + lo
 // (the difference formed in FP64).
 __global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int l, const int32_t* __restrict__ bstart,
@@ -1699,6 +1765,62 @@ int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V) {
     case HODLRDD_PREC_FP16: return unpack_typed<__half>(h, b, U, V);
     default: return unpack_typed<__nv_bfloat16>(h, b, U, V);
   }
+}
+
+namespace {
+template <int D>
+void launch_direct_d(hodlrdd_s* h, cudaStream_t st, const float* xt, float* y) {
+  const Plan& P = h->plan;
+  const float kc = (float)kernel_const(h->K);
+  const float ks = (float)h->K.scale, kd = (float)h->K.diag;
+  const int grid = (int)((h->N + 2 * kDirectThreads - 1) / (2 * kDirectThreads));
+  const float4* Hi = P.hi4[0].p;
+  const float4* Lo = P.lo4[0].p;
+  switch (h->K.id) {
+#define HD_DIRECT(K) \
+  case K: k_direct<D, K><<<grid, kDirectThreads, 0, st>>>(Hi, Lo, xt, h->N, kc, ks, kd, h->perm.p, y); break;
+    HD_DIRECT(HODLRDD_K_LOG) HD_DIRECT(HODLRDD_K_INV_R) HD_DIRECT(HODLRDD_K_MATERN32) HD_DIRECT(HODLRDD_K_GAUSS)
+    HD_DIRECT(HODLRDD_K_EXP) HD_DIRECT(HODLRDD_K_INV_R2_4D) HD_DIRECT(HODLRDD_K_R) HD_DIRECT(HODLRDD_K_SIN)
+    default: k_direct<D, HODLRDD_K_INV_SQRT1P><<<grid, kDirectThreads, 0, st>>>(Hi, Lo, xt, h->N, kc, ks, kd,
+                                                                                h->perm.p, y);
+#undef HD_DIRECT
+  }
+}
+}  // namespace
+
+int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st) {
+  if (h->opt.precision == HODLRDD_PREC_FP64 || h->d > 3) {
+    set_error("hodlrdd_direct: needs an FP32, FP16 or BF16 handle and d <= 3");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
+  Plan& P = h->plan;
+  if (P.hi4.empty()) P.hi4.resize(h->kappa + 1);
+  if (P.lo4.empty()) P.lo4.resize(h->kappa + 1);
+  if (!P.hi4[0].p) {  // cube-relative coordinates, made on the first call
+    std::vector<double> hlo(h->lo, h->lo + h->d);
+    DevBuf<double> dlo;
+    HD_TRY(upload(dlo, hlo, st));
+    HD_TRY(P.hi4[0].alloc(h->N));
+    HD_TRY(P.lo4[0].alloc(h->N));
+    const Level& L = h->lv[0];
+    k_relhilo<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(
+        h->pts64.p, h->N, h->d, 0, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[0], P.hi4[0].p, P.lo4[0].p);
+    HD_CUDA(cudaGetLastError());
+    HD_CUDA(cudaStreamSynchronize(st));
+  }
+  float* xt = reinterpret_cast<float*>(h->xt.p) + (size_t)kGuard;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  k_gather<float, float, 1><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p,
+                                                                                                   h->N, 1, 0, xt);
+  switch (h->d) {
+    case 1: launch_direct_d<1>(h, st, xt, y); break;
+    case 2: launch_direct_d<2>(h, st, xt, y); break;
+    default: launch_direct_d<3>(h, st, xt, y); break;
+  }
+  HD_CUDA(cudaGetLastError());
+  h->launches += 2;
+  return HODLRDD_OK;
 }
 
 int read_error_word(hodlrdd_s* h, int32_t* code) {

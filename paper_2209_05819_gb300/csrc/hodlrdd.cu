@@ -298,6 +298,25 @@ int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* str
   return HODLRDD_OK;
 }
 
+int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream) {
+  if (!h || !x || !y) {
+    set_error("hodlrdd_direct: NULL handle or pointer");
+    return HODLRDD_ERR_INVALID;
+  }
+  const size_t bytes = (size_t)h->N * sizeof(float);
+  const char* xa = static_cast<const char*>(x);
+  char* ya = static_cast<char*>(y);
+  if (xa < ya + bytes && ya < xa + bytes) {
+    set_error("hodlrdd_direct: x and y overlap");
+    return HODLRDD_ERR_INVALID;
+  }
+  if (pointer_kind(x) != 1 || pointer_kind(y) != 1) {
+    set_error("hodlrdd_direct: x and y must be device memory");
+    return HODLRDD_ERR_INVALID;
+  }
+  return launch_direct(h, static_cast<const float*>(x), static_cast<float*>(y), static_cast<cudaStream_t>(stream));
+}
+
 int hodlrdd_destroy(hodlrdd_handle h) {
   destroy(h);
   return HODLRDD_OK;

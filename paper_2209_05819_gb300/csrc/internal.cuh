@@ -379,6 +379,7 @@ int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& 
 int build_plan(hodlrdd_s* h);
 int alloc_workspace(hodlrdd_s* h);
 int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
+int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
 int read_error_word(hodlrdd_s* h, int32_t* code);
 size_t elem_size(int precision);

@@ -237,3 +237,42 @@ def test_near_field_tiles_and_lists_agree(env, d, N, kernel, params, leaf, tol):
         h.sync()
         assert relerr(ys[-1], y64) <= MIXED_BOUND["fp32"], mode
     assert relerr(ys[0], ys[1]) <= 2 * MIXED_BOUND["fp32"]
+
+
+DIRECT_CASES = [
+    (1, 3000, W.K_EXP, (1, 0, 1.0, 0)),
+    (2, 4000, W.K_LOG, None),
+    (3, 6000, W.K_INV_R, None),
+    (3, 5000, W.K_MATERN32, (1, 0, 0.2, 0)),
+    (3, 3000, W.K_INV_R2_4D, None),
+    (2, 3000, W.K_SIN, None),
+    (3, 4000, W.K_INV_R, (1.0 / 4000, 1.0, 0, 0)),  # I + K/N
+]
+
+
+@pytest.mark.parametrize("d,N,kernel,params", DIRECT_CASES)
+def test_direct_sum_matches_oracle(env, d, N, kernel, params):
+    """The on-the-fly O(N^2) GPU product equals the oracle's FP64 direct sum
+    within the FP32 bound."""
+    torch, oracle, hd = env
+    w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), 32, 1e-8, nrhs=1, seed=N + 11 * d)
+    h = gpu_handle(hd, w, precision="fp32")
+    x = torch.from_numpy(np.ascontiguousarray(w.x[:, 0], dtype=np.float32)).cuda()
+    y = h.direct(x)
+    torch.cuda.synchronize()
+    yd = oracle.direct(w.points, w.kernel, w.params, w.x)
+    assert relerr(y.cpu().numpy()[:, None], yd) <= MIXED_BOUND["fp32"]
+
+
+def test_direct_rejects_fp64_and_host_buffers(env):
+    torch, oracle, hd = env
+    w = W.make("t", 2, 500, W.K_LOG, (1, 0, 0, 0), 32, 1e-8, seed=2)
+    h64 = gpu_handle(hd, w)
+    x = torch.zeros(500, dtype=torch.float32, device="cuda")
+    with pytest.raises(hd.HodlrddError) as e:
+        h64.direct(x)
+    assert e.value.status == hd.ERR_UNSUPPORTED
+    h32 = gpu_handle(hd, w, precision="fp32")
+    with pytest.raises(hd.HodlrddError) as e:
+        h32.direct(np.zeros(500, np.float32), np.zeros(500, np.float32))
+    assert e.value.status == hd.ERR_INVALID
