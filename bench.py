@@ -383,6 +383,15 @@ def main():
     t_e2e = time_steps(lambda: h.matvec(xh, yh), n_e2e, 1, torch, stream)
     e2e_units, e2e_sec = aggregate(units * n_e2e, t_e2e, dist, device="cuda")
     io_bytes = x.element_size() * x.numel()
+    # serving latency: one request = one synchronous call with host x and y
+    lat = []
+    for _ in range(max(20, min(args.steps, 200))):
+        t0 = time.perf_counter()
+        h.matvec(xh, yh)
+        lat.append(1e3 * (time.perf_counter() - t0))
+    lat.sort()
+    serving = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+               "requests": len(lat), "request": "one matvec through hodlrdd_matvec with pinned host x and y"}
 
     # roofline of the dominant kernel (bytes it must move per launch / its mean duration)
     ub, vb, tr, scales = factor_bytes(h, args.precision)
@@ -430,6 +439,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_units / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }

@@ -236,7 +236,9 @@ struct PanelCfg {
   static constexpr int kSlot = kStageBytes + kScal + kMetaBytes;
   static constexpr int kRed = kConsumerWarps * 32 * 8 * (int)sizeof(Acc);
   static constexpr int kFit = (kDynSmemMax - kRed) / kSlot;
-  static constexpr int kStagesN = kFit < 6 ? kFit : 6;
+  // four slots keep 128 KB in flight per SM and leave shared memory and
+  // registers for one near-field tile CTA beside the panel CTA
+  static constexpr int kStagesN = kFit < 4 ? kFit : 4;
   static constexpr size_t kSmem = (size_t)kStagesN * kSlot + kRed;
   static_assert(kStagesN >= 3, "panel ring needs at least three slots");
 };
@@ -363,11 +365,12 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     const Stage st = meta->st;
     const Panel P = meta->P;
     const Acc* sv = reinterpret_cast<const Acc*>(base + kStageBytes) + meta->lead;
+    // chunks per line RC, rounded up to a power of two 2^lg; line classes NT / 2^lg
     const int RC = P.ld / E;
-    int RCP = 1;
-    while (RCP < RC) RCP <<= 1;
-    const int CG = NT / RCP;
-    const int rc = ct % RCP, cg = ct / RCP;
+    const int lg = RC > 1 ? 32 - __clz(RC - 1) : 0;
+    const int RCP = 1 << lg;
+    const int CG = NT >> lg;
+    const int rc = ct & (RCP - 1), cg = ct >> lg;
     if (st.ng) {
 #pragma unroll
       for (int e = 0; e < E; ++e)
@@ -437,9 +440,10 @@ __global__ void __launch_bounds__(kSegThreads, 1)
         for (int e = 0; e < E; ++e)
 #pragma unroll
           for (int r = 0; r < NR; ++r) acc[e][r] += __shfl_xor_sync(0xffffffffu, acc[e][r], o);
-      const int WG = RCP > 32 ? RCP / 32 : 1;  // warps per line class
-      const int NG = kConsumerWarps / WG;      // line classes left after the warp step
-      const int sub = cw % WG, g = cw / WG;
+      const int lw = lg > 5 ? lg - 5 : 0;      // log2 of the warps per line class
+      const int WG = 1 << lw;
+      const int NG = kConsumerWarps >> lw;     // line classes left after the warp step
+      const int sub = cw & (WG - 1), g = cw >> lw;
       const bool holds = lane < (RCP < 32 ? RCP : 32);
       if (NG > 1) {
 #pragma unroll
@@ -643,9 +647,8 @@ __device__ __forceinline__ float f32k(float s, float c) {
 // distance itself. Sources are staged through shared memory in chunks planned
 // on the host (entry .z = position in the chunk, .w on a chunk's first entry =
 // the entry after the chunk); then threads holding two target rows each sweep
-// the chunk in S source stripes.
-//   FINAL:  y[perm[i]] = scale * sum + diag * x_i + sum over levels of y_l(i)
-//   else:   ylev_l[i] += scale * sum
+// the chunk in S source stripes. Result: ynear[i] += scale * sum + diag * x_i
+// (diag is passed as 0 except for the pass that owns the diagonal).
 constexpr int kTileThreads = 256;
 constexpr int kTileRows = 256;
 constexpr int kTileCap = 1024;
@@ -673,14 +676,12 @@ __device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, con
   return s;
 }
 
-template <int D, int KID, bool FINAL>
+template <int D, int KID>
 __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                       const int4* __restrict__ srcs, const float4* __restrict__ soff,
                                                       const float4* __restrict__ Hi, const float4* __restrict__ Lo,
-                                                      const float* __restrict__ xt, int64_t N, float kc,
-                                                      float kscale, float kdiag, float* __restrict__ ylev_l,
-                                                      const float* __restrict__ ylev, int kappa,
-                                                      const int32_t* __restrict__ perm, float* __restrict__ y) {
+                                                      const float* __restrict__ xt, float kc, float kscale,
+                                                      float kdiag, float* __restrict__ ynear) {
   __shared__ float4 shi[kTileCap];  // hi coordinates in the task's frame, x_j in .w
   __shared__ float4 slo[kTileCap];  // lo coordinates
   __shared__ float red[kTileThreads], red2[kTileThreads];
@@ -754,13 +755,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
         if (!v) continue;
         const int row = q == 0 ? ra : rb;
         const float acc = q == 0 ? acc_a : acc_b;
-        if constexpr (FINAL) {
-          float tot = kscale * acc + kdiag * (q == 0 ? xa : xb);
-          for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + row];
-          y[perm[row]] = tot;
-        } else {
-          ylev_l[row] += kscale * acc;
-        }
+        ynear[row] += kscale * acc + kdiag * (q == 0 ? xa : xb);
       }
     }
     __syncthreads();  // red and the staging arrays are reused by the next task
@@ -855,6 +850,17 @@ __global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int 
     }
     Hi[i] = make_float4(hv[0], hv[1], hv[2], 0.f);
     Lo[i] = make_float4(lv[0], lv[1], lv[2], 0.f);
+  }
+}
+
+// y[perm[i]] = near(i) + sum over levels of y_l(i) (packed path).
+template <class IO>
+__global__ void k_finish(const float* __restrict__ ynear, const float* __restrict__ ylev, int kappa, int64_t N,
+                         const int32_t* __restrict__ perm, IO* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    float tot = ynear[i];
+    for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + i];
+    y[perm[i]] = (IO)tot;
   }
 }
 
@@ -1494,6 +1500,7 @@ int alloc_workspace(hodlrdd_s* h) {
   HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * nr * acc));
   const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1});
   HD_TRY(h->pbuf.alloc((size_t)prows * nr * acc));
+  if (h->plan.tasks4.n > 0) HD_TRY(h->ynear.alloc(h->N));
   HD_TRY(h->err.alloc(1));
   HD_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes(), h->st));
   HD_CUDA(cudaMemsetAsync(h->tbuf.p, 0, h->tbuf.bytes(), h->st));
@@ -1505,8 +1512,8 @@ int alloc_workspace(hodlrdd_s* h) {
 namespace {
 
 // Tracing: take 5 events for one chunk from the handle's pool.
-int chunk_events(hodlrdd_s* h, cudaEvent_t* ev) {
-  for (int i = 0; i < 5; ++i) {
+int chunk_events(hodlrdd_s* h, cudaEvent_t* ev, int n) {
+  for (int i = 0; i < n; ++i) {
     if (h->ev_pool.empty()) {
       cudaEvent_t e;
       HD_CUDA(cudaEventCreate(&e));
@@ -1515,7 +1522,7 @@ int chunk_events(hodlrdd_s* h, cudaEvent_t* ev) {
     ev[i] = h->ev_pool.back();
     h->ev_pool.pop_back();
   }
-  h->ev_pending.emplace_back(ev, ev + 5);
+  h->ev_pending.emplace_back(ev, ev + n);
   return HODLRDD_OK;
 }
 
@@ -1540,67 +1547,55 @@ int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl,
 }
 
 template <int D, int KID>
-void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, float* y) {
+void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
   const float ks = (float)h->K.scale, kd = (float)h->K.diag;
+  float* yn = h->ynear.p;
   // one CTA per task (the hardware scheduler balances tasks of unequal size)
   auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
   for (const DenseLevel& DL : P.coarse4) {
-    k_tile<D, KID, false><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(
-        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, h->N, kc, ks, kd,
-        yl + (int64_t)(DL.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
+    k_tile<D, KID><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
+                                                                P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks,
+                                                                0.f, yn);
     h->launches += 1;
   }
   if (P.excl4.t1 > P.excl4.t0) {
     // low-rank leaf blocks that the parent tiles also evaluate: subtract them
-    k_tile<D, KID, false><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
-        P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p,
-        xt, h->N, kc, -ks, kd,
-        yl + (int64_t)(P.excl4.level - 1) * h->N, yl, h->kappa, h->perm.p, y);
+    k_tile<D, KID><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
+        P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p, xt,
+        kc, -ks, 0.f, yn);
     h->launches += 1;
   }
-  k_tile<D, KID, true><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
+  k_tile<D, KID><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
       P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
-      h->N, kc, ks, kd, nullptr,
-      yl, h->kappa, h->perm.p, y);
+      kc, ks, kd, yn);
   h->launches += 1;
 }
 
 template <int D>
-void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, float* y) {
+void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   switch (h->K.id) {
-    case HODLRDD_K_LOG: launch_tiles_k<D, HODLRDD_K_LOG>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_INV_R: launch_tiles_k<D, HODLRDD_K_INV_R>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_MATERN32: launch_tiles_k<D, HODLRDD_K_MATERN32>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_GAUSS: launch_tiles_k<D, HODLRDD_K_GAUSS>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_EXP: launch_tiles_k<D, HODLRDD_K_EXP>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_INV_R2_4D: launch_tiles_k<D, HODLRDD_K_INV_R2_4D>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_R: launch_tiles_k<D, HODLRDD_K_R>(h, st, sms, xt, yl, y); break;
-    case HODLRDD_K_SIN: launch_tiles_k<D, HODLRDD_K_SIN>(h, st, sms, xt, yl, y); break;
-    default: launch_tiles_k<D, HODLRDD_K_INV_SQRT1P>(h, st, sms, xt, yl, y); break;
+    case HODLRDD_K_LOG: launch_tiles_k<D, HODLRDD_K_LOG>(h, st, xt); break;
+    case HODLRDD_K_INV_R: launch_tiles_k<D, HODLRDD_K_INV_R>(h, st, xt); break;
+    case HODLRDD_K_MATERN32: launch_tiles_k<D, HODLRDD_K_MATERN32>(h, st, xt); break;
+    case HODLRDD_K_GAUSS: launch_tiles_k<D, HODLRDD_K_GAUSS>(h, st, xt); break;
+    case HODLRDD_K_EXP: launch_tiles_k<D, HODLRDD_K_EXP>(h, st, xt); break;
+    case HODLRDD_K_INV_R2_4D: launch_tiles_k<D, HODLRDD_K_INV_R2_4D>(h, st, xt); break;
+    case HODLRDD_K_R: launch_tiles_k<D, HODLRDD_K_R>(h, st, xt); break;
+    case HODLRDD_K_SIN: launch_tiles_k<D, HODLRDD_K_SIN>(h, st, xt); break;
+    default: launch_tiles_k<D, HODLRDD_K_INV_SQRT1P>(h, st, xt); break;
   }
 }
 
-// Packed dense / near-field launches (FP32, d <= 3, one right-hand side, y of
-// type float with leading dimension 1).
-template <class IO>
-int launch_tiles(hodlrdd_s* h, cudaStream_t st, int sms, const float* xt, float* yl, IO* y, int ldy, int c0) {
-  if constexpr (!std::is_same<IO, float>::value) {
-    set_error("packed near field needs float output");
-    return HODLRDD_ERR_UNSUPPORTED;
-  } else {
-    if (ldy != 1 || c0 != 0) {
-      set_error("packed near field is for one right-hand side");
-      return HODLRDD_ERR_UNSUPPORTED;
-    }
-    switch (h->d) {
-      case 1: launch_tiles_d<1>(h, st, sms, xt, yl, y); break;
-      case 2: launch_tiles_d<2>(h, st, sms, xt, yl, y); break;
-      default: launch_tiles_d<3>(h, st, sms, xt, yl, y); break;
-    }
-    HD_CUDA(cudaGetLastError());
-    return HODLRDD_OK;
+// Packed near-field launches (FP32, d <= 3, one right-hand side) on stream st,
+// accumulating into ynear (zeroed here).
+void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * sizeof(float), st);
+  switch (h->d) {
+    case 1: launch_tiles_d<1>(h, st, xt); break;
+    case 2: launch_tiles_d<2>(h, st, xt); break;
+    default: launch_tiles_d<3>(h, st, xt); break;
   }
 }
 
@@ -1614,17 +1609,31 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   Acc* xt = reinterpret_cast<Acc*>(h->xt.p) + (size_t)kGuard * NR;
   Acc* t = reinterpret_cast<Acc*>(h->tbuf.p) + (size_t)kGuard * NR;
   Acc* yl = reinterpret_cast<Acc*>(h->ylev.p);
-  cudaEvent_t ev[5];
+  cudaEvent_t ev[7];
   const bool prof = h->profiling;
+  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
   if (prof) {
-    HD_TRY(chunk_events(h, ev));
+    HD_TRY(chunk_events(h, ev, packed ? 7 : 5));
     HD_CUDA(cudaEventRecord(ev[0], st));
   }
-  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
   k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
                                                                                               ldx, c0, xt);
   h->launches += 1;
   if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
+  // the near field needs only x_t: on the packed path it runs on the aux
+  // stream beside the low-rank applies (HBM-bound against instruction-bound)
+  // and joins before the final sum; it is enqueued after the V-apply so that
+  // the persistent panel CTAs are placed first
+  if (packed) HD_CUDA(cudaEventRecord(h->ev_fork, st));
+  auto fork_near = [&]() -> int {
+    if (!packed) return HODLRDD_OK;
+    HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
+    if constexpr (NR == 1 && !F64) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
+    if (prof) HD_CUDA(cudaEventRecord(ev[6], h->aux));
+    HD_CUDA(cudaEventRecord(h->ev_join, h->aux));
+    return HODLRDD_OK;
+  };
   using C = PanelCfg<T, NR>;
   const float* sa = Fac<T>::scaled ? h->sv.p : nullptr;
   const float* sb = Fac<T>::scaled ? h->su.p : nullptr;
@@ -1643,6 +1652,7 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
       }
     }
   }
+  HD_TRY(fork_near());
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
   if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
     k_panel<T, NR, false><<<P.us.ctas, kSegThreads, C::kSmem, st>>>(
@@ -1657,8 +1667,12 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
-    if constexpr (NR == 1 && !F64)
-      HD_TRY((launch_tiles<IO>(h, st, sms, reinterpret_cast<const float*>(xt), yl, y, ldx, c0)));
+    HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
+    if constexpr (NR == 1 && !F64) {
+      k_finish<IO><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(
+          h->ynear.p, reinterpret_cast<const float*>(yl), h->kappa, h->N, h->perm.p, y);
+      h->launches += 1;
+    }
   } else switch (h->d) {
     case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
     case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;

@@ -319,6 +319,8 @@ struct hodlrdd_s {
   hodlrdd_options opt{};
   int device = 0;
   cudaStream_t st = nullptr;  // the handle's own stream (build, staging)
+  cudaStream_t aux = nullptr; // second stream: the packed near field runs beside the low-rank applies
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // tree
   int B = 0, kappa = 0;
@@ -353,12 +355,13 @@ struct hodlrdd_s {
   // xt and tbuf carry zero guards of kGuard elements on both sides
   hd::DevBuf<char> xt, tbuf, ylev, xstage, ystage;
   hd::DevBuf<char> pbuf;       // partial sums of cut panels
+  hd::DevBuf<float> ynear;     // packed near-field sums (tree order)
   hd::DevBuf<int32_t> err;     // device error word of bounded waits
 
   // tracing: events between matvec stages, resolved by hodlrdd_get_profile
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::vector<cudaEvent_t>> ev_pending;  // per chunk: 5 events
+  std::vector<std::vector<cudaEvent_t>> ev_pending;  // per chunk: 5 events on the matvec stream (+ 2 on aux)
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_chunks = 0;
   int64_t launches = 0;
