@@ -341,16 +341,20 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 
   const int cw = warp - 1;
   const int ct = cw * 32 + lane;
-  // FP32 with one or two right-hand sides: compensated (Kahan) accumulation
-  // of the per-stage sums; otherwise plain accumulation (register budget)
+  // FP32 with one or two right-hand sides: plain sums over up to kKahanStages
+  // stages, added to the total with compensation (Kahan); otherwise plain
+  // accumulation (register budget)
   constexpr bool KAHAN = std::is_same<T, float>::value && NR <= 2;
-  Acc acc[E][NR], cmp[E][NR];
+  constexpr int kKahanStages = 4;
+  Acc acc[E][NR], cmp[E][NR], sum[E][NR];
+  int nsum = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e)
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       acc[e][r] = Acc(0);
       cmp[e][r] = Acc(0);
+      sum[e][r] = Acc(0);
     }
   // V-apply writers (line class 0) fetch their output indices and scales when
   // a panel starts, so the panel's end does not wait on them
@@ -378,7 +382,9 @@ __global__ void __launch_bounds__(kSegThreads, 1)
         for (int r = 0; r < NR; ++r) {
           acc[e][r] = Acc(0);
           cmp[e][r] = Acc(0);
+          sum[e][r] = Acc(0);
         }
+      nsum = 0;
       if constexpr (VMODE) {
         if (cg == 0 && rc < RC && P.part < 0) {
 #pragma unroll
@@ -392,11 +398,6 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     }
     if (rc < RC) {
       if constexpr (KAHAN) {
-        Acc sum[E][NR];
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-#pragma unroll
-          for (int r = 0; r < NR; ++r) sum[e][r] = Acc(0);
 #pragma unroll 4
         for (int k = cg; k < st.nseg; k += CG) {
           Acc f[E];
@@ -406,15 +407,19 @@ __global__ void __launch_bounds__(kSegThreads, 1)
 #pragma unroll
             for (int r = 0; r < NR; ++r) sum[e][r] += f[e] * sv[k * NR + r];
         }
+        if (++nsum == kKahanStages || st.last) {
 #pragma unroll
-        for (int e = 0; e < E; ++e)
+          for (int e = 0; e < E; ++e)
 #pragma unroll
-          for (int r = 0; r < NR; ++r) {
-            const Acc y = sum[e][r] - cmp[e][r];
-            const Acc s2 = acc[e][r] + y;
-            cmp[e][r] = (s2 - acc[e][r]) - y;
-            acc[e][r] = s2;
-          }
+            for (int r = 0; r < NR; ++r) {
+              const Acc y = sum[e][r] - cmp[e][r];
+              const Acc s2 = acc[e][r] + y;
+              cmp[e][r] = (s2 - acc[e][r]) - y;
+              acc[e][r] = s2;
+              sum[e][r] = Acc(0);
+            }
+          nsum = 0;
+        }
       } else {
 #pragma unroll 4
         for (int k = cg; k < st.nseg; k += CG) {
