@@ -25,6 +25,7 @@ SOURCES = {
     "aca.cu": ["--fmad=false"],
     "apply.cu": [],
     "noalloc.cu": [],
+    "near.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

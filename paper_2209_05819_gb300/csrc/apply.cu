@@ -44,7 +44,6 @@ constexpr int kStageBytes = 32768;
 constexpr int kConsumerWarps = 16;
 constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
 constexpr int kPanelRows = 512;                // rows per U panel
-constexpr int kGuard = 16;                        // zero elements around xt and t (per rhs)
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at GB300 clocks
 
 enum { ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_DRAIN = 3 };
@@ -613,262 +612,6 @@ __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, i
 // point is one float4 (box-relative coordinates, x_t in .w); a source box is an
 // int4 {J0, n} and its exact box offset; the kernel function is a template
 // parameter so the pair loop has no branch on it.
-// Hardware reciprocal (square root) approximations, PTX rsqrt / rcp
-// .approx.ftz (relative error below 2^-22); the packed path treats squared
-// distances below the smallest normal FP32 number as coincident points.
-__device__ __forceinline__ float rsqrt_hw(float s) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  return r;
-}
-__device__ __forceinline__ float rcp_hw(float s) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  return r;
-}
-constexpr float kTinySq = 1.17549435e-38f;  // smallest normal FP32 number
-
-template <int KID>
-__device__ __forceinline__ float f32k(float s, float c) {
-  if constexpr (KID == HODLRDD_K_LOG) return s == 0.0f ? 0.0f : 0.5f * logf(s);
-  else if constexpr (KID == HODLRDD_K_INV_R) return s < kTinySq ? 0.0f : rsqrt_hw(s);
-  else if constexpr (KID == HODLRDD_K_MATERN32) {
-    const float a = c * sqrtf(s);
-    return (1.0f + a) * expf(-a);
-  } else if constexpr (KID == HODLRDD_K_GAUSS) return expf(-c * s);
-  else if constexpr (KID == HODLRDD_K_EXP) return expf(-c * sqrtf(s));
-  else if constexpr (KID == HODLRDD_K_INV_R2_4D) return s < kTinySq ? 0.0f : c * rcp_hw(s);
-  else if constexpr (KID == HODLRDD_K_R) return sqrtf(s);
-  else if constexpr (KID == HODLRDD_K_SIN) return sinf(sqrtf(s));
-  else return rsqrt_hw(1.0f + sqrtf(s));
-}
-
-// Packed dense work (FP32, d <= 3, one right-hand side), one CTA per task.
-// A task is up to kTileRows target rows [I0, I0 + m) of one box I at level l
-// and a list of source ranges J. Coordinates are box-relative at level l and
-// kept as FP32 pairs hi + lo (split from FP64 at build); a source is moved into
-// I's frame by the exact FP32 offset (c_J - c_I) h_l with an error-free sum, so
-// x_i - x_j = (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy of the
-// distance itself. Sources are staged through shared memory in chunks planned
-// on the host (entry .z = position in the chunk, .w on a chunk's first entry =
-// the entry after the chunk); then threads holding two target rows each sweep
-// the chunk in S source stripes. Result: ynear[i] += scale * sum + diag * x_i
-// (diag is passed as 0 except for the pass that owns the diagonal).
-constexpr int kTileThreads = 256;
-constexpr int kTileRows = 256;
-constexpr int kTileCap = 1024;
-
-// a + b = s + e exactly (Knuth's two-sum).
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-  return s;
-}
-
-template <int D>
-__device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, const float4& sh, const float4& sl) {
-  float t = (th.x - sh.x) + (tl.x - sl.x);
-  float s = t * t;
-  if (D > 1) {
-    t = (th.y - sh.y) + (tl.y - sl.y);
-    s = fmaf(t, t, s);
-  }
-  if (D > 2) {
-    t = (th.z - sh.z) + (tl.z - sl.z);
-    s = fmaf(t, t, s);
-  }
-  return s;
-}
-
-template <int D, int KID>
-__global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
-                                                      const int4* __restrict__ srcs, const float4* __restrict__ soff,
-                                                      const float4* __restrict__ Hi, const float4* __restrict__ Lo,
-                                                      const float* __restrict__ xt, float kc, float kscale,
-                                                      float kdiag, float* __restrict__ ynear) {
-  __shared__ float4 shi[kTileCap];  // hi coordinates in the task's frame, x_j in .w
-  __shared__ float4 slo[kTileCap];  // lo coordinates
-  __shared__ float red[kTileThreads], red2[kTileThreads];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
-    const int4 T = tasks[it];
-    // each thread holds two target rows, gi and gi + G
-    int G = 1;
-    while (2 * G < T.y) G <<= 1;
-    const int S = kTileThreads / G;
-    const int gi = tid % G, stripe = tid / G;
-    const bool va = gi < T.y, vb = gi + G < T.y;
-    const int ra = T.x + gi, rb = T.x + gi + G;
-    float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
-    float xa = 0.f, xb = 0.f;
-    if (va) {
-      tha = Hi[ra];
-      tla = Lo[ra];
-      xa = xt[ra];
-    }
-    if (vb) {
-      thb = Hi[rb];
-      tlb = Lo[rb];
-      xb = xt[rb];
-    }
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-    for (int e = T.z; e < T.w;) {
-      const int e1 = srcs[e].w;
-      __syncthreads();  // the previous chunk has been consumed
-      for (int b = e + warp; b < e1; b += kTileThreads / 32) {
-        const int4 sj = srcs[b];
-        const float4 of = soff[b];
-        for (int k = lane; k < sj.y; k += 32) {
-          const float4 h = Hi[sj.x + k], l = Lo[sj.x + k];
-          float ex, ey, ez;
-          const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
-          shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
-          slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
-        }
-      }
-      const int4 lastb = srcs[e1 - 1];
-      const int n = lastb.z + lastb.y;
-      __syncthreads();
-      int f = stripe;
-      for (; f + S < n; f += 2 * S) {
-        const float4 h0 = shi[f], l0 = slo[f], h1 = shi[f + S], l1 = slo[f + S];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-        a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
-        b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
-      }
-      if (f < n) {
-        const float4 h0 = shi[f], l0 = slo[f];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-      }
-      e = e1;
-    }
-    red[tid] = a0 + a1;
-    red2[tid] = b0 + b1;
-    __syncthreads();
-    if (stripe == 0) {
-      float acc_a = 0.f, acc_b = 0.f;
-      for (int s = 0; s < S; ++s) {
-        acc_a += red[s * G + gi];
-        acc_b += red2[s * G + gi];
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const bool v = q == 0 ? va : vb;
-        if (!v) continue;
-        const int row = q == 0 ? ra : rb;
-        const float acc = q == 0 ? acc_a : acc_b;
-        ynear[row] += kscale * acc + kdiag * (q == 0 ? xa : xb);
-      }
-    }
-    __syncthreads();  // red and the staging arrays are reused by the next task
-  }
-}
-
-// Direct on-the-fly product y = K x over all N^2 pairs (FP32 arithmetic, d <=
-// 3, one right-hand side): the exact-by-definition comparator of the HODLRdD
-// product. Coordinates relative to the bounding cube's corner as FP32 hi + lo
-// pairs; each CTA holds 2 x kDirectThreads targets and streams every source
-// through shared memory; sums are compensated.
-constexpr int kDirectThreads = 128;
-
-template <int D, int KID>
-__global__ void __launch_bounds__(kDirectThreads) k_direct(const float4* __restrict__ Hi,
-                                                          const float4* __restrict__ Lo,
-                                                          const float* __restrict__ xt, int64_t N, float kc,
-                                                          float kscale, float kdiag,
-                                                          const int32_t* __restrict__ perm, float* __restrict__ y) {
-  __shared__ float4 shi[kTileCap];
-  __shared__ float4 slo[kTileCap];
-  const int tid = threadIdx.x;
-  const int64_t ra = (int64_t)blockIdx.x * 2 * kDirectThreads + tid, rb = ra + kDirectThreads;
-  float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
-  if (ra < N) {
-    tha = Hi[ra];
-    tla = Lo[ra];
-  }
-  if (rb < N) {
-    thb = Hi[rb];
-    tlb = Lo[rb];
-  }
-  // compensated (Kahan) sums: N terms per target
-  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, ca0 = 0.f, ca1 = 0.f, cb0 = 0.f, cb1 = 0.f;
-  auto kadd = [](float& sum, float& comp, float term) {
-    const float yv = term - comp;
-    const float t = sum + yv;
-    comp = (t - sum) - yv;
-    sum = t;
-  };
-  for (int64_t c0 = 0; c0 < N; c0 += kTileCap) {
-    const int n = N - c0 < kTileCap ? (int)(N - c0) : kTileCap;
-    __syncthreads();  // the previous chunk has been consumed
-    for (int k = tid; k < n; k += kDirectThreads) {
-      float4 h = Hi[c0 + k];
-      h.w = xt[c0 + k];
-      shi[k] = h;
-      slo[k] = Lo[c0 + k];
-    }
-    __syncthreads();
-    int f = 0;
-    for (; f + 1 < n; f += 2) {
-      const float4 h0 = shi[f], l0 = slo[f], h1 = shi[f + 1], l1 = slo[f + 1];
-      kadd(a0, ca0, f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc) * h0.w);
-      kadd(b0, cb0, f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc) * h0.w);
-      kadd(a1, ca1, f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc) * h1.w);
-      kadd(b1, cb1, f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc) * h1.w);
-    }
-    if (f < n) {
-      const float4 h0 = shi[f], l0 = slo[f];
-      kadd(a0, ca0, f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc) * h0.w);
-      kadd(b0, cb0, f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc) * h0.w);
-    }
-  }
-  a0 -= ca0;
-  a1 -= ca1;
-  b0 -= cb0;
-  b1 -= cb1;
-  if (ra < N) y[perm[ra]] = kscale * (a0 + a1) + kdiag * xt[ra];
-  if (rb < N) y[perm[rb]] = kscale * (b0 + b1) + kdiag * xt[rb];
-}
-
-// Box-relative coordinates at level l as FP32 pairs: x - (lo + c_box h) = hi + lo
-// (the difference formed in FP64).
-__global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int l, const int32_t* __restrict__ bstart,
-                          const uint64_t* __restrict__ bkey, int64_t nb, const double* __restrict__ lo, double h,
-                          float4* __restrict__ Hi, float4* __restrict__ Lo) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t a = 0, b = nb;  // last box with bstart <= i
-    while (b - a > 1) {
-      const int64_t mid = (a + b) >> 1;
-      if (bstart[mid] <= i) a = mid; else b = mid;
-    }
-    const uint64_t key = bkey[a];
-    float hv[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < d && k < 3; ++k) {
-      int64_t c = 0;
-      for (int bit = 0; bit < l; ++bit) c |= (int64_t)((key >> (d * bit + k)) & 1u) << bit;
-      const double v = p64[(int64_t)k * N + i] - (lo[k] + (double)c * h);
-      hv[k] = __double2float_rn(v);
-      lv[k] = __double2float_rn(v - (double)hv[k]);
-    }
-    Hi[i] = make_float4(hv[0], hv[1], hv[2], 0.f);
-    Lo[i] = make_float4(lv[0], lv[1], lv[2], 0.f);
-  }
-}
-
-// y[perm[i]] = near(i) + sum over levels of y_l(i) (packed path).
-template <class IO>
-__global__ void k_finish(const float* __restrict__ ynear, const float* __restrict__ ylev, int kappa, int64_t N,
-                         const int32_t* __restrict__ perm, IO* __restrict__ y) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    float tot = ynear[i];
-    for (int l = 1; l <= kappa; ++l) tot += ylev[(int64_t)(l - 1) * N + i];
-    y[perm[i]] = (IO)tot;
-  }
-}
-
 template <class Acc, class IO, int NR>
 __global__ void k_gather(const IO* __restrict__ x, const int32_t* __restrict__ perm, int64_t N, int ldx, int c0,
                          Acc* __restrict__ xt) {
@@ -1338,13 +1081,13 @@ int build_plan(hodlrdd_s* h) {
     int64_t cI[kMaxDim], cJ[kMaxDim];
     coords(l, I, cI);
     coords(l, J, cJ);
-    float v[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < d && k < 3; ++k) v[k] = (float)((double)(cJ[k] - cI[k]) * P.h_box[l]);
-    sl.push_back({make_int2(L.h_bstart[J], L.h_bstart[J + 1] - L.h_bstart[J]), make_float4(v[0], v[1], v[2], 0.f)});
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < d && k < 4; ++k) v[k] = (float)((double)(cJ[k] - cI[k]) * P.h_box[l]);
+    sl.push_back({make_int2(L.h_bstart[J], L.h_bstart[J + 1] - L.h_bstart[J]), make_float4(v[0], v[1], v[2], v[3])});
     need4[l] = 1;
   };
   P.coarse4.clear();
-  if (!f64 && d <= 3) {
+  if (!f64 && d <= 4) {
     for (int l = 1; l < h->kappa; ++l) {
       const Level& L = h->lv[l];
       DenseLevel DL;
@@ -1473,7 +1216,7 @@ int build_plan(hodlrdd_s* h) {
           h->pts64.p, h->N, d, l, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[l], P.rel[l].p);
       HD_CUDA(cudaGetLastError());
     }
-    if (d <= 3) {
+    if (d <= 4) {
       P.hi4.clear();
       P.lo4.clear();
       P.hi4.resize(h->kappa + 1);
@@ -1482,10 +1225,7 @@ int build_plan(hodlrdd_s* h) {
         if (!need4[l]) continue;
         HD_TRY(P.hi4[l].alloc(h->N));
         HD_TRY(P.lo4[l].alloc(h->N));
-        const Level& L = h->lv[l];
-        k_relhilo<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(
-            h->pts64.p, h->N, d, l, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[l], P.hi4[l].p, P.lo4[l].p);
-        HD_CUDA(cudaGetLastError());
+        HD_TRY(launch_relhilo(h, l, P.hi4[l].p, P.lo4[l].p, dlo.p, st));
       }
       HD_TRY(upload(P.tasks4, t4, st));
       HD_TRY(upload(P.srcs4, s4, st));
@@ -1505,7 +1245,7 @@ int alloc_workspace(hodlrdd_s* h) {
   HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * nr * acc));
   const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1});
   HD_TRY(h->pbuf.alloc((size_t)prows * nr * acc));
-  if (h->plan.tasks4.n > 0) HD_TRY(h->ynear.alloc(h->N));
+  if (h->plan.tasks4.n > 0) HD_TRY(h->ynear.alloc((size_t)h->N * nr));
   HD_TRY(h->err.alloc(1));
   HD_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes(), h->st));
   HD_CUDA(cudaMemsetAsync(h->tbuf.p, 0, h->tbuf.bytes(), h->st));
@@ -1551,59 +1291,6 @@ int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl,
   return HODLRDD_OK;
 }
 
-template <int D, int KID>
-void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
-  const Plan& P = h->plan;
-  const float kc = (float)kernel_const(h->K);
-  const float ks = (float)h->K.scale, kd = (float)h->K.diag;
-  float* yn = h->ynear.p;
-  // one CTA per task (the hardware scheduler balances tasks of unequal size)
-  auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
-  for (const DenseLevel& DL : P.coarse4) {
-    k_tile<D, KID><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
-                                                                P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks,
-                                                                0.f, yn);
-    h->launches += 1;
-  }
-  if (P.excl4.t1 > P.excl4.t0) {
-    // low-rank leaf blocks that the parent tiles also evaluate: subtract them
-    k_tile<D, KID><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
-        P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p, xt,
-        kc, -ks, 0.f, yn);
-    h->launches += 1;
-  }
-  k_tile<D, KID><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
-      P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
-      kc, ks, kd, yn);
-  h->launches += 1;
-}
-
-template <int D>
-void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, const float* xt) {
-  switch (h->K.id) {
-    case HODLRDD_K_LOG: launch_tiles_k<D, HODLRDD_K_LOG>(h, st, xt); break;
-    case HODLRDD_K_INV_R: launch_tiles_k<D, HODLRDD_K_INV_R>(h, st, xt); break;
-    case HODLRDD_K_MATERN32: launch_tiles_k<D, HODLRDD_K_MATERN32>(h, st, xt); break;
-    case HODLRDD_K_GAUSS: launch_tiles_k<D, HODLRDD_K_GAUSS>(h, st, xt); break;
-    case HODLRDD_K_EXP: launch_tiles_k<D, HODLRDD_K_EXP>(h, st, xt); break;
-    case HODLRDD_K_INV_R2_4D: launch_tiles_k<D, HODLRDD_K_INV_R2_4D>(h, st, xt); break;
-    case HODLRDD_K_R: launch_tiles_k<D, HODLRDD_K_R>(h, st, xt); break;
-    case HODLRDD_K_SIN: launch_tiles_k<D, HODLRDD_K_SIN>(h, st, xt); break;
-    default: launch_tiles_k<D, HODLRDD_K_INV_SQRT1P>(h, st, xt); break;
-  }
-}
-
-// Packed near-field launches (FP32, d <= 3, one right-hand side) on stream st,
-// accumulating into ynear (zeroed here).
-void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt) {
-  cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * sizeof(float), st);
-  switch (h->d) {
-    case 1: launch_tiles_d<1>(h, st, xt); break;
-    case 2: launch_tiles_d<2>(h, st, xt); break;
-    default: launch_tiles_d<3>(h, st, xt); break;
-  }
-}
-
 template <class T, class IO, int NR>
 int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t st) {
   using Acc = typename Fac<T>::acc;
@@ -1616,7 +1303,10 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   Acc* yl = reinterpret_cast<Acc*>(h->ylev.p);
   cudaEvent_t ev[7];
   const bool prof = h->profiling;
-  const bool packed = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
+  // packed near field: one right-hand side in d <= 3 (kernel-specialised
+  // tiles), else FP32 multi-RHS tiles for d <= 4
+  const bool packed1 = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
+  const bool packed = !F64 && h->d <= 4 && P.tasks4.n > 0;
   if (prof) {
     HD_TRY(chunk_events(h, ev, packed ? 7 : 5));
     HD_CUDA(cudaEventRecord(ev[0], st));
@@ -1634,7 +1324,10 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     if (!packed) return HODLRDD_OK;
     HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
-    if constexpr (NR == 1 && !F64) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
+    if constexpr (!F64) {
+      if (packed1) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
+      else HD_TRY(launch_tiles_nr(h, h->aux, reinterpret_cast<const float*>(xt), NR));
+    }
     if (prof) HD_CUDA(cudaEventRecord(ev[6], h->aux));
     HD_CUDA(cudaEventRecord(h->ev_join, h->aux));
     return HODLRDD_OK;
@@ -1673,11 +1366,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
-    if constexpr (NR == 1 && !F64) {
-      k_finish<IO><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(
-          h->ynear.p, reinterpret_cast<const float*>(yl), h->kappa, h->N, h->perm.p, y);
-      h->launches += 1;
-    }
+    if constexpr (!F64 && std::is_same<IO, float>::value)
+      HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), y, NR, ldx, c0));
   } else switch (h->d) {
     case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
     case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
@@ -1784,62 +1474,6 @@ int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V) {
     case HODLRDD_PREC_FP16: return unpack_typed<__half>(h, b, U, V);
     default: return unpack_typed<__nv_bfloat16>(h, b, U, V);
   }
-}
-
-namespace {
-template <int D>
-void launch_direct_d(hodlrdd_s* h, cudaStream_t st, const float* xt, float* y) {
-  const Plan& P = h->plan;
-  const float kc = (float)kernel_const(h->K);
-  const float ks = (float)h->K.scale, kd = (float)h->K.diag;
-  const int grid = (int)((h->N + 2 * kDirectThreads - 1) / (2 * kDirectThreads));
-  const float4* Hi = P.hi4[0].p;
-  const float4* Lo = P.lo4[0].p;
-  switch (h->K.id) {
-#define HD_DIRECT(K) \
-  case K: k_direct<D, K><<<grid, kDirectThreads, 0, st>>>(Hi, Lo, xt, h->N, kc, ks, kd, h->perm.p, y); break;
-    HD_DIRECT(HODLRDD_K_LOG) HD_DIRECT(HODLRDD_K_INV_R) HD_DIRECT(HODLRDD_K_MATERN32) HD_DIRECT(HODLRDD_K_GAUSS)
-    HD_DIRECT(HODLRDD_K_EXP) HD_DIRECT(HODLRDD_K_INV_R2_4D) HD_DIRECT(HODLRDD_K_R) HD_DIRECT(HODLRDD_K_SIN)
-    default: k_direct<D, HODLRDD_K_INV_SQRT1P><<<grid, kDirectThreads, 0, st>>>(Hi, Lo, xt, h->N, kc, ks, kd,
-                                                                                h->perm.p, y);
-#undef HD_DIRECT
-  }
-}
-}  // namespace
-
-int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st) {
-  if (h->opt.precision == HODLRDD_PREC_FP64 || h->d > 3) {
-    set_error("hodlrdd_direct: needs an FP32, FP16 or BF16 handle and d <= 3");
-    return HODLRDD_ERR_UNSUPPORTED;
-  }
-  Plan& P = h->plan;
-  if (P.hi4.empty()) P.hi4.resize(h->kappa + 1);
-  if (P.lo4.empty()) P.lo4.resize(h->kappa + 1);
-  if (!P.hi4[0].p) {  // cube-relative coordinates, made on the first call
-    std::vector<double> hlo(h->lo, h->lo + h->d);
-    DevBuf<double> dlo;
-    HD_TRY(upload(dlo, hlo, st));
-    HD_TRY(P.hi4[0].alloc(h->N));
-    HD_TRY(P.lo4[0].alloc(h->N));
-    const Level& L = h->lv[0];
-    k_relhilo<<<(int)std::min<int64_t>((h->N + 255) / 256, 152 * 16), 256, 0, st>>>(
-        h->pts64.p, h->N, h->d, 0, L.bstart.p, L.bkey.p, L.nb, dlo.p, P.h_box[0], P.hi4[0].p, P.lo4[0].p);
-    HD_CUDA(cudaGetLastError());
-    HD_CUDA(cudaStreamSynchronize(st));
-  }
-  float* xt = reinterpret_cast<float*>(h->xt.p) + (size_t)kGuard;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  k_gather<float, float, 1><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p,
-                                                                                                   h->N, 1, 0, xt);
-  switch (h->d) {
-    case 1: launch_direct_d<1>(h, st, xt, y); break;
-    case 2: launch_direct_d<2>(h, st, xt, y); break;
-    default: launch_direct_d<3>(h, st, xt, y); break;
-  }
-  HD_CUDA(cudaGetLastError());
-  h->launches += 2;
-  return HODLRDD_OK;
 }
 
 int read_error_word(hodlrdd_s* h, int32_t* code) {

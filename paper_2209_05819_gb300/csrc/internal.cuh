@@ -383,6 +383,15 @@ int build_plan(hodlrdd_s* h);
 int alloc_workspace(hodlrdd_s* h);
 int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
 int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st);
+// Near field (near.cu).
+constexpr int kGuard = 16;        // zero elements around xt and t (per right-hand side)
+constexpr int kTileThreads = 256; // threads of a near-field tile CTA
+constexpr int kTileRows = 256;    // target rows per tile task
+constexpr int kTileCap = 1024;    // staged source points per chunk
+void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt);
+int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr);
+int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, float* y, int nr, int ldy, int c0);
+int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
 int read_error_word(hodlrdd_s* h, int32_t* code);
 size_t elem_size(int precision);
