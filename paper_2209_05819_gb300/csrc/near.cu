@@ -283,25 +283,9 @@ __global__ void k_finish(const float* __restrict__ ynear, const float* __restric
   }
 }
 
-// The kernel function chosen at run time (the multi-RHS tiles amortise the
-// branch over NR products per pair).
-__device__ __forceinline__ float f32k_rt(int kid, float s, float c) {
-  switch (kid) {
-    case HODLRDD_K_LOG: return f32k<HODLRDD_K_LOG>(s, c);
-    case HODLRDD_K_INV_R: return f32k<HODLRDD_K_INV_R>(s, c);
-    case HODLRDD_K_MATERN32: return f32k<HODLRDD_K_MATERN32>(s, c);
-    case HODLRDD_K_GAUSS: return f32k<HODLRDD_K_GAUSS>(s, c);
-    case HODLRDD_K_EXP: return f32k<HODLRDD_K_EXP>(s, c);
-    case HODLRDD_K_INV_R2_4D: return f32k<HODLRDD_K_INV_R2_4D>(s, c);
-    case HODLRDD_K_R: return f32k<HODLRDD_K_R>(s, c);
-    case HODLRDD_K_SIN: return f32k<HODLRDD_K_SIN>(s, c);
-    default: return f32k<HODLRDD_K_INV_SQRT1P>(s, c);
-  }
-}
-
 // Packed dense work for NR right-hand sides (FP32 arithmetic, d <= 4), one CTA
-// per task as in k_tile, two target rows per thread: each pair's kernel value
-// multiplies the NR values of its source. x_t and ynear hold NR values per
+// per task as in k_tile, two target rows per thread, specialised on the kernel
+// function: each pair's kernel value multiplies the NR values of its source. x_t and ynear hold NR values per
 // point. Dynamic shared memory: kTileCap staged sources (hi, lo, NR values)
 // and the stripe reduction.
 template <int NR>
@@ -326,13 +310,13 @@ __device__ __forceinline__ void load_x(const float* p, float (&v)[NR]) {
   }
 }
 
-template <int D, int NR>
+template <int D, int NR, int KID>
 __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                          const int4* __restrict__ srcs,
                                                          const float4* __restrict__ soff,
                                                          const float4* __restrict__ Hi, const float4* __restrict__ Lo,
-                                                         const float* __restrict__ xt, int kid, float kc,
-                                                         float kscale, float kdiag, float* __restrict__ ynear) {
+                                                         const float* __restrict__ xt, float kc, float kscale,
+                                                         float kdiag, float* __restrict__ ynear) {
   extern __shared__ __align__(16) char tsm[];
   float4* shi = reinterpret_cast<float4*>(tsm);
   float4* slo = shi + kTileCap;
@@ -385,8 +369,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
 #pragma unroll 2
       for (int f = stripe; f < n; f += S) {
         const float4 hs = shi[f], ls = slo[f];
-        const float ka = f32k_rt(kid, sqdist2<D>(tha, tla, hs, ls), kc);
-        const float kb = f32k_rt(kid, sqdist2<D>(thb, tlb, hs, ls), kc);
+        const float ka = f32k<KID>(sqdist2<D>(tha, tla, hs, ls), kc);
+        const float kb = f32k<KID>(sqdist2<D>(thb, tlb, hs, ls), kc);
         float xv[NR];
         load_x<NR>(sx + f * NR, xv);
 #pragma unroll
@@ -477,37 +461,51 @@ void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt) {
 
 
 namespace {
-template <int D, int NR>
-int launch_tiles_nr_dn(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+template <int D, int NR, int KID>
+int launch_tiles_nr_dnk(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   static bool attr = false;
   if (!attr) {
-    HD_CUDA(cudaFuncSetAttribute(k_tile_nr<D, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HD_CUDA(cudaFuncSetAttribute(k_tile_nr<D, NR, KID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_nr_smem<NR>()));
     attr = true;
   }
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
   const float ks = (float)h->K.scale, kd = (float)h->K.diag;
-  const int kid = h->K.id;
   float* yn = h->ynear.p;
   const size_t smem = tile_nr_smem<NR>();
   auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
   for (const DenseLevel& DL : P.coarse4) {
-    k_tile_nr<D, NR><<<grid(DL.t1 - DL.t0), kTileThreads, smem, st>>>(
-        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kid, kc, ks, 0.f, yn);
+    k_tile_nr<D, NR, KID><<<grid(DL.t1 - DL.t0), kTileThreads, smem, st>>>(
+        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks, 0.f, yn);
     h->launches += 1;
   }
   if (P.excl4.t1 > P.excl4.t0) {
-    k_tile_nr<D, NR><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, smem, st>>>(
+    k_tile_nr<D, NR, KID><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, smem, st>>>(
         P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p, xt,
-        kid, kc, -ks, 0.f, yn);
+        kc, -ks, 0.f, yn);
     h->launches += 1;
   }
-  k_tile_nr<D, NR><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, smem, st>>>(
+  k_tile_nr<D, NR, KID><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, smem, st>>>(
       P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
-      kid, kc, ks, kd, yn);
+      kc, ks, kd, yn);
   h->launches += 1;
   return HODLRDD_OK;
+}
+
+template <int D, int NR>
+int launch_tiles_nr_dn(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  switch (h->K.id) {
+    case HODLRDD_K_LOG: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_LOG>(h, st, xt);
+    case HODLRDD_K_INV_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R>(h, st, xt);
+    case HODLRDD_K_MATERN32: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_MATERN32>(h, st, xt);
+    case HODLRDD_K_GAUSS: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_GAUSS>(h, st, xt);
+    case HODLRDD_K_EXP: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_EXP>(h, st, xt);
+    case HODLRDD_K_INV_R2_4D: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R2_4D>(h, st, xt);
+    case HODLRDD_K_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_R>(h, st, xt);
+    case HODLRDD_K_SIN: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_SIN>(h, st, xt);
+    default: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_SQRT1P>(h, st, xt);
+  }
 }
 
 template <int D>
