@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--cpu-sample-n", type=int, default=32768)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-many-rhs", action="store_true", help="skip the many-right-hand-side (d=4, nrhs 64) line")
     return p.parse_args()
 
 
@@ -254,6 +255,33 @@ def cpu_baseline(args, rank_w):
                       f"{nrow} rows scaled to all rows"}
 
 
+def many_rhs_line(args, torch, stream, hd):
+    """The many-right-hand-side workload in the headline precision, its error
+    against the FP64 form, and the plain FP64 time."""
+    import workloads as W
+
+    w = W.many_rhs_4d(seed=args.seed)
+    pts = torch.from_numpy(w.points).cuda()
+    out = {"workload": f"d=4 N={w.N} uniform [0,1]^4, Matern-3/2 l=0.2, leaf {w.leaf}, tol {w.tol:g}, "
+                       f"nrhs {w.nrhs}"}
+    res = {}
+    for prec in (args.precision, "fp64"):
+        h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, max_nrhs=w.nrhs)
+        io = torch.float64 if prec == "fp64" else torch.float32
+        x = torch.from_numpy(np.ascontiguousarray(w.x)).to(io).cuda()
+        y = torch.empty_like(x)
+        n = 5 if prec != "fp64" else 1
+        t = time_steps(lambda: h.matvec(x, y), n, 1, torch, stream)
+        res[prec] = (t / n, y.double())
+        h.close()
+    t32, y32 = res[args.precision]
+    t64, y64 = res["fp64"]
+    err = float((torch.linalg.norm(y32 - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
+    out.update({"ms_per_matvec": 1e3 * t32, "value": w.N * w.nrhs / t32, "unit": UNIT,
+                "rel_err_vs_fp64": err, "fp64_ms_per_matvec": 1e3 * t64, "speedup_vs_fp64": t64 / t32})
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -412,6 +440,11 @@ def main():
             "stage_ms": {k: round(v, 4) for k, v in stage.items()},
             "stage_share": {k: round(v / sum(stage.values()), 4) for k, v in stage.items()}}
 
+    # many right-hand sides (d=4, N=65536, Matern-3/2, leaf 128, tol 1e-8, nrhs 64)
+    many = None
+    if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
+        many = many_rhs_line(args, torch, stream, hd)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w)
@@ -429,6 +462,7 @@ def main():
             "rel_err_vs_fp64": err, "meets_err_bar": (err is not None and err <= ERR_BAR),
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
             "direct_gpu": direct,
+            "many_rhs": many,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
                                                    "t_pack_ms")},
             "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],

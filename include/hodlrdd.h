@@ -80,8 +80,9 @@ typedef struct hodlrdd_options {
                            0: every IL block is applied through its ACA factors, as
                            in Algorithm 2. */
   int max_nrhs;         /* >= 1 (default 8). Right-hand sides are processed in chunks
-                           of at most 8 through a workspace sized at build; any nrhs
-                           is accepted */
+                           through a workspace sized at build: chunks of up to 16 for
+                           FP32 handles with d <= 4 when max_nrhs >= 16, else up to 8;
+                           any nrhs is accepted */
   int aca_max_rank;     /* cap on the ACA rank of blocks larger than 2048 rows or
                            columns (default 1024); a block that does not converge
                            within its cap is applied exactly instead */

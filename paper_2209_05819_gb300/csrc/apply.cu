@@ -1238,7 +1238,10 @@ int build_plan(hodlrdd_s* h) {
 }
 
 int alloc_workspace(hodlrdd_s* h) {
-  const int nr = 8;
+  // chunks of up to 16 right-hand sides (FP32 with the packed near field)
+  // when the caller asked for more than 8, else up to 8
+  const int nr = h->opt.max_nrhs >= 16 && h->opt.precision == HODLRDD_PREC_FP32 && h->d <= 4 ? 16 : 8;
+  h->wnr = nr;
   const size_t acc = h->opt.precision == HODLRDD_PREC_FP64 ? 8 : 4;
   HD_TRY(h->xt.alloc(((size_t)h->N + 2 * kGuard) * nr * acc));
   HD_TRY(h->tbuf.alloc(((size_t)h->total_rank + 2 * kGuard) * nr * acc));
@@ -1368,12 +1371,17 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if constexpr (!F64 && std::is_same<IO, float>::value)
       HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), y, NR, ldx, c0));
-  } else switch (h->d) {
-    case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
-    case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
-    case 3: HD_TRY((launch_dense<Acc, IO, NR, 3, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
-    case 4: HD_TRY((launch_dense<Acc, IO, NR, 4, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
-    default: HD_TRY((launch_dense<Acc, IO, NR, 0, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+  } else if constexpr (NR <= 8) {
+    switch (h->d) {
+      case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+      case 2: HD_TRY((launch_dense<Acc, IO, NR, 2, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+      case 3: HD_TRY((launch_dense<Acc, IO, NR, 3, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+      case 4: HD_TRY((launch_dense<Acc, IO, NR, 4, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+      default: HD_TRY((launch_dense<Acc, IO, NR, 0, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
+    }
+  } else {
+    set_error("matvec: chunks of 16 right-hand sides need the packed near field");
+    return HODLRDD_ERR_UNSUPPORTED;
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[4], st));
   HD_CUDA(cudaGetLastError());
@@ -1396,6 +1404,7 @@ int set_smem_attr() {
   HD_TRY((set_smem_attr_nr<T, 2>()));
   HD_TRY((set_smem_attr_nr<T, 4>()));
   HD_TRY((set_smem_attr_nr<T, 8>()));
+  if constexpr (std::is_same<T, float>::value) HD_TRY((set_smem_attr_nr<T, 16>()));
   done = true;
   return HODLRDD_OK;
 }
@@ -1406,7 +1415,12 @@ int matvec_typed(hodlrdd_s* h, const IO* x, IO* y, int nrhs, cudaStream_t st) {
   int c0 = 0;
   while (c0 < nrhs) {
     const int rem = nrhs - c0;
-    if (rem >= 8) { HD_TRY((matvec_chunk<T, IO, 8>(h, x, y, nrhs, c0, st))); c0 += 8; }
+    bool wide = false;
+    if constexpr (std::is_same<T, float>::value) wide = rem >= 16 && h->wnr >= 16 && h->plan.tasks4.n > 0;
+    if (wide) {
+      if constexpr (std::is_same<T, float>::value) HD_TRY((matvec_chunk<T, IO, 16>(h, x, y, nrhs, c0, st)));
+      c0 += 16;
+    } else if (rem >= 8) { HD_TRY((matvec_chunk<T, IO, 8>(h, x, y, nrhs, c0, st))); c0 += 8; }
     else if (rem >= 4) { HD_TRY((matvec_chunk<T, IO, 4>(h, x, y, nrhs, c0, st))); c0 += 4; }
     else if (rem >= 2) { HD_TRY((matvec_chunk<T, IO, 2>(h, x, y, nrhs, c0, st))); c0 += 2; }
     else { HD_TRY((matvec_chunk<T, IO, 1>(h, x, y, nrhs, c0, st))); c0 += 1; }

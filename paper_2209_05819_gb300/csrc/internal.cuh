@@ -354,6 +354,7 @@ struct hodlrdd_s {
   // matvec workspace (right-hand sides are processed in chunks of at most 8);
   // xt and tbuf carry zero guards of kGuard elements on both sides
   hd::DevBuf<char> xt, tbuf, ylev, xstage, ystage;
+  int wnr = 8;                 // right-hand sides per chunk the workspace holds (8 or 16)
   hd::DevBuf<char> pbuf;       // partial sums of cut panels
   hd::DevBuf<float> ynear;     // packed near-field sums (tree order)
   hd::DevBuf<int32_t> err;     // device error word of bounded waits

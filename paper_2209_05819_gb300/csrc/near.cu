@@ -288,9 +288,12 @@ __global__ void k_finish(const float* __restrict__ ynear, const float* __restric
 // function: each pair's kernel value multiplies the NR values of its source. x_t and ynear hold NR values per
 // point. Dynamic shared memory: kTileCap staged sources (hi, lo, NR values)
 // and the stripe reduction.
+// The stripe reduction (kTileThreads x 2 x NR floats) reuses the staging area.
 template <int NR>
 constexpr size_t tile_nr_smem() {
-  return (size_t)kTileCap * (2 * sizeof(float4) + NR * sizeof(float)) + (size_t)kTileThreads * 2 * NR * sizeof(float);
+  const size_t stage = (size_t)kTileCap * (2 * sizeof(float4) + NR * sizeof(float));
+  const size_t red = (size_t)kTileThreads * 2 * NR * sizeof(float);
+  return stage > red ? stage : red;
 }
 
 template <int NR>
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
   float4* shi = reinterpret_cast<float4*>(tsm);
   float4* slo = shi + kTileCap;
   float* sx = reinterpret_cast<float*>(slo + kTileCap);
-  float* red = sx + (size_t)kTileCap * NR;  // kTileThreads * 2 * NR
+  float* red = reinterpret_cast<float*>(tsm);  // kTileThreads * 2 * NR, after the last chunk
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
     const int4 T = tasks[it];
@@ -381,6 +384,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
       }
       e = e1;
     }
+    __syncthreads();  // every thread is done with the staged sources
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       red[(2 * tid) * NR + r] = aa[r];
@@ -514,7 +518,8 @@ int launch_tiles_nr_d(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr) {
     case 1: return launch_tiles_nr_dn<D, 1>(h, st, xt);
     case 2: return launch_tiles_nr_dn<D, 2>(h, st, xt);
     case 4: return launch_tiles_nr_dn<D, 4>(h, st, xt);
-    default: return launch_tiles_nr_dn<D, 8>(h, st, xt);
+    case 8: return launch_tiles_nr_dn<D, 8>(h, st, xt);
+    default: return launch_tiles_nr_dn<D, 16>(h, st, xt);
   }
 }
 
@@ -548,7 +553,8 @@ int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, float* y, in
     case 1: k_finish<1><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
     case 2: k_finish<2><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
     case 4: k_finish<4><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
-    default: k_finish<8><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
+    case 8: k_finish<8><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
+    default: k_finish<16><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
   }
   h->launches += 1;
   HD_CUDA(cudaGetLastError());

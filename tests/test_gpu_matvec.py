@@ -295,3 +295,21 @@ def test_fp32_four_dims_multi_rhs(env, nrhs, kernel, params):
     y32 = gpu_matvec(h32, w.x)
     h32.sync()
     assert relerr(y32, y64) <= (MIXED_BOUND["fp32"] if nrhs < 4 else FP32_WIDE_BOUND)
+
+
+@pytest.mark.parametrize("d,nrhs", [(3, 16), (4, 20), (2, 35)])
+def test_fp32_wide_chunks(env, d, nrhs):
+    """With max_nrhs >= 16 an FP32 handle applies chunks of 16 right-hand sides
+    (panels and near-field tiles 16 wide); every column agrees with the FP64 form
+    and with the same columns applied alone."""
+    torch, oracle, hd = env
+    w = W.make("t", d, 7000, W.K_MATERN32 if d == 4 else W.K_INV_R, (1, 0, 0.3, 0) if d == 4 else (1, 0, 0, 0),
+               40, 1e-7, nrhs=nrhs, seed=7000 + nrhs)
+    h64 = gpu_handle(hd, w)
+    hw = gpu_handle(hd, w, precision="fp32", max_nrhs=64)
+    y64 = gpu_matvec(h64, w.x)
+    yw = gpu_matvec(hw, w.x)
+    hw.sync()
+    assert relerr(yw, y64) <= FP32_WIDE_BOUND
+    y1 = gpu_matvec(hw, w.x[:, 3:4])
+    assert relerr(yw[:, 3:4], y1) <= 2 * FP32_WIDE_BOUND
