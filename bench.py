@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-many-rhs", action="store_true", help="skip the many-right-hand-side (d=4, nrhs 64) line")
+    p.add_argument("--no-solve", action="store_true", help="skip the integral-equation solve line")
     return p.parse_args()
 
 
@@ -282,6 +283,32 @@ def many_rhs_line(args, torch, stream, hd):
     return out
 
 
+def solve_line(args, torch, hd, N=65536):
+    """(I + K/N) u = b on N points of the benchmark distribution, to a relative
+    FP64 residual of 1e-10: GMRES on the headline-precision operator inside FP64
+    refinement, against GMRES on the FP64 operator alone."""
+    import workloads as W
+
+    w = W.precision_3d(N=N, seed=args.seed, system=True)
+    pts = torch.from_numpy(w.points).cuda()
+    h64 = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp64")
+    hlo = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision)
+    b = torch.from_numpy(np.ascontiguousarray(w.x[:, 0])).cuda()
+    out = {"workload": f"(I + K/N) u = b, d=3 N={N} uniform [-1,1]^3, F=1/r, leaf {w.leaf}, tol {w.tol:g}; "
+                       "GMRES(50), x0 = 0, stop at ||b - K x|| <= 1e-10 ||b|| with the FP64 operator"}
+    for name, inner in (("mixed", hlo), ("fp64", h64)):
+        hd.solve(inner, h64, b, tol=1e-10)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = hd.solve(inner, h64, b, tol=1e-10)
+        torch.cuda.synchronize()
+        out[name] = {"ms": 1e3 * (time.perf_counter() - t0), **st}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    hlo.close()
+    h64.close()
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -445,6 +472,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
         many = many_rhs_line(args, torch, stream, hd)
 
+    # second-kind system (I + K/N) u = b: mixed-precision GMRES with FP64 refinement
+    solve = None
+    if rank == 0 and world == 1 and not args.no_solve and args.precision != "fp64":
+        solve = solve_line(args, torch, hd)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w)
@@ -463,6 +495,7 @@ def main():
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
             "direct_gpu": direct,
             "many_rhs": many,
+            "solve": solve,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
                                                    "t_pack_ms")},
             "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],

@@ -217,6 +217,46 @@ int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, int nrhs, v
 int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream);
 
 /*
+ * Solves K x = b, K the handles' kernel matrix, by restarted GMRES on a fast
+ * operator inside iterative refinement with the FP64 operator: the use of the
+ * hierarchical product for the second-kind integral equation (I + K/N) u = b
+ * (diag = 1, scale = 1/N) of the paper's numerical experiments. Each
+ * refinement step solves A d = r with GMRES(restart) on `inner` (classical
+ * Gram-Schmidt applied twice, FP64 dot products) to a relative reduction of
+ * inner_tol, then x += d and r = b - K x with the FP64 matvec of `outer`. x0 = 0;
+ * stops when ||b - K x||_2 <= tol ||b||_2 for the FP64 operator.
+ *
+ *  inner   any-precision handle (FP32 / FP16 / BF16 for speed, FP64 works).
+ *  outer   FP64 handle of the same points and kernel (may be `inner` itself).
+ *  b, x    device, N doubles each, ORIGINAL point order; x is overwritten;
+ *          they must not overlap.
+ *  opt     NULL for the defaults (hodlrdd_solve_options_default).
+ *  stats   optional.
+ *
+ * Synchronous. Allocates its Krylov basis (N x (restart + 1) values) per call.
+ * HODLRDD_ERR_NUMERIC when tol is not reached within max_refine steps (x holds
+ * the last iterate).
+ */
+typedef struct hodlrdd_solve_options {
+  double tol;           /* relative residual of the FP64 operator (default 1e-10) */
+  double inner_tol;     /* residual reduction per inner GMRES solve (default 1e-5) */
+  int restart;          /* GMRES restart length (default 50) */
+  int max_inner_iters;  /* fast matvecs per refinement step (default 500) */
+  int max_refine;       /* refinement steps (default 20) */
+  int reserved[5];      /* set to 0 */
+} hodlrdd_solve_options;
+
+typedef struct hodlrdd_solve_stats {
+  int refinements;       /* FP64 residual evaluations after an inner solve */
+  int inner_iterations;  /* fast-operator matvecs in GMRES */
+  double residual;       /* final ||b - K x|| / ||b|| with the FP64 operator */
+} hodlrdd_solve_stats;
+
+int hodlrdd_solve_options_default(hodlrdd_solve_options* opt);
+int hodlrdd_solve(hodlrdd_handle inner, hodlrdd_handle outer, const double* b, double* x,
+                  const hodlrdd_solve_options* opt, hodlrdd_solve_stats* stats, void* stream);
+
+/*
  * Waits for all device work (cudaDeviceSynchronize) and reports failures the
  * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
  * their bounded waits expired (the y of that matvec is then invalid). Clears the

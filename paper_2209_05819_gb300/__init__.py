@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     HodlrddError,
     header_functions,
     load,
+    solve,
 )
 
 K_LOG, K_INV_R, K_MATERN32, K_GAUSS, K_EXP, K_INV_R2_4D, K_R, K_SIN, K_INV_SQRT1P = range(9)

@@ -34,6 +34,15 @@ class Options(C.Structure):
                 ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("reserved", C.c_int * 7)]
 
 
+class SolveOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("restart", C.c_int), ("max_inner_iters", C.c_int),
+                ("max_refine", C.c_int), ("reserved", C.c_int * 5)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("refinements", C.c_int), ("inner_iterations", C.c_int), ("residual", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("d", C.c_int), ("kappa", C.c_int), ("precision", C.c_int), ("max_rank", C.c_int),
@@ -68,6 +77,8 @@ def load():
         "hodlrdd_matvec": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_matvec_noalloc": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_direct": (i32, [vp, vp, vp, vp]),
+        "hodlrdd_solve_options_default": (i32, [C.POINTER(SolveOptions)]),
+        "hodlrdd_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOptions), C.POINTER(SolveStats), vp]),
         "hodlrdd_destroy": (i32, [vp]),
         "hodlrdd_get_stats": (i32, [vp, C.POINTER(Stats)]),
         "hodlrdd_error_string": (C.c_char_p, [i32]),
@@ -319,6 +330,25 @@ class Handle:
         V = np.ascontiguousarray(V_all, np.float64)
         _check(self._lib.hodlrdd_import_factors(self._h, r.ctypes.data, dn.ctypes.data, U.ctypes.data,
                                                 V.ctypes.data), "hodlrdd_import_factors")
+
+
+def solve(inner: "Handle", outer: "Handle", b, x=None, tol: float = 1e-10, inner_tol: float = 1e-5,
+          restart: int = 50, max_inner_iters: int = 500, max_refine: int = 20, stream=None):
+    """x with K x = b: GMRES on `inner` inside FP64 refinement with `outer`
+    (b, x: CUDA float64 tensors, original order). Returns (x, stats)."""
+    lib = load()
+    o = SolveOptions()
+    lib.hodlrdd_solve_options_default(C.byref(o))
+    o.tol, o.inner_tol, o.restart = float(tol), float(inner_tol), int(restart)
+    o.max_inner_iters, o.max_refine = int(max_inner_iters), int(max_refine)
+    if x is None:
+        x = b.new_empty(b.shape)
+    st = SolveStats()
+    ba, kb = _ptr(b)
+    xa, kx = _ptr(x)
+    _check(lib.hodlrdd_solve(inner._h, outer._h, ba, xa, C.byref(o), C.byref(st), _stream_ptr(stream)),
+           "hodlrdd_solve")
+    return x, {"refinements": st.refinements, "inner_iterations": st.inner_iterations, "residual": st.residual}
 
 
 def debug_fail_alloc_after(k: int):

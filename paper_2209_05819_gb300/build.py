@@ -26,6 +26,7 @@ SOURCES = {
     "apply.cu": [],
     "noalloc.cu": [],
     "near.cu": [],
+    "solve.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]
