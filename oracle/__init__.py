@@ -63,6 +63,8 @@ def _load():
                                      C.POINTER(C.c_int), _i64p, _i64p, _f64p, _f64p]
         lib.or_build.argtypes = [_f64p, C.c_int, C.c_int64, C.c_int, _f64p, C.c_int, C.c_double, C.c_int,
                                  C.POINTER(C.c_void_p)]
+        lib.or_build_ex.argtypes = [_f64p, C.c_int, C.c_int64, C.c_int, _f64p, C.c_int, C.c_double, C.c_int,
+                                    C.c_int, C.POINTER(C.c_void_p)]
         lib.or_destroy.argtypes = [C.c_void_p]
         lib.or_destroy.restype = None
         lib.or_info.argtypes = [C.c_void_p, _i64p]
@@ -147,7 +149,7 @@ def aca_dense(A, tol, flags=0):
 class Tree:
     """The oracle's HODLRdD representation of K for one point set."""
 
-    def __init__(self, points, kernel, params=None, leaf=64, tol=1e-8, dense_if_cheaper=False):
+    def __init__(self, points, kernel, params=None, leaf=64, tol=1e-8, dense_if_cheaper=False, admissible_face_dim=0):
         lib = _load()
         pts = np.ascontiguousarray(points, dtype=np.float64)
         self.N, self.d = pts.shape
@@ -155,7 +157,8 @@ class Tree:
         self.params = _params(params)
         h = C.c_void_p()
         flags = FLAG_DENSE_IF_CHEAPER if dense_if_cheaper else 0
-        rc = lib.or_build(pts, self.d, self.N, self.kernel, self.params, int(leaf), float(tol), flags, C.byref(h))
+        rc = lib.or_build_ex(pts, self.d, self.N, self.kernel, self.params, int(leaf), float(tol), flags,
+                             int(admissible_face_dim), C.byref(h))
         if rc:
             raise ValueError(f"or_build failed ({rc})")
         self._h = h

@@ -129,6 +129,7 @@ struct Block {
 struct Tree {
   Problem P;
   int leaf = 0, flags = 0, B = 0, kappa = 0;
+  int amax = 0;  // admissible face dimension: -1 strong, 0 HODLRdD, d - 1 weak
   double tol = 0.0;
   std::vector<double> lo;
   double side = 0.0, inv = 0.0;
@@ -250,6 +251,13 @@ void build_levels(Tree& T) {
 // at the parent's level, and Algorithm 2 would then add them twice.
 // Far-field = at least one box away (Chebyshev index distance >= 2); sharing a
 // d'-surface = Chebyshev distance 1 with d' zero offsets; a vertex = d' = 0.
+//
+// The admissibility is parameterised by amax, the largest dimension of a face
+// two touching boxes may share and still be compressed: amax = 0 is HODLRdD
+// (far-field and vertex-sharing), amax = -1 the strong condition of H-matrices
+// (far-field only), amax = d - 1 the weak condition of HODLR (every sibling).
+// Then clan(i) takes the parent-level boxes sharing a face of dimension > amax,
+// and the leaf near list the boxes sharing a face of dimension > amax.
 void classify(Tree& T) {
   const int d = T.P.d;
   T.iloff.assign(T.kappa + 1, std::vector<int64_t>(1, 0));
@@ -269,29 +277,31 @@ void classify(Tree& T) {
       for (int64_t j = 0; j < nb; ++j) {
         if (j == i) continue;
         const int64_t* c_j = &coords[(size_t)j * d];
-        // Parent relation: same parent, or parents sharing a d' >= 1 surface.
-        bool pnear = true, pzero = false, psame = true;
+        // Parent relation: same parent, or parents sharing a face of
+        // dimension > amax (number of zero offsets).
+        bool pnear = true, psame = true;
+        int pzeros = 0;
         for (int k = 0; k < d; ++k) {
           int64_t dp = (c_j[k] >> 1) - (c_i[k] >> 1);
           if (dp < -1 || dp > 1) pnear = false;
-          if (dp == 0) pzero = true; else psame = false;
+          if (dp == 0) ++pzeros; else psame = false;
         }
-        if (!pnear || !(psame || pzero)) continue;
+        if (!pnear || !(psame || pzeros > T.amax)) continue;
         int64_t cheb = 0;
-        bool vertex = true;
+        int zeros = 0;
         for (int k = 0; k < d; ++k) {
           int64_t dl = c_j[k] - c_i[k];
           int64_t a = dl < 0 ? -dl : dl;
           cheb = std::max(cheb, a);
-          if (a != 1) vertex = false;
+          if (a == 0) ++zeros;
         }
-        if (cheb >= 2 || vertex) idx.push_back(j);
+        if (cheb >= 2 || zeros <= T.amax) idx.push_back(j);
       }
       off[i + 1] = (int64_t)idx.size();
     }
   }
   // Leaf near field (Algorithm 2's dense part): self and every leaf sharing a
-  // d' >= 1 hyper-surface, in ascending box order.
+  // face of dimension > amax (d' >= 1 for HODLRdD), in ascending box order.
   const int l = T.kappa;
   const int64_t nb = (int64_t)T.bkey[l].size();
   std::vector<int64_t> coords((size_t)nb * d);
@@ -300,15 +310,15 @@ void classify(Tree& T) {
   T.nearidx.clear();
   for (int64_t i = 0; i < nb; ++i) {
     for (int64_t j = 0; j < nb; ++j) {
-      bool zero = false;
+      int zeros = 0;
       int64_t cheb = 0;
       for (int k = 0; k < d; ++k) {
         int64_t dl = coords[(size_t)j * d + k] - coords[(size_t)i * d + k];
         int64_t a = dl < 0 ? -dl : dl;
         cheb = std::max(cheb, a);
-        if (dl == 0) zero = true;
+        if (dl == 0) ++zeros;
       }
-      if (cheb <= 1 && zero) T.nearidx.push_back(j);  // includes j == i
+      if (cheb <= 1 && zeros > T.amax) T.nearidx.push_back(j);  // includes j == i (d zeros)
     }
     T.nearoff[i + 1] = (int64_t)T.nearidx.size();
   }
@@ -633,11 +643,12 @@ int or_aca_dense(const double* A, int64_t m, int64_t n, double tol, int flags, i
   return 0;
 }
 
-int or_build(const double* pts, int d, int64_t N, int kid, const double* prm, int leaf, double tol, int flags,
-             or_tree** out) {
+int or_build_ex(const double* pts, int d, int64_t N, int kid, const double* prm, int leaf, double tol, int flags,
+                int amax, or_tree** out) {
   double p4[4] = {1.0, 0.0, 0.0, 0.0};
   if (prm) std::memcpy(p4, prm, sizeof p4);
   if (!out || !pts || d < 1 || d > 8 || N < 1 || leaf < 1 || !(tol > 0.0) || !valid_kernel(kid, p4)) return 1;
+  if (amax < -1 || amax > d - 1) return 1;
   for (int64_t i = 0; i < N * d; ++i)
     if (!std::isfinite(pts[i])) return 1;
   Tree* T = new (std::nothrow) Tree();
@@ -649,12 +660,18 @@ int or_build(const double* pts, int d, int64_t N, int kid, const double* prm, in
   T->leaf = leaf;
   T->tol = tol;
   T->flags = flags;
+  T->amax = amax;
   bounding_cube(*T);
   build_levels(*T);
   classify(*T);
   compress(*T);
   *out = reinterpret_cast<or_tree*>(T);
   return 0;
+}
+
+int or_build(const double* pts, int d, int64_t N, int kid, const double* prm, int leaf, double tol, int flags,
+             or_tree** out) {
+  return or_build_ex(pts, d, N, kid, prm, leaf, tol, flags, 0, out);
 }
 
 void or_destroy(or_tree* h) { delete reinterpret_cast<Tree*>(h); }
