@@ -92,7 +92,12 @@ typedef struct hodlrdd_options {
                            parent and of its neighbours sharing a d' >= 1 face (low-rank
                            leaf IL blocks inside the tile are subtracted), 2 = one task
                            per leaf box over its near and dense IL lists */
-  int reserved[7];      /* set to 0 */
+  int admissible_face_dim; /* admissibility of touching boxes: the largest
+                           dimension of a shared face for which an IL block is still
+                           compressed. 0 (default): HODLRdD (far-field and
+                           vertex-sharing); -1: strong, far-field only (H-matrix);
+                           d - 1: weak, every sibling (HODLR). Valid: -1 .. d - 1 */
+  int reserved[6];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64

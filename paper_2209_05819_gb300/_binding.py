@@ -31,7 +31,8 @@ class HodlrddError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
-                ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("reserved", C.c_int * 7)]
+                ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("admissible_face_dim", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class SolveOptions(C.Structure):
@@ -150,7 +151,7 @@ class Handle:
 
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
-                 aca_max_rank: int = 1024, near_mode: int = 0):
+                 aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -166,6 +167,7 @@ class Handle:
         opt.max_nrhs = int(max_nrhs)
         opt.aca_max_rank = int(aca_max_rank)
         opt.near_mode = int(near_mode)
+        opt.admissible_face_dim = int(admissible_face_dim)
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:

@@ -1118,7 +1118,7 @@ int build_plan(hodlrdd_s* h) {
         for (int64_t b = b0; b < b1; ++b) (h->h_dense[b] ? list_pairs : excl_pairs) += m * h->h_bn[b];
       }
     }
-    // neighbours of parent boxes sharing a d' >= 1 face, and the box itself
+    // neighbours of parent boxes sharing a face of dimension > amax (non-admissible), and the box itself
     std::vector<std::vector<int64_t>> nbr;
     if (lk >= 1) {
       const int lp = lk - 1;
@@ -1132,15 +1132,16 @@ int build_plan(hodlrdd_s* h) {
         coords(lp, pb, c);
         for (int64_t code = 0; code < nd; ++code) {
           int64_t t = code;
-          bool inside = true, some_zero = false;
+          bool inside = true;
+          int zeros = 0;
           for (int k = 0; k < d; ++k) {
             const int64_t delta = t % 3 - 1;
             t /= 3;
             q[k] = c[k] + delta;
-            some_zero |= delta == 0;
+            zeros += delta == 0;
             inside &= q[k] >= 0 && q[k] < side;
           }
-          if (!inside || !some_zero) continue;
+          if (!inside || zeros <= h->opt.admissible_face_dim) continue;  // non-admissible neighbours and itself
           uint64_t key = 0;
           for (int bit = 0; bit < lp; ++bit)
             for (int k = 0; k < d; ++k) key |= (uint64_t)((q[k] >> bit) & 1) << (d * bit + k);

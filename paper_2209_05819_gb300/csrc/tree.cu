@@ -198,11 +198,13 @@ __device__ __forceinline__ int64_t find_box(const uint64_t* __restrict__ a, int6
 }
 
 // Interaction list of every box at level l >= 1. Candidates are the children of
-// the parent and of each parent-level box sharing a d' >= 1 hyper-surface with
-// the parent (offset in {-1,0,1}^d with at least one zero); a candidate j != i is
-// kept when far (Chebyshev index distance >= 2) or vertex-sharing (all |delta| = 1).
+// the parent and of each parent-level box sharing a face of dimension > amax
+// with the parent (offset in {-1,0,1}^d with more than amax zeros; amax = 0 for
+// HODLRdD, i.e. a d' >= 1 hyper-surface); a candidate j != i is kept when far
+// (Chebyshev index distance >= 2) or touching along a face of dimension <= amax
+// (for HODLRdD: vertex-sharing, all |delta| = 1).
 template <bool FILL>
-__global__ void k_il(int d, int l, int64_t nb, const uint64_t* __restrict__ bkey, int64_t nbp,
+__global__ void k_il(int d, int l, int amax, int64_t nb, const uint64_t* __restrict__ bkey, int64_t nbp,
                      const uint64_t* __restrict__ pkey, const int32_t* __restrict__ pcfirst,
                      const int32_t* __restrict__ off, int32_t* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,28 +219,29 @@ __global__ void k_il(int d, int l, int64_t nb, const uint64_t* __restrict__ bkey
   int64_t pos = FILL ? off[i] : 0;
   for (int t = 0; t < nd; ++t) {
     int tt = t;
-    bool zero = false, ok = true;
+    int zeros = 0;
+    bool ok = true;
     for (int k = 0; k < d; ++k) {
       int dk = tt % 3 - 1;
       tt /= 3;
       q[k] = p[k] + dk;
-      if (dk == 0) zero = true;
+      if (dk == 0) ++zeros;
       if (q[k] < 0 || q[k] >= sidep) ok = false;
     }
-    if (!ok || !zero) continue;
+    if (!ok || zeros <= amax) continue;  // the parent itself has d zeros
     int64_t P = find_box(pkey, nbp, enc(q, d, l - 1));
     if (P < 0) continue;
     for (int32_t j = pcfirst[P]; j < pcfirst[P + 1]; ++j) {
       if (j == i) continue;
       dec(bkey[j], d, l, cj);
       int64_t cheb = 0;
-      bool vertex = true;
+      int jz = 0;
       for (int k = 0; k < d; ++k) {
         int64_t a = llabs(cj[k] - c[k]);
         cheb = max(cheb, a);
-        if (a != 1) vertex = false;
+        if (a == 0) ++jz;
       }
-      if (cheb >= 2 || vertex) {
+      if (cheb >= 2 || jz <= amax) {
         if (FILL) out[pos++] = j; else ++cnt;
       }
     }
@@ -246,10 +249,11 @@ __global__ void k_il(int d, int l, int64_t nb, const uint64_t* __restrict__ bkey
   if (!FILL) out[i] = cnt;
 }
 
-// Leaf near list: the box itself and every leaf sharing a d' >= 1 hyper-surface.
+// Leaf near list: the box itself and every leaf sharing a face of dimension >
+// amax (HODLRdD: a d' >= 1 hyper-surface).
 template <bool FILL>
-__global__ void k_near(int d, int l, int64_t nb, const uint64_t* __restrict__ bkey, const int32_t* __restrict__ off,
-                       int32_t* __restrict__ out) {
+__global__ void k_near(int d, int l, int amax, int64_t nb, const uint64_t* __restrict__ bkey,
+                       const int32_t* __restrict__ off, int32_t* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int64_t c[kMaxDim], q[kMaxDim];
@@ -261,15 +265,16 @@ __global__ void k_near(int d, int l, int64_t nb, const uint64_t* __restrict__ bk
   int64_t pos = FILL ? off[i] : 0;
   for (int t = 0; t < nd; ++t) {
     int tt = t;
-    bool zero = false, ok = true;
+    int zeros = 0;
+    bool ok = true;
     for (int k = 0; k < d; ++k) {
       int dk = tt % 3 - 1;
       tt /= 3;
       q[k] = c[k] + dk;
-      if (dk == 0) zero = true;
+      if (dk == 0) ++zeros;
       if (q[k] < 0 || q[k] >= side) ok = false;
     }
-    if (!ok || !zero) continue;
+    if (!ok || zeros <= amax) continue;  // the box itself has d zeros
     int64_t j = find_box(bkey, nb, enc(q, d, l));
     if (j < 0) continue;
     if (FILL) out[pos++] = (int32_t)j; else ++cnt;
@@ -443,7 +448,7 @@ int build_lists(hodlrdd_s* h) {
     DevBuf<int32_t> cnt;
     HD_TRY(cnt.alloc(L.nb));
     const int gb = (int)((L.nb + 127) / 128);
-    k_il<false><<<gb, 128, 0, st>>>(d, l, L.nb, L.bkey.p, P.nb, P.bkey.p, P.cfirst.p, nullptr, cnt.p);
+    k_il<false><<<gb, 128, 0, st>>>(d, l, h->opt.admissible_face_dim, L.nb, L.bkey.p, P.nb, P.bkey.p, P.cfirst.p, nullptr, cnt.p);
     HD_CUDA(cudaGetLastError());
     int64_t nnz = 0;
     HD_TRY(counts_to_offsets(cnt.p, L.nb, L.iloff, &nnz, st));
@@ -453,7 +458,7 @@ int build_lists(hodlrdd_s* h) {
     }
     HD_TRY(L.ilidx.alloc(nnz));
     if (nnz) {
-      k_il<true><<<gb, 128, 0, st>>>(d, l, L.nb, L.bkey.p, P.nb, P.bkey.p, P.cfirst.p, L.iloff.p, L.ilidx.p);
+      k_il<true><<<gb, 128, 0, st>>>(d, l, h->opt.admissible_face_dim, L.nb, L.bkey.p, P.nb, P.bkey.p, P.cfirst.p, L.iloff.p, L.ilidx.p);
       HD_CUDA(cudaGetLastError());
       HD_TRY(sort_segments(L.iloff, L.nb, L.ilidx, nnz, st));
     }
@@ -465,12 +470,12 @@ int build_lists(hodlrdd_s* h) {
   DevBuf<int32_t> cnt;
   HD_TRY(cnt.alloc(L.nb));
   const int gb = (int)((L.nb + 127) / 128);
-  k_near<false><<<gb, 128, 0, st>>>(d, h->kappa, L.nb, L.bkey.p, nullptr, cnt.p);
+  k_near<false><<<gb, 128, 0, st>>>(d, h->kappa, h->opt.admissible_face_dim, L.nb, L.bkey.p, nullptr, cnt.p);
   HD_CUDA(cudaGetLastError());
   int64_t nnz = 0;
   HD_TRY(counts_to_offsets(cnt.p, L.nb, h->nearoff, &nnz, st));
   HD_TRY(h->nearidx.alloc(nnz));
-  k_near<true><<<gb, 128, 0, st>>>(d, h->kappa, L.nb, L.bkey.p, h->nearoff.p, h->nearidx.p);
+  k_near<true><<<gb, 128, 0, st>>>(d, h->kappa, h->opt.admissible_face_dim, L.nb, L.bkey.p, h->nearoff.p, h->nearidx.p);
   HD_CUDA(cudaGetLastError());
   HD_TRY(sort_segments(h->nearoff, L.nb, h->nearidx, nnz, st));
   HD_TRY(download(h->h_nearoff, h->nearoff.p, L.nb + 1, st));

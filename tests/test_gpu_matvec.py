@@ -313,3 +313,24 @@ def test_fp32_wide_chunks(env, d, nrhs):
     assert relerr(yw, y64) <= FP32_WIDE_BOUND
     y1 = gpu_matvec(hw, w.x[:, 3:4])
     assert relerr(yw[:, 3:4], y1) <= 2 * FP32_WIDE_BOUND
+
+
+@pytest.mark.parametrize("d,amax", [(2, -1), (2, 1), (3, -1), (3, 2)])
+def test_matvec_any_admissibility(env, d, amax):
+    """Strong and weak admissibility end to end: the FP64 product equals the
+    oracle's under the same structure (pivots agreeing) and the FP32 packed
+    form (leaf tiles and lists) stays within the FP32 bound of it."""
+    torch, oracle, hd = env
+    w = W.make("t", d, 5000, W.K_INV_R if d == 3 else W.K_LOG, (1, 0, 0, 0), 32, 1e-8, nrhs=1, seed=50 + d)
+    T = oracle.Tree(w.points, w.kernel, w.params, w.leaf, w.tol, dense_if_cheaper=True, admissible_face_dim=amax)
+    h64 = gpu_handle(hd, w, admissible_face_dim=amax)
+    y64 = gpu_matvec(h64, w.x)
+    if np.array_equal(T.blocks()[:, 7:9], h64.blocks()[:, 7:9]):
+        assert relerr(y64, T.matvec(w.x)) <= 1e-10
+    yd = oracle.direct(w.points, w.kernel, w.params, w.x)
+    assert relerr(y64, yd) <= (10 if amax < d - 1 else 100) * w.tol
+    for mode in (1, 2):
+        h32 = gpu_handle(hd, w, precision="fp32", admissible_face_dim=amax, near_mode=mode)
+        y32 = gpu_matvec(h32, w.x)
+        h32.sync()
+        assert relerr(y32, y64) <= MIXED_BOUND["fp32"], mode

@@ -102,3 +102,41 @@ def test_nonfinite_points_rejected_on_device(env):
     with pytest.raises(hd.HodlrddError) as e:
         hd.Handle(pts, W.K_INV_R, None, 8, 1e-6)
     assert e.value.status == hd.ERR_INVALID
+
+
+ADM_CASES = [
+    (dict(d=2, N=4096, kernel=W.K_LOG, leaf=40, seed=10), -1),
+    (dict(d=2, N=4096, kernel=W.K_LOG, leaf=40, seed=10), 1),
+    (dict(d=3, N=12000, kernel=W.K_INV_R, leaf=32, seed=11), -1),
+    (dict(d=3, N=12000, kernel=W.K_INV_R, leaf=32, seed=11), 1),
+    (dict(d=3, N=12000, kernel=W.K_INV_R, leaf=32, seed=11), 2),
+    (dict(d=4, N=5000, kernel=W.K_LOG, leaf=20, seed=12, dist="clustered"), 2),
+]
+
+
+@pytest.mark.parametrize("kw,amax", ADM_CASES)
+def test_lists_bit_exact_any_admissibility(env, kw, amax):
+    """Strong (-1), intermediate and weak (d - 1) admissibility: IL and near
+    lists and the block table equal the oracle's."""
+    torch, oracle, hd = env
+    w = _workload(kw)
+    T = oracle.Tree(w.points, w.kernel, w.params, w.leaf, w.tol, admissible_face_dim=amax)
+    h = gpu_handle(hd, w, admissible_face_dim=amax)
+    for l in range(1, T.kappa + 1):
+        oo, io = T.il(l)
+        og, ig = h.il(l)
+        assert np.array_equal(oo, og) and np.array_equal(io, ig), l
+    no, nio = T.near()
+    ng, nig = h.near()
+    assert np.array_equal(no, ng) and np.array_equal(nio, nig)
+    assert np.array_equal(T.blocks()[:, :7], h.blocks()[:, :7])
+    h.close()
+
+
+def test_admissibility_out_of_range_rejected(env):
+    torch, oracle, hd = env
+    w = _workload(dict(d=2, N=500, kernel=W.K_LOG, leaf=20, seed=1))
+    for amax in (-2, 2):
+        with pytest.raises(hd.HodlrddError) as e:
+            gpu_handle(hd, w, admissible_face_dim=amax)
+        assert e.value.status == hd.ERR_INVALID
