@@ -230,6 +230,7 @@ __device__ void aca_block(const Team& T, const AcaArgs& A, int32_t b, double* Us
     const double piv = Vs[(size_t)k * n + bj];
     if (tid == 0) { S.sig[k] = istar; S.tau[k] = bj; }
     for (int q = tid; q < k; q += TS) S.sv[q] = Vs[(size_t)q * n + bj];
+    T.sync();  // every thread holds piv before row k (and with it the pivot entry) is rescaled
     for (int j = tid; j < n; j += TS) Vs[(size_t)k * n + j] = Vs[(size_t)k * n + j] / piv;
     T.sync();
     // residual column j*
