@@ -262,6 +262,31 @@ int hodlrdd_solve(hodlrdd_handle inner, hodlrdd_handle outer, const double* b, d
                   const hodlrdd_solve_options* opt, hodlrdd_solve_stats* stats, void* stream);
 
 /*
+ * Batched products over many resident handles (uneven trees, one request per
+ * handle): the library's addition for serving many instances at once. The
+ * requests are captured once into a CUDA graph, spread over up to 8 streams
+ * inside it so small trees run side by side, and every hodlrdd_batch_run replays
+ * it with one graph launch.
+ *
+ * hodlrdd_batch_create
+ *  handles  count distinct handles (a handle may appear once); none profiling.
+ *  nrhs     right-hand sides of each request (>= 1).
+ *  Applies every request once (set-up), then captures; allocates the batch's
+ *  own input and output buffers (N_i x nrhs_i each). The handles must outlive
+ *  the batch and must not run other work while a batch run is in flight.
+ * hodlrdd_batch_run
+ *  x[i], y[i]  host or device, N_i x nrhs_i row-major, ORIGINAL point order, in
+ *              the element type of handle i. Copies in, one graph launch,
+ *              copies out, all on `stream`; synchronous when any pointer is on
+ *              the host. Results equal those of hodlrdd_matvec on each handle
+ *              (bitwise).
+ */
+typedef struct hodlrdd_batch_s* hodlrdd_batch;
+int hodlrdd_batch_create(const hodlrdd_handle* handles, const int* nrhs, int count, hodlrdd_batch* out);
+int hodlrdd_batch_run(hodlrdd_batch b, const void* const* x, void* const* y, void* stream);
+int hodlrdd_batch_destroy(hodlrdd_batch b);
+
+/*
  * Waits for all device work (cudaDeviceSynchronize) and reports failures the
  * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
  * their bounded waits expired (the y of that matvec is then invalid). Clears the

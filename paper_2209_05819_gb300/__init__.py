@@ -8,6 +8,7 @@ CUDA library, there is no CPU fallback):
     Handle.stats()                                              ranks, sizes, phase times
 """
 from ._binding import (  # noqa: F401
+    Batch,
     ERR_CUDA,
     ERR_INVALID,
     ERR_NUMERIC,

@@ -78,6 +78,9 @@ def load():
         "hodlrdd_matvec": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_matvec_noalloc": (i32, [vp, vp, vp, i32, vp]),
         "hodlrdd_direct": (i32, [vp, vp, vp, vp]),
+        "hodlrdd_batch_create": (i32, [C.POINTER(vp), C.POINTER(C.c_int), i32, C.POINTER(vp)]),
+        "hodlrdd_batch_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
+        "hodlrdd_batch_destroy": (i32, [vp]),
         "hodlrdd_solve_options_default": (i32, [C.POINTER(SolveOptions)]),
         "hodlrdd_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOptions), C.POINTER(SolveStats), vp]),
         "hodlrdd_destroy": (i32, [vp]),
@@ -351,6 +354,45 @@ def solve(inner: "Handle", outer: "Handle", b, x=None, tol: float = 1e-10, inner
     _check(lib.hodlrdd_solve(inner._h, outer._h, ba, xa, C.byref(o), C.byref(st), _stream_ptr(stream)),
            "hodlrdd_solve")
     return x, {"refinements": st.refinements, "inner_iterations": st.inner_iterations, "residual": st.residual}
+
+
+class Batch:
+    """One request per handle, captured into a CUDA graph and replayed."""
+
+    def __init__(self, handles, nrhs):
+        lib = load()
+        self._handles = list(handles)
+        n = len(self._handles)
+        hs = (C.c_void_p * n)(*[h._h for h in self._handles])
+        nr = (C.c_int * n)(*[int(k) for k in nrhs])
+        self.nrhs = [int(k) for k in nrhs]
+        b = C.c_void_p()
+        _check(lib.hodlrdd_batch_create(hs, nr, n, C.byref(b)), "hodlrdd_batch_create")
+        self._b = b
+        self._lib = lib
+
+    def run(self, xs, ys=None, stream=None):
+        """y_i = K_i x_i for every request; xs / ys: numpy or torch arrays."""
+        n = len(self._handles)
+        if ys is None:
+            ys = [np.empty(x.shape, dtype=h.io_dtype) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+                  for x, h in zip(xs, self._handles)]
+        keep = [_ptr(a) for a in list(xs) + list(ys)]
+        xp = (C.c_void_p * n)(*[keep[i][0] for i in range(n)])
+        yp = (C.c_void_p * n)(*[keep[n + i][0] for i in range(n)])
+        _check(self._lib.hodlrdd_batch_run(self._b, xp, yp, _stream_ptr(stream)), "hodlrdd_batch_run")
+        return ys
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.hodlrdd_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def debug_fail_alloc_after(k: int):

@@ -27,6 +27,7 @@ SOURCES = {
     "noalloc.cu": [],
     "near.cu": [],
     "solve.cu": [],
+    "batch.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]
