@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-many-rhs", action="store_true", help="skip the many-right-hand-side (d=4, nrhs 64) line")
     p.add_argument("--no-solve", action="store_true", help="skip the integral-equation solve line")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-trees line")
     return p.parse_args()
 
 
@@ -309,6 +310,49 @@ def solve_line(args, torch, hd, N=65536):
     return out
 
 
+def batch_line(args, torch, hd):
+    """48 clustered d=3 sets (N log-uniform in [2048, 131072], Gaussian h=0.5 +
+    1e-3 I, leaf 64, tol 1e-6, 1..16 right-hand sides each), resident at once:
+    one batch run (inputs resident, one graph launch) against one product per
+    handle in turn, and the per-run latency."""
+    import workloads as W
+
+    ws = W.uneven_instances()
+    t0 = time.perf_counter()
+    hs = [hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision=args.precision,
+                    max_nrhs=16) for w in ws]
+    t_build = time.perf_counter() - t0
+    units = sum(w.N * w.nrhs for w in ws)
+    xs = [torch.from_numpy(np.ascontiguousarray(w.x, dtype=np.float32)).cuda() for w in ws]
+    ys = [torch.empty_like(x) for x in xs]
+    b = hd.Batch(hs, [w.nrhs for w in ws])
+
+    def seq():
+        for h, x, y in zip(hs, xs, ys):
+            h.matvec(x, y)
+
+    out = {"workload": f"48 clustered d=3 sets, N log-uniform 2048..131072 (total {sum(w.N for w in ws)}), "
+                       f"Gaussian h=0.5 + 1e-3 I, leaf 64, tol 1e-6, 1..16 right-hand sides",
+           "build_s": t_build}
+    for name, fn in (("sequential", seq), ("batch_graph", lambda: b.run(xs, ys))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        lat = []
+        for _ in range(20):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0))
+        lat.sort()
+        out[name] = {"value": units / (statistics.median(lat) / 1e3), "unit": UNIT, "p50_ms": lat[len(lat) // 2],
+                     "p99_ms": lat[-1]}
+    b.close()
+    for h in hs:
+        h.close()
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -477,6 +521,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_solve and args.precision != "fp64":
         solve = solve_line(args, torch, hd)
 
+    # 48 uneven trees served as one replayed CUDA graph
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch and args.precision != "fp64":
+        batch = batch_line(args, torch, hd)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, w)
@@ -496,6 +545,7 @@ def main():
             "direct_gpu": direct,
             "many_rhs": many,
             "solve": solve,
+            "batch": batch,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
                                                    "t_pack_ms")},
             "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],
