@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-many-rhs", action="store_true", help="skip the many-right-hand-side (d=4, nrhs 64) line")
     p.add_argument("--no-solve", action="store_true", help="skip the integral-equation solve line")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-trees line")
+    p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     return p.parse_args()
 
 
@@ -284,6 +285,46 @@ def many_rhs_line(args, torch, stream, hd):
     return out
 
 
+def skeleton_line(args, torch, stream, hd, w, pts, x, y64):
+    """The memory-efficient skeleton form (pivots + LU of K(sigma, tau), entries
+    evaluated on the fly) on the headline workload: FP32 form against the FP64
+    stored-factor product, and the FP64 skeleton form; time, error and memory."""
+    out = {"workload": "the headline workload, low-rank blocks in the skeleton form"}
+    hs = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp32", lowrank_form="skeleton")
+    y = torch.empty_like(x)
+    n = max(5, min(args.steps // 20, 50))
+    t = time_steps(lambda: hs.matvec(x, y), n, 3, torch, stream)
+    hs.set_profiling(True)
+    hs.matvec(x, y)
+    torch.cuda.synchronize()
+    prof = hs.profile()
+    hs.set_profiling(False)
+    s = hs.stats()
+    err = None
+    if y64 is not None:
+        err = float((torch.linalg.norm(y.double() - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
+    out["fp32"] = {"ms_per_step": 1e3 * t / n, "value": w.N * w.nrhs * n / t, "unit": UNIT, "steps": n,
+                   "rel_err_vs_fp64": err, "device_gb": s["device_bytes"] / 1e9,
+                   "skeleton_gb": s["skeleton_bytes"] / 1e9, "skeleton_terms": s["skeleton_terms"],
+                   "total_rank": s["total_rank"], "kernel_evals_lowrank": s["skeleton_pairs"],
+                   "lowrank_evals_per_s": s["skeleton_pairs"] * n / t,
+                   "stage_ms": {"rows_and_solve": prof["vapply_ms"], "cols": prof["uapply_ms"],
+                                "near": prof["near_ms"]}}
+    hs.close()
+    if not args.no_fp64:
+        h6 = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp64", lowrank_form="skeleton")
+        x64 = x.double()
+        y6 = torch.empty_like(x64)
+        t6 = time_steps(lambda: h6.matvec(x64, y6), 3, 1, torch, stream)
+        e6 = None
+        if y64 is not None:
+            e6 = float((torch.linalg.norm(y6 - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
+        out["fp64"] = {"ms_per_step": 1e3 * t6 / 3, "rel_err_vs_stored_fp64": e6,
+                       "device_gb": h6.stats()["device_bytes"] / 1e9}
+        h6.close()
+    return out
+
+
 def solve_line(args, torch, hd, N=65536):
     """(I + K/N) u = b on N points of the benchmark distribution, to a relative
     FP64 residual of 1e-10: GMRES on the headline-precision operator inside FP64
@@ -444,6 +485,7 @@ def main():
     # plain FP64 form, and the headline form's error against it
     fp64 = None
     err = None
+    y64 = None
     if not args.no_fp64:
         if args.precision == "fp64":
             h64, x64 = h, x
@@ -458,7 +500,8 @@ def main():
         num = torch.linalg.norm((y.to(torch.float64) - y64), dim=0)
         den = torch.linalg.norm(y64, dim=0)
         err = float((num / den).max().item())
-        fp64 = {"value": units * n64 / t64, "ms_per_step": 1e3 * t64 / n64, "build_ms": h64.stats()["t_build_ms"]}
+        fp64 = {"value": units * n64 / t64, "ms_per_step": 1e3 * t64 / n64, "build_ms": h64.stats()["t_build_ms"],
+                "device_gb": h64.stats()["device_bytes"] / 1e9}
         if h64 is not h:
             h64.close()
 
@@ -516,6 +559,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
         many = many_rhs_line(args, torch, stream, hd)
 
+    # the memory-efficient skeleton form of the low-rank blocks
+    skel = None
+    if rank == 0 and world == 1 and not args.no_skeleton and args.precision == "fp32" and nrhs == 1:
+        skel = skeleton_line(args, torch, stream, hd, w, pts, x, y64)
+
     # second-kind system (I + K/N) u = b: mixed-precision GMRES with FP64 refinement
     solve = None
     if rank == 0 and world == 1 and not args.no_solve and args.precision != "fp64":
@@ -544,6 +592,7 @@ def main():
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
             "direct_gpu": direct,
             "many_rhs": many,
+            "skeleton": skel,
             "solve": solve,
             "batch": batch,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",

@@ -97,7 +97,19 @@ typedef struct hodlrdd_options {
                            compressed. 0 (default): HODLRdD (far-field and
                            vertex-sharing); -1: strong, far-field only (H-matrix);
                            d - 1: weak, every sibling (HODLR). Valid: -1 .. d - 1 */
-  int reserved[6];      /* set to 0 */
+  int lowrank_form;     /* what a low-rank block keeps after the build (Eq. keq2).
+                           0 (default): the factors U_b (|I| x p) and V_b (|J| x p),
+                           streamed from HBM by every product.
+                           1: the memory-efficient skeleton form: the ACA pivot rows
+                           sigma and columns tau and the LU factors of K(sigma, tau)
+                           (p x p, FP64); each product evaluates K(sigma, J) and
+                           K(I, tau) on the fly and solves with L and U. The FP32
+                           form keeps the leading terms an FP32 evaluation resolves
+                           (see skeleton_terms) and stores W = U^-1 L^-1 instead. Needs
+                           precision FP64 or FP32, d <= 4 and ranks <= 1024; right-hand
+                           sides are applied one at a time. The build still holds the
+                           FP64 factors of every block while it runs. */
+  int reserved[5];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64
@@ -129,6 +141,14 @@ typedef struct hodlrdd_stats {
   int64_t factor_bytes_u;    /* bytes of the U panels (per level and target box) */
   int64_t factor_bytes_v;    /* bytes of the V panels (per level and source box) */
   int64_t total_rank;        /* sum of ranks: length of the t vector of the V-apply */
+  int lowrank_form;          /* the build option (0 factors, 1 skeleton) */
+  int64_t skeleton_bytes;    /* skeleton form: bytes of the LU factors, pivot lists and task
+                                lists (factor_bytes then counts the LU factors and pivots) */
+  int64_t skeleton_pairs;    /* skeleton form: kernel evaluations of its low-rank blocks per
+                                product and right-hand side, sum of p' (|I| + |J|) */
+  int64_t skeleton_terms;    /* skeleton form: sum of the kept ranks p'. FP64 keeps every ACA
+                                term (p' = p); FP32 keeps the leading terms whose pivot is at
+                                least 2^-23 of the largest pivot before it */
 } hodlrdd_stats;
 
 /* Fills *opt with the defaults described above. */
@@ -358,7 +378,8 @@ int hodlrdd_get_blocks(hodlrdd_handle h, int64_t* rec);
 int hodlrdd_get_pivots(hodlrdd_handle h, int64_t b, int64_t* sigma, int64_t* tau);
 
 /* FP64 copy of block b's factors as applied (after the precision conversion and
- * scales): U m x rank, V n x rank, column-major. */
+ * scales): U m x rank, V n x rank, column-major. HODLRDD_ERR_UNSUPPORTED for a
+ * handle in the skeleton form (it keeps no factors). */
 int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V);
 
 /*
@@ -367,6 +388,8 @@ int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V);
  * block, U_b (m x rank, column-major) and V_b (n x rank). The factors are then
  * packed in the handle's precision exactly as after hodlrdd_build. Used to check
  * the matvec against a reference representation independently of the ACA.
+ * HODLRDD_ERR_UNSUPPORTED for a handle in the skeleton form (imported factors
+ * carry no pivots).
  */
 int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t* dense, const double* U_all,
                            const double* V_all);

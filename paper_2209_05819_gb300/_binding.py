@@ -32,7 +32,7 @@ class HodlrddError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
                 ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("admissible_face_dim", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("lowrank_form", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class SolveOptions(C.Structure):
@@ -55,6 +55,8 @@ class Stats(C.Structure):
         ("t_tree_ms", C.c_double), ("t_classify_ms", C.c_double), ("t_aca_ms", C.c_double),
         ("t_pack_ms", C.c_double), ("t_build_ms", C.c_double), ("device_bytes", C.c_int64),
         ("factor_bytes_u", C.c_int64), ("factor_bytes_v", C.c_int64), ("total_rank", C.c_int64),
+        ("lowrank_form", C.c_int), ("skeleton_bytes", C.c_int64), ("skeleton_pairs", C.c_int64),
+        ("skeleton_terms", C.c_int64),
     ]
 
 
@@ -149,12 +151,18 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+# What a low-rank block keeps: its factors U_b, V_b, or the skeleton (pivots and
+# the LU factors of K(sigma, tau)) with kernel entries evaluated on the fly.
+LOWRANK_FORM = {"factors": 0, "skeleton": 1}
+
+
 class Handle:
     """A HODLRdD representation of K on the current CUDA device."""
 
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
-                 aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0):
+                 aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0,
+                 lowrank_form: str = "factors"):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -171,6 +179,7 @@ class Handle:
         opt.aca_max_rank = int(aca_max_rank)
         opt.near_mode = int(near_mode)
         opt.admissible_face_dim = int(admissible_face_dim)
+        opt.lowrank_form = LOWRANK_FORM[lowrank_form]
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:

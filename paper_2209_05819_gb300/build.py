@@ -28,6 +28,7 @@ SOURCES = {
     "near.cu": [],
     "solve.cu": [],
     "batch.cu": [],
+    "skeleton.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

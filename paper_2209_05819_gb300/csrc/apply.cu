@@ -1050,6 +1050,8 @@ int build_plan(hodlrdd_s* h) {
   std::vector<int4> t4, s4;
   std::vector<float4> o4;                  // per source entry: (c_J - c_I) h_l
   std::vector<char> need4(h->kappa + 1, 0);
+  if (h->opt.lowrank_form == 1)  // the FP32 skeleton form evaluates every level's low-rank blocks
+    for (int l = 1; l <= h->kappa; ++l) need4[l] = 1;
   std::vector<std::pair<int2, float4>> sl; // current task's sources: {J0, n}, offset
   P.packed_pairs = 0;
   auto add_task = [&](int32_t I0, int32_t m) {
@@ -1340,9 +1342,16 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   const float* sa = Fac<T>::scaled ? h->sv.p : nullptr;
   const float* sb = Fac<T>::scaled ? h->su.p : nullptr;
   Acc* pb = reinterpret_cast<Acc*>(h->pbuf.p);
+  const bool skel = h->opt.lowrank_form == 1;
+  if (skel && NR != 1) {
+    set_error("matvec: the skeleton form applies one right-hand side at a time");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
   if (h->kappa >= 1) {
     HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)h->kappa * h->N * NR * sizeof(Acc), st));
-    if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
+    if (skel) {
+      HD_TRY(launch_skeleton_rows(h, st, xt, t));
+    } else if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
       k_panel<T, NR, true><<<P.vs.ctas, kSegThreads, C::kSmem, st>>>(
           reinterpret_cast<const T*>(P.vs.data.p), P.vs.panels.p, P.vs.stages.p, P.vs.cta.p, xt, t, P.vmap.p, sa, sb,
           pb, h->err.p);
@@ -1356,7 +1365,9 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   HD_TRY(fork_near());
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
-  if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
+  if (skel && h->kappa >= 1) {
+    HD_TRY(launch_skeleton_cols(h, st, t, yl));
+  } else if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
     k_panel<T, NR, false><<<P.us.ctas, kSegThreads, C::kSmem, st>>>(
         reinterpret_cast<const T*>(P.us.data.p), P.us.panels.p, P.us.stages.p, P.us.cta.p, t, yl, nullptr, nullptr,
         nullptr, pb, h->err.p);
@@ -1414,6 +1425,10 @@ template <class T, class IO>
 int matvec_typed(hodlrdd_s* h, const IO* x, IO* y, int nrhs, cudaStream_t st) {
   HD_TRY(set_smem_attr<T>());
   int c0 = 0;
+  if (h->opt.lowrank_form == 1) {  // skeleton form: one right-hand side per pass
+    for (; c0 < nrhs; ++c0) HD_TRY((matvec_chunk<T, IO, 1>(h, x, y, nrhs, c0, st)));
+    return HODLRDD_OK;
+  }
   while (c0 < nrhs) {
     const int rem = nrhs - c0;
     bool wide = false;

@@ -125,6 +125,9 @@ void fill_stats(hodlrdd_s* h) {
                             P.us.splits.bytes() + P.vmap.bytes() + h->pbuf.bytes() + P.tasks.bytes() +
                             P.srcs.bytes() + P.soff.bytes() + P.tasks4.bytes() + P.srcs4.bytes() +
                             P.soff4.bytes());
+  bytes += (int64_t)(P.sk_lu.bytes() + P.sk_luoff.bytes() + P.sk_blist.bytes() + P.sk_rtask.bytes() +
+                     P.sk_rsum.bytes() + P.sk_rows.bytes() + P.sk_ctask.bytes() + P.sk_cols.bytes() +
+                     P.sk_boff.bytes() + P.sk_part.bytes() + P.sk_hi.bytes() + P.sk_lo.bytes());
   for (auto& a : P.hi4) bytes += (int64_t)a.bytes();
   for (auto& a : P.lo4) bytes += (int64_t)a.bytes();
   for (auto& r : P.rel) bytes += (int64_t)r.bytes();
@@ -135,6 +138,10 @@ void fill_stats(hodlrdd_s* h) {
   s.factor_bytes_u = P.us.elems * es;
   s.factor_bytes_v = P.vs.elems * es;
   s.total_rank = h->total_rank;
+  s.lowrank_form = h->opt.lowrank_form;
+  s.skeleton_bytes = P.sk_bytes;
+  s.skeleton_pairs = P.sk_pairs;
+  s.skeleton_terms = P.sk_terms;
 }
 
 int validate_build(const double* points, int d, int64_t N, int kernel_id, const double* prm, int leaf, double tol,
@@ -152,6 +159,18 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (o.admissible_face_dim < -1 || o.admissible_face_dim > d - 1) {
     set_error("hodlrdd_build: admissible_face_dim must be in -1 .. d - 1");
     return HODLRDD_ERR_INVALID;
+  }
+  if (o.lowrank_form < 0 || o.lowrank_form > 1) { set_error("hodlrdd_build: lowrank_form must be 0 or 1"); return HODLRDD_ERR_INVALID; }
+  if (o.lowrank_form == 1) {
+    if (o.precision != HODLRDD_PREC_FP64 && o.precision != HODLRDD_PREC_FP32) {
+      set_error("hodlrdd_build: the skeleton form needs precision FP64 or FP32");
+      return HODLRDD_ERR_UNSUPPORTED;
+    }
+    if (d > 4) { set_error("hodlrdd_build: the skeleton form needs d <= 4"); return HODLRDD_ERR_UNSUPPORTED; }
+    if (o.aca_max_rank > 1024) {
+      set_error("hodlrdd_build: the skeleton form needs aca_max_rank <= 1024");
+      return HODLRDD_ERR_UNSUPPORTED;
+    }
   }
   return HODLRDD_OK;
 }
@@ -190,10 +209,12 @@ int do_build(hodlrdd_s* h, const double* points) {
   HD_TRY(run_aca(h, U64, V64, uoff64, voff64));
   h->stats.t_aca_ms = ms_since(t);
   t = std::chrono::steady_clock::now();
-  HD_TRY(pack_factors(h, U64, V64, uoff64, voff64));
+  if (h->opt.lowrank_form == 1) HD_TRY(build_skeleton(h, U64, V64, uoff64, voff64));
+  else HD_TRY(pack_factors(h, U64, V64, uoff64, voff64));
   U64.release();
   V64.release();
   HD_TRY(build_plan(h));
+  if (h->opt.lowrank_form == 1) HD_TRY(build_skeleton_plan(h));
   HD_TRY(alloc_workspace(h));
   HD_CUDA(cudaStreamSynchronize(h->st));
   h->stats.t_pack_ms = ms_since(t);
@@ -432,12 +453,20 @@ int hodlrdd_get_pivots(hodlrdd_handle h, int64_t b, int64_t* sigma, int64_t* tau
 
 int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V) {
   if (!h || b < 0 || b >= h->nblk) return HODLRDD_ERR_INVALID;
+  if (h->opt.lowrank_form != 0) {
+    set_error("hodlrdd_get_factors: the handle is in the skeleton form (no factors kept)");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
   return unpack_block(h, b, U, V);
 }
 
 int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t* dense, const double* U_all,
                            const double* V_all) {
   if (!h || (!rank && h->nblk) || (!dense && h->nblk)) return HODLRDD_ERR_INVALID;
+  if (h->opt.lowrank_form != 0) {
+    set_error("hodlrdd_import_factors: the handle is in the skeleton form");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
   const int64_t nblk = h->nblk;
   std::vector<int64_t> uoff64(nblk + 1, 0), voff64(nblk + 1, 0), toff(nblk + 1, 0);
   for (int64_t b = 0; b < nblk; ++b) {

@@ -280,6 +280,17 @@ struct DenseLevel {
   int64_t t0 = 0, t1 = 0;  // task range
 };
 
+// One task of the skeleton apply: a contiguous range of points (the sources
+// of a pivot-row task, the targets of a column task) and a range of a gathered
+// pivot list (the targets of a row task, the sources of a column task).
+struct SkTask {
+  int32_t a0, n;   // contiguous points [a0, a0 + n), tree order
+  int32_t r0, r1;  // gathered entries [r0, r1)
+  int32_t level;   // tree level of the blocks
+  int32_t pout;    // row tasks of a cut group: its first partial sum; else -1
+  int32_t pad0, pad1;
+};
+
 struct Plan {
   Stream vs, us;                   // V per (level, source box); U per (level, target box)
   DevBuf<int32_t> vmap;            // V panel outputs -> t index
@@ -305,6 +316,28 @@ struct Plan {
   bool tiles = false;              // leaf4 runs over parent tiles at level kappa - 1
   int64_t packed_pairs = 0;        // kernel evaluations of the packed path
   std::vector<double> h_box;       // per level: reference side h'_l (20 significant bits)
+  // skeleton form (lowrank_form = 1): pivots and LU factors of K(sigma, tau)
+  // per low-rank block, kernel entries evaluated on the fly
+  DevBuf<SkTask> sk_rtask;         // K(sigma, J) x(J): per source box, pivot-row group, source chunk
+  DevBuf<int4> sk_rsum;            // {r0, r1, first partial, chunks} of row groups cut into chunks
+  DevBuf<int4> sk_rows;            // pivot rows grouped by source box: {point, slot, block, 0}
+  DevBuf<SkTask> sk_ctask;         // y_l(I) += K(I, tau) w: per target box and row chunk
+  DevBuf<int2> sk_cols;            // by slot: {pivot column point, block}
+  DevBuf<float4> sk_boff;          // per block: (c_J - c_I) h_l, exact in FP32
+  DevBuf<double> sk_lu;            // per block, p' x p' column-major: FP64 form L (lower, with diagonal) and
+                                   // U (strict upper); FP32 form W = U^-1 L^-1
+  DevBuf<int64_t> sk_luoff;        // per block: first element of its p x p matrix
+  DevBuf<int32_t> sk_blist;        // blocks with a non-empty skeleton, for the triangular solves
+  DevBuf<int32_t> sk_rank;         // per block: skeleton rank p' <= p (leading ACA terms kept)
+  DevBuf<int64_t> sk_toff;         // per block: first slot of its p' values in t
+  std::vector<int32_t> h_sk_rank;
+  std::vector<int64_t> h_sk_toff;
+  DevBuf<char> sk_part;            // partial sums of cut row groups (accumulator type)
+  DevBuf<const float4*> sk_hi, sk_lo;  // per level: box-relative coordinates (FP32 form)
+  int64_t sk_parts = 0;            // partial sums per product
+  int64_t sk_pairs = 0;            // kernel evaluations per product and right-hand side
+  int64_t sk_terms = 0;            // sum of the skeleton ranks p'
+  int64_t sk_bytes = 0;            // bytes of the skeleton data (LU, pivot lists, offsets, tasks)
 };
 
 }  // namespace hd
@@ -394,6 +427,12 @@ int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr);
 int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, float* y, int nr, int ldy, int c0);
 int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
+// Skeleton form (skeleton.cu).
+int build_skeleton(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
+                   const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64);
+int build_skeleton_plan(hodlrdd_s* h);
+int launch_skeleton_rows(hodlrdd_s* h, cudaStream_t st, const void* xt, void* t);
+int launch_skeleton_cols(hodlrdd_s* h, cudaStream_t st, const void* t, void* ylev);
 int read_error_word(hodlrdd_s* h, int32_t* code);
 size_t elem_size(int precision);
 }  // namespace hd

@@ -5,49 +5,11 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "pairs.cuh"
 
 namespace hd {
 
 namespace {
-
-// Hardware reciprocal (square root) approximations, PTX rsqrt / rcp
-// .approx.ftz (relative error below 2^-22); the packed path treats squared
-// distances below the smallest normal FP32 number as coincident points.
-__device__ __forceinline__ float rsqrt_hw(float s) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  return r;
-}
-__device__ __forceinline__ float rcp_hw(float s) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  return r;
-}
-constexpr float kTinySq = 1.17549435e-38f;  // smallest normal FP32 number
-
-__device__ __forceinline__ float sqrt_hw(float s) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  return r;
-}
-
-// Kernel functions of r = sqrt(s) for the packed near field: hardware
-// approximations for square roots and reciprocals, the CUDA fast exponential
-// (__expf) for the exponential kernels.
-template <int KID>
-__device__ __forceinline__ float f32k(float s, float c) {
-  if constexpr (KID == HODLRDD_K_LOG) return s == 0.0f ? 0.0f : 0.5f * logf(s);
-  else if constexpr (KID == HODLRDD_K_INV_R) return s < kTinySq ? 0.0f : rsqrt_hw(s);
-  else if constexpr (KID == HODLRDD_K_MATERN32) {
-    const float a = c * sqrt_hw(s);
-    return (1.0f + a) * __expf(-a);
-  } else if constexpr (KID == HODLRDD_K_GAUSS) return __expf(-c * s);
-  else if constexpr (KID == HODLRDD_K_EXP) return __expf(-c * sqrt_hw(s));
-  else if constexpr (KID == HODLRDD_K_INV_R2_4D) return s < kTinySq ? 0.0f : c * rcp_hw(s);
-  else if constexpr (KID == HODLRDD_K_R) return sqrt_hw(s);
-  else if constexpr (KID == HODLRDD_K_SIN) return sinf(sqrt_hw(s));
-  else return rsqrt_hw(1.0f + sqrt_hw(s));
-}
 
 // Packed dense work (FP32, d <= 3, one right-hand side), one CTA per task.
 // A task is up to kTileRows target rows [I0, I0 + m) of one box I at level l
@@ -60,33 +22,6 @@ __device__ __forceinline__ float f32k(float s, float c) {
 // the entry after the chunk); then threads holding two target rows each sweep
 // the chunk in S source stripes. Result: ynear[i] += scale * sum + diag * x_i
 // (diag is passed as 0 except for the pass that owns the diagonal).
-
-// a + b = s + e exactly (Knuth's two-sum).
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-  return s;
-}
-
-template <int D>
-__device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, const float4& sh, const float4& sl) {
-  float t = (th.x - sh.x) + (tl.x - sl.x);
-  float s = t * t;
-  if (D > 1) {
-    t = (th.y - sh.y) + (tl.y - sl.y);
-    s = fmaf(t, t, s);
-  }
-  if (D > 2) {
-    t = (th.z - sh.z) + (tl.z - sl.z);
-    s = fmaf(t, t, s);
-  }
-  if (D > 3) {
-    t = (th.w - sh.w) + (tl.w - sl.w);
-    s = fmaf(t, t, s);
-  }
-  return s;
-}
 
 template <int D, int KID>
 __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
