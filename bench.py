@@ -176,9 +176,9 @@ def measured_peaks():
 # launch by the bytes processed (traffic grows with the factor bytes). It is
 # reported only while the apply source is the one that was captured.
 TRAFFIC_CAPTURE = {
-    "apply_sha256": "82aa959a069cb88044c23b440e3bb22b7bd5945dd13ad5c3405c2d582cdf2cc2",
+    "apply_sha256": "cd6dba15f1d5d072cf7a721b205bcf8737365799aab1c083501cf486ec7aae9c",
     "precision": "fp32", "nrhs": 1,
-    "ratio": {"vapply": 1.0038, "uapply": 1.0012},  # mean of the captured launches
+    "ratio": {"vapply": 1.0035, "uapply": 1.0012},  # mean of the captured launches
 }
 
 
