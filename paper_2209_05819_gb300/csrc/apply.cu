@@ -419,6 +419,32 @@ __global__ void __launch_bounds__(kSegThreads, 1)
             }
           nsum = 0;
         }
+      } else if constexpr ((NR * sizeof(Acc)) % 16 == 0) {
+        // a line's NR vector values are 16-byte aligned (the lead pad is zero
+        // when NR values fill whole 16-byte units): vector loads, and one line
+        // per iteration so that the NR x E accumulators stay in registers
+        constexpr int VW = 16 / (int)sizeof(Acc);
+        using Vec = typename std::conditional<sizeof(Acc) == 4, float4, double2>::type;
+#pragma unroll 1
+        for (int k = cg; k < st.nseg; k += CG) {
+          Acc f[E];
+          Fac<T>::chunk(base + ((int64_t)k * P.ld + (int64_t)rc * E) * sizeof(T), f);
+          const Vec* v4 = reinterpret_cast<const Vec*>(sv + k * NR);
+#pragma unroll
+          for (int r4 = 0; r4 < NR / VW; ++r4) {
+            const Vec vv = v4[r4];
+            Acc xv[VW];
+            if constexpr (VW == 4) {
+              xv[0] = vv.x; xv[1] = vv.y; xv[2] = vv.z; xv[3] = vv.w;
+            } else {
+              xv[0] = vv.x; xv[1] = vv.y;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+#pragma unroll
+              for (int r = 0; r < VW; ++r) acc[e][r4 * VW + r] += f[e] * xv[r];
+          }
+        }
       } else {
 #pragma unroll 4
         for (int k = cg; k < st.nseg; k += CG) {
@@ -1054,10 +1080,25 @@ int build_plan(hodlrdd_s* h) {
     for (int l = 1; l <= h->kappa; ++l) need4[l] = 1;
   std::vector<std::pair<int2, float4>> sl; // current task's sources: {J0, n}, offset
   P.packed_pairs = 0;
+  // rows per task: kTileRows, halved (down to 64) while the leaf pass would
+  // have fewer than eight tasks per SM, so that trees with few large parent
+  // boxes (high d, large leaves) still spread over every SM
+  int32_t rows_cap = kTileRows;
+  if (h->kappa >= 1) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const Level& LP = h->lv[h->kappa - 1];
+    auto leaf_tasks = [&](int32_t rows) {
+      int64_t n = 0;
+      for (int64_t pb = 0; pb < LP.nb; ++pb) n += (LP.h_bstart[pb + 1] - LP.h_bstart[pb] + rows - 1) / rows;
+      return n;
+    };
+    while (rows_cap > 64 && leaf_tasks(rows_cap) < 8 * (int64_t)sms) rows_cap /= 2;
+  }
   auto add_task = [&](int32_t I0, int32_t m) {
     int64_t nsrc = 0;
     for (auto& so : sl) nsrc += so.first.y;
-    for (int32_t r0 = 0; r0 < m; r0 += kTileRows) {
+    for (int32_t r0 = 0; r0 < m; r0 += rows_cap) {
       const int32_t s0 = (int32_t)s4.size();
       int32_t first = s0, pos = 0;
       for (auto& so : sl)
@@ -1073,7 +1114,7 @@ int build_plan(hodlrdd_s* h) {
           pos += np;
         }
       if ((int32_t)s4.size() > first) s4[first].w = (int32_t)s4.size();
-      const int32_t mr = std::min(kTileRows, m - r0);
+      const int32_t mr = std::min(rows_cap, m - r0);
       t4.push_back(make_int4(I0 + r0, mr, s0, (int32_t)s4.size()));
       P.packed_pairs += (int64_t)mr * nsrc;
     }
