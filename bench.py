@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
+    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16", "fp32+fp16"])
     p.add_argument("--n", type=int, default=262144)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--seed", type=int, default=0)
@@ -201,7 +201,7 @@ def factor_bytes(h, precision):
     """Algorithmic bytes of the packed U and V streams (incl. alignment pads) and scales."""
     s = h.stats()
     tr = int(s["total_rank"])
-    scales = 8 * tr if precision in ("fp16", "bf16") else 0
+    scales = 8 * tr if precision in ("fp16", "bf16") else 8 * int(s["tail_cols"]) if precision == "fp32+fp16" else 0
     return int(s["factor_bytes_u"]), int(s["factor_bytes_v"]), tr, scales
 
 
@@ -268,7 +268,10 @@ def many_rhs_line(args, torch, stream, hd):
     out = {"workload": f"d=4 N={w.N} uniform [0,1]^4, Matern-3/2 l=0.2, leaf {w.leaf}, tol {w.tol:g}, "
                        f"nrhs {w.nrhs}"}
     res = {}
-    for prec in (args.precision, "fp64"):
+    # wide chunks (16 right-hand sides) need uniform FP32 factors
+    prec_lo = "fp32" if args.precision == "fp32+fp16" else args.precision
+    out["precision"] = prec_lo
+    for prec in (prec_lo, "fp64"):
         h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, max_nrhs=w.nrhs)
         io = torch.float64 if prec == "fp64" else torch.float32
         x = torch.from_numpy(np.ascontiguousarray(w.x)).to(io).cuda()
@@ -277,7 +280,7 @@ def many_rhs_line(args, torch, stream, hd):
         t = time_steps(lambda: h.matvec(x, y), n, 1, torch, stream)
         res[prec] = (t / n, y.double())
         h.close()
-    t32, y32 = res[args.precision]
+    t32, y32 = res[prec_lo]
     t64, y64 = res["fp64"]
     err = float((torch.linalg.norm(y32 - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
     out.update({"ms_per_matvec": 1e3 * t32, "value": w.N * w.nrhs / t32, "unit": UNIT,
@@ -561,7 +564,7 @@ def main():
 
     # the memory-efficient skeleton form of the low-rank blocks
     skel = None
-    if rank == 0 and world == 1 and not args.no_skeleton and args.precision == "fp32" and nrhs == 1:
+    if rank == 0 and world == 1 and not args.no_skeleton and args.precision in ("fp32", "fp32+fp16") and nrhs == 1:
         skel = skeleton_line(args, torch, stream, hd, w, pts, x, y64)
 
     # second-kind system (I + K/N) u = b: mixed-precision GMRES with FP64 refinement
@@ -582,7 +585,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16+f32", "bf16": "bf16+f32"}[
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16+f32", "bf16": "bf16+f32",
+                                           "fp32+fp16": "f32 (factors f32 + f16)"}[
                 args.precision], "data": "synthetic",
             "config": {"workload": workload_name(w), "precision": args.precision,
                        "factors": f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"

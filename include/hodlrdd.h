@@ -64,12 +64,19 @@ enum hodlrdd_kernel {
  *  FP32: factors FP32, arithmetic FP32; x and y are float.
  *  FP16 / BF16: factors 16-bit with one FP32 scale per factor column, kernel
  *  evaluation and accumulation FP32; x and y are float.
+ *  FP32_FP16: arithmetic FP32; each block's leading ACA terms stored in FP32 and
+ *  its trailing terms, those after the last term with ||u_k|| ||v_k|| above
+ *  2^-13 of the block's Frobenius norm (estimated from the terms), in FP16 with
+ *  one FP32 power-of-two scale per column, so that their rounding stays below
+ *  the FP32 rounding of the block; x and y are float. Right-hand sides are
+ *  applied in chunks of at most 8.
  * The compression itself (ACA) always runs in FP64. */
 enum hodlrdd_precision {
   HODLRDD_PREC_FP64 = 0,
   HODLRDD_PREC_FP32 = 1,
   HODLRDD_PREC_FP16 = 2,
-  HODLRDD_PREC_BF16 = 3
+  HODLRDD_PREC_BF16 = 3,
+  HODLRDD_PREC_FP32_FP16 = 4
 };
 
 typedef struct hodlrdd_options {
@@ -138,7 +145,8 @@ typedef struct hodlrdd_stats {
   double t_pack_ms;          /* factor packing / precision conversion, task lists */
   double t_build_ms;         /* whole build, wall clock */
   int64_t device_bytes;      /* device memory held by the handle */
-  int64_t factor_bytes_u;    /* bytes of the U panels (per level and target box) */
+  int64_t factor_bytes_u;    /* bytes of the U panels (per level and target box; FP32_FP16:
+                                both element types) */
   int64_t factor_bytes_v;    /* bytes of the V panels (per level and source box) */
   int64_t total_rank;        /* sum of ranks: length of the t vector of the V-apply */
   int lowrank_form;          /* the build option (0 factors, 1 skeleton) */
@@ -146,6 +154,7 @@ typedef struct hodlrdd_stats {
                                 lists (factor_bytes then counts the LU factors and pivots) */
   int64_t skeleton_pairs;    /* skeleton form: kernel evaluations of its low-rank blocks per
                                 product and right-hand side, sum of p' (|I| + |J|) */
+  int64_t tail_cols;         /* FP32_FP16: factor columns stored in FP16 (of total_rank) */
   int64_t skeleton_terms;    /* skeleton form: sum of the kept ranks p'. FP64 keeps every ACA
                                 term (p' = p); FP32 keeps the leading terms whose pivot is at
                                 least 2^-23 of the largest pivot before it */

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhodlrdd.so")
 HEADER = os.path.join(ROOT, "include", "hodlrdd.h")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_NUMERIC = range(7)
-PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "fp32+fp16": 4}
 MAX_LEVELS = 64
 
 
@@ -56,7 +56,7 @@ class Stats(C.Structure):
         ("t_pack_ms", C.c_double), ("t_build_ms", C.c_double), ("device_bytes", C.c_int64),
         ("factor_bytes_u", C.c_int64), ("factor_bytes_v", C.c_int64), ("total_rank", C.c_int64),
         ("lowrank_form", C.c_int), ("skeleton_bytes", C.c_int64), ("skeleton_pairs", C.c_int64),
-        ("skeleton_terms", C.c_int64),
+        ("tail_cols", C.c_int64), ("skeleton_terms", C.c_int64),
     ]
 
 

@@ -33,7 +33,8 @@ namespace hd {
 size_t elem_size(int precision) {
   switch (precision) {
     case HODLRDD_PREC_FP64: return 8;
-    case HODLRDD_PREC_FP32: return 4;
+    case HODLRDD_PREC_FP32:
+    case HODLRDD_PREC_FP32_FP16: return 4;  // the FP16 tail is counted separately
     default: return 2;
   }
 }
@@ -649,17 +650,39 @@ __global__ void k_gather(const IO* __restrict__ x, const int32_t* __restrict__ p
 }
 
 // ---------------------------------------------------------------- packing ----
-// Column source offsets in the FP64 ACA output: colU[c] / colV[c] for global
-// column c = toff[b] + k.
+// Column source offsets in the FP64 ACA output: colU[c] / colV[c] for the t
+// index c of ACA column k of block b: c = thead[b] + k for k < kb[b] (the
+// leading columns), ttail[b] + k - kb[b] for the others.
 __global__ void k_colmap(int64_t nblk, const int32_t* __restrict__ rank, const int32_t* __restrict__ bm,
-                         const int32_t* __restrict__ bn, const int64_t* __restrict__ toff,
+                         const int32_t* __restrict__ bn, const int32_t* __restrict__ kb,
+                         const int64_t* __restrict__ thead, const int64_t* __restrict__ ttail,
                          const int64_t* __restrict__ uoff64, const int64_t* __restrict__ voff64,
                          int64_t* __restrict__ colU, int64_t* __restrict__ colV) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x)
     for (int k = 0; k < rank[b]; ++k) {
-      colU[toff[b] + k] = uoff64[b] + (int64_t)k * bm[b];
-      colV[toff[b] + k] = voff64[b] + (int64_t)k * bn[b];
+      const int64_t c = k < kb[b] ? thead[b] + k : ttail[b] + (k - kb[b]);
+      colU[c] = uoff64[b] + (int64_t)k * bm[b];
+      colV[c] = voff64[b] + (int64_t)k * bn[b];
     }
+}
+
+// ||u_c||_2 ||v_c||_2 per column (one warp per column).
+__global__ void k_termnorm(int64_t ncol, const int64_t* __restrict__ colU, const int64_t* __restrict__ colV,
+                           const int32_t* __restrict__ colrows_u, const int32_t* __restrict__ colrows_v,
+                           const double* __restrict__ U64, const double* __restrict__ V64, double* __restrict__ tn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncol; c += nw) {
+    double su = 0.0, sv = 0.0;
+    for (int i = lane; i < colrows_u[c]; i += 32) su = fma(U64[colU[c] + i], U64[colU[c] + i], su);
+    for (int i = lane; i < colrows_v[c]; i += 32) sv = fma(V64[colV[c] + i], V64[colV[c] + i], sv);
+    for (int o = 16; o; o >>= 1) {
+      su += __shfl_xor_sync(0xffffffffu, su, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if (lane == 0) tn[c] = sqrt(su) * sqrt(sv);
+  }
 }
 
 // One warp per column: power-of-two scale >= max |entry| (16-bit), else 1.
@@ -829,50 +852,63 @@ int upload_stream(Stream& S, cudaStream_t st) {
   return HODLRDD_OK;
 }
 
+// The columns one storage part holds: block b contributes its ACA columns
+// [k0[b], k1[b]) with t indices tfirst[b] + (k - k0[b]); the t indices of one
+// target box's columns are consecutive (the U-apply reads them as one range).
+struct ColPart {
+  std::vector<int32_t> k0, k1;
+  std::vector<int64_t> tfirst;
+};
+
+// Panels of one part in element type T: V per (level, source box), U per
+// (level, target box); packs them from the FP64 ACA output. U outputs go to
+// y_l slice offset yoff. `track` records the per-block panel positions that
+// hodlrdd_get_factors reads back.
 template <class T>
-int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
-               const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64) {
+int pack_part(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, const DevBuf<int64_t>& colU,
+              const DevBuf<int64_t>& colV, const ColPart& cp, Stream& vs, Stream& us, DevBuf<int32_t>& vmap,
+              bool track, int64_t yoff) {
   cudaStream_t st = h->st;
   constexpr int E = Fac<T>::E;
   const int64_t nblk = h->nblk;
   Plan& P = h->plan;
   auto roundE = [&](int64_t v) { return (v + E - 1) / E * E; };
+  auto ncols = [&](int64_t b) { return cp.k1[b] - cp.k0[b]; };
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  if ((int64_t)h->total_rank + 2 * kGuard >= INT32_MAX || (int64_t)h->kappa * h->N >= INT32_MAX) {
-    set_error("problem too large for 32-bit vector indices");
-    return HODLRDD_ERR_UNSUPPORTED;
-  }
 
   // V panels: per level and source box, the concatenated columns of its
   // low-rank IL blocks (in block order) in row-major panels of at most
   // vpanel_width<T>() columns; line k = source point J0 + k
-  P.vs.h_lp.clear();
-  P.h_vpanel.assign(nblk, -1);
-  P.h_vcol.assign(nblk, 0);
+  vs.h_lp.clear();
+  if (track) {
+    P.h_vpanel.assign(nblk, -1);
+    P.h_vcol.assign(nblk, 0);
+  }
   std::vector<int32_t> hmap, vfirst_v, out0_v;
-  hmap.reserve((size_t)h->total_rank);
   int64_t off = 0;
   for (int l = 1; l <= h->kappa; ++l) {
     std::vector<int64_t> bs;
     for (int64_t b = h->h_blk_off[l]; b < h->h_blk_off[l + 1]; ++b)
-      if (h->h_rank[b] > 0) bs.push_back(b);
+      if (ncols(b) > 0) bs.push_back(b);
     std::stable_sort(bs.begin(), bs.end(), [&](int64_t a, int64_t b) { return h->h_bJ0[a] < h->h_bJ0[b]; });
     for (size_t i = 0; i < bs.size();) {
       size_t j = i;
       const int32_t J0 = h->h_bJ0[bs[i]], n = h->h_bn[bs[i]];
-      const int64_t first = (int64_t)P.vs.h_lp.size(), m0 = (int64_t)hmap.size();
+      const int64_t first = (int64_t)vs.h_lp.size(), m0 = (int64_t)hmap.size();
       for (; j < bs.size() && h->h_bJ0[bs[j]] == J0; ++j) {
         const int64_t b = bs[j];
-        P.h_vpanel[b] = first;
-        P.h_vcol[b] = (int32_t)((int64_t)hmap.size() - m0);
-        for (int k = 0; k < h->h_rank[b]; ++k) hmap.push_back((int32_t)(h->h_toff[b] + k));
+        if (track) {
+          P.h_vpanel[b] = first;
+          P.h_vcol[b] = (int32_t)((int64_t)hmap.size() - m0);
+        }
+        for (int k = 0; k < ncols(b); ++k) hmap.push_back((int32_t)(cp.tfirst[b] + k));
       }
       const int64_t Q = (int64_t)hmap.size() - m0;
       for (int64_t c0 = 0; c0 < Q; c0 += vpanel_width<T>()) {
         const int32_t R = (int32_t)std::min<int64_t>(vpanel_width<T>(), Q - c0);
         const int32_t ld = (int32_t)roundE(R);
-        P.vs.h_lp.push_back(LPanel{off, ld, R, n});
+        vs.h_lp.push_back(LPanel{off, ld, R, n});
         vfirst_v.push_back(J0);
         out0_v.push_back((int32_t)(m0 + c0));
         off += (int64_t)ld * n;
@@ -880,12 +916,14 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
       i = j;
     }
   }
-  P.vs.elems = off;
+  vs.elems = off;
   // U panels: per (level, box) with low-rank blocks, rows in panels of at most
   // kPanelRows, column-major over the box's concatenated IL columns
-  P.us.h_lp.clear();
-  P.h_ugroup.assign(nblk, -1);
-  P.h_ucol.assign(nblk, 0);
+  us.h_lp.clear();
+  if (track) {
+    P.h_ugroup.assign(nblk, -1);
+    P.h_ucol.assign(nblk, 0);
+  }
   std::vector<int32_t> prow0, vfirst_u, out0_u;
   off = 0;
   for (int l = 1; l <= h->kappa; ++l) {
@@ -894,74 +932,171 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
       const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
       int64_t Pi = 0, tf = -1;
       for (int64_t b = b0; b < b1; ++b)
-        if (h->h_rank[b] > 0) {
-          if (tf < 0) tf = h->h_toff[b];
-          P.h_ugroup[b] = (int64_t)P.us.h_lp.size();
-          P.h_ucol[b] = (int32_t)Pi;
-          Pi += h->h_rank[b];
+        if (ncols(b) > 0) {
+          if (tf < 0) tf = cp.tfirst[b];
+          if (track) {
+            P.h_ugroup[b] = (int64_t)us.h_lp.size();
+            P.h_ucol[b] = (int32_t)Pi;
+          }
+          Pi += ncols(b);
         }
       if (Pi == 0) continue;
       const int32_t I0 = L.h_bstart[i], m = L.h_bstart[i + 1] - I0;
       for (int32_t r0 = 0; r0 < m; r0 += kPanelRows) {
         const int32_t R = std::min(kPanelRows, m - r0);
         const int32_t ld = (int32_t)roundE(R);
-        P.us.h_lp.push_back(LPanel{off, ld, R, (int32_t)Pi});
+        us.h_lp.push_back(LPanel{off, ld, R, (int32_t)Pi});
         prow0.push_back(r0);
         vfirst_u.push_back((int32_t)tf);
-        out0_u.push_back((int32_t)((int64_t)(l - 1) * h->N + I0 + r0));
+        out0_u.push_back((int32_t)(yoff + (int64_t)(l - 1) * h->N + I0 + r0));
         off += (int64_t)ld * Pi;
       }
     }
   }
-  P.us.elems = off;
-  schedule_stream(P.vs, vfirst_v, out0_v, sizeof(T), sms);
-  schedule_stream(P.us, vfirst_u, out0_u, sizeof(T), sms);
+  us.elems = off;
+  schedule_stream(vs, vfirst_v, out0_v, sizeof(T), sms);
+  schedule_stream(us, vfirst_u, out0_u, sizeof(T), sms);
 
-  // column maps, scales, packing
-  const int64_t ncol = h->total_rank;
-  DevBuf<int64_t> colU, colV, du64, dv64;
-  DevBuf<int32_t> crows_u, crows_v, dprow0, dpcol0, dvm0;
+  DevBuf<int32_t> dprow0, dpcol0, dvm0;
   DevBuf<LPanel> dvlp, dulp;
-  std::vector<int32_t> hcru(std::max<int64_t>(ncol, 1)), hcrv(std::max<int64_t>(ncol, 1));
-  for (int64_t b = 0; b < nblk; ++b)
-    for (int k = 0; k < h->h_rank[b]; ++k) {
-      hcru[h->h_toff[b] + k] = h->h_bm[b];
-      hcrv[h->h_toff[b] + k] = h->h_bn[b];
-    }
+  HD_TRY(upload(dprow0, prow0, st));
+  HD_TRY(upload(dpcol0, vfirst_u, st));
+  HD_TRY(upload(dvm0, out0_v, st));
+  HD_TRY(upload(dvlp, vs.h_lp, st));
+  HD_TRY(upload(dulp, us.h_lp, st));
+  HD_TRY(upload(vmap, hmap, st));
+  HD_TRY(vs.data.alloc((size_t)std::max<int64_t>(vs.elems, E) * sizeof(T)));
+  HD_TRY(us.data.alloc((size_t)std::max<int64_t>(us.elems, E) * sizeof(T)));
+  HD_TRY(upload_stream(vs, st));
+  HD_TRY(upload_stream(us, st));
+  const int64_t nvp = (int64_t)vs.h_lp.size(), nup = (int64_t)us.h_lp.size();
+  if (nvp)
+    k_packV<T><<<(int)std::min<int64_t>(nvp, sms * 16), 256, 0, st>>>(
+        nvp, dvlp.p, dvm0.p, vmap.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(vs.data.p));
+  if (nup)
+    k_packU<T><<<(int)std::min<int64_t>(nup, sms * 16), 256, 0, st>>>(
+        nup, dulp.p, dprow0.p, dpcol0.p, colU.p, U64.p, h->su.p, reinterpret_cast<T*>(us.data.p));
+  HD_CUDA(cudaGetLastError());
+  HD_CUDA(cudaStreamSynchronize(st));
+  return HODLRDD_OK;
+}
+
+// Relative size below which an ACA term is stored in FP16 by the mixed form:
+// ||u_k|| ||v_k|| <= 2^-13 ||A_b||_F (estimate), so that the FP16 rounding
+// (2^-11 of each entry, power-of-two column scales) of such a term stays below
+// 2^-24 of the block, the FP32 rounding of the leading terms.
+constexpr double kTailEta = 1.0 / 8192.0;
+
+// Packs the factors: uniform element type T, or (mixed) the leading terms of
+// each block in FP32 and its trailing terms (every term after the last one
+// above kTailEta of the block) in FP16 with per-column scales.
+template <class T>
+int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
+               const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64, bool mixed) {
+  cudaStream_t st = h->st;
+  const int64_t nblk = h->nblk;
+  Plan& P = h->plan;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if ((int64_t)h->total_rank + 2 * kGuard >= INT32_MAX || 2 * (int64_t)h->kappa * h->N >= INT32_MAX) {
+    set_error("problem too large for 32-bit vector indices");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
+  const int64_t ncol = h->total_rank;
+  DevBuf<int64_t> colU, colV, du64, dv64, dthead, dttail;
+  DevBuf<int32_t> crows_u, crows_v, dkb;
   HD_TRY(colU.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(colV.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(upload(du64, uoff64, st));
   HD_TRY(upload(dv64, voff64, st));
-  HD_TRY(upload(crows_u, hcru, st));
-  HD_TRY(upload(crows_v, hcrv, st));
-  HD_TRY(upload(dprow0, prow0, st));
-  HD_TRY(upload(dpcol0, vfirst_u, st));
-  HD_TRY(upload(dvm0, out0_v, st));
-  HD_TRY(upload(dvlp, P.vs.h_lp, st));
-  HD_TRY(upload(dulp, P.us.h_lp, st));
-  HD_TRY(upload(P.vmap, hmap, st));
   HD_TRY(h->su.alloc(std::max<int64_t>(ncol, 1)));
   HD_TRY(h->sv.alloc(std::max<int64_t>(ncol, 1)));
-  HD_TRY(P.vs.data.alloc((size_t)std::max<int64_t>(P.vs.elems, E) * sizeof(T)));
-  HD_TRY(P.us.data.alloc((size_t)std::max<int64_t>(P.us.elems, E) * sizeof(T)));
-  HD_TRY(upload_stream(P.vs, st));
-  HD_TRY(upload_stream(P.us, st));
-  if (ncol > 0) {
-    k_colmap<<<(int)std::min<int64_t>((nblk + 255) / 256, 4096), 256, 0, st>>>(
-        nblk, h->rank.p, h->bm.p, h->bn.p, h->toff.p, du64.p, dv64.p, colU.p, colV.p);
-    k_colscale<<<grid_warps(ncol, sms), 256, 0, st>>>(ncol, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p,
-                                                      Fac<T>::scaled ? 1 : 0, h->su.p, h->sv.p);
-    const int64_t nvp = (int64_t)P.vs.h_lp.size(), nup = (int64_t)P.us.h_lp.size();
-    if (nvp)
-      k_packV<T><<<(int)std::min<int64_t>(nvp, sms * 16), 256, 0, st>>>(
-          nvp, dvlp.p, dvm0.p, P.vmap.p, colV.p, V64.p, h->sv.p, reinterpret_cast<T*>(P.vs.data.p));
-    if (nup)
-      k_packU<T><<<(int)std::min<int64_t>(nup, sms * 16), 256, 0, st>>>(
-          nup, dulp.p, dprow0.p, dpcol0.p, colU.p, U64.p, h->su.p, reinterpret_cast<T*>(P.us.data.p));
+  // per-block split: leading kb[b] columns (head), the rest (tail)
+  std::vector<int32_t> kb(h->h_rank.begin(), h->h_rank.end());
+  auto number = [&](std::vector<int64_t>& thead, std::vector<int64_t>& ttail) -> int64_t {
+    thead.assign(nblk, 0);
+    ttail.assign(nblk, 0);
+    int64_t H = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+      thead[b] = H;
+      H += kb[b];
+    }
+    int64_t t = H;
+    for (int64_t b = 0; b < nblk; ++b) {
+      ttail[b] = t;
+      t += h->h_rank[b] - kb[b];
+    }
+    return H;
+  };
+  auto colmap = [&](const std::vector<int64_t>& thead, const std::vector<int64_t>& ttail) -> int {
+    std::vector<int32_t> hcru(std::max<int64_t>(ncol, 1)), hcrv(std::max<int64_t>(ncol, 1));
+    for (int64_t b = 0; b < nblk; ++b)
+      for (int k = 0; k < h->h_rank[b]; ++k) {
+        const int64_t c = k < kb[b] ? thead[b] + k : ttail[b] + (k - kb[b]);
+        hcru[c] = h->h_bm[b];
+        hcrv[c] = h->h_bn[b];
+      }
+    HD_TRY(upload(crows_u, hcru, st));
+    HD_TRY(upload(crows_v, hcrv, st));
+    HD_TRY(upload(dkb, kb, st));
+    HD_TRY(upload(dthead, thead, st));
+    HD_TRY(upload(dttail, ttail, st));
+    if (ncol > 0)
+      k_colmap<<<(int)std::min<int64_t>((nblk + 255) / 256, 4096), 256, 0, st>>>(
+          nblk, h->rank.p, h->bm.p, h->bn.p, dkb.p, dthead.p, dttail.p, du64.p, dv64.p, colU.p, colV.p);
     HD_CUDA(cudaGetLastError());
+    return HODLRDD_OK;
+  };
+  std::vector<int64_t> thead, ttail;
+  int64_t H = number(thead, ttail);
+  HD_TRY(colmap(thead, ttail));
+  if (mixed && ncol > 0) {
+    DevBuf<double> tn;
+    HD_TRY(tn.alloc(ncol));
+    k_termnorm<<<grid_warps(ncol, sms), 256, 0, st>>>(ncol, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p, tn.p);
+    HD_CUDA(cudaGetLastError());
+    std::vector<double> htn;
+    HD_TRY(download(htn, tn.p, (size_t)ncol, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    for (int64_t b = 0; b < nblk; ++b) {
+      const int p = h->h_rank[b];
+      double S = 0.0;
+      for (int k = 0; k < p; ++k) S += htn[thead[b] + k] * htn[thead[b] + k];
+      S = std::sqrt(S);
+      int k = p;
+      while (k > 0 && htn[thead[b] + k - 1] <= kTailEta * S) --k;
+      kb[b] = k;
+    }
+    H = number(thead, ttail);
+    HD_TRY(colmap(thead, ttail));
   }
-  HD_CUDA(cudaStreamSynchronize(st));
-  h->factor_bytes = (P.vs.elems + P.us.elems) * (int64_t)sizeof(T) + (Fac<T>::scaled ? 2 * ncol * 4 : 0);
+  P.tail_cols = ncol - H;
+  // scales: 1 for FP32 / FP64 columns, a power of two >= the column's largest
+  // entry for 16-bit columns
+  if (H > 0)
+    k_colscale<<<grid_warps(H, sms), 256, 0, st>>>(H, colU.p, colV.p, crows_u.p, crows_v.p, U64.p, V64.p,
+                                                   Fac<T>::scaled ? 1 : 0, h->su.p, h->sv.p);
+  if (ncol > H)
+    k_colscale<<<grid_warps(ncol - H, sms), 256, 0, st>>>(ncol - H, colU.p + H, colV.p + H, crows_u.p + H,
+                                                          crows_v.p + H, U64.p, V64.p, 1, h->su.p + H, h->sv.p + H);
+  HD_CUDA(cudaGetLastError());
+  ColPart head, tail;
+  head.k0.assign(nblk, 0);
+  head.k1 = kb;
+  head.tfirst = thead;
+  HD_TRY(pack_part<T>(h, U64, V64, colU, colV, head, P.vs, P.us, P.vmap, !mixed, 0));
+  h->factor_bytes = (P.vs.elems + P.us.elems) * (int64_t)sizeof(T) + (Fac<T>::scaled ? 2 * H * 4 : 0);
+  P.vs2 = Stream();
+  P.us2 = Stream();
+  P.vmap2.release();
+  if (mixed) {
+    tail.k0 = kb;
+    tail.k1.assign(h->h_rank.begin(), h->h_rank.end());
+    tail.tfirst = ttail;
+    HD_TRY(pack_part<__half>(h, U64, V64, colU, colV, tail, P.vs2, P.us2, P.vmap2, false,
+                             (int64_t)h->kappa * h->N));
+    h->factor_bytes += (P.vs2.elems + P.us2.elems) * 2 + 2 * (ncol - H) * 4;
+  }
   return HODLRDD_OK;
 }
 
@@ -976,10 +1111,11 @@ int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& 
     h->factor_elems += (int64_t)h->h_rank[b] * (h->h_bm[b] + h->h_bn[b]);
   }
   switch (h->opt.precision) {
-    case HODLRDD_PREC_FP64: return pack_typed<double>(h, U64, V64, uoff64, voff64);
-    case HODLRDD_PREC_FP32: return pack_typed<float>(h, U64, V64, uoff64, voff64);
-    case HODLRDD_PREC_FP16: return pack_typed<__half>(h, U64, V64, uoff64, voff64);
-    default: return pack_typed<__nv_bfloat16>(h, U64, V64, uoff64, voff64);
+    case HODLRDD_PREC_FP64: return pack_typed<double>(h, U64, V64, uoff64, voff64, false);
+    case HODLRDD_PREC_FP32: return pack_typed<float>(h, U64, V64, uoff64, voff64, false);
+    case HODLRDD_PREC_FP32_FP16: return pack_typed<float>(h, U64, V64, uoff64, voff64, true);
+    case HODLRDD_PREC_FP16: return pack_typed<__half>(h, U64, V64, uoff64, voff64, false);
+    default: return pack_typed<__nv_bfloat16>(h, U64, V64, uoff64, voff64, false);
   }
 }
 
@@ -1281,6 +1417,11 @@ int build_plan(hodlrdd_s* h) {
   return HODLRDD_OK;
 }
 
+// y_l slices the U-applies write: one per level, two with the FP16 tail.
+int level_slices(const hodlrdd_s* h) {
+  return h->kappa * (h->opt.precision == HODLRDD_PREC_FP32_FP16 ? 2 : 1);
+}
+
 int alloc_workspace(hodlrdd_s* h) {
   // chunks of up to 16 right-hand sides (FP32 with the packed near field)
   // when the caller asked for more than 8, else up to 8
@@ -1289,8 +1430,10 @@ int alloc_workspace(hodlrdd_s* h) {
   const size_t acc = h->opt.precision == HODLRDD_PREC_FP64 ? 8 : 4;
   HD_TRY(h->xt.alloc(((size_t)h->N + 2 * kGuard) * nr * acc));
   HD_TRY(h->tbuf.alloc(((size_t)h->total_rank + 2 * kGuard) * nr * acc));
-  HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * nr * acc));
-  const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1});
+  HD_TRY(h->ylev.alloc((size_t)std::max(level_slices(h), 1) * h->N * nr * acc));
+  // the FP16 tail streams run beside the FP32 ones: their partial sums follow
+  const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1}) +
+                        std::max<int64_t>(h->plan.vs2.part_rows, h->plan.us2.part_rows);
   HD_TRY(h->pbuf.alloc((size_t)prows * nr * acc));
   if (h->plan.tasks4.n > 0) HD_TRY(h->ynear.alloc((size_t)h->N * nr));
   HD_TRY(h->err.alloc(1));
@@ -1332,7 +1475,7 @@ int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl,
   const float* rel = F64 ? nullptr : P.rel[h->kappa].p;
   k_dense<Acc, IO, NR, D, F64, true><<<grid_warps(P.leaf.t1 - P.leaf.t0, sms), 256, 0, st>>>(
       P.tasks.p, P.leaf.t0, P.leaf.t1, P.srcs.p, P.soff.p, rel, h->pts64.p, h->N, h->d, h->K.id, kc, h->K.scale,
-      h->K.diag, xt, nullptr, yl, h->kappa, h->perm.p, y, ldy, c0);
+      h->K.diag, xt, nullptr, yl, level_slices(h), h->perm.p, y, ldy, c0);
   h->launches += 1;
   HD_CUDA(cudaGetLastError());
   return HODLRDD_OK;
@@ -1388,8 +1531,31 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     set_error("matvec: the skeleton form applies one right-hand side at a time");
     return HODLRDD_ERR_UNSUPPORTED;
   }
+  const bool mixed = h->opt.precision == HODLRDD_PREC_FP32_FP16;
+  Acc* pb2 = pb + (size_t)std::max<int64_t>({P.vs.part_rows, P.us.part_rows, 1}) * NR;
   if (h->kappa >= 1) {
-    HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)h->kappa * h->N * NR * sizeof(Acc), st));
+    HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)level_slices(h) * h->N * NR * sizeof(Acc), st));
+    if constexpr (std::is_same<T, float>::value && NR <= 8) {
+      // mixed storage: the FP16 tail columns (their own t indices and partial
+      // sums) on the third stream, so that its CTAs fill the FP32 launch's tail
+      if (mixed) {
+        HD_CUDA(cudaEventRecord(h->ev_fork2, st));
+        HD_CUDA(cudaStreamWaitEvent(h->aux2, h->ev_fork2, 0));
+        if (P.vs2.ctas > 0 && !P.vs2.h_stages.empty()) {
+          using C2 = PanelCfg<__half, NR>;
+          k_panel<__half, NR, true><<<P.vs2.ctas, kSegThreads, C2::kSmem, h->aux2>>>(
+              reinterpret_cast<const __half*>(P.vs2.data.p), P.vs2.panels.p, P.vs2.stages.p, P.vs2.cta.p, xt, t,
+              P.vmap2.p, h->sv.p, h->su.p, pb2, h->err.p);
+          h->launches += 1;
+          if (!P.vs2.h_splits.empty()) {
+            k_combine<Acc, NR, true><<<(int)P.vs2.h_cwork.size(), 256, 0, h->aux2>>>(
+                P.vs2.splits.p, P.vs2.cwork.p, pb2, t, P.vmap2.p, h->sv.p, h->su.p);
+            h->launches += 1;
+          }
+        }
+        HD_CUDA(cudaEventRecord(h->ev_vtail, h->aux2));
+      }
+    }
     if (skel) {
       HD_TRY(launch_skeleton_rows(h, st, xt, t));
     } else if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
@@ -1403,9 +1569,33 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
         h->launches += 1;
       }
     }
+    if constexpr (std::is_same<T, float>::value && NR <= 8) {
+      // the join of the FP16 tail V-apply (launched beside the FP32 one)
+      if (mixed) HD_CUDA(cudaStreamWaitEvent(st, h->ev_vtail, 0));
+    }
   }
   HD_TRY(fork_near());
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
+  if constexpr (std::is_same<T, float>::value && NR <= 8) {
+    // FP16 tail U-apply on the third stream (its own y_l slices), after every t is written
+    if (mixed && h->kappa >= 1) {
+      HD_CUDA(cudaEventRecord(h->ev_vdone, st));
+      HD_CUDA(cudaStreamWaitEvent(h->aux2, h->ev_vdone, 0));
+      if (P.us2.ctas > 0 && !P.us2.h_stages.empty()) {
+        using C2 = PanelCfg<__half, NR>;
+        k_panel<__half, NR, false><<<P.us2.ctas, kSegThreads, C2::kSmem, h->aux2>>>(
+            reinterpret_cast<const __half*>(P.us2.data.p), P.us2.panels.p, P.us2.stages.p, P.us2.cta.p, t, yl,
+            nullptr, nullptr, nullptr, pb2, h->err.p);
+        h->launches += 1;
+        if (!P.us2.h_splits.empty()) {
+          k_combine<Acc, NR, false><<<(int)P.us2.h_cwork.size(), 256, 0, h->aux2>>>(
+              P.us2.splits.p, P.us2.cwork.p, pb2, yl, nullptr, nullptr, nullptr);
+          h->launches += 1;
+        }
+      }
+      HD_CUDA(cudaEventRecord(h->ev_utail, h->aux2));
+    }
+  }
   if (skel && h->kappa >= 1) {
     HD_TRY(launch_skeleton_cols(h, st, t, yl));
   } else if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
@@ -1419,11 +1609,14 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
       h->launches += 1;
     }
   }
+  if constexpr (std::is_same<T, float>::value && NR <= 8) {
+    if (mixed && h->kappa >= 1) HD_CUDA(cudaStreamWaitEvent(st, h->ev_utail, 0));  // the FP16 tail U-apply
+  }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if constexpr (!F64 && std::is_same<IO, float>::value)
-      HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), y, NR, ldx, c0));
+      HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), level_slices(h), y, NR, ldx, c0));
   } else if constexpr (NR <= 8) {
     switch (h->d) {
       case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;
@@ -1465,6 +1658,7 @@ int set_smem_attr() {
 template <class T, class IO>
 int matvec_typed(hodlrdd_s* h, const IO* x, IO* y, int nrhs, cudaStream_t st) {
   HD_TRY(set_smem_attr<T>());
+  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) HD_TRY(set_smem_attr<__half>());
   int c0 = 0;
   if (h->opt.lowrank_form == 1) {  // skeleton form: one right-hand side per pass
     for (; c0 < nrhs; ++c0) HD_TRY((matvec_chunk<T, IO, 1>(h, x, y, nrhs, c0, st)));
@@ -1492,6 +1686,7 @@ int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t s
     case HODLRDD_PREC_FP64:
       return matvec_typed<double, double>(h, static_cast<const double*>(x), static_cast<double*>(y), nrhs, st);
     case HODLRDD_PREC_FP32:
+    case HODLRDD_PREC_FP32_FP16:
       return matvec_typed<float, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
     case HODLRDD_PREC_FP16:
       return matvec_typed<__half, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);

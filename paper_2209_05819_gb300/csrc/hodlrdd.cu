@@ -122,7 +122,10 @@ void fill_stats(hodlrdd_s* h) {
                             h->xt.bytes() + h->tbuf.bytes() + h->ylev.bytes() + h->xstage.bytes() +
                             h->ystage.bytes() + P.vs.data.bytes() + P.us.data.bytes() + P.vs.panels.bytes() +
                             P.us.panels.bytes() + P.vs.stages.bytes() + P.us.stages.bytes() + P.vs.splits.bytes() +
-                            P.us.splits.bytes() + P.vmap.bytes() + h->pbuf.bytes() + P.tasks.bytes() +
+                            P.us.splits.bytes() + P.vmap.bytes() + P.vs2.data.bytes() + P.us2.data.bytes() +
+                            P.vs2.panels.bytes() + P.us2.panels.bytes() + P.vs2.stages.bytes() +
+                            P.us2.stages.bytes() + P.vs2.splits.bytes() + P.us2.splits.bytes() + P.vmap2.bytes() +
+                            h->pbuf.bytes() + P.tasks.bytes() +
                             P.srcs.bytes() + P.soff.bytes() + P.tasks4.bytes() + P.srcs4.bytes() +
                             P.soff4.bytes());
   bytes += (int64_t)(P.sk_lu.bytes() + P.sk_luoff.bytes() + P.sk_blist.bytes() + P.sk_rtask.bytes() +
@@ -135,8 +138,9 @@ void fill_stats(hodlrdd_s* h) {
     bytes += (int64_t)(L.bstart.bytes() + L.bkey.bytes() + L.cfirst.bytes() + L.iloff.bytes() + L.ilidx.bytes());
   s.device_bytes = bytes;
   const int64_t es = (int64_t)elem_size(h->opt.precision);
-  s.factor_bytes_u = P.us.elems * es;
-  s.factor_bytes_v = P.vs.elems * es;
+  s.factor_bytes_u = P.us.elems * es + P.us2.elems * 2;
+  s.factor_bytes_v = P.vs.elems * es + P.vs2.elems * 2;
+  s.tail_cols = P.tail_cols;
   s.total_rank = h->total_rank;
   s.lowrank_form = h->opt.lowrank_form;
   s.skeleton_bytes = P.sk_bytes;
@@ -153,7 +157,7 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (leaf < 1) { set_error("hodlrdd_build: leaf_size must be >= 1"); return HODLRDD_ERR_INVALID; }
   if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("hodlrdd_build: tol must be > 0"); return HODLRDD_ERR_INVALID; }
   if (!kernel_ok(kernel_id, prm)) { set_error("hodlrdd_build: unknown kernel or invalid kernel parameters"); return HODLRDD_ERR_INVALID; }
-  if (o.precision < HODLRDD_PREC_FP64 || o.precision > HODLRDD_PREC_BF16) { set_error("hodlrdd_build: unknown precision"); return HODLRDD_ERR_INVALID; }
+  if (o.precision < HODLRDD_PREC_FP64 || o.precision > HODLRDD_PREC_FP32_FP16) { set_error("hodlrdd_build: unknown precision"); return HODLRDD_ERR_INVALID; }
   if (o.max_nrhs < 1 || o.aca_max_rank < 1) { set_error("hodlrdd_build: max_nrhs and aca_max_rank must be >= 1"); return HODLRDD_ERR_INVALID; }
   if (o.near_mode < 0 || o.near_mode > 2) { set_error("hodlrdd_build: near_mode must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
   if (o.admissible_face_dim < -1 || o.admissible_face_dim > d - 1) {
@@ -182,6 +186,11 @@ int do_build(hodlrdd_s* h, const double* points) {
   HD_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
   HD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   HD_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) {
+    HD_CUDA(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&h->ev_fork2, &h->ev_vtail, &h->ev_vdone, &h->ev_utail})
+      HD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   // the caller's points, as a device array (copied if they live on the host)
   DevBuf<double> staged;
   const double* dpts = points;
@@ -227,9 +236,12 @@ void destroy(hodlrdd_s* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   if (h->aux) cudaStreamSynchronize(h->aux);
-  cudaStream_t st = h->st, aux = h->aux;
+  if (h->aux2) cudaStreamSynchronize(h->aux2);
+  cudaStream_t st = h->st, aux = h->aux, aux2 = h->aux2;
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (cudaEvent_t e : {h->ev_fork2, h->ev_vtail, h->ev_vdone, h->ev_utail})
+    if (e) cudaEventDestroy(e);
   for (auto& v : h->ev_pending)
     for (cudaEvent_t e : v) {
       cudaEventSynchronize(e);
@@ -239,6 +251,7 @@ void destroy(hodlrdd_s* h) {
   delete h;
   if (st) cudaStreamDestroy(st);
   if (aux) cudaStreamDestroy(aux);
+  if (aux2) cudaStreamDestroy(aux2);
 }
 
 }  // namespace
@@ -455,6 +468,10 @@ int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V) {
   if (!h || b < 0 || b >= h->nblk) return HODLRDD_ERR_INVALID;
   if (h->opt.lowrank_form != 0) {
     set_error("hodlrdd_get_factors: the handle is in the skeleton form (no factors kept)");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
+  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) {
+    set_error("hodlrdd_get_factors: not available for the mixed FP32 / FP16 storage");
     return HODLRDD_ERR_UNSUPPORTED;
   }
   return unpack_block(h, b, U, V);

@@ -294,6 +294,11 @@ struct SkTask {
 struct Plan {
   Stream vs, us;                   // V per (level, source box); U per (level, target box)
   DevBuf<int32_t> vmap;            // V panel outputs -> t index
+  // mixed FP32 / FP16 storage: the trailing terms of each block in FP16 panels
+  // (U outputs to a second set of kappa level slices)
+  Stream vs2, us2;
+  DevBuf<int32_t> vmap2;
+  int64_t tail_cols = 0;           // columns stored in FP16
   std::vector<int64_t> h_vpanel;   // block -> first whole V panel of its source box (or -1)
   std::vector<int32_t> h_vcol;     // block -> first column within its source box's V panels
   std::vector<int64_t> h_ugroup;   // block -> first whole U panel of its (level, box) (or -1)
@@ -354,6 +359,9 @@ struct hodlrdd_s {
   cudaStream_t st = nullptr;  // the handle's own stream (build, staging)
   cudaStream_t aux = nullptr; // second stream: the packed near field runs beside the low-rank applies
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // third stream: the FP16 tail panels of the mixed storage, beside the FP32 panels
+  cudaStream_t aux2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_vtail = nullptr, ev_vdone = nullptr, ev_utail = nullptr;
 
   // tree
   int B = 0, kappa = 0;
@@ -424,7 +432,7 @@ constexpr int kTileRows = 256;    // target rows per tile task
 constexpr int kTileCap = 1024;    // staged source points per chunk
 void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt);
 int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr);
-int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, float* y, int nr, int ldy, int c0);
+int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0);
 int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
 // Skeleton form (skeleton.cu).

@@ -200,18 +200,19 @@ __global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int 
   }
 }
 
-// y[perm[i] * ldy + c0 + r] = near(i, r) + sum over levels of y_l(i, r), for
-// NR right-hand sides stored NR per point.
+// y[perm[i] * ldy + c0 + r] = near(i, r) + sum over the level slices of
+// y_l(i, r) (one per level, two with the mixed storage's FP16 tail), for NR
+// right-hand sides stored NR per point.
 template <int NR>
-__global__ void k_finish(const float* __restrict__ ynear, const float* __restrict__ ylev, int kappa, int64_t N,
+__global__ void k_finish(const float* __restrict__ ynear, const float* __restrict__ ylev, int slices, int64_t N,
                          const int32_t* __restrict__ perm, float* __restrict__ y, int ldy, int c0) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     float tot[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) tot[r] = ynear[i * NR + r];
-    for (int l = 1; l <= kappa; ++l)
+    for (int l = 0; l < slices; ++l)
 #pragma unroll
-      for (int r = 0; r < NR; ++r) tot[r] += ylev[((int64_t)(l - 1) * N + i) * NR + r];
+      for (int r = 0; r < NR; ++r) tot[r] += ylev[((int64_t)l * N + i) * NR + r];
     float* out = y + (int64_t)perm[i] * ldy + c0;
 #pragma unroll
     for (int r = 0; r < NR; ++r) out[r] = tot[r];
@@ -480,16 +481,16 @@ int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr) {
 }
 
 // y = near + sum of the level slices, scattered to the original order.
-int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, float* y, int nr, int ldy, int c0) {
+int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   const int grid = (int)std::min<int64_t>((h->N + 255) / 256, sms * 16);
   switch (nr) {
-    case 1: k_finish<1><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
-    case 2: k_finish<2><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
-    case 4: k_finish<4><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
-    case 8: k_finish<8><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
-    default: k_finish<16><<<grid, 256, 0, st>>>(h->ynear.p, ylev, h->kappa, h->N, h->perm.p, y, ldy, c0); break;
+    case 1: k_finish<1><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 2: k_finish<2><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 4: k_finish<4><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 8: k_finish<8><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    default: k_finish<16><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
   }
   h->launches += 1;
   HD_CUDA(cudaGetLastError());
