@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16", "bf16", "fp32+fp16"])
+    p.add_argument("--precision", default="fp32+fp16", choices=["fp64", "fp32", "fp16", "bf16", "fp32+fp16"])
     p.add_argument("--n", type=int, default=262144)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--seed", type=int, default=0)
@@ -170,15 +170,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# DRAM traffic of the apply kernels per algorithmic byte, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum per launch) of the d=3 N=65536
-# case of this workload in FP32 with one right-hand side; scaled to a full
-# launch by the bytes processed (traffic grows with the factor bytes). It is
-# reported only while the apply source is the one that was captured.
+# DRAM traffic of each apply stage (its panel and combine launches) per
+# algorithmic byte, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch) of the d=3 N=65536 case of this workload
+# with one right-hand side, per storage precision; scaled to a full launch by
+# the bytes processed (traffic grows with the factor bytes). It is reported
+# only while the apply source is the one that was captured.
 TRAFFIC_CAPTURE = {
-    "apply_sha256": "0ee44df8a3a90960ba76232a7be60bba8f3a3368359b4ff8f208769f5c5d06ef",
-    "precision": "fp32", "nrhs": 1,
-    "ratio": {"vapply": 1.0035, "uapply": 1.0013},  # mean of the captured launches
+    "apply_sha256": "efdf5db419ee4d15347a16253858dcd3f23c8b585218a327c68db6a518c15904",
+    "nrhs": 1,
+    "ratio": {"fp32": {"vapply": 1.0114, "uapply": 1.0025},  # mean over the captured matvecs
+              "fp32+fp16": {"vapply": 1.0081, "uapply": 1.0013}},
 }
 
 
@@ -191,10 +193,10 @@ def apply_source_sha256():
 
 def scaled_traffic(kernel, algo_bytes, precision, nrhs):
     c = TRAFFIC_CAPTURE
-    if (c["apply_sha256"] is None or kernel not in c["ratio"] or precision != c["precision"] or nrhs != c["nrhs"]
-            or apply_source_sha256() != c["apply_sha256"]):
+    r = c["ratio"].get(precision, {})
+    if c["apply_sha256"] is None or kernel not in r or nrhs != c["nrhs"] or apply_source_sha256() != c["apply_sha256"]:
         return None
-    return c["ratio"][kernel] * algo_bytes
+    return r[kernel] * algo_bytes
 
 
 def factor_bytes(h, precision):
@@ -362,8 +364,10 @@ def batch_line(args, torch, hd):
     import workloads as W
 
     ws = W.uneven_instances()
+    # up to 16 right-hand sides per set: uniform FP32 factors take them in one chunk
+    prec = "fp32" if args.precision == "fp32+fp16" else args.precision
     t0 = time.perf_counter()
-    hs = [hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision=args.precision,
+    hs = [hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision=prec,
                     max_nrhs=16) for w in ws]
     t_build = time.perf_counter() - t0
     units = sum(w.N * w.nrhs for w in ws)
@@ -377,7 +381,7 @@ def batch_line(args, torch, hd):
 
     out = {"workload": f"48 clustered d=3 sets, N log-uniform 2048..131072 (total {sum(w.N for w in ws)}), "
                        f"Gaussian h=0.5 + 1e-3 I, leaf 64, tol 1e-6, 1..16 right-hand sides",
-           "build_s": t_build}
+           "build_s": t_build, "precision": prec}
     for name, fn in (("sequential", seq), ("batch_graph", lambda: b.run(xs, ys))):
         for _ in range(3):
             fn()
@@ -545,8 +549,9 @@ def main():
     stage = {"vapply": prof["vapply_ms"] / n_chunks, "uapply": prof["uapply_ms"] / n_chunks,
              "near": prof["near_ms"] / n_chunks, "gather": prof["gather_ms"] / n_chunks}
     nr = min(nrhs, 8)
+    slices = s["kappa"] * (2 if args.precision == "fp32+fp16" else 1)  # y_l slices the U-applies write
     algo = {"vapply": vb + scales + tr * nr * acc + w.N * nr * acc,
-            "uapply": ub + tr * nr * acc + s["kappa"] * w.N * nr * acc}
+            "uapply": ub + tr * nr * acc + slices * w.N * nr * acc}
     dom = max(("vapply", "uapply"), key=lambda k: stage[k])
     peak, peak_kind = measured_peaks()
     achieved = algo[dom] / (stage[dom] / 1e3) / 1e9
@@ -589,8 +594,10 @@ def main():
                                            "fp32+fp16": "f32 (factors f32 + f16)"}[
                 args.precision], "data": "synthetic",
             "config": {"workload": workload_name(w), "precision": args.precision,
-                       "factors": f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"
-                       else "fp64", "parallelism": f"replicas x{world}",
+                       "factors": ("leading ACA terms FP32, trailing terms FP16 with FP32 column scales, FP32 "
+                                   "arithmetic" if args.precision == "fp32+fp16" else
+                                   f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"
+                                   else "fp64"), "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2: {(ub + vb) / 1e9:.2f} GB of factors streamed per step"},
             "rel_err_vs_fp64": err, "meets_err_bar": (err is not None and err <= ERR_BAR),
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
