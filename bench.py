@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-solve", action="store_true", help="skip the integral-equation solve line")
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-trees line")
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
+    p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     return p.parse_args()
 
 
@@ -330,6 +331,74 @@ def skeleton_line(args, torch, stream, hd, w, pts, x, y64):
     return out
 
 
+def serving_line(args, torch, hd, rates=(200.0, 50.0), seconds=3.0, n_models=6, budget_gb=40.0, workers=4):
+    """Requests arriving over time against models resident under an HBM budget:
+    Poisson arrivals, 70% products / 30% solves of second-kind systems
+    (I + K/N) u = b, d in {2, 3, 4}, N log-uniform in [4096, 262144], four
+    kernels; latency from submission to completion, per kind."""
+    import workloads as W
+
+    rng = np.random.default_rng(args.seed + 77)
+    kernels = [(W.K_LOG, 0.0), (W.K_INV_R, 0.0), (W.K_MATERN32, 0.2), (W.K_GAUSS, 0.5)]
+    specs = []
+    for i in range(n_models):
+        d = int(rng.integers(2, 5))
+        N = int(round(np.exp(rng.uniform(np.log(4096), np.log(262144)))))
+        k, p0 = kernels[i % len(kernels)]
+        leaf = 64 if d <= 3 else 128
+        tol = {W.K_LOG: 1e-8, W.K_INV_R: 1e-7, W.K_MATERN32: 1e-7, W.K_GAUSS: 1e-6}[k]
+        specs.append(W.make(f"s{i}", d, N, k, (1.0 / N, 1.0, p0, 0.0), leaf, tol, nrhs=1, seed=2000 + i))
+    srv = hd.Server(int(budget_gb * 1e9), workers=workers)
+    ids = [srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision=args.precision) for w in specs]
+    xs32 = [np.ascontiguousarray(w.x, dtype=np.float32) for w in specs]
+    t0 = time.perf_counter()
+    warm = [srv.submit(ids[i], specs[i].x, kind=hd.REQ_SOLVE) for i in range(n_models)]
+    warm += [srv.submit(ids[i], xs32[i]) for i in range(n_models)]
+    for r in warm:
+        srv.wait(r)
+    t_warm = time.perf_counter() - t0
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+    out = {"workload": f"{n_models} second-kind systems (I + K/N): d in 2..4, N log-uniform in [4096, 262144] "
+                       f"(N = {[w.N for w in specs]}), log r / 1/r / Matern-3/2 / Gaussian; Poisson arrivals for "
+                       f"{seconds:g} s, 70% products / 30% solves (GMRES + FP64 refinement to 1e-10); {workers} "
+                       f"workers; budget {budget_gb:g} GB; latency = submission to completion",
+           "precision": args.precision, "warm_up_s": t_warm, "runs": []}
+    for rate in rates:
+        # arrivals: exponential gaps at `rate`, kind and model drawn per request
+        n = int(rate * seconds)
+        gaps = rng.exponential(1.0 / rate, n)
+        kinds = rng.random(n) < 0.3
+        models = rng.integers(0, n_models, n)
+        reqs = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for j in range(n):
+            t_next += gaps[j]
+            while time.perf_counter() < t_next:
+                time.sleep(max(0.0, min(t_next - time.perf_counter(), 0.001)))
+            m = int(models[j])
+            if kinds[j]:
+                reqs.append(("solve", srv.submit(ids[m], specs[m].x, kind=hd.REQ_SOLVE)))
+            else:
+                reqs.append(("matvec", srv.submit(ids[m], xs32[m])))
+        lat = {"matvec": [], "solve": []}
+        for kind, r in reqs:
+            _, ms = srv.wait(r)
+            lat[kind].append(ms)
+        t_all = time.perf_counter() - t_start
+        out["runs"].append({
+            "offered_rps": rate, "requests": n, "achieved_rps": n / t_all,
+            "matvec": {"count": len(lat["matvec"]), "p50_ms": pct(lat["matvec"], 0.5),
+                       "p99_ms": pct(lat["matvec"], 0.99)},
+            "solve": {"count": len(lat["solve"]), "p50_ms": pct(lat["solve"], 0.5), "p99_ms": pct(lat["solve"], 0.99)}})
+    out["server"] = srv.stats()
+    srv.close()
+    return out
+
+
 def solve_line(args, torch, hd, N=65536):
     """(I + K/N) u = b on N points of the benchmark distribution, to a relative
     FP64 residual of 1e-10: GMRES on the headline-precision operator inside FP64
@@ -577,6 +646,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_solve and args.precision != "fp64":
         solve = solve_line(args, torch, hd)
 
+    # requests over resident models under an HBM budget
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve and args.precision != "fp64":
+        serve = serving_line(args, torch, hd)
+
     # 48 uneven trees served as one replayed CUDA graph
     batch = None
     if rank == 0 and world == 1 and not args.no_batch and args.precision != "fp64":
@@ -606,6 +680,7 @@ def main():
             "skeleton": skel,
             "solve": solve,
             "batch": batch,
+            "serving_loop": serve,
             "build": {k: round(s[k], 1) for k in ("t_build_ms", "t_tree_ms", "t_classify_ms", "t_aca_ms",
                                                    "t_pack_ms")},
             "structure": {"kappa": s["kappa"], "n_blocks": s["n_blocks"], "n_lowrank": s["n_lowrank"],

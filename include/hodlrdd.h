@@ -267,7 +267,10 @@ int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream);
  *  opt     NULL for the defaults (hodlrdd_solve_options_default).
  *  stats   optional.
  *
- * Synchronous. Allocates its Krylov basis (N x (restart + 1) values) per call.
+ * Synchronous. The Krylov basis (N x (restart + 1) values) and the other
+ * scratch are allocated on the first solve with `inner` (or when a later solve
+ * needs more) and kept in that handle until it is destroyed, so repeated solves
+ * allocate nothing; one solve at a time per inner handle.
  * HODLRDD_ERR_NUMERIC when tol is not reached within max_refine steps (x holds
  * the last iterate).
  */
@@ -402,6 +405,58 @@ int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V);
  */
 int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t* dense, const double* U_all,
                            const double* V_all);
+
+/*
+ * Serving: a request loop over models kept resident under a device-memory
+ * budget (the library's addition for many instances of uneven size arriving
+ * over time, such as the paper's batched uses).
+ *
+ * hodlrdd_server_create
+ *  budget_bytes  device bytes the resident handles may hold (hodlrdd_stats
+ *                device_bytes, summed); during a build the new handle may
+ *                briefly exceed it.
+ *  workers       host threads (1..64), one CUDA stream each, on the current
+ *                device. Requests start in arrival order; products of different
+ *                models run side by side; requests for one model run one at a
+ *                time.
+ * hodlrdd_server_add
+ *  Registers a model (host copy of the points; same arguments as
+ *  hodlrdd_build_ex, opt may be NULL). It is built on its first request and
+ *  stays resident until the budget needs its memory: then the least recently
+ *  used idle models are destroyed, and rebuilt when asked for again.
+ *  *model_id receives 0, 1, 2, ... in registration order.
+ * hodlrdd_server_submit
+ *  kind = HODLRDD_REQ_MATVEC: y = K x, x and y as for hodlrdd_matvec (host or
+ *  device, element type of the model's precision).
+ *  kind = HODLRDD_REQ_SOLVE: K u = b column by column through hodlrdd_solve
+ *  with the model as the fast operator and an FP64 twin of it (built on the
+ *  first solve, counted in the budget) as the refinement operator; x = b and
+ *  y = u are HOST arrays of N x nrhs doubles, original point order.
+ *  Buffers must stay valid until the request is waited for. Asynchronous;
+ *  *request_id identifies the request.
+ * hodlrdd_server_wait
+ *  Blocks until the request has finished and returns its status (the worker's
+ *  error detail is copied to the calling thread's hodlrdd_last_error); a request
+ *  is waited for once. latency_ms (optional) receives submit-to-done time.
+ * hodlrdd_server_stats
+ *  out[0] resident device bytes, out[1] resident models, out[2] builds so far,
+ *  out[3] evictions so far, out[4] queued requests not yet started.
+ * hodlrdd_server_destroy
+ *  Finishes queued requests, stops the workers, destroys every handle.
+ * Results equal those of hodlrdd_matvec / hodlrdd_solve on the model's handle
+ * alone (bitwise for products).
+ */
+enum { HODLRDD_REQ_MATVEC = 0, HODLRDD_REQ_SOLVE = 1 };
+typedef struct hodlrdd_server_s* hodlrdd_server;
+int hodlrdd_server_create(int64_t budget_bytes, int workers, hodlrdd_server* out);
+int hodlrdd_server_add(hodlrdd_server s, const double* points, int d, int64_t N, int kernel_id,
+                       const double* kernel_params, int leaf_size, double tol, const hodlrdd_options* opt,
+                       int64_t* model_id);
+int hodlrdd_server_submit(hodlrdd_server s, int64_t model_id, int kind, const void* x, void* y, int nrhs,
+                          int64_t* request_id);
+int hodlrdd_server_wait(hodlrdd_server s, int64_t request_id, double* latency_ms);
+int hodlrdd_server_stats(hodlrdd_server s, int64_t* out);
+int hodlrdd_server_destroy(hodlrdd_server s);
 
 #ifdef __cplusplus
 }

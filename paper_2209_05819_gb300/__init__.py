@@ -6,6 +6,9 @@ CUDA library, there is no CPU fallback):
     Handle(points, kernel, params, leaf, tol, precision=...)   build (Algorithm 1)
     Handle.matvec(x)                                            y = K x (Algorithm 2)
     Handle.stats()                                              ranks, sizes, phase times
+    solve(inner, outer, b)                                      GMRES with FP64 refinement
+    Batch(handles, nrhs).run(xs)                                graph-replayed batch of products
+    Server(budget).add / submit / wait                          request loop under an HBM budget
 """
 from ._binding import (  # noqa: F401
     Batch,
@@ -17,7 +20,10 @@ from ._binding import (  # noqa: F401
     ERR_UNSUPPORTED,
     OK,
     PREC,
+    REQ_MATVEC,
+    REQ_SOLVE,
     Handle,
+    Server,
     HodlrddError,
     header_functions,
     load,

@@ -102,6 +102,12 @@ def load():
         "hodlrdd_set_profiling": (i32, [vp, i32]),
         "hodlrdd_sync": (i32, [vp]),
         "hodlrdd_get_profile": (i32, [vp, vp, C.POINTER(i64), C.POINTER(i64)]),
+        "hodlrdd_server_create": (i32, [i64, i32, C.POINTER(vp)]),
+        "hodlrdd_server_add": (i32, [vp, vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(i64)]),
+        "hodlrdd_server_submit": (i32, [vp, i64, i32, vp, vp, i32, C.POINTER(i64)]),
+        "hodlrdd_server_wait": (i32, [vp, i64, C.POINTER(dbl)]),
+        "hodlrdd_server_stats": (i32, [vp, vp]),
+        "hodlrdd_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -396,6 +402,86 @@ class Batch:
         if getattr(self, "_b", None):
             self._lib.hodlrdd_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+REQ_MATVEC, REQ_SOLVE = 0, 1
+
+
+class Server:
+    """Request loop over models kept resident under a device-memory budget."""
+
+    def __init__(self, budget_bytes: int, workers: int = 4):
+        lib = load()
+        s = C.c_void_p()
+        _check(lib.hodlrdd_server_create(int(budget_bytes), int(workers), C.byref(s)), "hodlrdd_server_create")
+        self._s = s
+        self._lib = lib
+        self._keep = {}
+        self._models = []
+
+    def add(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8, precision: str = "fp32",
+            **options) -> int:
+        """Register a model (host points, N x d); returns its id."""
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        opt = Options()
+        self._lib.hodlrdd_options_default(C.byref(opt))
+        opt.precision = PREC[precision]
+        for k, v in options.items():
+            setattr(opt, k, LOWRANK_FORM[v] if k == "lowrank_form" else int(v))
+        p = np.zeros(4, np.float64)
+        p[0] = 1.0
+        if params is not None:
+            v = np.asarray(params, np.float64).reshape(-1)
+            p[: min(4, v.size)] = v[:4]
+        mid = C.c_int64()
+        _check(self._lib.hodlrdd_server_add(self._s, pts.ctypes.data, pts.shape[1], pts.shape[0], int(kernel),
+                                            p.ctypes.data, int(leaf), float(tol), C.byref(opt), C.byref(mid)),
+               "hodlrdd_server_add")
+        self._models.append((pts.shape[0], np.float64 if precision == "fp64" else np.float32))
+        return mid.value
+
+    def submit(self, model: int, x, kind: int = REQ_MATVEC, y=None) -> int:
+        """Queue y = K x (kind REQ_MATVEC) or K u = b (REQ_SOLVE, FP64 host arrays)."""
+        N, io = self._models[model] if 0 <= model < len(self._models) else (0, np.float32)
+        if kind == REQ_SOLVE:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            io = np.float64
+        if y is None:
+            y = np.empty(x.shape, dtype=io) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+        nrhs = 1 if x.ndim == 1 else int(x.shape[1])
+        xa, kx = _ptr(x)
+        ya, ky = _ptr(y)
+        rid = C.c_int64()
+        _check(self._lib.hodlrdd_server_submit(self._s, int(model), int(kind), xa, ya, nrhs, C.byref(rid)),
+               "hodlrdd_server_submit")
+        self._keep[rid.value] = (kx, ky)
+        return rid.value
+
+    def wait(self, request: int):
+        """(result, latency in ms) of a request."""
+        lat = C.c_double()
+        st = self._lib.hodlrdd_server_wait(self._s, int(request), C.byref(lat))
+        kx, ky = self._keep.pop(request, (None, None))
+        _check(st, "hodlrdd_server_wait")
+        return ky, lat.value
+
+    def stats(self) -> dict:
+        out = np.zeros(5, np.int64)
+        _check(self._lib.hodlrdd_server_stats(self._s, out.ctypes.data), "hodlrdd_server_stats")
+        return {"resident_bytes": int(out[0]), "resident_models": int(out[1]), "builds": int(out[2]),
+                "evictions": int(out[3]), "queued": int(out[4])}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.hodlrdd_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
 
     def __del__(self):
         try:

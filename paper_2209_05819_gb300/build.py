@@ -29,6 +29,7 @@ SOURCES = {
     "solve.cu": [],
     "batch.cu": [],
     "skeleton.cu": [],
+    "server.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <string>
 #include <utility>
+#include <memory>
 #include <vector>
 
 #include "../../include/hodlrdd.h"
@@ -399,6 +400,8 @@ struct hodlrdd_s {
   hd::DevBuf<char> pbuf;       // partial sums of cut panels
   hd::DevBuf<float> ynear;     // packed near-field sums (tree order)
   hd::DevBuf<int32_t> err;     // device error word of bounded waits
+  std::shared_ptr<void> solve_scratch;  // hodlrdd_solve's buffers when this handle is the inner operator
+  bool solve_scratch_f64 = false;
 
   // tracing: events between matvec stages, resolved by hodlrdd_get_profile
   bool profiling = false;

@@ -1,0 +1,373 @@
+// A request loop over HODLRdD models kept resident under a device-memory
+// budget: the serving side of the batched-trees use (many instances, uneven
+// sizes, products and second-kind solves arriving over time).
+//
+// A model is a point set with its kernel and build options. It is built on its
+// first request and stays resident; when the handles' device bytes exceed the
+// budget, the least recently used idle models are destroyed (and rebuilt if
+// asked for again). A solve request also keeps an FP64 twin of the model as the
+// refinement operator. Worker threads, one CUDA stream each, take requests in
+// arrival order; products of different models run side by side, requests for
+// one model run one at a time (its workspace). Every result equals the one the
+// model's handle gives alone (the same kernels on the same data).
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <string>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hd {
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Model {
+  std::vector<double> points;  // host copy, N x d row-major
+  int d = 0;
+  int64_t N = 0;
+  int kid = 0;
+  double prm[4] = {1.0, 0.0, 0.0, 0.0};
+  int leaf = 0;
+  double tol = 0.0;
+  hodlrdd_options opt{};
+  hodlrdd_s* h = nullptr;    // built on first use
+  hodlrdd_s* h64 = nullptr;  // FP64 twin, built on the first solve (unless opt is FP64)
+  int64_t bytes = 0;         // device bytes of h and h64
+  int64_t last_bytes = 0;    // size when last resident (0: never built)
+  uint64_t last_use = 0;
+  int running = 0;           // requests past residency, running on it (never evicted meanwhile)
+  std::mutex run;            // one request at a time on its workspace
+};
+
+struct Request {
+  int64_t model = 0;
+  int kind = 0;
+  const void* x = nullptr;
+  void* y = nullptr;
+  int nrhs = 1;
+  int status = HODLRDD_OK;
+  std::string msg;  // the worker's error detail
+  bool done = false;
+  double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
+};
+
+int64_t handle_bytes(hodlrdd_s* h) {
+  if (!h) return 0;
+  hodlrdd_stats s;
+  return hodlrdd_get_stats(h, &s) == HODLRDD_OK ? s.device_bytes : 0;
+}
+
+}  // namespace
+}  // namespace hd
+
+struct hodlrdd_server_s {
+  int device = 0;
+  int64_t budget = 0;
+  std::vector<std::unique_ptr<hd::Model>> models;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, hd::Request> reqs;
+  std::mutex mu;  // models' residency fields, queue, requests, counters
+  std::condition_variable cv_work, cv_done;
+  std::mutex build_mu;  // one build at a time
+  std::vector<std::thread> workers;
+  bool stop = false;
+  int64_t resident = 0, builds = 0, evictions = 0, next_id = 1;
+  uint64_t tick = 0;
+};
+
+namespace hd {
+namespace {
+
+// Destroys least recently used models that no request is running on (other
+// than keep) until the resident bytes fit the budget. Called with s->mu held,
+// by the holder of s->build_mu only.
+void evict_locked(hodlrdd_server_s* s, const Model* keep) {
+  while (s->resident > s->budget) {
+    Model* victim = nullptr;
+    for (auto& m : s->models)
+      if (m.get() != keep && (m->h || m->h64) && m->running == 0 && (!victim || m->last_use < victim->last_use))
+        victim = m.get();
+    if (!victim) return;
+    if (victim->h) hodlrdd_destroy(victim->h);
+    if (victim->h64) hodlrdd_destroy(victim->h64);
+    victim->h = victim->h64 = nullptr;
+    s->resident -= victim->bytes;
+    victim->bytes = 0;
+    s->evictions++;
+  }
+}
+
+// Makes m resident (and its FP64 twin for a solve) and, on success, counts
+// the caller as running on it (so that no build evicts it until it is done).
+// Builds are serialised; a build that leaves the budget exceeded waits for
+// running requests to finish and evicts their models, and fails with
+// HODLRDD_ERR_OOM only when nothing else is left to evict.
+int ensure(hodlrdd_server_s* s, Model& m, bool twin) {
+  auto needs_locked = [&](bool& need_h, bool& need_64) {
+    need_h = m.h == nullptr;
+    need_64 = twin && m.opt.precision != HODLRDD_PREC_FP64 && m.h64 == nullptr;
+    return need_h || need_64;
+  };
+  bool need_h = false, need_64 = false;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!needs_locked(need_h, need_64)) {  // resident: no wait on builds
+      m.running++;
+      return HODLRDD_OK;
+    }
+  }
+  std::lock_guard<std::mutex> build(s->build_mu);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!needs_locked(need_h, need_64)) {
+      m.running++;
+      return HODLRDD_OK;
+    }
+    // room first, from the model's last known size when it was resident before
+    const int64_t want = s->resident + (need_h ? m.last_bytes : 0);
+    if (want > s->budget) {
+      const int64_t saved = s->resident;
+      s->resident = want;
+      evict_locked(s, &m);
+      s->resident -= want - saved;
+    }
+  }
+  if (need_h) {
+    hodlrdd_s* h = nullptr;
+    HD_TRY(hodlrdd_build_ex(m.points.data(), m.d, m.N, m.kid, m.prm, m.leaf, m.tol, &m.opt, &h));
+    std::lock_guard<std::mutex> lk(s->mu);
+    m.h = h;
+    s->builds++;
+  }
+  if (need_64) {
+    hodlrdd_options o64 = m.opt;
+    o64.precision = HODLRDD_PREC_FP64;
+    o64.lowrank_form = 0;
+    hodlrdd_s* h = nullptr;
+    HD_TRY(hodlrdd_build_ex(m.points.data(), m.d, m.N, m.kid, m.prm, m.leaf, m.tol, &o64, &h));
+    std::lock_guard<std::mutex> lk(s->mu);
+    m.h64 = h;
+    s->builds++;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  const int64_t b = handle_bytes(m.h) + handle_bytes(m.h64);
+  s->resident += b - m.bytes;
+  m.bytes = m.last_bytes = b;
+  for (;;) {
+    evict_locked(s, &m);
+    if (s->resident <= s->budget) {
+      m.running++;
+      return HODLRDD_OK;
+    }
+    bool others = false;
+    for (auto& o : s->models) others |= o.get() != &m && o->running > 0;
+    if (!others) break;
+    s->cv_done.wait(lk);  // a running request finishes without builds: its model becomes evictable
+  }
+  // the model alone does not fit: do not keep it
+  if (m.h) hodlrdd_destroy(m.h);
+  if (m.h64) hodlrdd_destroy(m.h64);
+  m.h = m.h64 = nullptr;
+  s->resident -= m.bytes;
+  m.bytes = 0;
+  set_error("hodlrdd_server: the model does not fit the device-memory budget");
+  return HODLRDD_ERR_OOM;
+}
+
+// Device staging of one worker for solves (grown on demand).
+struct Staging {
+  DevBuf<double> b, x;
+  int grow(int64_t n) {
+    if ((int64_t)b.n < n) HD_TRY(b.alloc(n));
+    if ((int64_t)x.n < n) HD_TRY(x.alloc(n));
+    return HODLRDD_OK;
+  }
+};
+
+int run_request(Model& m, const Request& r, cudaStream_t st, Staging& sg) {
+  std::lock_guard<std::mutex> one(m.run);
+  if (r.kind == HODLRDD_REQ_MATVEC) {
+    HD_TRY(hodlrdd_matvec(m.h, r.x, r.y, r.nrhs, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    return hodlrdd_sync(m.h);
+  }
+  // solve, one right-hand side per column, FP64 b and x on the host
+  hodlrdd_s* outer = m.opt.precision == HODLRDD_PREC_FP64 ? m.h : m.h64;
+  HD_TRY(sg.grow(m.N));
+  const double* b = static_cast<const double*>(r.x);
+  double* x = static_cast<double*>(r.y);
+  std::vector<double> col(m.N);
+  for (int c = 0; c < r.nrhs; ++c) {
+    for (int64_t i = 0; i < m.N; ++i) col[i] = b[i * r.nrhs + c];
+    HD_CUDA(cudaMemcpyAsync(sg.b.p, col.data(), m.N * sizeof(double), cudaMemcpyHostToDevice, st));
+    HD_TRY(hodlrdd_solve(m.h, outer, sg.b.p, sg.x.p, nullptr, nullptr, st));
+    HD_CUDA(cudaMemcpyAsync(col.data(), sg.x.p, m.N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < m.N; ++i) x[i * r.nrhs + c] = col[i];
+  }
+  return HODLRDD_OK;
+}
+
+void worker(hodlrdd_server_s* s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+  Staging sg;
+  for (;;) {
+    int64_t id = 0;
+    Model* m = nullptr;
+    Request r;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop && s->queue.empty()) break;
+      id = s->queue.front();
+      s->queue.pop_front();
+      Request& q = s->reqs[id];
+      q.t_start = now_ms();
+      r = q;
+      m = s->models[(size_t)r.model].get();
+      m->last_use = ++s->tick;
+    }
+    int rc = have_stream ? ensure(s, *m, r.kind == HODLRDD_REQ_SOLVE) : HODLRDD_ERR_CUDA;
+    const bool ran = rc == HODLRDD_OK;
+    if (ran) rc = run_request(*m, r, st, sg);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (ran) m->running--;
+      m->last_use = ++s->tick;
+      Request& q = s->reqs[id];
+      q.status = rc;
+      if (rc != HODLRDD_OK) q.msg = hodlrdd_last_error();
+      q.done = true;
+      q.t_done = now_ms();
+    }
+    s->cv_done.notify_all();
+  }
+  if (st) cudaStreamDestroy(st);
+}
+
+}  // namespace
+}  // namespace hd
+
+using namespace hd;
+
+extern "C" int hodlrdd_server_create(int64_t budget_bytes, int workers, hodlrdd_server* out) {
+  if (!out || budget_bytes <= 0 || workers < 1 || workers > 64) {
+    set_error("hodlrdd_server_create: NULL out, budget <= 0 or workers outside 1..64");
+    return HODLRDD_ERR_INVALID;
+  }
+  hodlrdd_server_s* s = new (std::nothrow) hodlrdd_server_s();
+  if (!s) return HODLRDD_ERR_OOM;
+  HD_CUDA(cudaGetDevice(&s->device));
+  s->budget = budget_bytes;
+  for (int i = 0; i < workers; ++i) s->workers.emplace_back(worker, s);
+  *out = s;
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_add(hodlrdd_server s, const double* points, int d, int64_t N, int kernel_id,
+                                  const double* kernel_params, int leaf_size, double tol,
+                                  const hodlrdd_options* opt, int64_t* model_id) {
+  if (!s || !points || !model_id || d < 1 || d > kMaxDim || N < 1 || leaf_size < 1 || !(tol > 0.0)) {
+    set_error("hodlrdd_server_add: invalid argument");
+    return HODLRDD_ERR_INVALID;
+  }
+  std::unique_ptr<Model> m(new (std::nothrow) Model());
+  if (!m) return HODLRDD_ERR_OOM;
+  m->points.assign(points, points + N * d);
+  m->d = d;
+  m->N = N;
+  m->kid = kernel_id;
+  if (kernel_params)
+    for (int k = 0; k < 4; ++k) m->prm[k] = kernel_params[k];
+  m->leaf = leaf_size;
+  m->tol = tol;
+  hodlrdd_options_default(&m->opt);
+  if (opt) m->opt = *opt;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *model_id = (int64_t)s->models.size();
+  s->models.push_back(std::move(m));
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_submit(hodlrdd_server s, int64_t model_id, int kind, const void* x, void* y, int nrhs,
+                                     int64_t* request_id) {
+  if (!s || !x || !y || !request_id || nrhs < 1 || (kind != HODLRDD_REQ_MATVEC && kind != HODLRDD_REQ_SOLVE)) {
+    set_error("hodlrdd_server_submit: invalid argument");
+    return HODLRDD_ERR_INVALID;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (model_id < 0 || model_id >= (int64_t)s->models.size()) {
+      set_error("hodlrdd_server_submit: unknown model");
+      return HODLRDD_ERR_INVALID;
+    }
+    const int64_t id = s->next_id++;
+    Request& r = s->reqs[id];
+    r.model = model_id;
+    r.kind = kind;
+    r.x = x;
+    r.y = y;
+    r.nrhs = nrhs;
+    r.t_submit = now_ms();
+    s->queue.push_back(id);
+    *request_id = id;
+  }
+  s->cv_work.notify_one();
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_wait(hodlrdd_server s, int64_t request_id, double* latency_ms) {
+  if (!s) return HODLRDD_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) {
+    set_error("hodlrdd_server_wait: unknown request");
+    return HODLRDD_ERR_INVALID;
+  }
+  s->cv_done.wait(lk, [&] { return it->second.done; });
+  const int rc = it->second.status;
+  if (rc != HODLRDD_OK) set_error(it->second.msg);  // the detail, on the caller's thread
+  if (latency_ms) latency_ms[0] = it->second.t_done - it->second.t_submit;
+  s->reqs.erase(it);
+  return rc;
+}
+
+extern "C" int hodlrdd_server_stats(hodlrdd_server s, int64_t* out) {
+  if (!s || !out) return HODLRDD_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int64_t res_models = 0;
+  for (auto& m : s->models) res_models += (m->h || m->h64) ? 1 : 0;
+  out[0] = s->resident;
+  out[1] = res_models;
+  out[2] = s->builds;
+  out[3] = s->evictions;
+  out[4] = (int64_t)s->queue.size();
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_destroy(hodlrdd_server s) {
+  if (!s) return HODLRDD_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& m : s->models) {
+    if (m->h) hodlrdd_destroy(m->h);
+    if (m->h64) hodlrdd_destroy(m->h64);
+  }
+  delete s;
+  return HODLRDD_OK;
+}

@@ -12,6 +12,9 @@
 #include <cmath>
 #include <vector>
 
+#include <memory>
+#include <new>
+
 #include "internal.cuh"
 
 namespace hd {
@@ -188,23 +191,51 @@ int gmres(hodlrdd_s* A, const T* r, T* d, int64_t N, int m, double tol_in, int m
   return HODLRDD_OK;
 }
 
+// Solver scratch kept in the inner handle between solves (grown on demand), so
+// that repeated solves allocate nothing: a cudaMalloc / cudaFree per solve would
+// synchronise the device under every other stream's work.
+template <class T>
+struct SolveScratch {
+  Work<T> W;
+  DevBuf<T> r_in, d_in;
+  DevBuf<double> r, y;
+  int64_t N = 0;
+  int m = 0;
+  int fit(int64_t n, int mm) {
+    if (n <= N && mm <= m) return HODLRDD_OK;
+    N = std::max(N, n);
+    m = std::max(m, mm);
+    HD_TRY(W.V.alloc((size_t)N * (m + 1)));
+    HD_TRY(W.w.alloc(N));
+    HD_TRY(W.part.alloc((size_t)kDotBlocks * (m + 1)));
+    HD_TRY(W.c.alloc(m + 1));
+    HD_TRY(r_in.alloc(N));
+    HD_TRY(d_in.alloc(N));
+    HD_TRY(r.alloc(N));
+    HD_TRY(y.alloc(N));
+    return HODLRDD_OK;
+  }
+};
+
 template <class T>
 int solve_typed(hodlrdd_s* inner, hodlrdd_s* outer, const double* b, double* x, const hodlrdd_solve_options& o,
                 hodlrdd_solve_stats* stats, cudaStream_t st) {
   const int64_t N = outer->N;
   const int m = o.restart;
   const int grid = grid_for(N);
-  Work<T> W;
-  DevBuf<T> r_in, d_in;
-  DevBuf<double> r, y;
-  HD_TRY(W.V.alloc((size_t)N * (m + 1)));
-  HD_TRY(W.w.alloc(N));
-  HD_TRY(W.part.alloc((size_t)kDotBlocks * (m + 1)));
-  HD_TRY(W.c.alloc(m + 1));
-  HD_TRY(r_in.alloc(N));
-  HD_TRY(d_in.alloc(N));
-  HD_TRY(r.alloc(N));
-  HD_TRY(y.alloc(N));
+  if (!inner->solve_scratch || inner->solve_scratch_f64 != std::is_same<T, double>::value) {
+    inner->solve_scratch = std::shared_ptr<void>(new (std::nothrow) SolveScratch<T>(),
+                                                 [](void* p) { delete static_cast<SolveScratch<T>*>(p); });
+    inner->solve_scratch_f64 = std::is_same<T, double>::value;
+    if (!inner->solve_scratch) return HODLRDD_ERR_OOM;
+  }
+  SolveScratch<T>& S = *static_cast<SolveScratch<T>*>(inner->solve_scratch.get());
+  HD_TRY(S.fit(N, m));
+  Work<T>& W = S.W;
+  DevBuf<T>& r_in = S.r_in;
+  DevBuf<T>& d_in = S.d_in;
+  DevBuf<double>& r = S.r;
+  DevBuf<double>& y = S.y;
   HD_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), st));
   double bnorm = 0.0, rnorm = 0.0;
   HD_TRY(norm2<double>(b, N, W.part, W.c, &bnorm, st));
