@@ -437,7 +437,8 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
  * hodlrdd_server_wait
  *  Blocks until the request has finished and returns its status (the worker's
  *  error detail is copied to the calling thread's hodlrdd_last_error); a request
- *  is waited for once. latency_ms (optional) receives submit-to-done time.
+ *  is waited for once. latency_ms (optional, two doubles) receives the
+ *  submit-to-done and the start-to-done (service) times in milliseconds.
  * hodlrdd_server_stats
  *  out[0] resident device bytes, out[1] resident models, out[2] builds so far,
  *  out[3] evictions so far, out[4] queued requests not yet started.

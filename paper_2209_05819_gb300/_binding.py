@@ -105,7 +105,7 @@ def load():
         "hodlrdd_server_create": (i32, [i64, i32, C.POINTER(vp)]),
         "hodlrdd_server_add": (i32, [vp, vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(i64)]),
         "hodlrdd_server_submit": (i32, [vp, i64, i32, vp, vp, i32, C.POINTER(i64)]),
-        "hodlrdd_server_wait": (i32, [vp, i64, C.POINTER(dbl)]),
+        "hodlrdd_server_wait": (i32, [vp, i64, vp]),
         "hodlrdd_server_stats": (i32, [vp, vp]),
         "hodlrdd_server_destroy": (i32, [vp]),
     }
@@ -463,13 +463,14 @@ class Server:
         self._keep[rid.value] = (kx, ky)
         return rid.value
 
-    def wait(self, request: int):
-        """(result, latency in ms) of a request."""
-        lat = C.c_double()
-        st = self._lib.hodlrdd_server_wait(self._s, int(request), C.byref(lat))
+    def wait(self, request: int, service: bool = False):
+        """(result, latency in ms) of a request; with service=True also the
+        start-to-done time: (result, latency, service)."""
+        lat = (C.c_double * 2)()
+        st = self._lib.hodlrdd_server_wait(self._s, int(request), lat)
         kx, ky = self._keep.pop(request, (None, None))
         _check(st, "hodlrdd_server_wait")
-        return ky, lat.value
+        return (ky, lat[0], lat[1]) if service else (ky, lat[0])
 
     def stats(self) -> dict:
         out = np.zeros(5, np.int64)

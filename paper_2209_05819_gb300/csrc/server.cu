@@ -338,7 +338,10 @@ extern "C" int hodlrdd_server_wait(hodlrdd_server s, int64_t request_id, double*
   s->cv_done.wait(lk, [&] { return it->second.done; });
   const int rc = it->second.status;
   if (rc != HODLRDD_OK) set_error(it->second.msg);  // the detail, on the caller's thread
-  if (latency_ms) latency_ms[0] = it->second.t_done - it->second.t_submit;
+  if (latency_ms) {
+    latency_ms[0] = it->second.t_done - it->second.t_submit;
+    latency_ms[1] = it->second.t_done - it->second.t_start;
+  }
   s->reqs.erase(it);
   return rc;
 }
