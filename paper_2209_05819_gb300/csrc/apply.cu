@@ -250,38 +250,42 @@ struct PanelMeta {
 };
 static_assert(sizeof(PanelMeta) <= kMetaBytes, "panel metadata exceeds its slot area");
 
-template <class T, int NR, bool VMODE>
-__global__ void __launch_bounds__(kSegThreads, 1)
-    k_panel(const T* __restrict__ F, const Panel* __restrict__ panels, const Stage* __restrict__ stages,
-            const int32_t* __restrict__ cta_first, const typename Fac<T>::acc* __restrict__ vec,
-            typename Fac<T>::acc* __restrict__ out, const int32_t* __restrict__ map, const float* __restrict__ sa,
-            const float* __restrict__ sb, typename Fac<T>::acc* __restrict__ part, int32_t* __restrict__ err) {
+// One stream's arguments (factor data, sub-panels, stages, CTA ranges, vector
+// in, outputs, V column map and scales, partial sums).
+template <class T>
+struct PanelArgs {
+  using Acc = typename Fac<T>::acc;
+  const T* F;
+  const Panel* panels;
+  const Stage* stages;
+  const int32_t* cta_first;
+  int ctas;
+  const Acc* vec;
+  Acc* out;
+  const int32_t* map;
+  const float* sa;
+  const float* sb;
+  Acc* part;
+};
+
+// Producer warp: bulk-copies this CTA's stages of one stream into the ring;
+// stage descriptors a batch ahead, panel records one stage ahead (registers)
+// and eight ahead (L2). `issued` counts every stage the ring has taken, over
+// the streams one launch applies. False when a bounded wait expired (the
+// copies already issued have then landed).
+template <class T, int NR>
+__device__ __forceinline__ bool panel_produce(const PanelArgs<T>& a, char* smem, uint64_t* full, uint64_t* empty,
+                                              int& issued, int32_t* err, uint64_t once) {
   using Acc = typename Fac<T>::acc;
   using C = PanelCfg<T, NR>;
-  constexpr int E = Fac<T>::E;
   constexpr int NS = C::kStagesN;
-  constexpr int NT = kConsumerWarps * 32;
   constexpr int A1 = 16 / (int)sizeof(Acc);  // vector elements per 16 bytes
-  extern __shared__ __align__(128) char smem[];
-  __shared__ __align__(8) uint64_t full[NS], empty[NS];
-  Acc* red = reinterpret_cast<Acc*>(smem + (size_t)NS * C::kSlot);  // NT * 8
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = cta_first[blockIdx.x], q1 = cta_first[blockIdx.x + 1];
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  if (warp == 0) {
-    // producer: stage descriptors a batch ahead, panel records one stage ahead
-    // (registers) and eight ahead (L2)
-    const uint64_t once = l2_evict_first();
-    int issued = 0;
+  {
+    const int lane = threadIdx.x & 31;
+    const int q0 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x] : 0;
+    const int q1 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x + 1] : 0;
+    const Stage* __restrict__ stages = a.stages;
+    const Panel* __restrict__ panels = a.panels;
     bool ok = true;
     StageRegs ca, cb;
     load_stage_regs(ca, stages, q0 + lane, q1);
@@ -289,8 +293,8 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     Stage st_next = pick_stage(ca, cb, 0);
     Panel P_next{};
     if (q0 < q1) P_next = panels[st_next.g];
-    for (int q = q0; q < q1; ++q, ++issued) {
-      const int k = issued & 31;
+    for (int q = q0, j = 0; q < q1; ++q, ++j, ++issued) {
+      const int k = j & 31;
       const Stage st = st_next;
       const Panel Pq = P_next;
       if (q + 1 < q1) {
@@ -319,16 +323,16 @@ __global__ void __launch_bounds__(kSegThreads, 1)
         char* base = smem + (size_t)slot * C::kSlot;
         PanelMeta* meta = reinterpret_cast<PanelMeta*>(base + kStageBytes + C::kScal);
         const int64_t v0 = ((int64_t)Pq.vfirst + st.s) * NR;
-        const int a = (int)(v0 % A1);
+        const int la = (int)(v0 % A1);
         meta->st = st;
         meta->P = Pq;
-        meta->lead = a;
+        meta->lead = la;
         __threadfence_block();
         const uint32_t fbytes = (uint32_t)st.nelem * sizeof(T);
-        const uint32_t sbytes = (uint32_t)(((a + st.nseg * NR) * (int)sizeof(Acc) + 15) & ~15);
+        const uint32_t sbytes = (uint32_t)(((la + st.nseg * NR) * (int)sizeof(Acc) + 15) & ~15);
         mbar_expect_tx(&full[slot], fbytes + sbytes);
-        bulk_g2s_once(base, F + st.off, fbytes, &full[slot], once);
-        bulk_g2s(base + kStageBytes, vec + (v0 - a), sbytes, &full[slot]);
+        bulk_g2s_once(base, a.F + st.off, fbytes, &full[slot], once);
+        bulk_g2s(base + kStageBytes, a.vec + (v0 - la), sbytes, &full[slot]);
       }
       __syncwarp();
     }
@@ -336,9 +340,29 @@ __global__ void __launch_bounds__(kSegThreads, 1)
       // drain: copies already issued must land before the CTA's smem goes away
       for (int k = max(0, issued - NS); k < issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, err, ERR_WAIT_DRAIN);
     }
-    return;
+    return ok;
   }
 
+}
+
+// Consumer warps: apply this CTA's stages of one stream; ibase = the ring index
+// of its first stage. False when a bounded wait expired.
+template <class T, int NR, bool VMODE>
+__device__ __forceinline__ bool panel_consume(const PanelArgs<T>& a, char* smem, uint64_t* full, uint64_t* empty,
+                                              typename Fac<T>::acc* red, int ibase, int32_t* err) {
+  using Acc = typename Fac<T>::acc;
+  using C = PanelCfg<T, NR>;
+  constexpr int E = Fac<T>::E;
+  constexpr int NS = C::kStagesN;
+  constexpr int NT = kConsumerWarps * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x] : 0;
+  const int q1 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x + 1] : 0;
+  const int32_t* __restrict__ map = a.map;
+  const float* __restrict__ sa = a.sa;
+  const float* __restrict__ sb = a.sb;
+  Acc* __restrict__ part = a.part;
+  Acc* __restrict__ out = a.out;
   const int cw = warp - 1;
   const int ct = cw * 32 + lane;
   // FP32 with one or two right-hand sides: plain sums over up to kKahanStages
@@ -361,9 +385,9 @@ __global__ void __launch_bounds__(kSegThreads, 1)
   int32_t oidx[VMODE ? E : 1];
   Acc oscl[VMODE ? E : 1];
   for (int q = q0; q < q1; ++q) {
-    const int i = q - q0;
+    const int i = ibase + (q - q0);
     const int slot = i % NS;
-    if (!mbar_wait(&full[slot], (i / NS) & 1, err, ERR_WAIT_FULL)) return;
+    if (!mbar_wait(&full[slot], (i / NS) & 1, err, ERR_WAIT_FULL)) return false;
     const char* base = smem + (size_t)slot * C::kSlot;
     const PanelMeta* meta = reinterpret_cast<const PanelMeta*>(base + kStageBytes + C::kScal);
     const Stage st = meta->st;
@@ -517,6 +541,61 @@ __global__ void __launch_bounds__(kSegThreads, 1)
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[slot]);
   }
+  return true;
+}
+
+template <int NR>
+__device__ __forceinline__ void panel_ring_init(uint64_t* full, uint64_t* empty, int ns) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+template <class T, int NR, bool VMODE>
+__global__ void __launch_bounds__(kSegThreads, 1) k_panel(PanelArgs<T> a, int32_t* __restrict__ err) {
+  using C = PanelCfg<T, NR>;
+  constexpr int NS = C::kStagesN;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS];
+  auto* red = reinterpret_cast<typename Fac<T>::acc*>(smem + (size_t)NS * C::kSlot);  // NT * 8
+  panel_ring_init<NR>(full, empty, NS);
+  if ((threadIdx.x >> 5) == 0) {
+    int issued = 0;
+    panel_produce<T, NR>(a, smem, full, empty, issued, err, l2_evict_first());
+    return;
+  }
+  panel_consume<T, NR, VMODE>(a, smem, full, empty, red, 0, err);
+}
+
+// Mixed storage: one launch applies the FP32 stream and then the FP16 stream of
+// the same stage through one ring (both have the same slot layout), so that the
+// two parts share one persistent CTA per SM instead of following each other.
+template <int NR, bool VMODE>
+__global__ void __launch_bounds__(kSegThreads, 1) k_panel_mix(PanelArgs<float> a, PanelArgs<__half> b,
+                                                              int32_t* __restrict__ err) {
+  using C = PanelCfg<float, NR>;
+  static_assert(C::kSlot == PanelCfg<__half, NR>::kSlot && C::kStagesN == PanelCfg<__half, NR>::kStagesN,
+                "the two element types must share the ring layout");
+  constexpr int NS = C::kStagesN;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS];
+  float* red = reinterpret_cast<float*>(smem + (size_t)NS * C::kSlot);
+  panel_ring_init<NR>(full, empty, NS);
+  if ((threadIdx.x >> 5) == 0) {
+    const uint64_t once = l2_evict_first();
+    int issued = 0;
+    if (!panel_produce<float, NR>(a, smem, full, empty, issued, err, once)) return;
+    panel_produce<__half, NR>(b, smem, full, empty, issued, err, once);
+    return;
+  }
+  const int na = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x + 1] - a.cta_first[blockIdx.x] : 0;
+  if (!panel_consume<float, NR, VMODE>(a, smem, full, empty, red, 0, err)) return;
+  panel_consume<__half, NR, VMODE>(b, smem, full, empty, red, na, err);
 }
 
 // Sums of cut panels: out = sum over the sub-panels' partials, in sub-panel
@@ -1533,84 +1612,71 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   const bool mixed = h->opt.precision == HODLRDD_PREC_FP32_FP16;
   Acc* pb2 = pb + (size_t)std::max<int64_t>({P.vs.part_rows, P.us.part_rows, 1}) * NR;
+  auto args = [&](const Stream& S, const Acc* vec, Acc* out, const int32_t* map, const float* a_, const float* b_,
+                  Acc* part) {
+    return PanelArgs<T>{reinterpret_cast<const T*>(S.data.p), S.panels.p, S.stages.p, S.cta.p, S.ctas, vec, out, map,
+                        a_, b_, part};
+  };
+  auto args16 = [&](const Stream& S, const float* vec, float* out, const int32_t* map, const float* a_,
+                    const float* b_, float* part) {
+    return PanelArgs<__half>{reinterpret_cast<const __half*>(S.data.p), S.panels.p, S.stages.p, S.cta.p, S.ctas, vec,
+                             out, map, a_, b_, part};
+  };
+  // one apply stage: uniform storage, or (mixed) the FP32 and FP16 streams in one launch
+  auto stage = [&](bool vmode, const Acc* vec, Acc* out) -> int {
+    const Stream& S1 = vmode ? P.vs : P.us;
+    const Stream& S2 = vmode ? P.vs2 : P.us2;
+    const int32_t* m1 = vmode ? P.vmap.p : nullptr;
+    const int32_t* m2 = vmode ? P.vmap2.p : nullptr;
+    const float* a1 = vmode ? sa : nullptr;
+    const float* b1 = vmode ? sb : nullptr;
+    bool launched = false;
+    if constexpr (std::is_same<T, float>::value && NR <= 8) {
+      if (mixed && (S1.ctas > 0 || S2.ctas > 0)) {
+        const int grid = std::max(S1.ctas, S2.ctas);
+        const PanelArgs<float> A = args(S1, vec, out, m1, nullptr, nullptr, pb);
+        const PanelArgs<__half> B =
+            args16(S2, vec, out, m2, vmode ? h->sv.p : nullptr, vmode ? h->su.p : nullptr, pb2);
+        if (vmode) k_panel_mix<NR, true><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
+        else k_panel_mix<NR, false><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
+        h->launches += 1;
+        launched = true;
+      }
+    }
+    if (!launched && S1.ctas > 0 && !S1.h_stages.empty()) {
+      const PanelArgs<T> A = args(S1, vec, out, m1, a1, b1, pb);
+      if (vmode) k_panel<T, NR, true><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
+      else k_panel<T, NR, false><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
+      h->launches += 1;
+    }
+    // sums of cut panels, each part from its own partial-sum area
+    if (!S1.h_splits.empty()) {
+      if (vmode) k_combine<Acc, NR, true><<<(int)S1.h_cwork.size(), 256, 0, st>>>(S1.splits.p, S1.cwork.p, pb, out,
+                                                                                   m1, a1, b1);
+      else k_combine<Acc, NR, false><<<(int)S1.h_cwork.size(), 256, 0, st>>>(S1.splits.p, S1.cwork.p, pb, out,
+                                                                                nullptr, nullptr, nullptr);
+      h->launches += 1;
+    }
+    if (mixed && !S2.h_splits.empty()) {
+      if (vmode) k_combine<Acc, NR, true><<<(int)S2.h_cwork.size(), 256, 0, st>>>(S2.splits.p, S2.cwork.p, pb2, out,
+                                                                                   m2, h->sv.p, h->su.p);
+      else k_combine<Acc, NR, false><<<(int)S2.h_cwork.size(), 256, 0, st>>>(S2.splits.p, S2.cwork.p, pb2, out,
+                                                                                nullptr, nullptr, nullptr);
+      h->launches += 1;
+    }
+    HD_CUDA(cudaGetLastError());
+    return HODLRDD_OK;
+  };
   if (h->kappa >= 1) {
     HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)level_slices(h) * h->N * NR * sizeof(Acc), st));
-    if constexpr (std::is_same<T, float>::value && NR <= 8) {
-      // mixed storage: the FP16 tail columns (their own t indices and partial
-      // sums) on the third stream, so that its CTAs fill the FP32 launch's tail
-      if (mixed) {
-        HD_CUDA(cudaEventRecord(h->ev_fork2, st));
-        HD_CUDA(cudaStreamWaitEvent(h->aux2, h->ev_fork2, 0));
-        if (P.vs2.ctas > 0 && !P.vs2.h_stages.empty()) {
-          using C2 = PanelCfg<__half, NR>;
-          k_panel<__half, NR, true><<<P.vs2.ctas, kSegThreads, C2::kSmem, h->aux2>>>(
-              reinterpret_cast<const __half*>(P.vs2.data.p), P.vs2.panels.p, P.vs2.stages.p, P.vs2.cta.p, xt, t,
-              P.vmap2.p, h->sv.p, h->su.p, pb2, h->err.p);
-          h->launches += 1;
-          if (!P.vs2.h_splits.empty()) {
-            k_combine<Acc, NR, true><<<(int)P.vs2.h_cwork.size(), 256, 0, h->aux2>>>(
-                P.vs2.splits.p, P.vs2.cwork.p, pb2, t, P.vmap2.p, h->sv.p, h->su.p);
-            h->launches += 1;
-          }
-        }
-        HD_CUDA(cudaEventRecord(h->ev_vtail, h->aux2));
-      }
-    }
-    if (skel) {
-      HD_TRY(launch_skeleton_rows(h, st, xt, t));
-    } else if (P.vs.ctas > 0 && !P.vs.h_stages.empty()) {
-      k_panel<T, NR, true><<<P.vs.ctas, kSegThreads, C::kSmem, st>>>(
-          reinterpret_cast<const T*>(P.vs.data.p), P.vs.panels.p, P.vs.stages.p, P.vs.cta.p, xt, t, P.vmap.p, sa, sb,
-          pb, h->err.p);
-      h->launches += 1;
-      if (!P.vs.h_splits.empty()) {
-        k_combine<Acc, NR, true><<<(int)P.vs.h_cwork.size(), 256, 0, st>>>(P.vs.splits.p, P.vs.cwork.p, pb, t,
-                                                                             P.vmap.p, sa, sb);
-        h->launches += 1;
-      }
-    }
-    if constexpr (std::is_same<T, float>::value && NR <= 8) {
-      // the join of the FP16 tail V-apply (launched beside the FP32 one)
-      if (mixed) HD_CUDA(cudaStreamWaitEvent(st, h->ev_vtail, 0));
-    }
+    if (skel) HD_TRY(launch_skeleton_rows(h, st, xt, t));
+    else HD_TRY(stage(true, xt, t));
   }
   HD_TRY(fork_near());
   if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
-  if constexpr (std::is_same<T, float>::value && NR <= 8) {
-    // FP16 tail U-apply on the third stream (its own y_l slices), after every t is written
-    if (mixed && h->kappa >= 1) {
-      HD_CUDA(cudaEventRecord(h->ev_vdone, st));
-      HD_CUDA(cudaStreamWaitEvent(h->aux2, h->ev_vdone, 0));
-      if (P.us2.ctas > 0 && !P.us2.h_stages.empty()) {
-        using C2 = PanelCfg<__half, NR>;
-        k_panel<__half, NR, false><<<P.us2.ctas, kSegThreads, C2::kSmem, h->aux2>>>(
-            reinterpret_cast<const __half*>(P.us2.data.p), P.us2.panels.p, P.us2.stages.p, P.us2.cta.p, t, yl,
-            nullptr, nullptr, nullptr, pb2, h->err.p);
-        h->launches += 1;
-        if (!P.us2.h_splits.empty()) {
-          k_combine<Acc, NR, false><<<(int)P.us2.h_cwork.size(), 256, 0, h->aux2>>>(
-              P.us2.splits.p, P.us2.cwork.p, pb2, yl, nullptr, nullptr, nullptr);
-          h->launches += 1;
-        }
-      }
-      HD_CUDA(cudaEventRecord(h->ev_utail, h->aux2));
-    }
-  }
-  if (skel && h->kappa >= 1) {
-    HD_TRY(launch_skeleton_cols(h, st, t, yl));
-  } else if (h->kappa >= 1 && P.us.ctas > 0 && !P.us.h_stages.empty()) {
-    k_panel<T, NR, false><<<P.us.ctas, kSegThreads, C::kSmem, st>>>(
-        reinterpret_cast<const T*>(P.us.data.p), P.us.panels.p, P.us.stages.p, P.us.cta.p, t, yl, nullptr, nullptr,
-        nullptr, pb, h->err.p);
-    h->launches += 1;
-    if (!P.us.h_splits.empty()) {
-      k_combine<Acc, NR, false><<<(int)P.us.h_cwork.size(), 256, 0, st>>>(P.us.splits.p, P.us.cwork.p, pb, yl,
-                                                                              nullptr, nullptr, nullptr);
-      h->launches += 1;
-    }
-  }
-  if constexpr (std::is_same<T, float>::value && NR <= 8) {
-    if (mixed && h->kappa >= 1) HD_CUDA(cudaStreamWaitEvent(st, h->ev_utail, 0));  // the FP16 tail U-apply
+  if (h->kappa >= 1) {
+    if (skel) HD_TRY(launch_skeleton_cols(h, st, t, yl));
+    else HD_TRY(stage(false, t, yl));
   }
   if (prof) HD_CUDA(cudaEventRecord(ev[3], st));
   if (packed) {
@@ -1639,6 +1705,10 @@ int set_smem_attr_nr() {
   const int smem = (int)PanelCfg<T, NR>::kSmem;
   HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if constexpr (std::is_same<T, float>::value && NR <= 8) {
+    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
   return HODLRDD_OK;
 }
 
@@ -1658,7 +1728,6 @@ int set_smem_attr() {
 template <class T, class IO>
 int matvec_typed(hodlrdd_s* h, const IO* x, IO* y, int nrhs, cudaStream_t st) {
   HD_TRY(set_smem_attr<T>());
-  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) HD_TRY(set_smem_attr<__half>());
   int c0 = 0;
   if (h->opt.lowrank_form == 1) {  // skeleton form: one right-hand side per pass
     for (; c0 < nrhs; ++c0) HD_TRY((matvec_chunk<T, IO, 1>(h, x, y, nrhs, c0, st)));

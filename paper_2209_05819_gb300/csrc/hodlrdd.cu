@@ -186,11 +186,6 @@ int do_build(hodlrdd_s* h, const double* points) {
   HD_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
   HD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   HD_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) {
-    HD_CUDA(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
-    for (cudaEvent_t* e : {&h->ev_fork2, &h->ev_vtail, &h->ev_vdone, &h->ev_utail})
-      HD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-  }
   // the caller's points, as a device array (copied if they live on the host)
   DevBuf<double> staged;
   const double* dpts = points;
@@ -236,12 +231,9 @@ void destroy(hodlrdd_s* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   if (h->aux) cudaStreamSynchronize(h->aux);
-  if (h->aux2) cudaStreamSynchronize(h->aux2);
-  cudaStream_t st = h->st, aux = h->aux, aux2 = h->aux2;
+  cudaStream_t st = h->st, aux = h->aux;
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  for (cudaEvent_t e : {h->ev_fork2, h->ev_vtail, h->ev_vdone, h->ev_utail})
-    if (e) cudaEventDestroy(e);
   for (auto& v : h->ev_pending)
     for (cudaEvent_t e : v) {
       cudaEventSynchronize(e);
@@ -251,7 +243,6 @@ void destroy(hodlrdd_s* h) {
   delete h;
   if (st) cudaStreamDestroy(st);
   if (aux) cudaStreamDestroy(aux);
-  if (aux2) cudaStreamDestroy(aux2);
 }
 
 }  // namespace

@@ -360,9 +360,6 @@ struct hodlrdd_s {
   cudaStream_t st = nullptr;  // the handle's own stream (build, staging)
   cudaStream_t aux = nullptr; // second stream: the packed near field runs beside the low-rank applies
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // third stream: the FP16 tail panels of the mixed storage, beside the FP32 panels
-  cudaStream_t aux2 = nullptr;
-  cudaEvent_t ev_fork2 = nullptr, ev_vtail = nullptr, ev_vdone = nullptr, ev_utail = nullptr;
 
   // tree
   int B = 0, kappa = 0;
