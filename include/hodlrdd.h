@@ -407,6 +407,16 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
                            const double* V_all);
 
 /*
+ * Test entry for the bounded device-side waits: runs, on the handle's stream,
+ * one wait on an mbarrier phase that nothing completes, bounded by `cycles`
+ * SM clock cycles (at most 8e9, about 4 s); it then records an error code in the
+ * handle's error word exactly as an expired wait in a matvec kernel does, and
+ * returns. The next hodlrdd_sync reports HODLRDD_ERR_TIMEOUT and clears the
+ * word; the handle stays usable. Synchronous.
+ */
+int hodlrdd_debug_expire_wait(hodlrdd_handle h, long long cycles);
+
+/*
  * Serving: a request loop over models kept resident under a device-memory
  * budget (the library's addition for many instances of uneven size arriving
  * over time, such as the paper's batched uses).
@@ -415,10 +425,13 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
  *  budget_bytes  device bytes the resident handles may hold (hodlrdd_stats
  *                device_bytes, summed); during a build the new handle may
  *                briefly exceed it.
- *  workers       host threads (1..64), one CUDA stream each, on the current
- *                device. Requests start in arrival order; products of different
- *                models run side by side; requests for one model run one at a
- *                time.
+ *  workers       host threads (1..64) on the current device, each with a
+ *                high-priority CUDA stream for products and a low-priority one
+ *                for solves. Queued products start before queued solves (they are
+ *                short), and at most workers - 1 solves run at once (with more
+ *                than one worker) so that one worker stays free for products;
+ *                each kind starts in arrival order. Products of different models
+ *                run side by side; requests for one model run one at a time.
  * hodlrdd_server_add
  *  Registers a model (host copy of the points; same arguments as
  *  hodlrdd_build_ex, opt may be NULL). It is built on its first request and

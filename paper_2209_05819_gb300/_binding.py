@@ -102,6 +102,7 @@ def load():
         "hodlrdd_set_profiling": (i32, [vp, i32]),
         "hodlrdd_sync": (i32, [vp]),
         "hodlrdd_get_profile": (i32, [vp, vp, C.POINTER(i64), C.POINTER(i64)]),
+        "hodlrdd_debug_expire_wait": (i32, [vp, C.c_longlong]),
         "hodlrdd_server_create": (i32, [i64, i32, C.POINTER(vp)]),
         "hodlrdd_server_add": (i32, [vp, vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(i64)]),
         "hodlrdd_server_submit": (i32, [vp, i64, i32, vp, vp, i32, C.POINTER(i64)]),
@@ -342,6 +343,10 @@ class Handle:
         V = np.zeros(max(n * rank, 1), np.float64)
         _check(self._lib.hodlrdd_get_factors(self._h, int(b), U.ctypes.data, V.ctypes.data), "hodlrdd_get_factors")
         return U[: m * rank].reshape(rank, m).T, V[: n * rank].reshape(rank, n).T
+
+    def debug_expire_wait(self, cycles: int = 2_000_000_000):
+        """Run one bounded device wait that nothing completes (test of the timeout path)."""
+        _check(self._lib.hodlrdd_debug_expire_wait(self._h, int(cycles)), "hodlrdd_debug_expire_wait")
 
     def import_factors(self, ranks, dense, U_all, V_all):
         r = np.ascontiguousarray(ranks, np.int32)

@@ -30,6 +30,7 @@ SOURCES = {
     "batch.cu": [],
     "skeleton.cu": [],
     "server.cu": [],
+    "debug.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

@@ -6,10 +6,14 @@
 // first request and stays resident; when the handles' device bytes exceed the
 // budget, the least recently used idle models are destroyed (and rebuilt if
 // asked for again). A solve request also keeps an FP64 twin of the model as the
-// refinement operator. Worker threads, one CUDA stream each, take requests in
-// arrival order; products of different models run side by side, requests for
-// one model run one at a time (its workspace). Every result equals the one the
-// model's handle gives alone (the same kernels on the same data).
+// refinement operator. Worker threads (each with a high-priority CUDA stream
+// for products and a low-priority one for solves) take queued
+// products first (they are short) and solves otherwise, with at most
+// workers - 1 solves at a time so that one worker stays free for products;
+// each kind in arrival order. Products of different models run side by side,
+// requests for one model run one at a time (its workspace). Every result
+// equals the one the model's handle gives alone (the same kernels on the same
+// data).
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -73,7 +77,7 @@ struct hodlrdd_server_s {
   int device = 0;
   int64_t budget = 0;
   std::vector<std::unique_ptr<hd::Model>> models;
-  std::deque<int64_t> queue;
+  std::deque<int64_t> queue_mv, queue_sv;  // products, solves
   std::unordered_map<int64_t, hd::Request> reqs;
   std::mutex mu;  // models' residency fields, queue, requests, counters
   std::condition_variable cv_work, cv_done;
@@ -82,6 +86,7 @@ struct hodlrdd_server_s {
   bool stop = false;
   int64_t resident = 0, builds = 0, evictions = 0, next_id = 1;
   uint64_t tick = 0;
+  int nworkers = 1, solves_running = 0;
 };
 
 namespace hd {
@@ -193,12 +198,27 @@ struct Staging {
   }
 };
 
+// The handle's bounded-wait error word after a product on st (already
+// synchronised), read and cleared on st: hodlrdd_sync would synchronise the
+// whole device, i.e. wait for every other worker's requests.
+int check_waits(hodlrdd_s* h, cudaStream_t st) {
+  if (!h->err.p) return HODLRDD_OK;
+  int32_t code = 0;
+  HD_CUDA(cudaMemcpyAsync(&code, h->err.p, sizeof code, cudaMemcpyDeviceToHost, st));
+  HD_CUDA(cudaStreamSynchronize(st));
+  if (code == 0) return HODLRDD_OK;
+  HD_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof code, st));
+  HD_CUDA(cudaStreamSynchronize(st));
+  set_error("a bounded device-side wait expired; the product is invalid");
+  return HODLRDD_ERR_TIMEOUT;
+}
+
 int run_request(Model& m, const Request& r, cudaStream_t st, Staging& sg) {
   std::lock_guard<std::mutex> one(m.run);
   if (r.kind == HODLRDD_REQ_MATVEC) {
     HD_TRY(hodlrdd_matvec(m.h, r.x, r.y, r.nrhs, st));
     HD_CUDA(cudaStreamSynchronize(st));
-    return hodlrdd_sync(m.h);
+    return check_waits(m.h, st);
   }
   // solve, one right-hand side per column, FP64 b and x on the host
   hodlrdd_s* outer = m.opt.precision == HODLRDD_PREC_FP64 ? m.h : m.h64;
@@ -219,8 +239,13 @@ int run_request(Model& m, const Request& r, cudaStream_t st, Staging& sg) {
 
 void worker(hodlrdd_server_s* s) {
   cudaSetDevice(s->device);
-  cudaStream_t st = nullptr;
-  const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+  // products on a high-priority stream, so that their CTAs are placed ahead of
+  // the long solves' as SMs free up; solves on a low-priority one
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t st_mv = nullptr, st_sv = nullptr;
+  const bool have_stream = cudaStreamCreateWithPriority(&st_mv, cudaStreamNonBlocking, hi) == cudaSuccess &&
+                           cudaStreamCreateWithPriority(&st_sv, cudaStreamNonBlocking, lo) == cudaSuccess;
   Staging sg;
   for (;;) {
     int64_t id = 0;
@@ -228,10 +253,18 @@ void worker(hodlrdd_server_s* s) {
     Request r;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-      if (s->stop && s->queue.empty()) break;
-      id = s->queue.front();
-      s->queue.pop_front();
+      const int max_solves = s->nworkers > 1 ? s->nworkers - 1 : 1;
+      auto ready = [&] { return !s->queue_mv.empty() || (!s->queue_sv.empty() && s->solves_running < max_solves); };
+      s->cv_work.wait(lk, [&] { return ready() || (s->stop && s->queue_mv.empty() && s->queue_sv.empty()); });
+      if (!ready()) break;  // stopping, nothing left
+      if (!s->queue_mv.empty()) {
+        id = s->queue_mv.front();
+        s->queue_mv.pop_front();
+      } else {
+        id = s->queue_sv.front();
+        s->queue_sv.pop_front();
+        s->solves_running++;
+      }
       Request& q = s->reqs[id];
       q.t_start = now_ms();
       r = q;
@@ -240,7 +273,7 @@ void worker(hodlrdd_server_s* s) {
     }
     int rc = have_stream ? ensure(s, *m, r.kind == HODLRDD_REQ_SOLVE) : HODLRDD_ERR_CUDA;
     const bool ran = rc == HODLRDD_OK;
-    if (ran) rc = run_request(*m, r, st, sg);
+    if (ran) rc = run_request(*m, r, r.kind == HODLRDD_REQ_SOLVE ? st_sv : st_mv, sg);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (ran) m->running--;
@@ -250,10 +283,13 @@ void worker(hodlrdd_server_s* s) {
       if (rc != HODLRDD_OK) q.msg = hodlrdd_last_error();
       q.done = true;
       q.t_done = now_ms();
+      if (r.kind == HODLRDD_REQ_SOLVE) s->solves_running--;
     }
     s->cv_done.notify_all();
+    s->cv_work.notify_all();  // a solve slot may have opened
   }
-  if (st) cudaStreamDestroy(st);
+  if (st_mv) cudaStreamDestroy(st_mv);
+  if (st_sv) cudaStreamDestroy(st_sv);
 }
 
 }  // namespace
@@ -270,6 +306,7 @@ extern "C" int hodlrdd_server_create(int64_t budget_bytes, int workers, hodlrdd_
   if (!s) return HODLRDD_ERR_OOM;
   HD_CUDA(cudaGetDevice(&s->device));
   s->budget = budget_bytes;
+  s->nworkers = workers;
   for (int i = 0; i < workers; ++i) s->workers.emplace_back(worker, s);
   *out = s;
   return HODLRDD_OK;
@@ -320,10 +357,10 @@ extern "C" int hodlrdd_server_submit(hodlrdd_server s, int64_t model_id, int kin
     r.y = y;
     r.nrhs = nrhs;
     r.t_submit = now_ms();
-    s->queue.push_back(id);
+    (kind == HODLRDD_REQ_SOLVE ? s->queue_sv : s->queue_mv).push_back(id);
     *request_id = id;
   }
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   return HODLRDD_OK;
 }
 
@@ -355,7 +392,7 @@ extern "C" int hodlrdd_server_stats(hodlrdd_server s, int64_t* out) {
   out[1] = res_models;
   out[2] = s->builds;
   out[3] = s->evictions;
-  out[4] = (int64_t)s->queue.size();
+  out[4] = (int64_t)(s->queue_mv.size() + s->queue_sv.size());
   return HODLRDD_OK;
 }
 

@@ -109,3 +109,21 @@ def test_rejections(env):
     assert e.value.status == hd.ERR_OOM
     tiny.close()
     srv.close()
+
+
+def test_bounded_wait_expiry_is_reported_and_recoverable(env):
+    """A bounded device wait that nothing completes (about a second) records its
+    error code; hodlrdd_sync reports ERR_TIMEOUT, clears it, and the handle's
+    next product is correct."""
+    torch, oracle, hd = env
+    w = models()[1]
+    h = gpu_handle(hd, w, precision="fp32")
+    x = np.ascontiguousarray(w.x, dtype=np.float32)
+    y0 = np.asarray(h.matvec(x))
+    h.debug_expire_wait(2_000_000_000)
+    with pytest.raises(hd.HodlrddError) as e:
+        h.sync()
+    assert e.value.status == hd.ERR_TIMEOUT
+    h.sync()  # cleared
+    assert np.array_equal(np.asarray(h.matvec(x)), y0)
+    h.close()
