@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched uneven-trees line")
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
+    p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
     return p.parse_args()
 
 
@@ -402,6 +403,44 @@ def serving_line(args, torch, hd, rates=(200.0, 50.0), seconds=3.0, n_models=6, 
     return out
 
 
+def admissibility_line(args, torch, stream, hd, N=65536):
+    """The paper's comparison of admissibility conditions on one workload:
+    strong (far-field only, H-matrix), HODLRdD (far-field and vertex-sharing),
+    weak (every sibling, HODLR). Build time, product time, stored bytes and
+    error against the GPU direct sum, per condition. In two dimensions, where
+    the weak condition's edge-sharing blocks still compress."""
+    import workloads as W
+
+    w = W.make("adm d=2 log r", 2, N, W.K_LOG, (1.0, 0.0, 0.0, 0.0), 64, 1e-8, nrhs=1, seed=args.seed)
+    pts = torch.from_numpy(w.points).cuda()
+    x = torch.from_numpy(np.ascontiguousarray(w.x[:, 0], dtype=np.float32)).cuda()
+    # uniform FP32 factors: this tree's finest low-rank level has 16-point boxes, whose one-stage panels
+    # the mixed storage would apply in two passes
+    prec = "fp32"
+    out = {"workload": f"d=2 N={N} uniform [-1,1]^2, F=log r, leaf {w.leaf}, tol {w.tol:g}, one right-hand side; "
+                       "error against the GPU direct O(N^2) sum (FP32, compensated)",
+           "precision": prec}
+    yd = None
+    for name, amax in (("strong_H", -1), ("hodlrdd", 0), ("weak_HODLR", 1)):
+        t0 = time.perf_counter()
+        h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, admissible_face_dim=amax)
+        t_build = time.perf_counter() - t0
+        if yd is None:
+            yd = torch.empty_like(x)
+            h.direct(x, yd)
+        y = torch.empty_like(x)
+        n = 10
+        t = time_steps(lambda: h.matvec(x, y), n, 3, torch, stream)
+        err = float((torch.linalg.norm(y.double() - yd.double()) / torch.linalg.norm(yd.double())).item())
+        s = h.stats()
+        out[name] = {"admissible_face_dim": amax, "build_s": t_build, "ms_per_step": 1e3 * t / n,
+                     "factor_gb": (s["factor_bytes_u"] + s["factor_bytes_v"]) / 1e9, "n_lowrank": s["n_lowrank"],
+                     "n_dense": s["n_dense"], "n_rank_capped": s["n_rank_capped"], "max_rank": s["max_rank"],
+                     "dense_pairs": s["dense_pairs"], "rel_err_vs_direct": err}
+        h.close()
+    return out
+
+
 def solve_line(args, torch, hd, N=65536):
     """(I + K/N) u = b on N points of the benchmark distribution, to a relative
     FP64 residual of 1e-10: GMRES on the headline-precision operator inside FP64
@@ -639,6 +678,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
         many = many_rhs_line(args, torch, stream, hd)
 
+    # the paper's admissibility comparison (H-matrix / HODLRdD / HODLR)
+    adm = None
+    if rank == 0 and world == 1 and not args.no_admissibility and args.precision != "fp64":
+        adm = admissibility_line(args, torch, stream, hd)
+
     # the memory-efficient skeleton form of the low-rank blocks
     skel = None
     if rank == 0 and world == 1 and not args.no_skeleton and args.precision in ("fp32", "fp32+fp16") and nrhs == 1:
@@ -681,6 +725,7 @@ def main():
             "direct_gpu": direct,
             "many_rhs": many,
             "skeleton": skel,
+            "admissibility": adm,
             "solve": solve,
             "batch": batch,
             "serving_loop": serve,
