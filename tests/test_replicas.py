@@ -83,3 +83,32 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert line["impl"] == "reference"
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+
+
+def test_secondary_bench_lines_record_their_failure():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def boom():
+        raise RuntimeError("no device")
+
+    assert bench.optional_line(boom) == {"error": "RuntimeError: no device"}
+    assert bench.optional_line(lambda a, b: a + b, 2, 3) == 5
+
+
+def test_traffic_is_scaled_only_for_the_captured_source_and_storage():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cap = bench.TRAFFIC_CAPTURE
+    saved = cap["apply_sha256"]
+    try:
+        cap["apply_sha256"] = bench.apply_source_sha256()
+        r = cap["ratio"]["fp32+fp16"]["vapply"]
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1) == r * 1e9
+        assert bench.scaled_traffic("vapply", 1e9, "bf16", 1) is None      # no capture for that storage
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 4) is None  # nor for other chunk widths
+        cap["apply_sha256"] = "0" * 64  # the apply source changed since the capture
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1) is None
+    finally:
+        cap["apply_sha256"] = saved
