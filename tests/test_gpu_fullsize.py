@@ -43,7 +43,8 @@ def pick(y, ranges):
 
 
 def test_benchmark_workload_d3_n262144(env):
-    """d=3, N=262144 uniform [-1,1]^3, 1/r, leaf 64, tol 1e-7, one right-hand side."""
+    """d=3, N=262144 uniform [-1,1]^3, 1/r, leaf 64, tol 1e-7, one right-hand side: FP64, FP32,
+    the mixed FP32 / FP16 storage (the benchmark's) and the FP32 skeleton form."""
     torch, oracle, hd = env
     w = W.precision_3d()
     pts = torch.from_numpy(w.points).cuda()
@@ -70,6 +71,16 @@ def test_benchmark_workload_d3_n262144(env):
     yh = h32.matvec(np.ascontiguousarray(w.x, dtype=np.float32))
     assert np.array_equal(np.asarray(yh), y32n)
     h32.close()
+    # the storage bench.py times by default: leading terms FP32, trailing terms FP16
+    hm = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp32+fp16")
+    m1 = hm.matvec(x32)
+    m2 = hm.matvec(x32)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2)
+    ymn = m1.cpu().numpy()
+    assert relerr(ymn, y64n) <= 1e-6
+    assert relerr(pick(ymn, ranges), yd) <= 10 * w.tol + FP32_BOUND
+    hm.close()
     # the skeleton form on the same workload
     hs = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp32", lowrank_form="skeleton")
     ys = hs.matvec(x32)
