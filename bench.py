@@ -201,6 +201,36 @@ def scaled_traffic(kernel, algo_bytes, precision, nrhs):
     return r[kernel] * algo_bytes
 
 
+# Algorithmic arithmetic of one kernel evaluation with its accumulation, for
+# F = 1/r in d dimensions: d subtractions and d multiply-adds form |x_i - x_j|^2,
+# one rsqrt evaluates F (a MUFU operation in FP32), and one FMA per right-hand
+# side adds F x_j. FP32 pipe operations per pair: 2d + nrhs; MUFU: 1. As FP64
+# flops (for the FP64 form): d + 2d - 1 for the distance, 1 for F, 2 nrhs.
+def near_roofline(s, d, nrhs, seconds, peaks):
+    pairs = int(s["dense_pairs"])
+    if seconds <= 0 or pairs == 0:
+        return None
+    ops = 2 * d + nrhs
+    fp32_ops_peak = peaks["fp32_tflops"] * 1e12 / 2  # FMA lane-operations per second
+    mufu_peak = peaks["mufu_rsqrt_gops"] * 1e9
+    achieved = pairs * ops / seconds
+    return {"kernel": "near field (k_tile, second stream)", "bound": "alu", "unit": "G FP32 ops/s",
+            "pairs": pairs, "ops_per_pair": ops, "achieved": achieved / 1e9, "peak": fp32_ops_peak / 1e9,
+            "frac": achieved / fp32_ops_peak, "mufu_frac": pairs / seconds / mufu_peak,
+            "stage_ms": 1e3 * seconds, "peak_source": "measured (hodlrdd_probe_peaks)", "traffic": None}
+
+
+def fp64_roofline(s, d, nrhs, seconds, peaks):
+    """The FP64 form against the measured FP64 FMA rate: every factor element in
+    one FMA per right-hand side, every near-field pair as counted above."""
+    flops = 2.0 * int(s["factor_elems"]) * nrhs + int(s["dense_pairs"]) * (3 * d + 2 * nrhs)
+    achieved = flops / seconds
+    peak = peaks["fp64_tflops"] * 1e12
+    return {"kernel": "whole FP64 matvec", "bound": "fp64", "unit": "TFLOP/s", "flops": flops,
+            "achieved": achieved / 1e12, "peak": peak / 1e12, "frac": achieved / peak,
+            "peak_source": "measured (hodlrdd_probe_peaks)", "traffic": None}
+
+
 def factor_bytes(h, precision):
     """Algorithmic bytes of the packed U and V streams (incl. alignment pads) and scales."""
     s = h.stats()
@@ -255,7 +285,7 @@ def cpu_baseline(args, rank_w):
     t_dir = (time.perf_counter() - t0) * ws.N / nrow
     extra = {"single_core_value": ws.N * ws.nrhs / t1, "direct_value": ws.N * ws.nrhs / t_dir,
              "machine": f"{os.uname().machine}, {cores} threads"}
-    return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle", **extra,
+    return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle", "sample_n": ws.N, **extra,
             "sample": f"oracle FP64 HODLRdD on a {ws.N}-point draw of the same distribution (d={ws.d}, 1/r, "
                       f"leaf {ws.leaf}, tol {ws.tol:g}); matvec median of {len(times)} runs; build {t_build:.1f} s; "
                       f"single_core_value: one matvec on one thread; direct_value: the oracle's direct sum on "
@@ -539,7 +569,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_name(w), "sample_n": ws.N},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "sample_n": ws.N},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -606,6 +637,9 @@ def main():
     h.sync()  # raises if a bounded device-side wait expired during the timed steps
     launches = prof["launches"] - launches0
     total_units, max_seconds = aggregate(units * args.steps, seconds, dist, device="cuda")
+    # measured FP32 / FP64 / MUFU throughput of this GPU at its current clocks:
+    # the denominators of the near-field and FP64 rooflines
+    peaks = hd.probe_peaks(stream)
     value = total_units / max_seconds
     ms_per_step = 1e3 * max_seconds / args.steps
 
@@ -627,8 +661,10 @@ def main():
         num = torch.linalg.norm((y.to(torch.float64) - y64), dim=0)
         den = torch.linalg.norm(y64, dim=0)
         err = float((num / den).max().item())
-        fp64 = {"value": units * n64 / t64, "ms_per_step": 1e3 * t64 / n64, "build_ms": h64.stats()["t_build_ms"],
-                "device_gb": h64.stats()["device_bytes"] / 1e9}
+        s64 = h64.stats()
+        fp64 = {"value": units * n64 / t64, "ms_per_step": 1e3 * t64 / n64, "build_ms": s64["t_build_ms"],
+                "device_gb": s64["device_bytes"] / 1e9,
+                "roofline": fp64_roofline(s64, w.d, nrhs, t64 / n64, peaks)}
         if h64 is not h:
             h64.close()
 
@@ -681,6 +717,9 @@ def main():
             "algorithmic_bytes_per_kernel": algo,
             "stage_ms": {k: round(v, 4) for k, v in stage.items()},
             "stage_share": {k: round(v / sum(stage.values()), 4) for k, v in stage.items()}}
+
+    roof["near"] = near_roofline(s, w.d, nrhs, stage["near"] / 1e3, peaks)
+    roof["fp64"] = fp64["roofline"] if fp64 else None
 
     # many right-hand sides (d=4, N=65536, Matern-3/2, leaf 128, tol 1e-8, nrhs 64)
     many = None
@@ -746,6 +785,7 @@ def main():
                               [round(v, 1) for v in s["mean_rank_per_level"]]},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "peaks_probe": peaks,
             "e2e": {"value": e2e_units / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             "serving": serving,

@@ -202,9 +202,11 @@ int hodlrdd_build_ex(const double* points, int d, int64_t N, int kernel_id, cons
  *
  * With device x and y the call is asynchronous on `stream`: it only enqueues
  * kernels and allocates nothing. With host x or y it stages through buffers the
- * handle owns and returns after y is written (synchronous). A handle's workspace
- * is shared: concurrent matvecs on one handle from different streams must be
- * serialised by the caller.
+ * handle owns and returns after y is written (synchronous), also when it fails.
+ * A handle's workspace is shared: concurrent matvecs on one handle from
+ * different streams must be serialised by the caller. The device current when
+ * the call is made must be the one the handle was built on (else
+ * HODLRDD_ERR_INVALID).
  */
 int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
 
@@ -229,7 +231,9 @@ int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* str
  * otherwise). Arguments, layout and synchronisation as hodlrdd_matvec. All calls
  * on one device share the one scratch: two calls in flight at the same time on
  * the same device (from several threads, or one thread's asynchronous work on
- * other streams) race on it and must be serialised by the caller.
+ * other streams) race on it and must be serialised by the caller. As for
+ * hodlrdd_matvec, the current device must be the handle's, and a call with a
+ * host buffer returns only after its copies have finished, also when it fails.
  */
 int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, int nrhs, void* stream);
 
@@ -272,7 +276,9 @@ int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream);
  * needs more) and kept in that handle until it is destroyed, so repeated solves
  * allocate nothing; one solve at a time per inner handle.
  * HODLRDD_ERR_NUMERIC when tol is not reached within max_refine steps (x holds
- * the last iterate).
+ * the last iterate). HODLRDD_ERR_TIMEOUT when a bounded device-side wait of a
+ * product on either handle expired since that handle's error word was last
+ * read (x is then invalid); the solve reads and clears both words.
  */
 typedef struct hodlrdd_solve_options {
   double tol;           /* relative residual of the FP64 operator (default 1e-10) */
@@ -415,6 +421,23 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
  * word; the handle stays usable. Synchronous.
  */
 int hodlrdd_debug_expire_wait(hodlrdd_handle h, long long cycles);
+
+/*
+ * Measurement aid (the paper has no counterpart): throughput of the arithmetic
+ * pipes the on-the-fly kernel evaluation and the FP64 form are bound by, on the
+ * current device, each timed with CUDA events on `stream` (best of three
+ * launches that fill every SM with independent dependency chains). Changes no
+ * device setting: the numbers are those of the clocks the GPU runs at.
+ *
+ *  out[0]  FP32 FMA throughput, TFLOP/s (2 flops per FMA)
+ *  out[1]  FP64 FMA throughput, TFLOP/s
+ *  out[2]  MUFU rsqrt.approx.f32, G operations/s
+ *  out[3]  MUFU ex2.approx.f32, G operations/s
+ *  out[4]  SM clock during the FP32 probe, MHz (cycles of one CTA over the
+ *          launch time: a lower bound)
+ *  n       entries of out to fill (<= 5 used). Synchronous; allocates 24 bytes.
+ */
+int hodlrdd_probe_peaks(double* out, int n, void* stream);
 
 /*
  * Serving: a request loop over models kept resident under a device-memory

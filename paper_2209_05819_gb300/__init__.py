@@ -9,6 +9,7 @@ CUDA library, there is no CPU fallback):
     solve(inner, outer, b)                                      GMRES with FP64 refinement
     Batch(handles, nrhs).run(xs)                                graph-replayed batch of products
     Server(budget).add / submit / wait                          request loop under an HBM budget
+    probe_peaks()                                               measured FP32 / FP64 / MUFU throughput
 """
 from ._binding import (  # noqa: F401
     Batch,
@@ -27,6 +28,7 @@ from ._binding import (  # noqa: F401
     HodlrddError,
     header_functions,
     load,
+    probe_peaks,
     solve,
 )
 

@@ -103,6 +103,7 @@ def load():
         "hodlrdd_sync": (i32, [vp]),
         "hodlrdd_get_profile": (i32, [vp, vp, C.POINTER(i64), C.POINTER(i64)]),
         "hodlrdd_debug_expire_wait": (i32, [vp, C.c_longlong]),
+        "hodlrdd_probe_peaks": (i32, [vp, i32, vp]),
         "hodlrdd_server_create": (i32, [i64, i32, C.POINTER(vp)]),
         "hodlrdd_server_add": (i32, [vp, vp, i32, i64, i32, vp, i32, dbl, C.POINTER(Options), C.POINTER(i64)]),
         "hodlrdd_server_submit": (i32, [vp, i64, i32, vp, vp, i32, C.POINTER(i64)]),
@@ -145,6 +146,41 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)!r}")
 
 
+def _check_io(a, name, N, io_dtype, device, like=None):
+    """Reject an x or y the C library would read or write out of bounds: the
+    leading dimension must be N, the element type the handle's (float64 for
+    FP64 handles, float32 otherwise), a CUDA tensor must sit on the handle's
+    device, and y must have x's shape. Raises ValueError before any C call."""
+    shape = tuple(int(v) for v in a.shape)
+    if len(shape) not in (1, 2) or shape[0] != N or (len(shape) == 2 and shape[1] < 1):
+        raise ValueError(f"{name}: shape {shape}, expected ({N},) or ({N}, nrhs)")
+    if like is not None and shape != tuple(int(v) for v in like.shape):
+        raise ValueError(f"{name}: shape {shape} differs from x's {tuple(int(v) for v in like.shape)}")
+    want = np.dtype(io_dtype)
+    if isinstance(a, np.ndarray):
+        got = a.dtype
+    else:
+        try:
+            got = np.dtype(str(a.dtype).replace("torch.", ""))
+        except TypeError:  # a type numpy does not know (bfloat16, ...)
+            got = str(a.dtype)
+        if getattr(a, "is_cuda", False) and device is not None and a.device.index != device:
+            raise ValueError(f"{name}: on cuda:{a.device.index}, the handle lives on cuda:{device}")
+    if got != want:
+        raise ValueError(f"{name}: element type {got}, the handle computes in {want}")
+
+
+def _current_device():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_device()
+    except ImportError:
+        pass
+    return None
+
+
 def _stream_ptr(stream):
     if stream is None:
         try:
@@ -176,6 +212,7 @@ class Handle:
         if points.ndim != 2:
             raise ValueError("points must be N x d")
         self.N, self.d = int(points.shape[0]), int(points.shape[1])
+        self.device = _current_device()  # the library builds on the current device
         self.precision = precision
         self.io_dtype = np.float64 if precision == "fp64" else np.float32
         opt = Options()
@@ -215,8 +252,14 @@ class Handle:
             pass
 
     # -- the product ---------------------------------------------------------------
+    def _io(self, x, y):
+        _check_io(x, "x", self.N, self.io_dtype, self.device)
+        if y is not None:
+            _check_io(y, "y", self.N, self.io_dtype, self.device, like=x)
+
     def matvec(self, x, y=None, stream=None):
         """y = K x. x: (N,) or (N, nrhs), numpy (host) or torch (host / CUDA)."""
+        self._io(x, y)
         nrhs = 1 if x.ndim == 1 else int(x.shape[1])
         if y is None:
             if isinstance(x, np.ndarray):
@@ -231,6 +274,11 @@ class Handle:
 
     def direct(self, x, y=None, stream=None):
         """y = K x by direct O(N^2) summation on the GPU (FP32; x a CUDA tensor, one column)."""
+        _check_io(x, "x", self.N, np.float32, self.device)
+        if x.ndim != 1 and int(x.shape[1]) != 1:
+            raise ValueError("x: the direct sum takes one right-hand side")
+        if y is not None:
+            _check_io(y, "y", self.N, np.float32, self.device, like=x)
         if y is None:
             y = x.new_empty(x.shape)
         xa, kx = _ptr(x)
@@ -241,6 +289,7 @@ class Handle:
     def matvec_noalloc(self, x, y=None, stream=None):
         """y = K x through hodlrdd_matvec_noalloc: host buffers are staged in the
         library's fixed static device scratch, never in newly allocated memory."""
+        self._io(x, y)
         nrhs = 1 if x.ndim == 1 else int(x.shape[1])
         if y is None:
             if isinstance(x, np.ndarray):
@@ -366,6 +415,14 @@ def solve(inner: "Handle", outer: "Handle", b, x=None, tol: float = 1e-10, inner
     lib.hodlrdd_solve_options_default(C.byref(o))
     o.tol, o.inner_tol, o.restart = float(tol), float(inner_tol), int(restart)
     o.max_inner_iters, o.max_refine = int(max_inner_iters), int(max_refine)
+    for name, a in (("b", b), ("x", x)):
+        if a is None:
+            continue
+        if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False):
+            raise ValueError(f"{name}: the solve takes CUDA tensors")
+        _check_io(a, name, outer.N, np.float64, outer.device, like=b if name == "x" else None)
+        if a.ndim != 1 and int(a.shape[1]) != 1:
+            raise ValueError(f"{name}: one right-hand side per solve")
     if x is None:
         x = b.new_empty(b.shape)
     st = SolveStats()
@@ -394,6 +451,14 @@ class Batch:
     def run(self, xs, ys=None, stream=None):
         """y_i = K_i x_i for every request; xs / ys: numpy or torch arrays."""
         n = len(self._handles)
+        if len(xs) != n or (ys is not None and len(ys) != n):
+            raise ValueError(f"one x (and y) per request: {n}")
+        for i, (x, h) in enumerate(zip(xs, self._handles)):
+            _check_io(x, f"xs[{i}]", h.N, h.io_dtype, h.device)
+            if x.ndim == 2 and int(x.shape[1]) != self.nrhs[i] or x.ndim == 1 and self.nrhs[i] != 1:
+                raise ValueError(f"xs[{i}]: {self.nrhs[i]} right-hand sides expected")
+            if ys is not None:
+                _check_io(ys[i], f"ys[{i}]", h.N, h.io_dtype, h.device, like=x)
         if ys is None:
             ys = [np.empty(x.shape, dtype=h.io_dtype) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
                   for x, h in zip(xs, self._handles)]
@@ -453,10 +518,17 @@ class Server:
 
     def submit(self, model: int, x, kind: int = REQ_MATVEC, y=None) -> int:
         """Queue y = K x (kind REQ_MATVEC) or K u = b (REQ_SOLVE, FP64 host arrays)."""
-        N, io = self._models[model] if 0 <= model < len(self._models) else (0, np.float32)
+        if not 0 <= model < len(self._models):
+            raise HodlrddError(ERR_INVALID, "hodlrdd_server_submit", "unknown model")
+        N, io = self._models[model]
         if kind == REQ_SOLVE:
+            if not isinstance(x, np.ndarray) or (y is not None and not isinstance(y, np.ndarray)):
+                raise ValueError("a solve request takes host (numpy) arrays")
             x = np.ascontiguousarray(x, dtype=np.float64)
             io = np.float64
+        _check_io(x, "x", N, io, _current_device())
+        if y is not None:
+            _check_io(y, "y", N, io, _current_device(), like=x)
         if y is None:
             y = np.empty(x.shape, dtype=io) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
         nrhs = 1 if x.ndim == 1 else int(x.shape[1])
@@ -494,6 +566,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def probe_peaks(stream=None) -> dict:
+    """Measured arithmetic throughput of the current device (hodlrdd_probe_peaks)."""
+    out = np.zeros(5, np.float64)
+    _check(load().hodlrdd_probe_peaks(out.ctypes.data, 5, _stream_ptr(stream)), "hodlrdd_probe_peaks")
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "mufu_rsqrt_gops": float(out[2]),
+            "mufu_ex2_gops": float(out[3]), "sm_mhz": float(out[4])}
 
 
 def debug_fail_alloc_after(k: int):

@@ -31,6 +31,7 @@ SOURCES = {
     "skeleton.cu": [],
     "server.cu": [],
     "debug.cu": [],
+    "probe.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

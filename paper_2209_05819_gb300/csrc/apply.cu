@@ -1714,15 +1714,15 @@ int set_smem_attr_nr() {
 
 template <class T>
 int set_smem_attr() {
-  static bool done = false;
-  if (done) return HODLRDD_OK;
-  HD_TRY((set_smem_attr_nr<T, 1>()));
-  HD_TRY((set_smem_attr_nr<T, 2>()));
-  HD_TRY((set_smem_attr_nr<T, 4>()));
-  HD_TRY((set_smem_attr_nr<T, 8>()));
-  if constexpr (std::is_same<T, float>::value) HD_TRY((set_smem_attr_nr<T, 16>()));
-  done = true;
-  return HODLRDD_OK;
+  static PerDeviceOnce once;
+  return once.run([] {
+    HD_TRY((set_smem_attr_nr<T, 1>()));
+    HD_TRY((set_smem_attr_nr<T, 2>()));
+    HD_TRY((set_smem_attr_nr<T, 4>()));
+    HD_TRY((set_smem_attr_nr<T, 8>()));
+    if constexpr (std::is_same<T, float>::value) HD_TRY((set_smem_attr_nr<T, 16>()));
+    return (int)HODLRDD_OK;
+  });
 }
 
 template <class T, class IO>
@@ -1809,6 +1809,19 @@ int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V) {
     case HODLRDD_PREC_FP16: return unpack_typed<__half>(h, b, U, V);
     default: return unpack_typed<__nv_bfloat16>(h, b, U, V);
   }
+}
+
+// The error word read and cleared on one stream, after the work on it: a
+// caller that waits for its own stream only (not the whole device).
+int take_error_word(hodlrdd_s* h, cudaStream_t st, int32_t* code) {
+  *code = 0;
+  if (!h->err.p) return HODLRDD_OK;
+  HD_CUDA(cudaMemcpyAsync(code, h->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  HD_CUDA(cudaStreamSynchronize(st));
+  if (*code == 0) return HODLRDD_OK;
+  HD_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), st));
+  HD_CUDA(cudaStreamSynchronize(st));
+  return HODLRDD_OK;
 }
 
 int read_error_word(hodlrdd_s* h, int32_t* code) {

@@ -246,6 +246,22 @@ void destroy(hodlrdd_s* h) {
 }
 
 }  // namespace
+
+// The handle's kernels, workspace and streams live on the device it was built
+// on; a call made while another device is current is rejected.
+int check_device(const hodlrdd_s* h, const char* who) {
+  int dev = 0;
+  HD_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "%s: the current device (%d) is not the handle's device (%d)", who, dev,
+                  h->device);
+    set_error(buf);
+    return HODLRDD_ERR_INVALID;
+  }
+  return HODLRDD_OK;
+}
+
 }  // namespace hd
 
 using namespace hd;
@@ -316,6 +332,7 @@ int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* str
     set_error("hodlrdd_matvec: x and y overlap");
     return HODLRDD_ERR_INVALID;
   }
+  HD_TRY(check_device(h, "hodlrdd_matvec"));
   const bool xdev = pointer_kind(x) == 1, ydev = pointer_kind(y) == 1;
   if (xdev && ydev) return launch_matvec(h, x, y, nrhs, st);
   // host buffers: stage through handle-owned device memory, then wait
@@ -328,10 +345,15 @@ int hodlrdd_matvec(hodlrdd_handle h, const void* x, void* y, int nrhs, void* str
     dx = h->xstage.p;
   }
   if (!ydev) dy = h->ystage.p;
-  HD_TRY(launch_matvec(h, dx, dy, nrhs, st));
-  if (!ydev) HD_CUDA(cudaMemcpyAsync(y, h->ystage.p, bytes, cudaMemcpyDeviceToHost, st));
-  HD_CUDA(cudaStreamSynchronize(st));
-  return HODLRDD_OK;
+  int rc = launch_matvec(h, dx, dy, nrhs, st);
+  if (rc == HODLRDD_OK && !ydev) {
+    const cudaError_t e = cudaMemcpyAsync(y, h->ystage.p, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(y)", __FILE__, __LINE__);
+  }
+  // also on failure: the copy from the caller's host x may still be in flight
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == HODLRDD_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  return rc;
 }
 
 int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream) {
@@ -350,6 +372,7 @@ int hodlrdd_direct(hodlrdd_handle h, const void* x, void* y, void* stream) {
     set_error("hodlrdd_direct: x and y must be device memory");
     return HODLRDD_ERR_INVALID;
   }
+  HD_TRY(check_device(h, "hodlrdd_direct"));
   return launch_direct(h, static_cast<const float*>(x), static_cast<float*>(y), static_cast<cudaStream_t>(stream));
 }
 

@@ -10,6 +10,7 @@
 #include <string>
 #include <utility>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "../../include/hodlrdd.h"
@@ -31,6 +32,25 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
     int s_ = (call);                 \
     if (s_ != HODLRDD_OK) return s_; \
   } while (0)
+
+// One-time set-up per device (function attributes such as the dynamic
+// shared-memory limit apply to the device current when they are set): run(f)
+// calls f once for each device ordinal it is called on, the current one, and
+// remembers success.
+struct PerDeviceOnce {
+  std::mutex mu;
+  uint64_t done = 0;  // bit per device ordinal
+  template <class F>
+  int run(F&& f) {
+    int dev = 0;
+    HD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && (done >> dev & 1u)) return HODLRDD_OK;
+    const int s = f();
+    if (s == HODLRDD_OK && dev >= 0 && dev < 64) done |= uint64_t(1) << dev;
+    return s;
+  }
+};
 
 // Test hook: make the k-th device allocation from now fail (k < 0: never).
 void debug_fail_alloc_after(int64_t k);
@@ -442,5 +462,7 @@ int build_skeleton_plan(hodlrdd_s* h);
 int launch_skeleton_rows(hodlrdd_s* h, cudaStream_t st, const void* xt, void* t);
 int launch_skeleton_cols(hodlrdd_s* h, cudaStream_t st, const void* t, void* ylev);
 int read_error_word(hodlrdd_s* h, int32_t* code);
+int take_error_word(hodlrdd_s* h, cudaStream_t st, int32_t* code);
+int check_device(const hodlrdd_s* h, const char* who);
 size_t elem_size(int precision);
 }  // namespace hd

@@ -403,12 +403,12 @@ void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt) {
 namespace {
 template <int D, int NR, int KID>
 int launch_tiles_nr_dnk(hodlrdd_s* h, cudaStream_t st, const float* xt) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  HD_TRY(attr.run([] {
     HD_CUDA(cudaFuncSetAttribute(k_tile_nr<D, NR, KID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_nr_smem<NR>()));
-    attr = true;
-  }
+    return (int)HODLRDD_OK;
+  }));
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
   const float ks = (float)h->K.scale, kd = (float)h->K.diag;

@@ -95,11 +95,12 @@ extern "C" int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, 
     set_error(buf);
     return HODLRDD_ERR_INVALID;
   }
+  // the handle's kernels and workspace, and the scratch the staging uses, are
+  // those of the device the handle was built on
+  HD_TRY(check_device(h, "hodlrdd_matvec_noalloc"));
   if (xdev && ydev) return launch_matvec(h, x, y, nrhs, st);
-  int dev = 0;
-  HD_CUDA(cudaGetDevice(&dev));
   char* scratch = nullptr;
-  HD_TRY(scratch_on(dev, &scratch));
+  HD_TRY(scratch_on(h->device, &scratch));
   const void* dx = x;
   void* dy = y;
   if (!xdev) {
@@ -107,8 +108,14 @@ extern "C" int hodlrdd_matvec_noalloc(hodlrdd_handle h, const void* x, void* y, 
     dx = scratch;
   }
   if (!ydev) dy = scratch + (xdev ? 0 : round_up(bytes, kScratchAlign));
-  HD_TRY(launch_matvec(h, dx, dy, nrhs, st));
-  if (!ydev) HD_CUDA(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, st));
-  HD_CUDA(cudaStreamSynchronize(st));
-  return HODLRDD_OK;
+  int rc = launch_matvec(h, dx, dy, nrhs, st);
+  if (rc == HODLRDD_OK && !ydev) {
+    const cudaError_t e = cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(y)", __FILE__, __LINE__);
+  }
+  // also when a launch failed: the copy from the caller's host x may still be
+  // in flight, and the caller may free x as soon as this call returns
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == HODLRDD_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  return rc;
 }

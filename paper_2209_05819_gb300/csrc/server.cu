@@ -146,12 +146,20 @@ int ensure(hodlrdd_server_s* s, Model& m, bool twin) {
       s->resident -= want - saved;
     }
   }
+  // each new handle is counted as soon as it exists, so that a failed build of
+  // the twin leaves the model's first handle resident and accounted
+  auto account_locked = [&] {
+    const int64_t b = handle_bytes(m.h) + handle_bytes(m.h64);
+    s->resident += b - m.bytes;
+    m.bytes = m.last_bytes = b;
+  };
   if (need_h) {
     hodlrdd_s* h = nullptr;
     HD_TRY(hodlrdd_build_ex(m.points.data(), m.d, m.N, m.kid, m.prm, m.leaf, m.tol, &m.opt, &h));
     std::lock_guard<std::mutex> lk(s->mu);
     m.h = h;
     s->builds++;
+    account_locked();
   }
   if (need_64) {
     hodlrdd_options o64 = m.opt;
@@ -162,23 +170,23 @@ int ensure(hodlrdd_server_s* s, Model& m, bool twin) {
     std::lock_guard<std::mutex> lk(s->mu);
     m.h64 = h;
     s->builds++;
+    account_locked();
   }
   std::unique_lock<std::mutex> lk(s->mu);
-  const int64_t b = handle_bytes(m.h) + handle_bytes(m.h64);
-  s->resident += b - m.bytes;
-  m.bytes = m.last_bytes = b;
   for (;;) {
     evict_locked(s, &m);
     if (s->resident <= s->budget) {
       m.running++;
       return HODLRDD_OK;
     }
-    bool others = false;
-    for (auto& o : s->models) others |= o.get() != &m && o->running > 0;
-    if (!others) break;
-    s->cv_done.wait(lk);  // a running request finishes without builds: its model becomes evictable
+    // wait while any request runs, on another model (it becomes evictable when
+    // done) or on this one (its handles cannot be destroyed under its kernels)
+    bool busy = false;
+    for (auto& o : s->models) busy |= o->running > 0;
+    if (!busy) break;
+    s->cv_done.wait(lk);
   }
-  // the model alone does not fit: do not keep it
+  // the model alone does not fit, and nothing runs on it: do not keep it
   if (m.h) hodlrdd_destroy(m.h);
   if (m.h64) hodlrdd_destroy(m.h64);
   m.h = m.h64 = nullptr;
@@ -202,13 +210,9 @@ struct Staging {
 // synchronised), read and cleared on st: hodlrdd_sync would synchronise the
 // whole device, i.e. wait for every other worker's requests.
 int check_waits(hodlrdd_s* h, cudaStream_t st) {
-  if (!h->err.p) return HODLRDD_OK;
   int32_t code = 0;
-  HD_CUDA(cudaMemcpyAsync(&code, h->err.p, sizeof code, cudaMemcpyDeviceToHost, st));
-  HD_CUDA(cudaStreamSynchronize(st));
+  HD_TRY(take_error_word(h, st, &code));
   if (code == 0) return HODLRDD_OK;
-  HD_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof code, st));
-  HD_CUDA(cudaStreamSynchronize(st));
   set_error("a bounded device-side wait expired; the product is invalid");
   return HODLRDD_ERR_TIMEOUT;
 }

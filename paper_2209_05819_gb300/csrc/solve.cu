@@ -260,6 +260,15 @@ int solve_typed(hodlrdd_s* inner, hodlrdd_s* outer, const double* b, double* x, 
     stats->residual = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   }
   HD_CUDA(cudaStreamSynchronize(st));
+  // a bounded wait that expired in any product of this solve makes its
+  // residuals and iterate invalid: report that before the convergence test
+  int32_t code_in = 0, code_out = 0;
+  HD_TRY(take_error_word(inner, st, &code_in));
+  if (outer != inner) HD_TRY(take_error_word(outer, st, &code_out));
+  if (code_in != 0 || code_out != 0) {
+    set_error("hodlrdd_solve: a bounded device-side wait expired in a product; x is invalid");
+    return HODLRDD_ERR_TIMEOUT;
+  }
   if (bnorm > 0.0 && rnorm > o.tol * bnorm) {
     set_error("hodlrdd_solve: tolerance not reached within max_refine refinement steps");
     return HODLRDD_ERR_NUMERIC;
@@ -319,6 +328,8 @@ extern "C" int hodlrdd_solve(hodlrdd_handle inner, hodlrdd_handle outer, const d
     set_error("hodlrdd_solve: b and x must be device memory");
     return HODLRDD_ERR_INVALID;
   }
+  HD_TRY(check_device(inner, "hodlrdd_solve"));
+  HD_TRY(check_device(outer, "hodlrdd_solve"));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (inner->opt.precision == HODLRDD_PREC_FP64) return solve_typed<double>(inner, outer, b, x, o, stats, st);
   return solve_typed<float>(inner, outer, b, x, o, stats, st);

@@ -48,3 +48,84 @@ def oracle_factors(T):
     U_all = np.concatenate(Us) if Us else np.zeros(1)
     V_all = np.concatenate(Vs) if Vs else np.zeros(1)
     return ranks, dense, U_all, V_all
+
+
+# kernels whose FP64 entries use only correctly rounded operations (sqrt,
+# division), so the GPU ACA reproduces the oracle's pivots on every block;
+# log, exp and sin come from different libraries on the two sides and can
+# flip a near-tie pivot in about one block in a hundred
+EXACT_KERNELS = (1, 5, 6, 8)  # 1/r, -1/(4 pi^2 r^2), r, 1/sqrt(1 + r)
+
+
+def pivot_mismatches(T, h):
+    """Blocks whose rank, dense flag or ACA pivots differ between the oracle
+    tree T and the GPU handle h (same block structure asserted)."""
+    bo, bg = T.blocks(), h.blocks()
+    assert np.array_equal(bo[:, :7], bg[:, :7])
+    out = []
+    for b in range(len(bo)):
+        ro, rg = int(bo[b, 7]), int(bg[b, 7])
+        if ro != rg or bo[b, 8] != bg[b, 8]:
+            out.append(b)
+            continue
+        if ro == 0:
+            continue
+        so, to, _, _ = T.factors(b)
+        sg, tg = h.pivots(b, rg)
+        if not (np.array_equal(so, sg) and np.array_equal(to, tg)):
+            out.append(b)
+    return out
+
+
+def assert_matches_oracle_hodlrdd(oracle, T, h, w, yg, tol, kernel, skeleton=False, base=1e-10, aca_factor=10.0):
+    """The GPU FP64 product yg against the oracle's HODLRdD product, with no
+    branch that skips the comparison.
+
+    Blocks where the GPU's ACA took the oracle's pivots give the same factors
+    (to rounding), so with every pivot agreeing the products agree to `base`.
+    Where a pivot differs (ulp-level differences between CUDA's and the host's
+    log / exp / sin flipping a near-tie), both factorisations still approximate
+    the exact block A_b = K(I, J), so the products may differ by at most
+        sum_b ||(A_b - O_b) x(J)|| + aca_factor tol ||A_b||_F ||x(J)||,
+    the oracle's own error on that block (computed) plus the GPU's, whose size
+    is asserted per block against the exact entries. Asserted: the fraction of
+    agreeing blocks (all of them for kernels in EXACT_KERNELS, >= 99% else),
+    the GPU's per-block error on the others, and the product bound per column."""
+    mism = pivot_mismatches(T, h)
+    nb = max(len(T.blocks()), 1)
+    frac = 1.0 - len(mism) / nb
+    if kernel in EXACT_KERNELS:
+        assert frac == 1.0, mism[:10]
+    else:
+        assert frac >= 0.99, frac
+    bo = T.blocks()
+    perm = T.perm()[0]
+    P = w.points[perm]
+    xt = np.asarray(w.x, np.float64).reshape(w.N, -1)[perm]
+    yo = T.matvec(w.x)
+    slack = np.zeros(xt.shape[1])
+    for b in mism:
+        I0, m, J0, n = (int(v) for v in bo[b, 3:7])
+        A = oracle.kernel_block(P[I0:I0 + m], P[J0:J0 + n], w.kernel, w.params)
+        xs = xt[J0:J0 + n]
+        An = np.linalg.norm(A)
+        ro = int(bo[b, 7])
+        if bo[b, 8] or ro == 0:
+            eo = np.zeros(xs.shape[1])
+        else:
+            _, _, Uo, Vo = T.factors(b)
+            eo = np.linalg.norm(A @ xs - Uo @ (Vo.T @ xs), axis=0)
+        rg = int(h.blocks()[b, 7])
+        if not h.blocks()[b, 8] and rg > 0:
+            if skeleton:
+                sg, tg = h.pivots(b, rg)
+                G = A[:, tg] @ np.linalg.solve(A[np.ix_(sg, tg)], A[sg, :])
+            else:
+                Ug, Vg = h.factors(b, m, n, rg)
+                G = Ug @ Vg.T
+            assert np.linalg.norm(A - G) <= aca_factor * tol * An, b
+        slack += eo + aca_factor * tol * An * np.linalg.norm(xs, axis=0)
+    diff = np.linalg.norm(np.asarray(yg, np.float64).reshape(w.N, -1) - yo, axis=0)
+    bound = base * np.linalg.norm(yo, axis=0) + slack
+    assert np.all(diff <= bound), (diff / np.linalg.norm(yo, axis=0), len(mism))
+    return frac, float(np.max(diff / np.linalg.norm(yo, axis=0)))

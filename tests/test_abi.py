@@ -100,3 +100,58 @@ def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError, match="no CPU fallback"):
         B.load()
+
+
+def _fake_handle(N=100, io=np.float32, device=0):
+    """A Handle whose C handle was never built: every check that runs before the
+    C call can be exercised without a GPU."""
+    h = B.Handle.__new__(B.Handle)
+    h.N, h.d, h.io_dtype, h.device, h._h, h._lib = N, 2, io, device, None, None
+    return h
+
+
+class _FakeCuda:
+    """Duck-typed CUDA tensor on another device (shape, dtype, device only)."""
+
+    def __init__(self, shape, dtype, index):
+        import torch
+
+        self.shape, self.ndim, self.dtype, self.is_cuda = shape, len(shape), dtype, True
+        self.device = torch.device("cuda", index)
+
+
+@pytest.mark.parametrize(
+    "x,y,match",
+    [
+        (np.zeros(99, np.float32), None, "shape"),                     # short x
+        (np.zeros((100, 2), np.float64), None, "element type"),         # FP64 x for an FP32 handle
+        (np.zeros((100, 2), np.float32), np.zeros((100, 3), np.float32), "differs"),
+        (np.zeros((100, 2), np.float32), np.zeros((50, 2), np.float32), "shape"),
+        (np.zeros((100, 2), np.float32), np.zeros((100, 2), np.float64), "element type"),
+        (np.zeros((100, 0), np.float32), None, "shape"),
+        (np.zeros((100, 2, 2), np.float32), None, "shape"),
+    ],
+)
+def test_binding_rejects_mismatched_buffers(x, y, match):
+    h = _fake_handle()
+    for f in (h.matvec, h.matvec_noalloc):
+        with pytest.raises(ValueError, match=match):
+            f(x, y)
+
+
+def test_binding_rejects_other_device_and_torch_types():
+    torch = pytest.importorskip("torch")
+    h = _fake_handle(io=np.float64, device=0)
+    with pytest.raises(ValueError, match="cuda:1"):
+        h.matvec(_FakeCuda((100, 1), torch.float64, 1))
+    with pytest.raises(ValueError, match="element type"):
+        h.matvec(torch.zeros(100, dtype=torch.float32))
+    with pytest.raises(ValueError, match="element type"):
+        h.matvec(torch.zeros(100, dtype=torch.bfloat16))
+    with pytest.raises(ValueError, match="shape"):
+        h.matvec(torch.zeros(100, dtype=torch.float64), torch.zeros(101, dtype=torch.float64))
+    h32 = _fake_handle()
+    with pytest.raises(ValueError, match="one right-hand side"):
+        h32.direct(torch.zeros((100, 2), dtype=torch.float32))
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        B.solve(h32, h, np.zeros(100), None)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from gpu_util import gpu_handle, gpu_matvec, oracle_factors, relerr, require_cuda
+from gpu_util import assert_matches_oracle_hodlrdd, gpu_handle, gpu_matvec, oracle_factors, relerr, require_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -69,9 +69,9 @@ def test_end_to_end_fp64(env, d, N, kernel, params, leaf, tol):
     yg = gpu_matvec(h, w.x)
     yd = oracle.direct(w.points, w.kernel, w.params, w.x)
     assert relerr(yg, yd) <= 10 * tol
-    same = np.array_equal(T.blocks()[:, 7:9], h.blocks()[:, 7:9])
-    if same:
-        assert relerr(yg, T.matvec(w.x)) <= 1e-10
+    # 1e-10 against the oracle's HODLRdD where every pivot agrees, the ACA
+    # bound on the few blocks where a library ulp flipped one
+    assert_matches_oracle_hodlrdd(oracle, T, h, w, yg, tol, kernel)
 
 
 def test_config1_plain_fp64(env):
@@ -325,8 +325,7 @@ def test_matvec_any_admissibility(env, d, amax):
     T = oracle.Tree(w.points, w.kernel, w.params, w.leaf, w.tol, dense_if_cheaper=True, admissible_face_dim=amax)
     h64 = gpu_handle(hd, w, admissible_face_dim=amax)
     y64 = gpu_matvec(h64, w.x)
-    if np.array_equal(T.blocks()[:, 7:9], h64.blocks()[:, 7:9]):
-        assert relerr(y64, T.matvec(w.x)) <= 1e-10
+    assert_matches_oracle_hodlrdd(oracle, T, h64, w, y64, w.tol, w.kernel)
     yd = oracle.direct(w.points, w.kernel, w.params, w.x)
     assert relerr(y64, yd) <= (10 if amax < d - 1 else 100) * w.tol
     for mode in (1, 2):

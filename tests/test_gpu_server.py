@@ -127,3 +127,96 @@ def test_bounded_wait_expiry_is_reported_and_recoverable(env):
     h.sync()  # cleared
     assert np.array_equal(np.asarray(h.matvec(x)), y0)
     h.close()
+
+
+def test_solve_whose_twin_does_not_fit_beside_running_products(env):
+    """Budget room for the FP32 model but not its FP64 twin: a solve on it fails
+    with ERR_OOM while products on the same model run on other workers. The
+    server must not free the model's handle under their kernels (it waits for
+    them), and every product stays bitwise equal to the model alone."""
+    torch, oracle, hd = env
+    w = models()[1]
+    ref, sizes = alone(hd, [w], "fp32")
+    h64 = gpu_handle(hd, w)
+    twin = h64.stats()["device_bytes"]
+    h64.close()
+    budget = sizes[0] + twin // 2
+    srv = hd.Server(budget, workers=3)
+    mid = srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision="fp32")
+    x = np.ascontiguousarray(w.x, dtype=np.float32)
+    y0, _ = srv.wait(srv.submit(mid, x))  # resident before the mix
+    assert np.array_equal(y0, ref[0])
+    prods = [srv.submit(mid, x) for _ in range(6)]
+    sol = srv.submit(mid, w.x, kind=hd.REQ_SOLVE)
+    prods += [srv.submit(mid, x) for _ in range(6)]
+    for r in prods:
+        y, _ = srv.wait(r)
+        assert np.array_equal(y, ref[0])
+    with pytest.raises(hd.HodlrddError) as e:
+        srv.wait(sol)
+    assert e.value.status == hd.ERR_OOM
+    y1, _ = srv.wait(srv.submit(mid, x))  # rebuilt if it was dropped
+    assert np.array_equal(y1, ref[0])
+    assert srv.stats()["resident_bytes"] <= budget
+    srv.close()
+
+
+def test_failed_twin_build_keeps_accounting_exact(env):
+    """A solve's first request builds the model and then its FP64 twin; an
+    allocation failure injected into the twin's build leaves the model resident
+    and its bytes counted (resident_bytes is the model's size, not 0)."""
+    torch, oracle, hd = env
+    from paper_2209_05819_gb300 import _binding as B
+
+    w = models()[0]
+    ref, _ = alone(hd, [w], "fp32")
+    h = gpu_handle(hd, w, precision="fp32")
+    size = h.stats()["device_bytes"]  # as built, before any host-buffer staging
+    h.close()
+    srv = hd.Server(int(64e9), workers=1)
+    mid = srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision="fp32")
+    hit_twin = False
+    try:
+        for k in range(0, 2000, 3):
+            B.debug_fail_alloc_after(k)
+            r = srv.submit(mid, w.x, kind=hd.REQ_SOLVE)
+            try:
+                srv.wait(r)
+                break  # both builds and the solve got through
+            except hd.HodlrddError as e:
+                assert e.value.status == hd.ERR_OOM
+            B.debug_fail_alloc_after(-1)
+            st = srv.stats()
+            assert st["resident_models"] in (0, 1)
+            if st["resident_models"] == 1:
+                # the model alone (its twin's build failed), or model and twin
+                # (a later allocation of the solve failed)
+                hit_twin |= st["resident_bytes"] == size
+                assert st["resident_bytes"] >= size
+            else:
+                assert st["resident_bytes"] == 0
+    finally:
+        B.debug_fail_alloc_after(-1)
+    assert hit_twin
+    y, _ = srv.wait(srv.submit(mid, np.ascontiguousarray(w.x, dtype=np.float32)))
+    assert np.array_equal(y, ref[0])
+    srv.close()
+
+
+def test_solve_reports_an_expired_wait(env):
+    """A bounded wait that expired on the inner handle before or during a solve
+    makes the solve return ERR_TIMEOUT (it reads and clears both handles' error
+    words); the next solve is clean."""
+    torch, oracle, hd = env
+    w = models()[1]
+    hi = gpu_handle(hd, w, precision="fp32")
+    ho = gpu_handle(hd, w)
+    b = torch.from_numpy(np.ascontiguousarray(w.x[:, 0])).cuda()
+    hi.debug_expire_wait(200_000_000)
+    with pytest.raises(hd.HodlrddError) as e:
+        hd.solve(hi, ho, b)
+    assert e.value.status == hd.ERR_TIMEOUT
+    x, st = hd.solve(hi, ho, b)
+    assert st["residual"] <= 1e-10
+    hi.sync()
+    ho.sync()

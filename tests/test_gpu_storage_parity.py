@@ -1,0 +1,128 @@
+"""Every storage form of the GPU product against the oracle's HODLRdD product on
+the oracle's own factors (Algorithm 2 with the factors of Eq. keq2).
+
+The oracle's ACA factors are imported into a GPU handle of each precision, so
+the block structure, ranks and factors are the oracle's and only the GPU's
+storage rounding and FP32 arithmetic remain:
+
+* against the oracle's FP64 product, each form stays within its stated bound
+  (FP32 and the mixed FP32 / FP16 storage 1e-6, FP16 2e-3, BF16 1.5e-2);
+* against tests/storage_model.py (the oracle's product with its factors rounded
+  by the GPU's storage rules, in numpy), every form, the 16-bit ones included,
+  agrees to the FP32 arithmetic bound ARITH below: a defect in a conversion, a
+  scale or the mixed storage's tail split shows up there, far below the
+  16-bit forms' own rounding;
+* the FP32 skeleton form against the oracle's skeleton form (Eq. keq2, the
+  memory-efficient apply) on the same pivots.
+
+ARITH: with the factor rounding modelled exactly, what remains is the GPU's FP32
+work on each output, about a few thousand products summed with compensation for
+one or two right-hand sides (error a few 2^-24 relative to the sum of
+magnitudes), and the near field's FP32 distances and kernel values (a few
+2^-24 per pair); the sums here are well conditioned (1/r, Matern positive;
+log r mixed sign but dominated by its smooth part), so 2^-24 times a
+conditioning of at most 8 covers them: 5e-7. Wider chunks (4-8 right-hand
+sides) accumulate without compensation: 2e-6.
+"""
+import numpy as np
+import pytest
+
+import storage_model as SM
+import workloads as W
+from gpu_util import gpu_handle, gpu_matvec, oracle_factors, pivot_mismatches, relerr, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+STATED = {"fp32": 1e-6, "fp32+fp16": 1e-6, "fp16": 2e-3, "bf16": 1.5e-2}
+ARITH = 5e-7
+ARITH_WIDE = 2e-6
+SKELETON_FP32_BOUND = 5e-6
+
+CASES = [
+    (3, 9000, W.K_INV_R, None, 32, 1e-8),
+    (2, 4096, W.K_LOG, None, 64, 1e-8),
+    (4, 6000, W.K_MATERN32, (1, 0, 0.3, 0), 64, 1e-7),
+]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = require_cuda()
+    import oracle
+    import paper_2209_05819_gb300 as hd
+
+    oracle.build()
+    return torch, oracle, hd
+
+
+_trees = {}
+
+
+def tree(oracle, case, nrhs):
+    key = (case, nrhs)
+    if key not in _trees:
+        d, N, kernel, params, leaf, tol = case
+        w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), leaf, tol, nrhs=nrhs, seed=N + 17 * d)
+        _trees.clear()  # one tree at a time keeps host memory small
+        _trees[key] = (w, oracle.Tree(w.points, w.kernel, w.params, leaf, tol, dense_if_cheaper=True))
+    return _trees[key]
+
+
+@pytest.mark.parametrize("case", CASES, ids=["invr_d3", "log_d2", "matern_d4"])
+@pytest.mark.parametrize("nrhs", [1, 2, 6])
+@pytest.mark.parametrize("precision", ["fp32", "fp32+fp16", "fp16", "bf16"])
+def test_storage_form_on_oracle_factors(env, case, nrhs, precision):
+    torch, oracle, hd = env
+    w, T = tree(oracle, case, nrhs)
+    h = gpu_handle(hd, w, precision=precision)
+    h.import_factors(*oracle_factors(T))
+    assert np.array_equal(h.blocks()[:, 7:9], T.blocks()[:, 7:9])
+    yg = gpu_matvec(h, w.x)
+    h.sync()
+    yo = T.matvec(w.x)
+    ym = SM.storage_product(T, w.x, precision)
+    e_model = relerr(yg, ym)
+    e_oracle = relerr(yg, yo)
+    print(f"{precision} nrhs={nrhs} {case[:3]}: vs storage model {e_model:.2e}, vs oracle {e_oracle:.2e}, "
+          f"model vs oracle {relerr(ym, yo):.2e}")
+    assert e_model <= (ARITH if nrhs <= 2 else ARITH_WIDE), e_model
+    assert e_oracle <= STATED[precision], e_oracle
+    if precision == "fp32+fp16":
+        s = h.stats()
+        assert s["tail_cols"] > 0  # the tail part is exercised
+
+
+def test_mixed_tail_split_matches_model(env):
+    """The mixed storage's head / tail split per block equals the model's rule on
+    the same factors: the count of FP16 columns agrees exactly."""
+    torch, oracle, hd = env
+    w, T = tree(oracle, CASES[0], 1)
+    h = gpu_handle(hd, w, precision="fp32+fp16")
+    h.import_factors(*oracle_factors(T))
+    tail = 0
+    rec = T.blocks()
+    for b in range(len(rec)):
+        if rec[b, 8] or rec[b, 7] == 0:
+            continue
+        _, _, U, V = T.factors(b)
+        tail += U.shape[1] - SM.head_terms(U, V)
+    assert h.stats()["tail_cols"] == tail
+
+
+@pytest.mark.parametrize("case", [CASES[0], (3, 6000, W.K_INV_R, (1.0 / 6000, 1.0, 0, 0), 32, 1e-9)],
+                         ids=["invr_d3", "second_kind_d3"])
+def test_fp32_skeleton_against_oracle_skeleton(env, case):
+    """1/r evaluates with correctly rounded operations only, so the GPU's FP64
+    ACA takes the oracle's pivots on every block (asserted); the FP32 skeleton
+    product then stays within its bound of the oracle's skeleton product."""
+    torch, oracle, hd = env
+    d, N, kernel, params, leaf, tol = case
+    w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), leaf, tol, nrhs=1, seed=N + 3)
+    T = oracle.Tree(w.points, w.kernel, w.params, leaf, tol, dense_if_cheaper=True)
+    h = gpu_handle(hd, w, precision="fp32", lowrank_form="skeleton")
+    assert pivot_mismatches(T, h) == []
+    ys = gpu_matvec(h, w.x)
+    h.sync()
+    e = relerr(ys, T.matvec(w.x, skeleton=True))
+    print(f"fp32 skeleton {case[:3]}: vs oracle skeleton {e:.2e}")
+    assert e <= SKELETON_FP32_BOUND, e
