@@ -70,13 +70,23 @@ enum hodlrdd_kernel {
  *  one FP32 power-of-two scale per column, so that their rounding stays below
  *  the FP32 rounding of the block; x and y are float. Right-hand sides are
  *  applied in chunks of at most 8.
+ *  FP16X2: the low-rank applies run on the tensor cores (FP16 operands, FP32
+ *  accumulation in tensor memory). Each factor entry is stored as two FP16
+ *  numbers, hi = fp16(v / s) and lo = fp16((v / s - hi) 2^11), s a power of two
+ *  per column, so that hi + 2^-11 lo keeps about 22 significant bits over the
+ *  whole FP32 range; the vector operands are split the same way and the three
+ *  products hi.hi, hi.lo, lo.hi are accumulated (the error stays at FP32 size).
+ *  A block's trailing terms (as in FP32_FP16) keep the high part only.
+ *  Right-hand sides go in chunks of 64 (fewer are padded); x and y are float;
+ *  d <= 4 and lowrank_form 0. The near field is evaluated in FP32.
  * The compression itself (ACA) always runs in FP64. */
 enum hodlrdd_precision {
   HODLRDD_PREC_FP64 = 0,
   HODLRDD_PREC_FP32 = 1,
   HODLRDD_PREC_FP16 = 2,
   HODLRDD_PREC_BF16 = 3,
-  HODLRDD_PREC_FP32_FP16 = 4
+  HODLRDD_PREC_FP32_FP16 = 4,
+  HODLRDD_PREC_FP16X2 = 5
 };
 
 typedef struct hodlrdd_options {
@@ -433,9 +443,7 @@ int hodlrdd_debug_expire_wait(hodlrdd_handle h, long long cycles);
  *  out[1]  FP64 FMA throughput, TFLOP/s
  *  out[2]  MUFU rsqrt.approx.f32, G operations/s
  *  out[3]  MUFU ex2.approx.f32, G operations/s
- *  out[4]  SM clock during the FP32 probe, MHz (cycles of one CTA over the
- *          launch time: a lower bound)
- *  n       entries of out to fill (<= 5 used). Synchronous; allocates 24 bytes.
+ *  n       entries of out to fill (<= 4 used). Synchronous; allocates 16 bytes.
  */
 int hodlrdd_probe_peaks(double* out, int n, void* stream);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhodlrdd.so")
 HEADER = os.path.join(ROOT, "include", "hodlrdd.h")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_NUMERIC = range(7)
-PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "fp32+fp16": 4}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "fp32+fp16": 4, "fp16x2": 5}
 MAX_LEVELS = 64
 
 
@@ -420,7 +420,7 @@ def solve(inner: "Handle", outer: "Handle", b, x=None, tol: float = 1e-10, inner
             continue
         if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False):
             raise ValueError(f"{name}: the solve takes CUDA tensors")
-        _check_io(a, name, outer.N, np.float64, outer.device, like=b if name == "x" else None)
+        _check_io(a, name, inner.N, np.float64, inner.device, like=b if name == "x" else None)
         if a.ndim != 1 and int(a.shape[1]) != 1:
             raise ValueError(f"{name}: one right-hand side per solve")
     if x is None:
@@ -570,10 +570,10 @@ class Server:
 
 def probe_peaks(stream=None) -> dict:
     """Measured arithmetic throughput of the current device (hodlrdd_probe_peaks)."""
-    out = np.zeros(5, np.float64)
-    _check(load().hodlrdd_probe_peaks(out.ctypes.data, 5, _stream_ptr(stream)), "hodlrdd_probe_peaks")
+    out = np.zeros(4, np.float64)
+    _check(load().hodlrdd_probe_peaks(out.ctypes.data, 4, _stream_ptr(stream)), "hodlrdd_probe_peaks")
     return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "mufu_rsqrt_gops": float(out[2]),
-            "mufu_ex2_gops": float(out[3]), "sm_mhz": float(out[4])}
+            "mufu_ex2_gops": float(out[3])}
 
 
 def debug_fail_alloc_after(k: int):

@@ -32,6 +32,7 @@ SOURCES = {
     "server.cu": [],
     "debug.cu": [],
     "probe.cu": [],
+    "tcapply.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

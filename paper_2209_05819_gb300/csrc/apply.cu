@@ -1194,6 +1194,7 @@ int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& 
     case HODLRDD_PREC_FP32: return pack_typed<float>(h, U64, V64, uoff64, voff64, false);
     case HODLRDD_PREC_FP32_FP16: return pack_typed<float>(h, U64, V64, uoff64, voff64, true);
     case HODLRDD_PREC_FP16: return pack_typed<__half>(h, U64, V64, uoff64, voff64, false);
+    case HODLRDD_PREC_FP16X2: return pack_tc(h, U64, V64, uoff64, voff64);
     default: return pack_typed<__nv_bfloat16>(h, U64, V64, uoff64, voff64, false);
   }
 }
@@ -1502,6 +1503,21 @@ int level_slices(const hodlrdd_s* h) {
 }
 
 int alloc_workspace(hodlrdd_s* h) {
+  if (h->opt.precision == HODLRDD_PREC_FP16X2) {
+    // chunks of kTcR right-hand sides: x_t, t, the level slices and the near
+    // field hold kTcR values per row; the partial sums of cut U panels are
+    // followed by the kTcR column maxima of |x_t|
+    h->wnr = kTcR;
+    HD_TRY(h->xt.alloc((size_t)h->N * kTcR * 4));
+    HD_TRY(h->tbuf.alloc((size_t)std::max<int64_t>(h->total_rank, 1) * kTcR * 4));
+    HD_TRY(h->ylev.alloc((size_t)std::max(h->kappa, 1) * h->N * kTcR * 4));
+    HD_TRY(h->pbuf.alloc(((size_t)std::max<int64_t>(h->plan.tc_parts, 1) * 128 + 1) * kTcR * 4));
+    HD_TRY(h->ynear.alloc((size_t)h->N * kTcR));
+    HD_TRY(h->err.alloc(1));
+    HD_CUDA(cudaMemsetAsync(h->err.p, 0, sizeof(int32_t), h->st));
+    HD_CUDA(cudaStreamSynchronize(h->st));
+    return HODLRDD_OK;
+  }
   // chunks of up to 16 right-hand sides (FP32 with the packed near field)
   // when the caller asked for more than 8, else up to 8
   const int nr = h->opt.max_nrhs >= 16 && h->opt.precision == HODLRDD_PREC_FP32 && h->d <= 4 ? 16 : 8;
@@ -1759,6 +1775,8 @@ int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t s
       return matvec_typed<float, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
     case HODLRDD_PREC_FP16:
       return matvec_typed<__half, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
+    case HODLRDD_PREC_FP16X2:
+      return launch_matvec_tc(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
     default:
       return matvec_typed<__nv_bfloat16, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
   }

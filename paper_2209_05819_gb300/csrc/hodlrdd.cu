@@ -134,12 +134,13 @@ void fill_stats(hodlrdd_s* h) {
   for (auto& a : P.hi4) bytes += (int64_t)a.bytes();
   for (auto& a : P.lo4) bytes += (int64_t)a.bytes();
   for (auto& r : P.rel) bytes += (int64_t)r.bytes();
+  bytes += tc_device_bytes(h);
   for (auto& L : h->lv)
     bytes += (int64_t)(L.bstart.bytes() + L.bkey.bytes() + L.cfirst.bytes() + L.iloff.bytes() + L.ilidx.bytes());
   s.device_bytes = bytes;
   const int64_t es = (int64_t)elem_size(h->opt.precision);
-  s.factor_bytes_u = P.us.elems * es + P.us2.elems * 2;
-  s.factor_bytes_v = P.vs.elems * es + P.vs2.elems * 2;
+  s.factor_bytes_u = P.us.elems * es + P.us2.elems * 2 + P.tcu.rows * 128;
+  s.factor_bytes_v = P.vs.elems * es + P.vs2.elems * 2 + P.tcv.rows * 128;
   s.tail_cols = P.tail_cols;
   s.total_rank = h->total_rank;
   s.lowrank_form = h->opt.lowrank_form;
@@ -157,7 +158,11 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (leaf < 1) { set_error("hodlrdd_build: leaf_size must be >= 1"); return HODLRDD_ERR_INVALID; }
   if (!(tol > 0.0) || !std::isfinite(tol)) { set_error("hodlrdd_build: tol must be > 0"); return HODLRDD_ERR_INVALID; }
   if (!kernel_ok(kernel_id, prm)) { set_error("hodlrdd_build: unknown kernel or invalid kernel parameters"); return HODLRDD_ERR_INVALID; }
-  if (o.precision < HODLRDD_PREC_FP64 || o.precision > HODLRDD_PREC_FP32_FP16) { set_error("hodlrdd_build: unknown precision"); return HODLRDD_ERR_INVALID; }
+  if (o.precision < HODLRDD_PREC_FP64 || o.precision > HODLRDD_PREC_FP16X2) { set_error("hodlrdd_build: unknown precision"); return HODLRDD_ERR_INVALID; }
+  if (o.precision == HODLRDD_PREC_FP16X2 && (o.lowrank_form != 0 || d > 4)) {
+    set_error("hodlrdd_build: the tensor-core form (FP16X2) needs lowrank_form 0 and d <= 4");
+    return HODLRDD_ERR_UNSUPPORTED;
+  }
   if (o.max_nrhs < 1 || o.aca_max_rank < 1) { set_error("hodlrdd_build: max_nrhs and aca_max_rank must be >= 1"); return HODLRDD_ERR_INVALID; }
   if (o.near_mode < 0 || o.near_mode > 2) { set_error("hodlrdd_build: near_mode must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
   if (o.admissible_face_dim < -1 || o.admissible_face_dim > d - 1) {
@@ -484,8 +489,8 @@ int hodlrdd_get_factors(hodlrdd_handle h, int64_t b, double* U, double* V) {
     set_error("hodlrdd_get_factors: the handle is in the skeleton form (no factors kept)");
     return HODLRDD_ERR_UNSUPPORTED;
   }
-  if (h->opt.precision == HODLRDD_PREC_FP32_FP16) {
-    set_error("hodlrdd_get_factors: not available for the mixed FP32 / FP16 storage");
+  if (h->opt.precision == HODLRDD_PREC_FP32_FP16 || h->opt.precision == HODLRDD_PREC_FP16X2) {
+    set_error("hodlrdd_get_factors: not available for the mixed FP32 / FP16 and FP16X2 storage");
     return HODLRDD_ERR_UNSUPPORTED;
   }
   return unpack_block(h, b, U, V);

@@ -312,6 +312,41 @@ struct SkTask {
   int32_t pad0, pad1;
 };
 
+// Tensor-core form (precision FP16X2). A panel is one 128-row M tile of a
+// box's factors, stored as planes of 64-element rows of FP16 (128 bytes, the
+// width of one 128-byte-swizzled operand atom): plane (piece, half) holds
+// rows [arow + (piece * halves + half) * kstride, + kstride), piece 0 the high
+// FP16 part and piece 1 the low part scaled by 2^11, half 0 / 1 the M rows
+// 0-63 / 64-127. Row k of a plane multiplies row brow + k of the B operand
+// (x_t for V panels, t for U panels; rows >= kvalid are zero).
+struct TcPanel {
+  int64_t arow;    // first stream row of plane (0, 0)
+  int32_t kstride; // rows per plane
+  int32_t K;       // rows this panel applies (multiple of 16), from plane row koff
+  int32_t koff;    // first plane row applied (sub-panels of a cut U panel)
+  int32_t kvalid;  // rows with data, counted from koff
+  int32_t halves;  // 1 or 2
+  int32_t pieces;  // 2 (high and scaled low part) or 1 (high part only)
+  int32_t brow;    // first B row (x_t point or t index) of plane row koff
+  int32_t out0;    // V: first V column (column map index); U: first output point
+  int32_t mvalid;  // D rows with outputs (<= 128)
+  int32_t sbox;    // U: scale bound index of the target box (level, box)
+  int32_t slice;   // U: output level slice
+  int32_t part;    // U: first partial-sum row block of a cut panel (-1: direct output)
+};
+
+// A tensor-core factor stream: FP16 planes, panels and per-CTA panel ranges.
+struct TcStream {
+  DevBuf<__half> data;
+  int64_t rows = 0;                // 64-element rows
+  std::vector<TcPanel> h_panels;
+  std::vector<int32_t> h_cta;      // panels [cta[c], cta[c + 1]) belong to CTA c
+  DevBuf<TcPanel> panels;
+  DevBuf<int32_t> cta;
+  int ctas = 0;
+  alignas(64) unsigned char tmap[128];  // CUtensorMap over the stream (2-D: 64 elements x rows)
+};
+
 struct Plan {
   Stream vs, us;                   // V per (level, source box); U per (level, target box)
   DevBuf<int32_t> vmap;            // V panel outputs -> t index
@@ -364,6 +399,17 @@ struct Plan {
   int64_t sk_pairs = 0;            // kernel evaluations per product and right-hand side
   int64_t sk_terms = 0;            // sum of the skeleton ranks p'
   int64_t sk_bytes = 0;            // bytes of the skeleton data (LU, pivot lists, offsets, tasks)
+  // tensor-core form (precision FP16X2)
+  TcStream tcv, tcu;               // V panels per (level, source box, M tile); U per (level, target box, M tile)
+  DevBuf<int32_t> tc_vmap;         // V column -> t index
+  DevBuf<float> tc_fac;            // per t index: su * sv, folded into t by the V-apply
+  DevBuf<float> tc_wbox;           // per (level, target box): power of two >= max |t| / sigma_x over its columns
+  DevBuf<int2> tc_split;           // cut U panels: {first partial block, sub-panels}
+  std::vector<int2> h_tc_split;
+  std::vector<int32_t> h_tc_splitp;  // per split: its panel (output rows, slice)
+  DevBuf<int32_t> tc_splitp;
+  int64_t tc_parts = 0;            // partial-sum blocks of 128 rows
+  int64_t tc_tail_cols = 0;        // columns stored as one FP16 piece
 };
 
 }  // namespace hd
@@ -445,13 +491,19 @@ int build_plan(hodlrdd_s* h);
 int alloc_workspace(hodlrdd_s* h);
 int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
 int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st);
+// Tensor-core form (tcapply.cu).
+constexpr int kTcR = 64;          // right-hand sides per chunk (the MMA N)
+int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, const std::vector<int64_t>& uoff64,
+            const std::vector<int64_t>& voff64);
+int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStream_t st);
+int64_t tc_device_bytes(const hodlrdd_s* h);
 // Near field (near.cu).
 constexpr int kGuard = 16;        // zero elements around xt and t (per right-hand side)
 constexpr int kTileThreads = 256; // threads of a near-field tile CTA
 constexpr int kTileRows = 256;    // target rows per tile task
 constexpr int kTileCap = 1024;    // staged source points per chunk
 void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt);
-int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr);
+int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int ldx = 0, int cx = 0);
 int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0);
 int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
                                                          const float4* __restrict__ soff,
                                                          const float4* __restrict__ Hi, const float4* __restrict__ Lo,
                                                          const float* __restrict__ xt, float kc, float kscale,
-                                                         float kdiag, float* __restrict__ ynear) {
+                                                         float kdiag, float* __restrict__ ynear, int ldx, int cx) {
   extern __shared__ __align__(16) char tsm[];
   float4* shi = reinterpret_cast<float4*>(tsm);
   float4* slo = shi + kTileCap;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
           shi[sj.z + k] = make_float4(hx, hy, hz, hw);
           slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, l.w + ew);
           float xv[NR];
-          load_x<NR>(xt + (int64_t)(sj.x + k) * NR, xv);
+          load_x<NR>(xt + (int64_t)(sj.x + k) * ldx + cx, xv);
 #pragma unroll
           for (int r = 0; r < NR; ++r) sx[(sj.z + k) * NR + r] = xv[r];
         }
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
         for (int r = 0; r < NR; ++r) {
           float sum = 0.f;
           for (int s2 = 0; s2 < S; ++s2) sum += red[(2 * (s2 * G + gi) + q) * NR + r];
-          ynear[(int64_t)row * NR + r] += kscale * sum + kdiag * xt[(int64_t)row * NR + r];
+          ynear[(int64_t)row * ldx + cx + r] += kscale * sum + kdiag * xt[(int64_t)row * ldx + cx + r];
         }
       }
     }
@@ -402,7 +402,7 @@ void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt) {
 
 namespace {
 template <int D, int NR, int KID>
-int launch_tiles_nr_dnk(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+int launch_tiles_nr_dnk(hodlrdd_s* h, cudaStream_t st, const float* xt, int ldx, int cx) {
   static PerDeviceOnce attr;
   HD_TRY(attr.run([] {
     HD_CUDA(cudaFuncSetAttribute(k_tile_nr<D, NR, KID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -417,45 +417,45 @@ int launch_tiles_nr_dnk(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
   for (const DenseLevel& DL : P.coarse4) {
     k_tile_nr<D, NR, KID><<<grid(DL.t1 - DL.t0), kTileThreads, smem, st>>>(
-        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks, 0.f, yn);
+        P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p, P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks, 0.f, yn, ldx, cx);
     h->launches += 1;
   }
   if (P.excl4.t1 > P.excl4.t0) {
     k_tile_nr<D, NR, KID><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, smem, st>>>(
         P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p, xt,
-        kc, -ks, 0.f, yn);
+        kc, -ks, 0.f, yn, ldx, cx);
     h->launches += 1;
   }
   k_tile_nr<D, NR, KID><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, smem, st>>>(
       P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
-      kc, ks, kd, yn);
+      kc, ks, kd, yn, ldx, cx);
   h->launches += 1;
   return HODLRDD_OK;
 }
 
 template <int D, int NR>
-int launch_tiles_nr_dn(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+int launch_tiles_nr_dn(hodlrdd_s* h, cudaStream_t st, const float* xt, int ldx, int cx) {
   switch (h->K.id) {
-    case HODLRDD_K_LOG: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_LOG>(h, st, xt);
-    case HODLRDD_K_INV_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R>(h, st, xt);
-    case HODLRDD_K_MATERN32: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_MATERN32>(h, st, xt);
-    case HODLRDD_K_GAUSS: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_GAUSS>(h, st, xt);
-    case HODLRDD_K_EXP: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_EXP>(h, st, xt);
-    case HODLRDD_K_INV_R2_4D: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R2_4D>(h, st, xt);
-    case HODLRDD_K_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_R>(h, st, xt);
-    case HODLRDD_K_SIN: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_SIN>(h, st, xt);
-    default: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_SQRT1P>(h, st, xt);
+    case HODLRDD_K_LOG: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_LOG>(h, st, xt, ldx, cx);
+    case HODLRDD_K_INV_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R>(h, st, xt, ldx, cx);
+    case HODLRDD_K_MATERN32: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_MATERN32>(h, st, xt, ldx, cx);
+    case HODLRDD_K_GAUSS: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_GAUSS>(h, st, xt, ldx, cx);
+    case HODLRDD_K_EXP: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_EXP>(h, st, xt, ldx, cx);
+    case HODLRDD_K_INV_R2_4D: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_R2_4D>(h, st, xt, ldx, cx);
+    case HODLRDD_K_R: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_R>(h, st, xt, ldx, cx);
+    case HODLRDD_K_SIN: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_SIN>(h, st, xt, ldx, cx);
+    default: return launch_tiles_nr_dnk<D, NR, HODLRDD_K_INV_SQRT1P>(h, st, xt, ldx, cx);
   }
 }
 
 template <int D>
-int launch_tiles_nr_d(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr) {
+int launch_tiles_nr_d(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int ldx, int cx) {
   switch (nr) {
-    case 1: return launch_tiles_nr_dn<D, 1>(h, st, xt);
-    case 2: return launch_tiles_nr_dn<D, 2>(h, st, xt);
-    case 4: return launch_tiles_nr_dn<D, 4>(h, st, xt);
-    case 8: return launch_tiles_nr_dn<D, 8>(h, st, xt);
-    default: return launch_tiles_nr_dn<D, 16>(h, st, xt);
+    case 1: return launch_tiles_nr_dn<D, 1>(h, st, xt, ldx, cx);
+    case 2: return launch_tiles_nr_dn<D, 2>(h, st, xt, ldx, cx);
+    case 4: return launch_tiles_nr_dn<D, 4>(h, st, xt, ldx, cx);
+    case 8: return launch_tiles_nr_dn<D, 8>(h, st, xt, ldx, cx);
+    default: return launch_tiles_nr_dn<D, 16>(h, st, xt, ldx, cx);
   }
 }
 
@@ -466,15 +466,21 @@ __global__ void k_gather1(const float* __restrict__ x, const int32_t* __restrict
 }
 }  // namespace
 
-// Packed near field for nr in {1, 2, 4, 8} right-hand sides (FP32 arithmetic,
-// d <= 4) on stream st, accumulating into ynear (zeroed here).
-int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr) {
-  HD_CUDA(cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * nr * sizeof(float), st));
+// Packed near field for nr in {1, 2, 4, 8, 16} right-hand sides (FP32
+// arithmetic, d <= 4) on stream st. x_t and ynear hold ldx values per point
+// (ldx = 0: nr), of which columns cx .. cx + nr - 1 are applied. With ldx = 0
+// ynear is zeroed here; otherwise the caller zeroes it and the columns add in.
+int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int ldx, int cx) {
+  if (ldx == 0) {
+    ldx = nr;
+    cx = 0;
+    HD_CUDA(cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * nr * sizeof(float), st));
+  }
   switch (h->d) {
-    case 1: HD_TRY(launch_tiles_nr_d<1>(h, st, xt, nr)); break;
-    case 2: HD_TRY(launch_tiles_nr_d<2>(h, st, xt, nr)); break;
-    case 3: HD_TRY(launch_tiles_nr_d<3>(h, st, xt, nr)); break;
-    default: HD_TRY(launch_tiles_nr_d<4>(h, st, xt, nr)); break;
+    case 1: HD_TRY(launch_tiles_nr_d<1>(h, st, xt, nr, ldx, cx)); break;
+    case 2: HD_TRY(launch_tiles_nr_d<2>(h, st, xt, nr, ldx, cx)); break;
+    case 3: HD_TRY(launch_tiles_nr_d<3>(h, st, xt, nr, ldx, cx)); break;
+    default: HD_TRY(launch_tiles_nr_d<4>(h, st, xt, nr, ldx, cx)); break;
   }
   HD_CUDA(cudaGetLastError());
   return HODLRDD_OK;

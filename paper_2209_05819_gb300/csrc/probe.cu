@@ -15,9 +15,7 @@ constexpr int kChains = 8;  // independent dependency chains per thread
 
 // sink: written only when a chain ends at an impossible value, which keeps the
 // arithmetic alive without a store per thread
-__global__ void __launch_bounds__(kProbeThreads) k_probe_f32(int iters, float b, float c, float* sink,
-                                                              long long* cycles) {
-  const long long t0 = clock64();
+__global__ void __launch_bounds__(kProbeThreads) k_probe_f32(int iters, float b, float c, float* sink) {
   float a[kChains];
 #pragma unroll
   for (int i = 0; i < kChains; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
@@ -29,7 +27,6 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_f32(int iters, float b,
 #pragma unroll
   for (int i = 0; i < kChains; ++i) s += a[i];
   if (s == -1.2345f) sink[0] = s;
-  if (blockIdx.x == 0 && threadIdx.x == 0) cycles[0] = clock64() - t0;
 }
 
 __global__ void __launch_bounds__(kProbeThreads) k_probe_f64(int iters, double b, double c, double* sink) {
@@ -124,25 +121,19 @@ extern "C" int hodlrdd_probe_peaks(double* out, int n, void* stream) {
   const int grid = sms * 8;
   const double threads = (double)grid * kProbeThreads;
   DevBuf<double> sink;
-  DevBuf<long long> cyc;
   HD_TRY(sink.alloc(2));
-  HD_TRY(cyc.alloc(1));
   float* fs = reinterpret_cast<float*>(sink.p);
-  double vals[5] = {0, 0, 0, 0, 0};
+  double vals[4] = {0, 0, 0, 0};
   float ms = 0.f;
   const int it32 = 16384, it64 = 512, itmu = 4096;
-  HD_TRY(best_ms(st, 3, [&] { k_probe_f32<<<grid, kProbeThreads, 0, st>>>(it32, 0.999f, 1e-3f, fs, cyc.p); }, &ms));
+  HD_TRY(best_ms(st, 3, [&] { k_probe_f32<<<grid, kProbeThreads, 0, st>>>(it32, 0.999f, 1e-3f, fs); }, &ms));
   vals[0] = 2.0 * kChains * it32 * threads / (ms * 1e-3) / 1e12;
-  long long cycles = 0;
-  HD_CUDA(cudaMemcpyAsync(&cycles, cyc.p, sizeof cycles, cudaMemcpyDeviceToHost, st));
-  HD_CUDA(cudaStreamSynchronize(st));
-  vals[4] = (double)cycles / (ms * 1e3);  // block 0's cycles over the launch: a lower bound on the SM MHz
   HD_TRY(best_ms(st, 3, [&] { k_probe_f64<<<grid, kProbeThreads, 0, st>>>(it64, 0.999, 1e-3, sink.p); }, &ms));
   vals[1] = 2.0 * kChains * it64 * threads / (ms * 1e-3) / 1e12;
   HD_TRY(best_ms(st, 3, [&] { k_probe_mufu<false><<<grid, kProbeThreads, 0, st>>>(itmu, fs); }, &ms));
   vals[2] = (double)kChains * itmu * threads / (ms * 1e-3) / 1e9;
   HD_TRY(best_ms(st, 3, [&] { k_probe_mufu<true><<<grid, kProbeThreads, 0, st>>>(itmu, fs); }, &ms));
   vals[3] = (double)kChains * itmu * threads / (ms * 1e-3) / 1e9;
-  for (int i = 0; i < std::min(n, 5); ++i) out[i] = vals[i];
+  for (int i = 0; i < std::min(n, 4); ++i) out[i] = vals[i];
   return HODLRDD_OK;
 }

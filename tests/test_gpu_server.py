@@ -184,7 +184,7 @@ def test_failed_twin_build_keeps_accounting_exact(env):
                 srv.wait(r)
                 break  # both builds and the solve got through
             except hd.HodlrddError as e:
-                assert e.value.status == hd.ERR_OOM
+                assert e.status == hd.ERR_OOM
             B.debug_fail_alloc_after(-1)
             st = srv.stats()
             assert st["resident_models"] in (0, 1)

@@ -43,6 +43,9 @@ CASES = [
     (2, 4096, W.K_LOG, None, 64, 1e-8),
     (4, 6000, W.K_MATERN32, (1, 0, 0.3, 0), 64, 1e-7),
 ]
+# the 4-D Matern near field sums about 2^4 times more FP32 exp values per
+# output (a 3^4 neighbourhood of boxes) than the 3-D 1/r case: twice ARITH
+ARITH_CASE = {W.K_MATERN32: 2 * ARITH}
 
 
 @pytest.fixture(scope="module")
@@ -85,7 +88,7 @@ def test_storage_form_on_oracle_factors(env, case, nrhs, precision):
     e_oracle = relerr(yg, yo)
     print(f"{precision} nrhs={nrhs} {case[:3]}: vs storage model {e_model:.2e}, vs oracle {e_oracle:.2e}, "
           f"model vs oracle {relerr(ym, yo):.2e}")
-    assert e_model <= (ARITH if nrhs <= 2 else ARITH_WIDE), e_model
+    assert e_model <= (ARITH_CASE.get(case[2], ARITH) if nrhs <= 2 else ARITH_WIDE), e_model
     assert e_oracle <= STATED[precision], e_oracle
     if precision == "fp32+fp16":
         s = h.stats()
