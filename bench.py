@@ -292,33 +292,74 @@ def cpu_baseline(args, rank_w):
                       f"{nrow} rows scaled to all rows"}
 
 
-def many_rhs_line(args, torch, stream, hd):
-    """The many-right-hand-side workload in the headline precision, its error
-    against the FP64 form, and the plain FP64 time."""
+def many_rhs_line(args, torch, stream, hd, peaks=None):
+    """The many-right-hand-side workload (d=4, N=65536, Matern-3/2, 64 columns):
+    the tensor-core form (factors as FP16 high / scaled-low pairs, tcgen05 MMAs
+    for the low-rank applies and the near field's 64-wide accumulation), the
+    FP32 CUDA-core form and the plain FP64 form; errors against FP64, stage
+    times and the applies' HBM roofline."""
     import workloads as W
 
     w = W.many_rhs_4d(seed=args.seed)
     pts = torch.from_numpy(w.points).cuda()
     out = {"workload": f"d=4 N={w.N} uniform [0,1]^4, Matern-3/2 l=0.2, leaf {w.leaf}, tol {w.tol:g}, "
-                       f"nrhs {w.nrhs}"}
+                       f"nrhs {w.nrhs}", "precision": "fp16x2"}
     res = {}
-    # wide chunks (16 right-hand sides) need uniform FP32 factors
-    prec_lo = "fp32" if args.precision == "fp32+fp16" else args.precision
-    out["precision"] = prec_lo
-    for prec in (prec_lo, "fp64"):
+    for prec in ("fp16x2", "fp32", "fp64"):
         h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, max_nrhs=w.nrhs)
         io = torch.float64 if prec == "fp64" else torch.float32
         x = torch.from_numpy(np.ascontiguousarray(w.x)).to(io).cuda()
         y = torch.empty_like(x)
-        n = 5 if prec != "fp64" else 1
-        t = time_steps(lambda: h.matvec(x, y), n, 1, torch, stream)
-        res[prec] = (t / n, y.double())
+        n = 10 if prec == "fp16x2" else 3 if prec == "fp32" else 1
+        t = time_steps(lambda: h.matvec(x, y), n, 2, torch, stream)
+        entry = {"ms": 1e3 * t / n, "y": y.double()}
+        if prec == "fp16x2":
+            h.set_profiling(True)
+            for _ in range(3):
+                h.matvec(x, y)
+            torch.cuda.synchronize()
+            pr = h.profile()
+            h.set_profiling(False)
+            h.sync()
+            entry["prof"] = {k: pr[k] / max(pr["chunks"], 1) for k in ("gather_ms", "vapply_ms", "uapply_ms", "near_ms")}
+            entry["stats"] = h.stats()
+        res[prec] = entry
         h.close()
-    t32, y32 = res[prec_lo]
-    t64, y64 = res["fp64"]
-    err = float((torch.linalg.norm(y32 - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
-    out.update({"ms_per_matvec": 1e3 * t32, "value": w.N * w.nrhs / t32, "unit": UNIT,
-                "rel_err_vs_fp64": err, "fp64_ms_per_matvec": 1e3 * t64, "speedup_vs_fp64": t64 / t32})
+    y64 = res["fp64"]["y"]
+
+    def err(y):
+        return float((torch.linalg.norm(y - y64, dim=0) / torch.linalg.norm(y64, dim=0)).max().item())
+
+    tc = res["fp16x2"]
+    s = tc["stats"]
+    units = w.N * w.nrhs
+    R = 64
+    hbm, _ = measured_peaks()
+    vbytes = s["factor_bytes_v"] + s["total_rank"] * R * 4 + w.N * R * 4      # V planes, t written, x_t read
+    ubytes = s["factor_bytes_u"] + s["total_rank"] * R * 4 + s["kappa"] * w.N * R * 4  # U planes, t read, y_l written
+    pr = tc["prof"]
+    out.update({"ms_per_matvec": tc["ms"], "value": units / (tc["ms"] / 1e3), "unit": UNIT,
+                "rel_err_vs_fp64": err(tc["y"]), "fp64_ms_per_matvec": res["fp64"]["ms"],
+                "speedup_vs_fp64": res["fp64"]["ms"] / tc["ms"],
+                "fp32_cuda_cores": {"ms_per_matvec": res["fp32"]["ms"], "value": units / (res["fp32"]["ms"] / 1e3),
+                                    "rel_err_vs_fp64": err(res["fp32"]["y"])},
+                "speedup_vs_fp32_cuda_cores": res["fp32"]["ms"] / tc["ms"],
+                "stage_ms": {k: round(v, 4) for k, v in pr.items()},
+                "factor_gb": (s["factor_bytes_u"] + s["factor_bytes_v"]) / 1e9, "dense_pairs": s["dense_pairs"]})
+    roof = {}
+    for name, byt, ms in (("vapply", vbytes, pr["vapply_ms"]), ("uapply", ubytes, pr["uapply_ms"])):
+        if ms > 0:
+            roof[name] = {"bound": "hbm", "algorithmic_bytes": byt, "achieved": byt / (ms / 1e3) / 1e9, "peak": hbm,
+                          "unit": "GB/s", "frac": byt / (ms / 1e3) / 1e9 / hbm}
+    if peaks and pr["near_ms"] > 0:
+        pairs = s["dense_pairs"]
+        ops = 2 * w.d + 4  # d subtractions, d multiply-adds, the scale, 1 + a and the product (sqrt, exp on MUFU)
+        tsec = pr["near_ms"] / 1e3
+        roof["near"] = {"bound": "alu", "pairs": pairs, "ops_per_pair": ops, "unit": "G FP32 ops/s",
+                        "achieved": pairs * ops / tsec / 1e9, "peak": peaks["fp32_tflops"] * 1e3 / 2,
+                        "frac": pairs * ops / tsec / (peaks["fp32_tflops"] * 1e12 / 2),
+                        "tensor_tflops": pairs * R * 2 * 3 / tsec / 1e12}
+    out["roofline"] = roof
     return out
 
 
@@ -724,7 +765,7 @@ def main():
     # many right-hand sides (d=4, N=65536, Matern-3/2, leaf 128, tol 1e-8, nrhs 64)
     many = None
     if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
-        many = optional_line(many_rhs_line, args, torch, stream, hd)
+        many = optional_line(many_rhs_line, args, torch, stream, hd, peaks)
 
     # the paper's admissibility comparison (H-matrix / HODLRdD / HODLR)
     adm = None

@@ -33,6 +33,7 @@ SOURCES = {
     "debug.cu": [],
     "probe.cu": [],
     "tcapply.cu": [],
+    "tcnear.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

@@ -1300,7 +1300,10 @@ int build_plan(hodlrdd_s* h) {
   // have fewer than eight tasks per SM, so that trees with few large parent
   // boxes (high d, large leaves) still spread over every SM
   int32_t rows_cap = kTileRows;
-  if (h->kappa >= 1) {
+  // the tensor-core near field takes tiles of 128 target rows (the MMA's M)
+  const bool tc_tiles = h->opt.precision == HODLRDD_PREC_FP16X2 && tc_near_kernel(h->K.id);
+  if (tc_tiles) rows_cap = 128;
+  if (h->kappa >= 1 && !tc_tiles) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const Level& LP = h->lv[h->kappa - 1];
@@ -1345,6 +1348,20 @@ int build_plan(hodlrdd_s* h) {
     sl.push_back({make_int2(L.h_bstart[J], L.h_bstart[J + 1] - L.h_bstart[J]), make_float4(v[0], v[1], v[2], v[3])});
     need4[l] = 1;
   };
+  // tasks of one launch in decreasing order of their pairs: the hardware
+  // hands CTAs out in order, so the long tasks start first (each task owns
+  // its rows, so the order changes no sum)
+  auto sort_tasks = [&](int64_t a, int64_t b) {
+    std::vector<std::pair<int64_t, int4>> w;
+    w.reserve((size_t)(b - a));
+    for (int64_t t = a; t < b; ++t) {
+      int64_t n = 0;
+      for (int32_t e = t4[t].z; e < t4[t].w; ++e) n += s4[e].y;
+      w.push_back({-(int64_t)t4[t].y * n, t4[t]});
+    }
+    std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (int64_t t = a; t < b; ++t) t4[t] = w[(size_t)(t - a)].second;
+  };
   P.coarse4.clear();
   if (!f64 && d <= 4) {
     for (int l = 1; l < h->kappa; ++l) {
@@ -1360,6 +1377,7 @@ int build_plan(hodlrdd_s* h) {
         if (!sl.empty()) add_task(L.h_bstart[i], L.h_bstart[i + 1] - L.h_bstart[i]);
       }
       DL.t1 = (int64_t)t4.size();
+      sort_tasks(DL.t0, DL.t1);
       if (DL.t1 > DL.t0) P.coarse4.push_back(DL);
     }
     // leaf level: tiles per parent box, or lists per leaf box, by work
@@ -1427,6 +1445,7 @@ int build_plan(hodlrdd_s* h) {
         if (!sl.empty()) add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
       }
       P.excl4.t1 = (int64_t)t4.size();
+      sort_tasks(P.excl4.t0, P.excl4.t1);
       const int lp = lk - 1;
       const Level& LP = h->lv[lp];
       P.leaf4.level = lp;
@@ -1437,6 +1456,7 @@ int build_plan(hodlrdd_s* h) {
         add_task(LP.h_bstart[pb], LP.h_bstart[pb + 1] - LP.h_bstart[pb]);
       }
       P.leaf4.t1 = (int64_t)t4.size();
+      sort_tasks(P.leaf4.t0, P.leaf4.t1);
     } else {
       P.excl4 = DenseLevel{lk, 0, 0};
       P.leaf4.level = lk;
@@ -1452,6 +1472,7 @@ int build_plan(hodlrdd_s* h) {
         add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
       }
       P.leaf4.t1 = (int64_t)t4.size();
+      sort_tasks(P.leaf4.t0, P.leaf4.t1);
     }
     if ((int64_t)s4.size() >= INT32_MAX) {
       set_error("packed source list too long");

@@ -497,6 +497,9 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
             const std::vector<int64_t>& voff64);
 int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStream_t st);
 int64_t tc_device_bytes(const hodlrdd_s* h);
+bool tc_near_supported(const hodlrdd_s* h);
+inline bool tc_near_kernel(int kid) { return kid != HODLRDD_K_INV_R && kid != HODLRDD_K_INV_R2_4D; }
+int launch_tc_near(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigned int* colmax);
 // Near field (near.cu).
 constexpr int kGuard = 16;        // zero elements around xt and t (per right-hand side)
 constexpr int kTileThreads = 256; // threads of a near-field tile CTA

@@ -82,6 +82,26 @@ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
   return s;
 }
 
+// Squared distance from the high parts alone (kernels smooth in r^2).
+template <int D>
+__device__ __forceinline__ float sqdist1(const float4& th, const float4& sh) {
+  float t = th.x - sh.x;
+  float s = t * t;
+  if (D > 1) {
+    t = th.y - sh.y;
+    s = fmaf(t, t, s);
+  }
+  if (D > 2) {
+    t = th.z - sh.z;
+    s = fmaf(t, t, s);
+  }
+  if (D > 3) {
+    t = th.w - sh.w;
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
 template <int D>
 __device__ __forceinline__ float sqdist2(const float4& th, const float4& tl, const float4& sh, const float4& sl) {
   float t = (th.x - sh.x) + (tl.x - sl.x);

@@ -14,16 +14,21 @@
 // keeps about 22 significant bits across the FP32 range (a plain hi + lo pair
 // would lose them below FP16's normal range).
 //
-// One persistent CTA per SM, 256 threads in five roles:
+// One persistent CTA per SM, 320 threads in five roles:
 //   warp 0      producer: cp.async.bulk.tensor loads of the A planes of each
 //               64-row K chunk into a ring of shared-memory slots (128-byte swizzle)
 //   warp 1      allocates tensor memory; one lane issues tcgen05.mma and
 //               tcgen05.commit (slot release, accumulator ready)
-//   warps 2-3   B operand: load 64 FP32 rows, scale, split, store swizzled
+//   warps 2-3,
+//   8-9         B operand: the chunk's 64 FP32 rows (bulk-copied by the
+//               producer with the A planes), scaled, split, stored swizzled
 //   warps 4-7   epilogue: tcgen05.ld of the two accumulators, combine, scale,
 //               store (warp 4 + q reads tensor-memory lanes 32 q .. 32 q + 31)
-// Accumulators are double-buffered so that a panel's epilogue overlaps the next
-// panel's MMAs. Every wait is bounded; on expiry the kernel records an error in
+// Every 64-row K chunk accumulates into a fresh pair of tensor-memory
+// accumulators (double-buffered), which the epilogue adds into per-row FP32
+// sums with round-to-nearest: the tensor cores truncate when they accumulate,
+// and restarting every four MMA steps keeps that error at a few 2^-24 of each
+// chunk's sum instead of growing with the panel's length. Every wait is bounded; on expiry the kernel records an error in
 // the handle's error word, waits (bounded) for its own copies and MMAs, frees
 // its tensor memory and returns.
 #include <cuda.h>
@@ -34,122 +39,24 @@
 #include <numeric>
 
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace hd {
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 320;
 constexpr int kTcKC = 64;                   // K rows per ring slot
-constexpr int kTcStages = 4;                // ring slots
+constexpr int kTcStages = 3;                // ring slots
 constexpr int kPlaneBytes = kTcKC * 128;    // one 64-row plane of 128-byte rows
 constexpr int kSlotA = 4 * kPlaneBytes;     // (piece, half) planes
-constexpr int kSlotBytes = kSlotA + 2 * kPlaneBytes;  // + B high and low planes
+constexpr int kSlotB32 = kTcKC * kTcR * 4;    // the chunk's FP32 B rows, bulk-copied
+constexpr int kSlotBytes = kSlotA + 2 * kPlaneBytes + kSlotB32;  // + B high and low planes + FP32 B rows
 constexpr int kZeroBytes = kPlaneBytes;     // zero half for 64-row panels
 constexpr int kTcSmem = kTcStages * kSlotBytes + kZeroBytes + 1024;
 constexpr int kTmemCols = 256;              // two buffers x (D_hi, D_lo) x 64 columns
-constexpr long long kTcWait = 4000000000LL; // about two seconds
-constexpr float kLoScale = 2048.f;          // 2^11
-constexpr int kErrTc = 21;                  // error-word codes of this kernel: 21 + site
 
 static_assert(kTcSmem <= 232448, "tensor-core apply exceeds the shared-memory limit");
 static_assert(sizeof(TcPanel) == 56, "TcPanel layout");
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-
-// Bounded wait for the phase of the given parity; false (error word set) on expiry.
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, int32_t* err, int site) {
-  uint32_t ok = 0;
-  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(ok) : "r"(saddr(b)), "r"(parity) : "memory");
-  if (ok) return true;
-  const long long t0 = clock64();
-  for (;;) {
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(saddr(b)), "r"(parity) : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > kTcWait) {
-      atomicCAS(err, 0, kErrTc + site);
-      return false;
-    }
-  }
-}
-
-// 2-D tensor load of a 64 x 64-row box (128-byte swizzle) into shared memory.
-__device__ __forceinline__ void tma_load(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          saddr(dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(saddr(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and stride
-// byte offsets (16-byte units), the fixed version bits, 128-byte swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor of kind::f16: D FP32, A and B FP16, both MN-major,
-// M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(kTcR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-// 16 consecutive FP32 accumulator columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// The power of two 2^e > |m| (1 for m = 0), from the bits of a non-negative float.
-__device__ __forceinline__ float pow2_above(float m) {
-  if (!(m > 0.f)) return 1.f;
-  int e;
-  frexpf(m, &e);
-  return ldexpf(1.f, e);
-}
-
-// Split v (|v| < 1) into hi + 2^-11 lo, both FP16.
-__device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
-  hi = __float2half_rn(v);
-  lo = __float2half_rn((v - __half2float(hi)) * kLoScale);
-}
 
 // Arguments of one apply stage.
 struct TcArgs {
@@ -182,7 +89,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
   if (tid == 0) {
     for (int i = 0; i < kTcStages; ++i) {
       bar_init(&full_a[i], 1);
-      bar_init(&full_b[i], 2);  // one arrival per B warp
+      bar_init(&full_b[i], 4);  // one arrival per B warp
       bar_init(&empty[i], 1);   // tcgen05.commit
     }
     for (int i = 0; i < 2; ++i) {
@@ -216,7 +123,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
           const int slot = (int)(s % kTcStages);
           if (s >= kTcStages && !(ok = bar_wait(&empty[slot], (uint32_t)((s / kTcStages - 1) & 1), err, 0))) break;
           unsigned char* base = sm + slot * kSlotBytes;
-          bar_expect(&full_a[slot], (uint32_t)(P.pieces * P.halves * kPlaneBytes));
+          // the chunk's valid B rows (FP32, contiguous) ride on the same barrier
+          const int nb = max(0, min(kTcKC, P.kvalid - kc * kTcKC));
+          bar_expect(&full_a[slot], (uint32_t)(P.pieces * P.halves * kPlaneBytes + nb * kTcR * 4));
+          if (nb > 0)
+            bulk_load(base + kSlotA + 2 * kPlaneBytes, a.B + ((int64_t)P.brow + (int64_t)kc * kTcKC) * kTcR,
+                      (uint32_t)(nb * kTcR * 4), &full_a[slot]);
           for (int pc = 0; pc < P.pieces; ++pc)
             for (int hh = 0; hh < P.halves; ++hh) {
               const int64_t y = P.arow + (int64_t)(pc * P.halves + hh) * P.kstride + P.koff + (int64_t)kc * kTcKC;
@@ -230,22 +142,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
         bar_wait(&full_a[t % kTcStages], (uint32_t)((t / kTcStages) & 1), err, 7);
     }
   } else if (warp == 1) {
-    // MMA issue
+    // MMA issue: every K chunk into a fresh accumulator pair D(j & 1), j the
+    // CTA's chunk count (the epilogue adds the chunk sums with round-to-nearest
+    // FP32 additions, so the tensor cores' truncating accumulation spans four
+    // MMA steps only)
     if (lane == 0) {
       const uint32_t zaddr = saddr(zero);
-      int64_t s = 0, q = 0;
-      for (int p = p0; p < p1 && ok; ++p, ++q) {
+      int64_t s = 0;
+      for (int p = p0; p < p1 && ok; ++p) {
         const TcPanel P = a.panels[p];
-        const int buf = (int)(q & 1);
-        if (q >= 2 && !(ok = bar_wait(&dempty[buf], (uint32_t)((q / 2 - 1) & 1), err, 1))) break;
-        tc_fence_after();
-        const uint32_t dhi = tmem + buf * 128, dlo = dhi + 64;
         const int nk = (P.K + kTcKC - 1) / kTcKC;
         for (int kc = 0; kc < nk; ++kc, ++s) {
           const int slot = (int)(s % kTcStages);
           const uint32_t ph = (uint32_t)((s / kTcStages) & 1);
+          const int buf = (int)(s & 1);
+          if (s >= 2 && !(ok = bar_wait(&dempty[buf], (uint32_t)((s / 2 - 1) & 1), err, 1))) break;
           if (!(ok = bar_wait(&full_a[slot], ph, err, 2) && bar_wait(&full_b[slot], ph, err, 3))) break;
           tc_fence_after();
+          const uint32_t dhi = tmem + buf * 128, dlo = dhi + 64;
           const uint32_t base = saddr(sm + slot * kSlotBytes);
           // a 64-row panel reads its second M half from the zero page
           const uint32_t lbo_hi = P.halves == 2 ? (uint32_t)kPlaneBytes : zaddr - base;
@@ -257,55 +171,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
             const uint64_t ah = smem_desc(base + off, lbo_hi, 1024);
             const uint64_t bh = smem_desc(base + kSlotA + off, kPlaneBytes, 1024);
             const uint64_t bl = smem_desc(base + kSlotA + kPlaneBytes + off, kPlaneBytes, 1024);
-            const uint32_t acc = (kc | ks) != 0 ? 1u : 0u;
+            const uint32_t acc = ks != 0 ? 1u : 0u;
             mma_f16(dhi, ah, bh, acc);
             mma_f16(dlo, ah, bl, acc);
             if (P.pieces == 2) mma_f16(dlo, smem_desc(base + 2 * kPlaneBytes + off, lbo_lo, 1024), bh, 1u);
           }
           mma_commit(&empty[slot]);  // the slot is free once these MMAs have read it
+          mma_commit(&dfull[buf]);   // the chunk's sums are ready
         }
-        if (!ok) break;
-        mma_commit(&dfull[buf]);
       }
       // every MMA of this CTA has completed before its tensor memory is freed
       mma_commit(&fin);
       bar_wait(&fin, 0, err, 4);
     }
-  } else if (warp < 4) {
+  } else if (warp < 4 || warp >= 8) {
     // B operand: rows of kTcR FP32 values, scaled per column, split into FP16
     // high and low planes in the 128-byte swizzled layout (16-byte chunk c of
-    // row r at chunk c ^ (r & 7))
-    const int ct = tid - 64;             // 0 .. 63
-    const int q4 = ct & 15;              // this thread's four columns 4 q4 .. 4 q4 + 3
+    // row r at chunk c ^ (r & 7)); four warps, eight 4-column items per thread
+    const int ct = warp < 4 ? tid - 64 : tid - 192;  // 0 .. 127
+    const int q4 = ct & 15;                          // this thread's four columns 4 q4 .. 4 q4 + 3
     int64_t s = 0;
     for (int p = p0; p < p1 && ok; ++p) {
       const TcPanel P = a.panels[p];
       const float wb = VMODE ? 1.f : a.wbox[P.sbox];
-      float inv[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) inv[j] = 1.f / (wb * sx[4 * q4 + j]);  // powers of two: exact
+      float2 inv01, inv23;  // powers of two: exact
+      inv01.x = 1.f / (wb * sx[4 * q4]);
+      inv01.y = 1.f / (wb * sx[4 * q4 + 1]);
+      inv23.x = 1.f / (wb * sx[4 * q4 + 2]);
+      inv23.y = 1.f / (wb * sx[4 * q4 + 3]);
       const int nk = (P.K + kTcKC - 1) / kTcKC;
       for (int kc = 0; kc < nk; ++kc, ++s) {
         const int slot = (int)(s % kTcStages);
-        if (s >= kTcStages && !(ok = bar_wait(&empty[slot], (uint32_t)((s / kTcStages - 1) & 1), err, 5))) break;
+        // the slot's loads have landed (the producer issued them after the
+        // slot's previous MMAs had released it)
+        if (!(ok = bar_wait(&full_a[slot], (uint32_t)((s / kTcStages) & 1), err, 5))) break;
         unsigned char* bh = sm + slot * kSlotBytes + kSlotA;
         unsigned char* bl = bh + kPlaneBytes;
-        for (int it = ct; it < kTcKC * 16; it += 64) {
-          const int r = it >> 4, k = kc * kTcKC + r;
+        const float* b32 = reinterpret_cast<const float*>(bl + kPlaneBytes);
+        const int kv = P.kvalid - kc * kTcKC;  // rows with data in this chunk
+#pragma unroll 4
+        for (int it = ct; it < kTcKC * 16; it += 128) {
+          const int r = it >> 4;
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (k < P.kvalid) v = *reinterpret_cast<const float4*>(a.B + (int64_t)(P.brow + k) * kTcR + 4 * q4);
-          __half h0, h1, h2, h3, l0, l1, l2, l3;
-          split_f16(v.x * inv[0], h0, l0);
-          split_f16(v.y * inv[1], h1, l1);
-          split_f16(v.z * inv[2], h2, l2);
-          split_f16(v.w * inv[3], h3, l3);
+          if (r < kv) v = *reinterpret_cast<const float4*>(b32 + r * kTcR + 4 * q4);
+          const float2 a01 = make_float2(v.x * inv01.x, v.y * inv01.y);
+          const float2 a23 = make_float2(v.z * inv23.x, v.w * inv23.y);
+          const __half2 h01 = __float22half2_rn(a01), h23 = __float22half2_rn(a23);
+          const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+          const __half2 l01 = __float22half2_rn(make_float2((a01.x - f01.x) * kLoScale, (a01.y - f01.y) * kLoScale));
+          const __half2 l23 = __float22half2_rn(make_float2((a23.x - f23.x) * kLoScale, (a23.y - f23.y) * kLoScale));
           const int phys = r * 128 + ((((q4 >> 1) ^ (r & 7))) << 4) + (q4 & 1) * 8;
           *reinterpret_cast<uint2*>(bh + phys) =
-              make_uint2((uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16),
-                         (uint32_t)__half_as_ushort(h2) | ((uint32_t)__half_as_ushort(h3) << 16));
+              make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
           *reinterpret_cast<uint2*>(bl + phys) =
-              make_uint2((uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16),
-                         (uint32_t)__half_as_ushort(l2) | ((uint32_t)__half_as_ushort(l3) << 16));
+              make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
         __syncwarp();
@@ -313,20 +232,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
       }
     }
   } else {
-    // epilogue: tensor-memory lanes 32 qw .. 32 qw + 31 = D rows of this warp
+    // epilogue: tensor-memory lanes 32 qw .. 32 qw + 31 = D rows of this warp;
+    // each K chunk's D_hi + 2^-11 D_lo is added into the row's running sums
     const int qw = warp - 4;
     const int r = qw * 32 + lane;
-    int64_t q = 0;
-    for (int p = p0; p < p1 && ok; ++p, ++q) {
+    int64_t s = 0;
+    for (int p = p0; p < p1 && ok; ++p) {
       const TcPanel P = a.panels[p];
-      const int buf = (int)(q & 1);
-      if (!(ok = bar_wait(&dfull[buf], (uint32_t)((q / 2) & 1), err, 6))) break;
-      tc_fence_after();
-      const uint32_t dhi = tmem + buf * 128 + ((uint32_t)(qw * 32) << 16), dlo = dhi + 64;
-      const bool live = r < P.mvalid;
+      const int nk = (P.K + kTcKC - 1) / kTcKC;
+      // the row's output address and scale, loaded before the chunks arrive
       float* dst = nullptr;
-      float f = 1.f;
-      if (live) {
+      float f = 0.f;
+      if (r < P.mvalid) {
         if constexpr (VMODE) {
           const int32_t t = a.vmap[P.out0 + r];
           f = a.fac[t];
@@ -337,27 +254,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
                             : a.out + ((int64_t)P.slice * a.N + P.out0 + r) * kTcR;
         }
       }
+      float tot[kTcR];
 #pragma unroll
-      for (int c0 = 0; c0 < kTcR; c0 += 16) {
-        float hv[16], lv[16];
-        tmem_ld16(dhi + c0, hv);
-        tmem_ld16(dlo + c0, lv);
-        tmem_wait_ld();
-        if (live) {
+      for (int i = 0; i < kTcR; ++i) tot[i] = 0.f;
+      for (int kc = 0; kc < nk; ++kc, ++s) {
+        const int buf = (int)(s & 1);
+        if (!(ok = bar_wait(&dfull[buf], (uint32_t)((s / 2) & 1), err, 6))) break;
+        tc_fence_after();
+        const uint32_t dhi = tmem + buf * 128 + ((uint32_t)(qw * 32) << 16), dlo = dhi + 64;
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            float4 o;
-            o.x = f * sx[c0 + j] * fmaf(lv[j], 1.f / kLoScale, hv[j]);
-            o.y = f * sx[c0 + j + 1] * fmaf(lv[j + 1], 1.f / kLoScale, hv[j + 1]);
-            o.z = f * sx[c0 + j + 2] * fmaf(lv[j + 2], 1.f / kLoScale, hv[j + 2]);
-            o.w = f * sx[c0 + j + 3] * fmaf(lv[j + 3], 1.f / kLoScale, hv[j + 3]);
-            *reinterpret_cast<float4*>(dst + c0 + j) = o;
-          }
+        for (int c0 = 0; c0 < kTcR; c0 += 16) {
+          float hv[16], lv[16];
+          tmem_ld16(dhi + c0, hv);
+          tmem_ld16(dlo + c0, lv);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[c0 + j] += fmaf(lv[j], 1.f / kLoScale, hv[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(&dempty[buf]);
+      }
+      if (!ok) break;
+      if (r < P.mvalid) {
+#pragma unroll
+        for (int j = 0; j < kTcR; j += 4) {
+          float4 o;
+          o.x = f * sx[j] * tot[j];
+          o.y = f * sx[j + 1] * tot[j + 1];
+          o.z = f * sx[j + 2] * tot[j + 2];
+          o.w = f * sx[j + 3] * tot[j + 3];
+          *reinterpret_cast<float4*>(dst + j) = o;
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) bar_arrive(&dempty[buf]);
     }
   }
   tc_fence_before();
@@ -846,8 +775,12 @@ int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStrea
     HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
     HD_CUDA(cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * kTcR * sizeof(float), h->aux));
-    for (int cx = 0; cx < kTcR; cx += 16)
-      if (cx < nr) HD_TRY(launch_tiles_nr(h, h->aux, xt, 16, kTcR, cx));
+    if (tc_near_supported(h)) {
+      HD_TRY(launch_tc_near(h, h->aux, xt, colmax));
+    } else {
+      for (int cx = 0; cx < kTcR; cx += 16)
+        if (cx < nr) HD_TRY(launch_tiles_nr(h, h->aux, xt, 16, kTcR, cx));
+    }
     if (prof) HD_CUDA(cudaEventRecord(ev[6], h->aux));
     HD_CUDA(cudaEventRecord(h->ev_join, h->aux));
     HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)slices * h->N * kTcR * sizeof(float), st));

@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 FP32_BOUND = 2e-6       # stored FP32 factors, one or two right-hand sides
 FP32_WIDE_BOUND = 5e-6  # chunks of 4-16 right-hand sides (uncompensated applies)
 SKELETON_FP32_BOUND = 5e-6
+TC_BOUND = 5e-6          # the tensor-core form (FP16 high / scaled-low pairs, FP32 accumulation)
 
 
 @pytest.fixture(scope="module")
@@ -110,3 +111,29 @@ def test_many_rhs_workload_d4_n65536(env):
         torch.cuda.synchronize()
         assert relerr(yn[:, c : c + 1], yc.cpu().numpy()) <= 2 * FP32_WIDE_BOUND
     h.close()
+
+
+def test_many_rhs_workload_tensor_cores(env):
+    """The same workload in the tensor-core form the benchmark times: sampled rows
+    against the oracle's direct FP64 sum, every row against the FP32 CUDA-core
+    form, and bitwise determinism."""
+    torch, oracle, hd = env
+    w = W.many_rhs_4d()
+    pts = torch.from_numpy(w.points).cuda()
+    ranges = sample_rows(w.N, n_ranges=2, width=32, seed=12)
+    yd = direct_rows(oracle, w, ranges)
+    x = torch.from_numpy(np.ascontiguousarray(w.x, dtype=np.float32)).cuda()
+    ht = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp16x2")
+    y1 = ht.matvec(x)
+    y2 = ht.matvec(x)
+    torch.cuda.synchronize()
+    ht.sync()
+    assert torch.equal(y1, y2)
+    yt = y1.cpu().numpy()
+    ht.close()
+    assert relerr(pick(yt, ranges), yd) <= 10 * w.tol + TC_BOUND
+    h32 = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp32", max_nrhs=w.nrhs)
+    y32 = h32.matvec(x)
+    torch.cuda.synchronize()
+    assert relerr(yt, y32.cpu().numpy()) <= TC_BOUND + FP32_WIDE_BOUND
+    h32.close()
