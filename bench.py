@@ -306,7 +306,10 @@ def many_rhs_line(args, torch, stream, hd, peaks=None):
                        f"nrhs {w.nrhs}", "precision": "fp16x2"}
     res = {}
     for prec in ("fp16x2", "fp32", "fp64"):
-        h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, max_nrhs=w.nrhs)
+        # the tensor-core form streams the coarse full-rank blocks as factors
+        # (dense-if-cheaper at the leaf level only); the others keep the default rule
+        h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=prec, max_nrhs=w.nrhs,
+                      dense_if_cheaper="leaf" if prec == "fp16x2" else True)
         io = torch.float64 if prec == "fp64" else torch.float32
         x = torch.from_numpy(np.ascontiguousarray(w.x)).to(io).cuda()
         y = torch.empty_like(x)

@@ -95,7 +95,11 @@ typedef struct hodlrdd_options {
                            as many numbers as the block, p (m + n) >= m n, is applied
                            exactly by evaluating the kernel on the fly (no storage).
                            0: every IL block is applied through its ACA factors, as
-                           in Algorithm 2. */
+                           in Algorithm 2.
+                           2: the rule holds at the leaf level only; coarser IL
+                           blocks keep their ACA factors whatever their rank (for the
+                           tensor-core form, which streams a factor entry in less time
+                           than it evaluates a kernel entry on the fly). */
   int max_nrhs;         /* >= 1 (default 8). Right-hand sides are processed in chunks
                            through a workspace sized at build: chunks of up to 16 for
                            FP32 handles with d <= 4 when max_nrhs >= 16, else up to 8;

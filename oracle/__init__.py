@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 FLAG_DENSE_IF_CHEAPER = 1
+FLAG_DENSE_LEAF_ONLY = 2
 
 _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 _u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
@@ -156,7 +157,9 @@ class Tree:
         self.kernel = int(kernel)
         self.params = _params(params)
         h = C.c_void_p()
-        flags = FLAG_DENSE_IF_CHEAPER if dense_if_cheaper else 0
+        # dense_if_cheaper: False / True, or "leaf" (the rule at the leaf level only)
+        flags = (FLAG_DENSE_IF_CHEAPER | FLAG_DENSE_LEAF_ONLY if dense_if_cheaper == "leaf"
+                 else FLAG_DENSE_IF_CHEAPER if dense_if_cheaper else 0)
         rc = lib.or_build_ex(pts, self.d, self.N, self.kernel, self.params, int(leaf), float(tol), flags,
                              int(admissible_face_dim), C.byref(h))
         if rc:

@@ -43,7 +43,7 @@ enum {
   K_INV_R2_4D = 5, K_R = 6, K_SIN = 7, K_INV_SQRT1P = 8, K_COUNT = 9
 };
 
-enum { FLAG_DENSE_IF_CHEAPER = 1 };
+enum { FLAG_DENSE_IF_CHEAPER = 1, FLAG_DENSE_LEAF_ONLY = 2 };
 
 struct Kern {
   int id;
@@ -453,7 +453,10 @@ void compress(Tree& T) {
     const int64_t* rows = &T.perm[B.I0];
     const int64_t* cols = &T.perm[B.J0];
     auto A = [&](int64_t i, int64_t j) { return T.P.entry(rows[i], cols[j]); };
-    aca(A, B.m, B.n, T.tol, T.flags, B);
+    // with FLAG_DENSE_LEAF_ONLY the storage rule holds at the leaf level only
+    int fl = T.flags;
+    if ((fl & FLAG_DENSE_LEAF_ONLY) && B.level < T.kappa) fl &= ~FLAG_DENSE_IF_CHEAPER;
+    aca(A, B.m, B.n, T.tol, fl, B);
   }
 }
 

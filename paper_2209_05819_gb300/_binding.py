@@ -218,7 +218,8 @@ class Handle:
         opt = Options()
         lib.hodlrdd_options_default(C.byref(opt))
         opt.precision = PREC[precision]
-        opt.dense_if_cheaper = 1 if dense_if_cheaper else 0
+        # True / False, or "leaf": the rule at the leaf level only (coarser blocks keep their factors)
+        opt.dense_if_cheaper = 2 if dense_if_cheaper == "leaf" else 1 if dense_if_cheaper else 0
         opt.max_nrhs = int(max_nrhs)
         opt.aca_max_rank = int(aca_max_rank)
         opt.near_mode = int(near_mode)

@@ -33,6 +33,7 @@ struct AcaArgs {
   int kid;
   double scale, p0, tol;
   int dense_if_cheaper;
+  const int8_t* dic_blk;  // per block: the dense-if-cheaper rule applies (null: dense_if_cheaper for all)
   const int32_t *I0, *m, *J0, *n;
   const int32_t* list;  // blocks of this bin, largest first
   int32_t nlist;
@@ -192,6 +193,7 @@ __device__ void aca_block(const Team& T, const AcaArgs& A, int32_t b, double* Us
   int k = 0, nused = 0, istar = 0;
   double Sf = 0.0;
   bool dense = false, capped = false;
+  const bool dic = A.dic_blk ? A.dic_blk[b] != 0 : A.dense_if_cheaper != 0;
   double xr[kMaxDim];
   while (true) {
     for (int c = 0; c < d; ++c) xr[c] = A.pts[(size_t)c * A.N + I0 + istar];
@@ -257,7 +259,7 @@ __device__ void aca_block(const Team& T, const AcaArgs& A, int32_t b, double* Us
     Sf = Sf + 2.0 * cross + uu * vv;
     ++k;
     T.sync();
-    if (A.dense_if_cheaper && (int64_t)k * (m + n) >= (int64_t)m * n) { dense = true; break; }
+    if (dic && (int64_t)k * (m + n) >= (int64_t)m * n) { dense = true; break; }
     if (sqrt(uu) * sqrt(vv) <= A.tol * sqrt(fmax(Sf, 0.0))) break;
     if (k == kmax) break;
     if (k == A.rcap) { dense = true; capped = true; break; }
@@ -375,7 +377,12 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
   }
   int dev_sms = 0;
   HD_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
-  const bool dic = h->opt.dense_if_cheaper != 0;
+  // dense_if_cheaper 2: the rule holds at the leaf level only, coarser blocks keep their factors
+  const int dmode = h->opt.dense_if_cheaper;
+  std::vector<int8_t> hdic((size_t)std::max<int64_t>(nblk, 1), 0);
+  for (int64_t b = 0; b < nblk; ++b) hdic[b] = dmode == 1 || (dmode == 2 && h->h_blevel[b] == h->kappa) ? 1 : 0;
+  DevBuf<int8_t> ddic;
+  HD_TRY(upload(ddic, hdic, h->st));
   for (auto& B : bins) {
     if (B.list.empty()) continue;
     std::sort(B.list.begin(), B.list.end(), [&](int32_t a, int32_t c) {
@@ -384,7 +391,7 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
     });
     for (int32_t b : B.list) {
       int64_t m = h->h_bm[b], n = h->h_bn[b];
-      int64_t natural = dic ? (m * n + (m + n) - 1) / (m + n) : std::min(m, n);
+      int64_t natural = hdic[b] ? (m * n + (m + n) - 1) / (m + n) : std::min(m, n);
       B.rcap = std::max<int>(B.rcap, (int)natural);
       B.mcap = std::max<int>(B.mcap, (int)m);
       B.ncap = std::max<int>(B.ncap, (int)n);
@@ -453,7 +460,8 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
   base.scale = h->K.scale;
   base.p0 = h->K.p0;
   base.tol = h->tol;
-  base.dense_if_cheaper = dic ? 1 : 0;
+  base.dense_if_cheaper = dmode == 1 ? 1 : 0;
+  base.dic_blk = ddic.p;
   base.I0 = h->bI0.p;
   base.m = h->bm.p;
   base.J0 = h->bJ0.p;

@@ -1352,6 +1352,7 @@ int build_plan(hodlrdd_s* h) {
   // hands CTAs out in order, so the long tasks start first (each task owns
   // its rows, so the order changes no sum)
   auto sort_tasks = [&](int64_t a, int64_t b) {
+    if (!tc_tiles) return;  // the CUDA-core tiles keep tree order (they run beside the applies)
     std::vector<std::pair<int64_t, int4>> w;
     w.reserve((size_t)(b - a));
     for (int64_t t = a; t < b; ++t) {

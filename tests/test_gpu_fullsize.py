@@ -123,7 +123,7 @@ def test_many_rhs_workload_tensor_cores(env):
     ranges = sample_rows(w.N, n_ranges=2, width=32, seed=12)
     yd = direct_rows(oracle, w, ranges)
     x = torch.from_numpy(np.ascontiguousarray(w.x, dtype=np.float32)).cuda()
-    ht = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp16x2")
+    ht = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp16x2", dense_if_cheaper="leaf")
     y1 = ht.matvec(x)
     y2 = ht.matvec(x)
     torch.cuda.synchronize()

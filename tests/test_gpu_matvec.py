@@ -333,3 +333,19 @@ def test_matvec_any_admissibility(env, d, amax):
         y32 = gpu_matvec(h32, w.x)
         h32.sync()
         assert relerr(y32, y64) <= MIXED_BOUND["fp32"], mode
+
+
+@pytest.mark.parametrize("d,N,kernel,params,leaf,tol", [(3, 8000, W.K_MATERN32, (1, 0, 0.3, 0), 32, 1e-8),
+                                                         (2, 6000, W.K_LOG, None, 32, 1e-10)])
+def test_dense_rule_leaf_only_fp64(env, d, N, kernel, params, leaf, tol):
+    """dense_if_cheaper="leaf" (coarse blocks keep their factors): the GPU FP64
+    product against the oracle's HODLRdD product built with the same rule."""
+    torch, oracle, hd = env
+    w = W.make("t", d, N, kernel, params or (1, 0, 0, 0), leaf, tol, nrhs=2, seed=N + 9)
+    T = oracle.Tree(w.points, w.kernel, w.params, leaf, tol, dense_if_cheaper="leaf")
+    h = gpu_handle(hd, w, dense_if_cheaper="leaf")
+    rec = h.blocks()
+    assert not rec[rec[:, 0] < h.stats()["kappa"], 8].any()
+    yg = gpu_matvec(h, w.x)
+    assert relerr(yg, oracle.direct(w.points, w.kernel, w.params, w.x)) <= 10 * tol
+    assert_matches_oracle_hodlrdd(oracle, T, h, w, yg, tol, kernel)

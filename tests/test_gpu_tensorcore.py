@@ -110,6 +110,21 @@ def test_second_kind_and_uneven_clusters(env):
     assert err <= TC_BOUND, err
 
 
+@pytest.mark.parametrize("nrhs", [1, 64])
+def test_dense_rule_leaf_only(env, nrhs):
+    """The tensor-core form with dense_if_cheaper="leaf" (coarse admissible
+    blocks streamed as factors, the leaf level evaluated on the fly) against
+    the FP64 form built with the same rule."""
+    torch, oracle, hd = env
+    w = W.make("t", 3, 8000, W.K_MATERN32, (1, 0, 0.3, 0), 32, 1e-8, nrhs=nrhs, seed=90 + nrhs)
+    h64 = gpu_handle(hd, w, dense_if_cheaper="leaf")
+    ht = gpu_handle(hd, w, precision="fp16x2", dense_if_cheaper="leaf")
+    assert np.array_equal(h64.blocks(), ht.blocks())
+    err = relerr(gpu_matvec(ht, w.x), gpu_matvec(h64, w.x))
+    ht.sync()
+    assert err <= TC_BOUND, err
+
+
 def test_rejected_configurations(env):
     torch, oracle, hd = env
     w5 = W.make("t", 5, 1500, W.K_GAUSS, (1, 0, 0.5, 0), 32, 1e-6, nrhs=1, seed=2)

@@ -79,3 +79,22 @@ def test_identity_shift_and_columns(oracle_mod):
     assert np.allclose(y - T0.matvec(w.x), w.x, rtol=0, atol=1e-13)
     for c in range(3):
         assert np.array_equal(T.matvec(w.x[:, c])[:, 0], y[:, c])
+
+
+def test_dense_rule_at_the_leaf_level_only(oracle_mod):
+    """dense_if_cheaper="leaf": the storage rule marks blocks dense at the leaf
+    level only; every coarser IL block keeps its ACA factors (rank up to
+    min(m, n)), and the product still meets the tolerance against the direct sum."""
+    import workloads as W
+
+    w = W.make("t", 3, 8000, W.K_MATERN32, (1, 0, 0.3, 0), 32, 1e-8, nrhs=2, seed=21)
+    T = oracle_mod.Tree(w.points, w.kernel, w.params, w.leaf, w.tol, dense_if_cheaper="leaf")
+    rec = T.blocks()
+    coarse = rec[:, 0] < T.kappa
+    assert coarse.any() and not rec[coarse, 8].any()
+    Tall = oracle_mod.Tree(w.points, w.kernel, w.params, w.leaf, w.tol, dense_if_cheaper=True)
+    assert np.array_equal(rec[~coarse, 7:9], Tall.blocks()[~coarse, 7:9])  # the leaf level is unchanged
+    assert Tall.blocks()[coarse, 8].any()  # the plain rule would have made some coarse block dense
+    yd = oracle_mod.direct(w.points, w.kernel, w.params, w.x)
+    err = np.max(np.linalg.norm(T.matvec(w.x) - yd, axis=0) / np.linalg.norm(yd, axis=0))
+    assert err <= 10 * w.tol
