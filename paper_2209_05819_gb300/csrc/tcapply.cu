@@ -46,11 +46,11 @@ namespace {
 
 constexpr int kTcThreads = 320;
 constexpr int kTcKC = 64;                   // K rows per ring slot
-constexpr int kTcStages = 3;                // ring slots
+constexpr int kTcStages = 4;                // ring slots
 constexpr int kPlaneBytes = kTcKC * 128;    // one 64-row plane of 128-byte rows
 constexpr int kSlotA = 4 * kPlaneBytes;     // (piece, half) planes
-constexpr int kSlotB32 = kTcKC * kTcR * 4;    // the chunk's FP32 B rows, bulk-copied
-constexpr int kSlotBytes = kSlotA + 2 * kPlaneBytes + kSlotB32;  // + B high and low planes + FP32 B rows
+constexpr int kSlotB32 = kTcKC * kTcR * 4;    // the chunk's FP32 B rows, bulk-copied, then converted in place
+constexpr int kSlotBytes = kSlotA + kSlotB32;  // A planes + B (FP32 rows, then the FP16 high and low planes)
 constexpr int kZeroBytes = kPlaneBytes;     // zero half for 64-row panels
 constexpr int kTcSmem = kTcStages * kSlotBytes + kZeroBytes + 1024;
 constexpr int kTmemCols = 256;              // two buffers x (D_hi, D_lo) x 64 columns
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
           const int nb = max(0, min(kTcKC, P.kvalid - kc * kTcKC));
           bar_expect(&full_a[slot], (uint32_t)(P.pieces * P.halves * kPlaneBytes + nb * kTcR * 4));
           if (nb > 0)
-            bulk_load(base + kSlotA + 2 * kPlaneBytes, a.B + ((int64_t)P.brow + (int64_t)kc * kTcKC) * kTcR,
+            bulk_load(base + kSlotA, a.B + ((int64_t)P.brow + (int64_t)kc * kTcKC) * kTcR,
                       (uint32_t)(nb * kTcR * 4), &full_a[slot]);
           for (int pc = 0; pc < P.pieces; ++pc)
             for (int hh = 0; hh < P.halves; ++hh) {
@@ -207,15 +207,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_apply(const __grid_constan
         if (!(ok = bar_wait(&full_a[slot], (uint32_t)((s / kTcStages) & 1), err, 5))) break;
         unsigned char* bh = sm + slot * kSlotBytes + kSlotA;
         unsigned char* bl = bh + kPlaneBytes;
-        const float* b32 = reinterpret_cast<const float*>(bl + kPlaneBytes);
+        const float* b32 = reinterpret_cast<const float*>(bh);
         const int kv = P.kvalid - kc * kTcKC;  // rows with data in this chunk
-#pragma unroll 4
-        for (int it = ct; it < kTcKC * 16; it += 128) {
-          const int r = it >> 4;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (r < kv) v = *reinterpret_cast<const float4*>(b32 + r * kTcR + 4 * q4);
-          const float2 a01 = make_float2(v.x * inv01.x, v.y * inv01.y);
-          const float2 a23 = make_float2(v.z * inv23.x, v.w * inv23.y);
+        // all four warps read their FP32 items before any FP16 plane overwrites them
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = (ct >> 4) + 8 * j;
+          v[j] = r < kv ? *reinterpret_cast<const float4*>(b32 + r * kTcR + 4 * q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int r = (ct >> 4) + 8 * j;
+          const float2 a01 = make_float2(v[j].x * inv01.x, v[j].y * inv01.y);
+          const float2 a23 = make_float2(v[j].z * inv23.x, v[j].w * inv23.y);
           const __half2 h01 = __float22half2_rn(a01), h23 = __float22half2_rn(a23);
           const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
           const __half2 l01 = __float22half2_rn(make_float2((a01.x - f01.x) * kLoScale, (a01.y - f01.y) * kLoScale));
@@ -770,8 +776,15 @@ int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStrea
     k_tc_gather<<<grid, 256, 0, st>>>(x, h->perm.p, h->N, nrhs, c0, nr, xt, colmax);
     h->launches += 1;
     if (prof) HD_CUDA(cudaEventRecord(ev[1], st));
-    // near field on the aux stream (reads x_t only)
+    // the near field needs x_t only: it runs on the aux stream beside the
+    // applies; it is enqueued after the V-apply, so that the persistent
+    // apply CTAs are placed first and the near-field CTAs fill the room left
     HD_CUDA(cudaEventRecord(h->ev_fork, st));
+    HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)slices * h->N * kTcR * sizeof(float), st));
+    TcArgs av{P.tcv.panels.p, P.tcv.cta.p, xt, reinterpret_cast<const float*>(colmax), P.tc_vmap.p, P.tc_fac.p,
+              P.tc_wbox.p, t, nullptr, h->N};
+    HD_TRY(tc_stage(true, P.tcv, av, h->err.p, st));
+    h->launches += P.tcv.h_panels.empty() ? 0 : 1;
     HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
     HD_CUDA(cudaMemsetAsync(h->ynear.p, 0, (size_t)h->N * kTcR * sizeof(float), h->aux));
@@ -783,11 +796,6 @@ int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStrea
     }
     if (prof) HD_CUDA(cudaEventRecord(ev[6], h->aux));
     HD_CUDA(cudaEventRecord(h->ev_join, h->aux));
-    HD_CUDA(cudaMemsetAsync(yl, 0, (size_t)slices * h->N * kTcR * sizeof(float), st));
-    TcArgs av{P.tcv.panels.p, P.tcv.cta.p, xt, reinterpret_cast<const float*>(colmax), P.tc_vmap.p, P.tc_fac.p,
-              P.tc_wbox.p, t, nullptr, h->N};
-    HD_TRY(tc_stage(true, P.tcv, av, h->err.p, st));
-    h->launches += P.tcv.h_panels.empty() ? 0 : 1;
     if (prof) HD_CUDA(cudaEventRecord(ev[2], st));
     TcArgs au{P.tcu.panels.p, P.tcu.cta.p, t, reinterpret_cast<const float*>(colmax), P.tc_vmap.p, P.tc_fac.p,
               P.tc_wbox.p, yl, pb, h->N};
