@@ -55,6 +55,10 @@ def parse():
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
+    p.add_argument("--only", default=None, choices=["many_rhs"],
+                   help="run only this workload's products (--steps of them after --warmup) and print its line; "
+                        "for profiling")
+    p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
     return p.parse_args()
 
 
@@ -628,10 +632,35 @@ def optional_line(fn, *a):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+def many_rhs_only(args):
+    """Products of the many-right-hand-side workload in the tensor-core form only
+    (d=4, Matern-3/2, leaf 128, tol 1e-8, 64 columns; N = --many-n)."""
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    import workloads as W
+    from paper_2209_05819_gb300 import build as cbuild
+
+    cbuild.build()
+    w = W.many_rhs_4d(N=args.many_n, seed=args.seed)
+    h = hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision="fp16x2",
+                  dense_if_cheaper="leaf")
+    x = torch.from_numpy(np.ascontiguousarray(w.x, dtype=np.float32)).cuda()
+    y = torch.empty_like(x)
+    t = time_steps(lambda: h.matvec(x, y), max(args.steps, 1), args.warmup, torch, torch.cuda.current_stream())
+    h.sync()
+    s = h.stats()
+    print(json.dumps({"workload": f"d=4 N={w.N} Matern-3/2 leaf {w.leaf} tol {w.tol:g} nrhs {w.nrhs} fp16x2",
+                      "ms_per_matvec": 1e3 * t / max(args.steps, 1), "factor_gb": (s["factor_bytes_u"] +
+                      s["factor_bytes_v"]) / 1e9, "dense_pairs": s["dense_pairs"], "kappa": s["kappa"]}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "many_rhs":
+        return many_rhs_only(args)
     import torch
 
     import paper_2209_05819_gb300 as hd
