@@ -287,13 +287,42 @@ def cpu_baseline(args, rank_w):
     t0 = time.perf_counter()
     oracle.direct(ws.points, ws.kernel, ws.params, ws.x, (0, nrow))
     t_dir = (time.perf_counter() - t0) * ws.N / nrow
+    # the plain FP64 configuration (d=2, N=4096, log r) in full on the oracle
+    c1 = W.plain_fp64_2d()
+    T1 = oracle.Tree(c1.points, c1.kernel, c1.params, c1.leaf, c1.tol, dense_if_cheaper=True)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        T1.matvec(c1.x)
+    t_c1 = (time.perf_counter() - t0) / 5
     extra = {"single_core_value": ws.N * ws.nrhs / t1, "direct_value": ws.N * ws.nrhs / t_dir,
-             "machine": f"{os.uname().machine}, {cores} threads"}
+             "plain_fp64_c1_value": c1.N / t_c1, "machine": f"{os.uname().machine}, {cores} threads"}
     return {"value": ws.N * ws.nrhs / t, "unit": UNIT, "cores": cores, "kind": "oracle", "sample_n": ws.N, **extra,
             "sample": f"oracle FP64 HODLRdD on a {ws.N}-point draw of the same distribution (d={ws.d}, 1/r, "
                       f"leaf {ws.leaf}, tol {ws.tol:g}); matvec median of {len(times)} runs; build {t_build:.1f} s; "
                       f"single_core_value: one matvec on one thread; direct_value: the oracle's direct sum on "
                       f"{nrow} rows scaled to all rows"}
+
+
+def plain_fp64_line(args, torch, stream, hd, peaks):
+    """The plain FP64 configuration (d=2, N=4096 uniform [-1,1]^2, log r with a
+    zero diagonal, leaf 64, tol 1e-8, one right-hand side): product time and its
+    fraction of the measured FP64 rate."""
+    import workloads as W
+
+    w = W.plain_fp64_2d()
+    h = hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision="fp64")
+    x = torch.from_numpy(np.ascontiguousarray(w.x)).cuda()
+    y = torch.empty_like(x)
+    n = 200
+    t = time_steps(lambda: h.matvec(x, y), n, 10, torch, stream) / n
+    s = h.stats()
+    h.close()
+    out = {"workload": f"d=2 N={w.N} uniform [-1,1]^2, F=log r (zero diagonal), leaf {w.leaf}, tol {w.tol:g}, nrhs 1",
+           "precision": "fp64", "ms_per_matvec": 1e3 * t, "value": w.N / t, "unit": UNIT,
+           "roofline": fp64_roofline(s, w.d, 1, t, peaks)}
+    out["note"] = ("a 4096-point tree is latency-bound: " + str(s["kappa"]) + " levels, "
+                   + str(s["n_blocks"]) + " blocks, about a dozen dependent launches per product")
+    return out
 
 
 def many_rhs_line(args, torch, stream, hd, peaks=None):
@@ -794,6 +823,11 @@ def main():
     roof["near"] = near_roofline(s, w.d, nrhs, stage["near"] / 1e3, peaks)
     roof["fp64"] = fp64["roofline"] if fp64 else None
 
+    # the plain FP64 configuration (d=2, N=4096, log r)
+    c1 = None
+    if rank == 0 and world == 1:
+        c1 = optional_line(plain_fp64_line, args, torch, stream, hd, peaks)
+
     # many right-hand sides (d=4, N=65536, Matern-3/2, leaf 128, tol 1e-8, nrhs 64)
     many = None
     if rank == 0 and world == 1 and not args.no_many_rhs and args.precision != "fp64":
@@ -844,6 +878,7 @@ def main():
             "rel_err_vs_fp64": err, "meets_err_bar": (err is not None and err <= ERR_BAR),
             "fp64": fp64, "speedup_vs_fp64": (value / (fp64["value"] * world)) if fp64 else None,
             "direct_gpu": direct,
+            "plain_fp64_c1": c1,
             "many_rhs": many,
             "skeleton": skel,
             "admissibility": adm,

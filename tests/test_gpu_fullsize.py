@@ -79,7 +79,8 @@ def test_benchmark_workload_d3_n262144(env):
     torch.cuda.synchronize()
     assert torch.equal(m1, m2)
     ymn = m1.cpu().numpy()
-    assert relerr(ymn, y64n) <= 1e-6
+    # measured 2.6e-7: a defect in the FP16 tail adding 5e-7 of error fails here
+    assert relerr(ymn, y64n) <= 5e-7
     assert relerr(pick(ymn, ranges), yd) <= 10 * w.tol + FP32_BOUND
     hm.close()
     # the skeleton form on the same workload
