@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
-    p.add_argument("--only", default=None, choices=["many_rhs"],
+    p.add_argument("--only", default=None, choices=["many_rhs", "batch"],
                    help="run only this workload's products (--steps of them after --warmup) and print its line; "
                         "for profiling")
     p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
@@ -613,6 +613,40 @@ def batch_line(args, torch, hd):
         lat.sort()
         out[name] = {"value": units / (statistics.median(lat) / 1e3), "unit": UNIT, "p50_ms": lat[len(lat) // 2],
                      "p99_ms": lat[-1]}
+    # the forest: the same 48 sets in the tensor-core form, merged into one
+    # launch per stage (64 columns wide, so every set's 1..16 columns ride along)
+    t0 = time.perf_counter()
+    ht = [hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision="fp16x2",
+                    max_nrhs=64, dense_if_cheaper="leaf") for w in ws]
+    f = hd.Forest(ht, [w.nrhs for w in ws])
+    t_forest = time.perf_counter() - t0
+    yf = [torch.empty_like(x) for x in xs]
+    for _ in range(3):
+        f.run(xs, yf)
+    lat = []
+    for _ in range(20):
+        t0 = time.perf_counter()
+        f.run(xs, yf)
+        lat.append(1e3 * (time.perf_counter() - t0))
+    lat.sort()
+    # errors against plain FP64 on every eighth set
+    errs = []
+    for i in range(0, len(ws), 8):
+        w = ws[i]
+        h64 = hd.Handle(torch.from_numpy(w.points).cuda(), w.kernel, w.params, w.leaf, w.tol, precision="fp64")
+        y64 = h64.matvec(torch.from_numpy(np.ascontiguousarray(w.x)).cuda())
+        e = torch.linalg.norm(yf[i].double() - y64, dim=0) / torch.linalg.norm(y64, dim=0)
+        errs.append(float(e.max().item()))
+        h64.close()
+    fs = f.stats()
+    out["forest_fp16x2"] = {"value": units / (statistics.median(lat) / 1e3), "unit": UNIT,
+                            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[-1], "build_s": t_forest,
+                            "launches_per_run": fs["launches_per_run"], "near_passes": fs["near_passes"],
+                            "rel_err_vs_fp64_max": max(errs), "err_sets": len(errs),
+                            "speedup_vs_batch_graph": out["batch_graph"]["p50_ms"] / lat[len(lat) // 2]}
+    f.close()
+    for h in ht:
+        h.close()
     b.close()
     for h in hs:
         h.close()
@@ -684,12 +718,26 @@ def many_rhs_only(args):
                       s["factor_bytes_v"]) / 1e9, "dense_pairs": s["dense_pairs"], "kappa": s["kappa"]}))
 
 
+def batch_only(args):
+    """The uneven-instances line alone (48 clustered d=3 sets: one graph-replayed
+    batch, one forest run), for profiling."""
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import build as cbuild
+
+    cbuild.build()
+    print(json.dumps(batch_line(args, torch, hd)))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.only == "many_rhs":
         return many_rhs_only(args)
+    if args.only == "batch":
+        return batch_only(args)
     import torch
 
     import paper_2209_05819_gb300 as hd

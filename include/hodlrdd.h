@@ -339,6 +339,46 @@ int hodlrdd_batch_run(hodlrdd_batch b, const void* const* x, void* const* y, voi
 int hodlrdd_batch_destroy(hodlrdd_batch b);
 
 /*
+ * A forest: products over many trees of the tensor-core form (FP16X2) merged
+ * into one launch per stage. The paper's kernel-SVM experiment (numerical
+ * experiments, "HODLRdD accelerated classical kernel SVM") trains on several
+ * data sets of uneven size, each iteration one product K v per kernel matrix;
+ * a forest serves such a set of independent products with the launches of one
+ * tree: one gather, one V-apply and one U-apply over the
+ * panels of all trees (the persistent CTAs balanced over the whole forest),
+ * one near-field launch per pass (pass k holds the k-th near-field range of
+ * every tree) and one final sum.
+ *
+ * hodlrdd_forest_create
+ *  handles  count distinct handles, all of precision HODLRDD_PREC_FP16X2 with a
+ *           bounded kernel (not 1/r or 1/r^2), the same d (<= 4), kernel and
+ *           shape parameters (scale and diagonal may differ), on the current
+ *           device, none profiling. They must outlive the forest; the forest
+ *           copies their factor planes, panels and near-field tables, so a
+ *           later hodlrdd_import_factors on a handle does not reach it.
+ *  nrhs     right-hand sides of each tree's request, 1..64.
+ *  Errors: HODLRDD_ERR_INVALID (NULL, count < 1, a repeated handle, nrhs out of
+ *  range, profiling on), HODLRDD_ERR_UNSUPPORTED (another precision or kernel,
+ *  trees that differ in d or kernel, sizes beyond 32-bit panel indices),
+ *  HODLRDD_ERR_OOM, HODLRDD_ERR_CUDA.
+ * hodlrdd_forest_run
+ *  x[i], y[i]  host or device FP32, N_i x nrhs_i row-major, ORIGINAL point
+ *              order. Runs on the forest's own streams after the work already
+ *              queued on `stream`, and returns when y is written (synchronous).
+ *              Each y[i] equals hodlrdd_matvec on handle i up to the order of
+ *              FP32 additions (the same arithmetic on the same data).
+ *  HODLRDD_ERR_TIMEOUT when a bounded device-side wait expired (y invalid).
+ * hodlrdd_forest_stats
+ *  out[5] = total points, bytes of the factor planes (both stages), apply
+ *  panels, near-field passes, kernel launches per run.
+ */
+typedef struct hodlrdd_forest_s* hodlrdd_forest;
+int hodlrdd_forest_create(const hodlrdd_handle* handles, const int* nrhs, int count, hodlrdd_forest* out);
+int hodlrdd_forest_run(hodlrdd_forest f, const void* const* x, void* const* y, void* stream);
+int hodlrdd_forest_stats(hodlrdd_forest f, int64_t* out);
+int hodlrdd_forest_destroy(hodlrdd_forest f);
+
+/*
  * Waits for all device work (cudaDeviceSynchronize) and reports failures the
  * handle's matvec kernels recorded on the device: HODLRDD_ERR_TIMEOUT when one of
  * their bounded waits expired (the y of that matvec is then invalid). Clears the

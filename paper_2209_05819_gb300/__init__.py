@@ -8,6 +8,7 @@ CUDA library, there is no CPU fallback):
     Handle.stats()                                              ranks, sizes, phase times
     solve(inner, outer, b)                                      GMRES with FP64 refinement
     Batch(handles, nrhs).run(xs)                                graph-replayed batch of products
+    Forest(handles, nrhs).run(xs)                               FP16X2 trees merged, one launch per stage
     Server(budget).add / submit / wait                          request loop under an HBM budget
     probe_peaks()                                               measured FP32 / FP64 / MUFU throughput
 """
@@ -19,6 +20,7 @@ from ._binding import (  # noqa: F401
     ERR_OOM,
     ERR_TIMEOUT,
     ERR_UNSUPPORTED,
+    Forest,
     OK,
     PREC,
     REQ_MATVEC,

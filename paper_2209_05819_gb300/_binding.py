@@ -83,6 +83,10 @@ def load():
         "hodlrdd_batch_create": (i32, [C.POINTER(vp), C.POINTER(C.c_int), i32, C.POINTER(vp)]),
         "hodlrdd_batch_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
         "hodlrdd_batch_destroy": (i32, [vp]),
+        "hodlrdd_forest_create": (i32, [C.POINTER(vp), C.POINTER(C.c_int), i32, C.POINTER(vp)]),
+        "hodlrdd_forest_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
+        "hodlrdd_forest_stats": (i32, [vp, C.POINTER(i64)]),
+        "hodlrdd_forest_destroy": (i32, [vp]),
         "hodlrdd_solve_options_default": (i32, [C.POINTER(SolveOptions)]),
         "hodlrdd_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOptions), C.POINTER(SolveStats), vp]),
         "hodlrdd_destroy": (i32, [vp]),
@@ -473,6 +477,59 @@ class Batch:
         if getattr(self, "_b", None):
             self._lib.hodlrdd_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Forest:
+    """Products over many FP16X2 trees merged into one launch per stage."""
+
+    def __init__(self, handles, nrhs):
+        lib = load()
+        self._handles = list(handles)
+        n = len(self._handles)
+        hs = (C.c_void_p * n)(*[h._h for h in self._handles])
+        nr = (C.c_int * n)(*[int(k) for k in nrhs])
+        self.nrhs = [int(k) for k in nrhs]
+        f = C.c_void_p()
+        _check(lib.hodlrdd_forest_create(hs, nr, n, C.byref(f)), "hodlrdd_forest_create")
+        self._f = f
+        self._lib = lib
+
+    def run(self, xs, ys=None, stream=None):
+        """y_i = K_i x_i for every tree; xs / ys: FP32 numpy or torch arrays."""
+        n = len(self._handles)
+        if len(xs) != n or (ys is not None and len(ys) != n):
+            raise ValueError(f"one x (and y) per tree: {n}")
+        for i, (x, h) in enumerate(zip(xs, self._handles)):
+            _check_io(x, f"xs[{i}]", h.N, h.io_dtype, h.device)
+            if x.ndim == 2 and int(x.shape[1]) != self.nrhs[i] or x.ndim == 1 and self.nrhs[i] != 1:
+                raise ValueError(f"xs[{i}]: {self.nrhs[i]} right-hand sides expected")
+            if ys is not None:
+                _check_io(ys[i], f"ys[{i}]", h.N, h.io_dtype, h.device, like=x)
+        if ys is None:
+            ys = [np.empty(x.shape, dtype=h.io_dtype) if isinstance(x, np.ndarray) else x.new_empty(x.shape)
+                  for x, h in zip(xs, self._handles)]
+        keep = [_ptr(a) for a in list(xs) + list(ys)]
+        xp = (C.c_void_p * n)(*[keep[i][0] for i in range(n)])
+        yp = (C.c_void_p * n)(*[keep[n + i][0] for i in range(n)])
+        _check(self._lib.hodlrdd_forest_run(self._f, xp, yp, _stream_ptr(stream)), "hodlrdd_forest_run")
+        return ys
+
+    def stats(self):
+        out = (C.c_int64 * 5)()
+        _check(self._lib.hodlrdd_forest_stats(self._f, out), "hodlrdd_forest_stats")
+        keys = ("points", "plane_bytes", "panels", "near_passes", "launches_per_run")
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def close(self):
+        if getattr(self, "_f", None):
+            self._lib.hodlrdd_forest_destroy(self._f)
+            self._f = None
 
     def __del__(self):
         try:

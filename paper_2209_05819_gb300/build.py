@@ -34,6 +34,7 @@ SOURCES = {
     "probe.cu": [],
     "tcapply.cu": [],
     "tcnear.cu": [],
+    "forest.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

@@ -500,6 +500,27 @@ int64_t tc_device_bytes(const hodlrdd_s* h);
 bool tc_near_supported(const hodlrdd_s* h);
 inline bool tc_near_kernel(int kid) { return kid != HODLRDD_K_INV_R && kid != HODLRDD_K_INV_R2_4D; }
 int launch_tc_near(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigned int* colmax);
+int launch_tc_near_raw(int d, int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs,
+                       const float4* soff, const float4* Hi, const float4* Lo, const float* xt,
+                       const unsigned int* colmax, float kc, float* ynear, const int2* tbase, const float2* tsd,
+                       int32_t* err);
+// tensor-core applies and combine over an explicit panel set (tcapply.cu)
+struct TcLaunch {
+  const TcStream* S;
+  const float* B;
+  const unsigned int* colmax;
+  const int32_t* vmap;
+  const float* fac;
+  const float* wbox;
+  float* out;
+  float* part;
+  int64_t N;
+};
+int launch_tc_stage(bool vmode, const TcLaunch& L, int32_t* err, cudaStream_t st);
+int launch_tc_combine(int64_t nsplit, const int2* split, const int32_t* splitp, const TcPanel* panels,
+                      const float* part, int64_t N, float* ylev, cudaStream_t st);
+void tc_schedule_stream(TcStream& S, int ctas);
+int tc_encode_tmap(TcStream& S);
 // Near field (near.cu).
 constexpr int kGuard = 16;        // zero elements around xt and t (per right-hand side)
 constexpr int kTileThreads = 256; // threads of a near-field tile CTA

@@ -817,3 +817,28 @@ int launch_matvec_tc(hodlrdd_s* h, const float* x, float* y, int nrhs, cudaStrea
 }
 
 }  // namespace hd
+
+namespace hd {
+
+// One apply stage over an explicit panel set (a handle's, or a forest's).
+int launch_tc_stage(bool vmode, const TcLaunch& L, int32_t* err, cudaStream_t st) {
+  HD_TRY(set_tc_attr());
+  const TcStream& S = *L.S;
+  TcArgs a{S.panels.p, S.cta.p, L.B, reinterpret_cast<const float*>(L.colmax), L.vmap, L.fac, L.wbox, L.out, L.part,
+           L.N};
+  return tc_stage(vmode, S, a, err, st);
+}
+
+int launch_tc_combine(int64_t nsplit, const int2* split, const int32_t* splitp, const TcPanel* panels,
+                      const float* part, int64_t N, float* ylev, cudaStream_t st) {
+  if (nsplit <= 0) return HODLRDD_OK;
+  k_tc_combine<<<(int)std::min<int64_t>(nsplit, 65535), 256, 0, st>>>(nsplit, split, splitp, panels, part, N, ylev);
+  HD_CUDA(cudaGetLastError());
+  return HODLRDD_OK;
+}
+
+void tc_schedule_stream(TcStream& S, int ctas) { tc_schedule(S, ctas); }
+
+int tc_encode_tmap(TcStream& S) { return encode_tmap(S); }
+
+}  // namespace hd

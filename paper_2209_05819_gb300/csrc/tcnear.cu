@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
                                                             const float* __restrict__ xt,
                                                             const unsigned int* __restrict__ colmax, float kc,
                                                             float kscale, float kdiag, float* __restrict__ ynear,
+                                                            const int2* __restrict__ tbase,
+                                                            const float2* __restrict__ tsd,
                                                             int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char nr_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(nr_raw) + 1023) & ~uintptr_t(1023));
@@ -137,6 +139,13 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
 
   for (int64_t it = t0 + blockIdx.x; it < t1 && ok; it += gridDim.x) {
     const int4 T = tasks[it];
+    // forest launches: the task's coordinate and point bases, scale and diagonal
+    const int2 base = tbase ? tbase[it] : make_int2(0, 0);
+    const float2 sd = tsd ? tsd[it] : make_float2(kscale, kdiag);
+    const float4* __restrict__ Ht = Hi + base.x;
+    const float4* __restrict__ Lt = Lo + base.x;
+    const float* __restrict__ xb = xt + (int64_t)base.y * kTcR;
+    float* __restrict__ yb = ynear + (int64_t)base.y * kTcR;
     for (int r0 = 0; r0 < T.y && ok; r0 += 128) {
       const int mm = min(128, T.y - r0);
       // the thread's 8 targets (rows r0 + 8 ac + i of the task)
@@ -146,8 +155,8 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
       for (int i = 0; i < 8; ++i) {
         const int r = 8 * ac + i;
         tv[i] = r < mm;
-        th[i] = tv[i] ? Hi[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tl[i] = tv[i] && !kSmooth ? Lo[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        th[i] = tv[i] ? Ht[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tl[i] = tv[i] && !kSmooth ? Lt[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       int c = 0;  // chunks of this tile; chunk c accumulates into D(c & 1), added into the total two chunks later
       for (int w0 = T.z; w0 < T.w && ok; w0 += kNrEntWin) {
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
               const int4 sj = srcs[w0 + e];
               const float4 of = soff[w0 + e];
               row = sj.x + (k - s_pre[e]);
-              const float4 ph = Hi[row], pl = Lo[row];
+              const float4 ph = Ht[row], pl = Lt[row];
               float ex, ey, ez, ew;
               h = make_float4(two_sum(ph.x, of.x, ex), two_sum(ph.y, of.y, ey), two_sum(ph.z, of.z, ez),
                               two_sum(ph.w, of.w, ew));
@@ -217,8 +226,8 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
               const int n0 = bq + 8 * half8;
               float v[8];
               if (row >= 0) {
-                const float4 a = *reinterpret_cast<const float4*>(xt + (int64_t)row * kTcR + n0);
-                const float4 b = *reinterpret_cast<const float4*>(xt + (int64_t)row * kTcR + n0 + 4);
+                const float4 a = *reinterpret_cast<const float4*>(xb + (int64_t)row * kTcR + n0);
+                const float4 b = *reinterpret_cast<const float4*>(xb + (int64_t)row * kTcR + n0 + 4);
                 v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
               } else {
 #pragma unroll
@@ -309,16 +318,16 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
           }
           if (r < mm) {
-            float* yp = ynear + row * kTcR + c0;
-            const float* xp = xt + row * kTcR + c0;
+            float* yp = yb + row * kTcR + c0;
+            const float* xp = xb + row * kTcR + c0;
 #pragma unroll
             for (int i = 0; i < 16; i += 4) {
               const float4 x4 = *reinterpret_cast<const float4*>(xp + i);
               float4 y4 = *reinterpret_cast<const float4*>(yp + i);
-              y4.x += kscale * s_sx[c0 + i] * v[i] + kdiag * x4.x;
-              y4.y += kscale * s_sx[c0 + i + 1] * v[i + 1] + kdiag * x4.y;
-              y4.z += kscale * s_sx[c0 + i + 2] * v[i + 2] + kdiag * x4.z;
-              y4.w += kscale * s_sx[c0 + i + 3] * v[i + 3] + kdiag * x4.w;
+              y4.x += sd.x * s_sx[c0 + i] * v[i] + sd.y * x4.x;
+              y4.y += sd.x * s_sx[c0 + i + 1] * v[i + 1] + sd.y * x4.y;
+              y4.z += sd.x * s_sx[c0 + i + 2] * v[i + 2] + sd.y * x4.z;
+              y4.w += sd.x * s_sx[c0 + i + 3] * v[i + 3] + sd.y * x4.w;
               *reinterpret_cast<float4*>(yp + i) = y4;
             }
           }
@@ -367,7 +376,7 @@ int tc_near_dk(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigned in
     const int grid = (int)std::min<int64_t>(n, INT32_MAX);
     k_tc_near<D, KID><<<grid, kNrThreads, kNrSmem, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
                                                           P.hi4[DL.level].p, P.lo4[DL.level].p, xt, colmax, kc, scale,
-                                                          diag, h->ynear.p, h->err.p);
+                                                          diag, h->ynear.p, nullptr, nullptr, h->err.p);
     h->launches += 1;
   };
   for (const DenseLevel& DL : P.coarse4) run(DL, ks, 0.f);
@@ -404,6 +413,60 @@ int launch_tc_near(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigne
     case 2: return tc_near_d<2>(h, st, xt, colmax);
     case 3: return tc_near_d<3>(h, st, xt, colmax);
     default: return tc_near_d<4>(h, st, xt, colmax);
+  }
+}
+
+}  // namespace hd
+
+namespace hd {
+namespace {
+
+template <int D, int KID>
+int tc_near_raw_dk(cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs, const float4* soff,
+                   const float4* Hi, const float4* Lo, const float* xt, const unsigned int* colmax, float kc,
+                   float* ynear, const int2* tbase, const float2* tsd, int32_t* err) {
+  static PerDeviceOnce attr;
+  HD_TRY(attr.run([] {
+    HD_CUDA(cudaFuncSetAttribute(k_tc_near<D, KID>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNrSmem));
+    return (int)HODLRDD_OK;
+  }));
+  if (ntask <= 0) return HODLRDD_OK;
+  k_tc_near<D, KID><<<(int)std::min<int64_t>(ntask, INT32_MAX), kNrThreads, kNrSmem, st>>>(
+      tasks, 0, ntask, srcs, soff, Hi, Lo, xt, colmax, kc, 1.f, 0.f, ynear, tbase, tsd, err);
+  HD_CUDA(cudaGetLastError());
+  return HODLRDD_OK;
+}
+
+template <int D>
+int tc_near_raw_d(int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs, const float4* soff,
+                  const float4* Hi, const float4* Lo, const float* xt, const unsigned int* colmax, float kc,
+                  float* ynear, const int2* tbase, const float2* tsd, int32_t* err) {
+#define HD_NEAR_RAW(K) tc_near_raw_dk<D, K>(st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err)
+  switch (kid) {
+    case HODLRDD_K_LOG: return HD_NEAR_RAW(HODLRDD_K_LOG);
+    case HODLRDD_K_MATERN32: return HD_NEAR_RAW(HODLRDD_K_MATERN32);
+    case HODLRDD_K_GAUSS: return HD_NEAR_RAW(HODLRDD_K_GAUSS);
+    case HODLRDD_K_EXP: return HD_NEAR_RAW(HODLRDD_K_EXP);
+    case HODLRDD_K_R: return HD_NEAR_RAW(HODLRDD_K_R);
+    case HODLRDD_K_SIN: return HD_NEAR_RAW(HODLRDD_K_SIN);
+    default: return HD_NEAR_RAW(HODLRDD_K_INV_SQRT1P);
+  }
+#undef HD_NEAR_RAW
+}
+
+}  // namespace
+
+// One launch of the tensor-core near field over tasks whose coordinate and
+// point bases, scale and diagonal come per task (tasks of several trees).
+int launch_tc_near_raw(int d, int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs,
+                       const float4* soff, const float4* Hi, const float4* Lo, const float* xt,
+                       const unsigned int* colmax, float kc, float* ynear, const int2* tbase, const float2* tsd,
+                       int32_t* err) {
+  switch (d) {
+    case 1: return tc_near_raw_d<1>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
+    case 2: return tc_near_raw_d<2>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
+    case 3: return tc_near_raw_d<3>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
+    default: return tc_near_raw_d<4>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
   }
 }
 
