@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
-    p.add_argument("--only", default=None, choices=["many_rhs", "batch"],
+    p.add_argument("--only", default=None, choices=["many_rhs", "batch", "solve"],
                    help="run only this workload's products (--steps of them after --warmup) and print its line; "
                         "for profiling")
     p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
@@ -548,7 +548,7 @@ def admissibility_line(args, torch, stream, hd, N=65536):
     return out
 
 
-def solve_line(args, torch, hd, N=65536):
+def solve_line(args, torch, hd, N=262144):
     """(I + K/N) u = b on N points of the benchmark distribution, to a relative
     FP64 residual of 1e-10: GMRES on the headline-precision operator inside FP64
     refinement, against GMRES on the FP64 operator alone."""
@@ -730,6 +730,17 @@ def batch_only(args):
     print(json.dumps(batch_line(args, torch, hd)))
 
 
+def solve_only(args):
+    """The integral-equation solve line alone (d=3, N=262144), for profiling."""
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import build as cbuild
+
+    cbuild.build()
+    print(json.dumps(solve_line(args, torch, hd)))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -738,6 +749,8 @@ def main():
         return many_rhs_only(args)
     if args.only == "batch":
         return batch_only(args)
+    if args.only == "solve":
+        return solve_only(args)
     import torch
 
     import paper_2209_05819_gb300 as hd
