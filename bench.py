@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default="fp32+fp16", choices=["fp64", "fp32", "fp16", "bf16", "fp32+fp16"])
+    p.add_argument("--near-coords", default="hi", choices=["hi", "hilo"],
+                   help="near-field tile coordinates of the headline product: hi only (default; distances carry "
+                        "2^-24 h absolute error) or hi + lo pairs (exact distances)")
     p.add_argument("--n", type=int, default=262144)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--seed", type=int, default=0)
@@ -766,7 +769,7 @@ def main():
     nrhs = w.nrhs
     units = w.N * nrhs
 
-    h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision)
+    h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision, near_coords=args.near_coords)
     s = h.stats()
     io = torch.float64 if args.precision == "fp64" else torch.float32
     x = torch.from_numpy(np.ascontiguousarray(w.x.reshape(w.N, nrhs))).to(io).cuda()
@@ -930,7 +933,7 @@ def main():
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16+f32", "bf16": "bf16+f32",
                                            "fp32+fp16": "f32 (factors f32 + f16)"}[
                 args.precision], "data": "synthetic",
-            "config": {"workload": workload_name(w), "precision": args.precision,
+            "config": {"workload": workload_name(w), "precision": args.precision, "near_coords": args.near_coords,
                        "factors": ("leading ACA terms FP32, trailing terms FP16 with FP32 column scales, FP32 "
                                    "arithmetic" if args.precision == "fp32+fp16" else
                                    f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"

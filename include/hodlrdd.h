@@ -130,7 +130,14 @@ typedef struct hodlrdd_options {
                            precision FP64 or FP32, d <= 4 and ranks <= 1024; right-hand
                            sides are applied one at a time. The build still holds the
                            FP64 factors of every block while it runs. */
-  int reserved[5];      /* set to 0 */
+  int near_coords;      /* coordinates of the single-right-hand-side FP32 near-field
+                           tiles (FP32/FP16/BF16 forms, d <= 3). 0 (default): each
+                           box-relative coordinate as an FP32 pair hi + lo, so that a
+                           distance keeps FP32 relative accuracy however close the two
+                           points are. 1: hi only, about 40% fewer operations per pair;
+                           a distance r then carries an absolute error of about
+                           2^-24 h (h the leaf box size), a relative error 2^-24 h / r */
+  int reserved[4];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64

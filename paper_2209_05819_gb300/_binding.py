@@ -32,7 +32,7 @@ class HodlrddError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
                 ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("admissible_face_dim", C.c_int),
-                ("lowrank_form", C.c_int), ("reserved", C.c_int * 5)]
+                ("lowrank_form", C.c_int), ("near_coords", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class SolveOptions(C.Structure):
@@ -200,6 +200,7 @@ def _stream_ptr(stream):
 
 # What a low-rank block keeps: its factors U_b, V_b, or the skeleton (pivots and
 # the LU factors of K(sigma, tau)) with kernel entries evaluated on the fly.
+NEAR_COORDS = {"hilo": 0, "hi": 1}
 LOWRANK_FORM = {"factors": 0, "skeleton": 1}
 
 
@@ -209,7 +210,7 @@ class Handle:
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
                  aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0,
-                 lowrank_form: str = "factors"):
+                 lowrank_form: str = "factors", near_coords: str = "hilo"):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -229,6 +230,8 @@ class Handle:
         opt.near_mode = int(near_mode)
         opt.admissible_face_dim = int(admissible_face_dim)
         opt.lowrank_form = LOWRANK_FORM[lowrank_form]
+        # "hilo": FP32 hi + lo coordinate pairs (exact distances); "hi": hi only
+        opt.near_coords = NEAR_COORDS[near_coords]
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:

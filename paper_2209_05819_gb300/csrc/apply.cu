@@ -14,7 +14,7 @@
 // (level, box) row-major over the concatenated columns of the box's IL blocks,
 // so a box's rows read one contiguous t vector. Each factor array is a stream
 // of 16-byte aligned segments, consumed by one persistent CTA per SM: a
-// producer lane moves 32 KB stages with cp.async.bulk into a shared-memory ring
+// producer lane moves 48 KB stages with cp.async.bulk into a shared-memory ring
 // guarded by mbarriers; consumer warps split every stage into lane teams sized
 // to the segment length and reduce with shuffles. Every output has one writer
 // and a fixed summation order (bitwise reproducible, no atomics on results).
@@ -41,7 +41,7 @@ size_t elem_size(int precision) {
 
 namespace {
 
-constexpr int kStageBytes = 32768;
+constexpr int kStageBytes = 49152;
 constexpr int kConsumerWarps = 16;
 constexpr int kSegThreads = 32 * (1 + kConsumerWarps);
 constexpr int kPanelRows = 512;                // rows per U panel
@@ -236,9 +236,11 @@ struct PanelCfg {
   static constexpr int kSlot = kStageBytes + kScal + kMetaBytes;
   static constexpr int kRed = kConsumerWarps * 32 * 8 * (int)sizeof(Acc);
   static constexpr int kFit = (kDynSmemMax - kRed) / kSlot;
-  // four slots keep 128 KB in flight per SM and leave shared memory and
-  // registers for one near-field tile CTA beside the panel CTA
-  static constexpr int kStagesN = kFit < 4 ? kFit : 4;
+  // three slots keep 144 KB in flight per SM and leave shared memory and
+  // registers for one near-field tile CTA beside the panel CTA (fewer, larger
+  // stages than four of 32 KB: the per-stage hand-over costs the consumers
+  // about as many instructions as a 32 KB stage's arithmetic)
+  static constexpr int kStagesN = kFit < 3 ? kFit : 3;
   static constexpr size_t kSmem = (size_t)kStagesN * kSlot + kRed;
   static_assert(kStagesN >= 3, "panel ring needs at least three slots");
 };
@@ -263,8 +265,7 @@ struct PanelArgs {
   const Acc* vec;
   Acc* out;
   const int32_t* map;
-  const float* sa;
-  const float* sb;
+  const float* scl;  // V: per output, the product of its column scales (16-bit streams), else null
   Acc* part;
 };
 
@@ -359,8 +360,7 @@ __device__ __forceinline__ bool panel_consume(const PanelArgs<T>& a, char* smem,
   const int q0 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x] : 0;
   const int q1 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x + 1] : 0;
   const int32_t* __restrict__ map = a.map;
-  const float* __restrict__ sa = a.sa;
-  const float* __restrict__ sb = a.sb;
+  const float* __restrict__ scl = a.scl;
   Acc* __restrict__ part = a.part;
   Acc* __restrict__ out = a.out;
   const int cw = warp - 1;
@@ -414,8 +414,9 @@ __device__ __forceinline__ bool panel_consume(const PanelArgs<T>& a, char* smem,
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const int w = rc * E + e;
+            // two independent loads, first used when the panel ends
             oidx[e] = w < P.R ? map[(int64_t)P.out0 + w] : 0;
-            oscl[e] = (sa && w < P.R) ? (Acc)(sa[oidx[e]] * sb[oidx[e]]) : Acc(1);
+            oscl[e] = (scl && w < P.R) ? (Acc)scl[(int64_t)P.out0 + w] : Acc(1);
           }
         }
       }
@@ -1069,6 +1070,25 @@ constexpr double kTailEta = 1.0 / 8192.0;
 // Packs the factors: uniform element type T, or (mixed) the leading terms of
 // each block in FP32 and its trailing terms (every term after the last one
 // above kTailEta of the block) in FP16 with per-column scales.
+// scl[c] = sv[map[c]] * su[map[c]]: the product of the column scales of each
+// V panel output of a 16-bit stream, so that a panel's writers load it
+// directly instead of through the column index.
+__global__ void k_vscl(int64_t n, const int32_t* __restrict__ map, const float* __restrict__ sv,
+                       const float* __restrict__ su, float* __restrict__ scl) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    scl[c] = sv[map[c]] * su[map[c]];
+}
+
+int fill_vscl(hodlrdd_s* h, const DevBuf<int32_t>& map, DevBuf<float>& scl) {
+  HD_TRY(scl.alloc(std::max<size_t>(map.n, 1)));
+  if (map.n > 0) {
+    k_vscl<<<(int)std::min<int64_t>(((int64_t)map.n + 255) / 256, 4096), 256, 0, h->st>>>((int64_t)map.n, map.p,
+                                                                                         h->sv.p, h->su.p, scl.p);
+    HD_CUDA(cudaGetLastError());
+  }
+  return HODLRDD_OK;
+}
+
 template <class T>
 int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
                const std::vector<int64_t>& uoff64, const std::vector<int64_t>& voff64, bool mixed) {
@@ -1165,6 +1185,9 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
   head.tfirst = thead;
   HD_TRY(pack_part<T>(h, U64, V64, colU, colV, head, P.vs, P.us, P.vmap, !mixed, 0));
   h->factor_bytes = (P.vs.elems + P.us.elems) * (int64_t)sizeof(T) + (Fac<T>::scaled ? 2 * H * 4 : 0);
+  P.vscl.release();
+  P.vscl2.release();
+  if (Fac<T>::scaled) HD_TRY(fill_vscl(h, P.vmap, P.vscl));
   P.vs2 = Stream();
   P.us2 = Stream();
   P.vmap2.release();
@@ -1174,6 +1197,7 @@ int pack_typed(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V6
     tail.tfirst = ttail;
     HD_TRY(pack_part<__half>(h, U64, V64, colU, colV, tail, P.vs2, P.us2, P.vmap2, false,
                              (int64_t)h->kappa * h->N));
+    HD_TRY(fill_vscl(h, P.vmap2, P.vscl2));
     h->factor_bytes += (P.vs2.elems + P.us2.elems) * 2 + 2 * (ncol - H) * 4;
   }
   return HODLRDD_OK;
@@ -1650,15 +1674,14 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   }
   const bool mixed = h->opt.precision == HODLRDD_PREC_FP32_FP16;
   Acc* pb2 = pb + (size_t)std::max<int64_t>({P.vs.part_rows, P.us.part_rows, 1}) * NR;
-  auto args = [&](const Stream& S, const Acc* vec, Acc* out, const int32_t* map, const float* a_, const float* b_,
-                  Acc* part) {
+  auto args = [&](const Stream& S, const Acc* vec, Acc* out, const int32_t* map, const float* scl, Acc* part) {
     return PanelArgs<T>{reinterpret_cast<const T*>(S.data.p), S.panels.p, S.stages.p, S.cta.p, S.ctas, vec, out, map,
-                        a_, b_, part};
+                        scl, part};
   };
-  auto args16 = [&](const Stream& S, const float* vec, float* out, const int32_t* map, const float* a_,
-                    const float* b_, float* part) {
+  auto args16 = [&](const Stream& S, const float* vec, float* out, const int32_t* map, const float* scl,
+                    float* part) {
     return PanelArgs<__half>{reinterpret_cast<const __half*>(S.data.p), S.panels.p, S.stages.p, S.cta.p, S.ctas, vec,
-                             out, map, a_, b_, part};
+                             out, map, scl, part};
   };
   // one apply stage: uniform storage, or (mixed) the FP32 and FP16 streams in one launch
   auto stage = [&](bool vmode, const Acc* vec, Acc* out) -> int {
@@ -1672,9 +1695,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     if constexpr (std::is_same<T, float>::value && NR <= 8) {
       if (mixed && (S1.ctas > 0 || S2.ctas > 0)) {
         const int grid = std::max(S1.ctas, S2.ctas);
-        const PanelArgs<float> A = args(S1, vec, out, m1, nullptr, nullptr, pb);
-        const PanelArgs<__half> B =
-            args16(S2, vec, out, m2, vmode ? h->sv.p : nullptr, vmode ? h->su.p : nullptr, pb2);
+        const PanelArgs<float> A = args(S1, vec, out, m1, nullptr, pb);
+        const PanelArgs<__half> B = args16(S2, vec, out, m2, vmode ? P.vscl2.p : nullptr, pb2);
         if (vmode) k_panel_mix<NR, true><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
         else k_panel_mix<NR, false><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
         h->launches += 1;
@@ -1682,7 +1704,7 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
       }
     }
     if (!launched && S1.ctas > 0 && !S1.h_stages.empty()) {
-      const PanelArgs<T> A = args(S1, vec, out, m1, a1, b1, pb);
+      const PanelArgs<T> A = args(S1, vec, out, m1, vmode && Fac<T>::scaled ? P.vscl.p : nullptr, pb);
       if (vmode) k_panel<T, NR, true><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
       else k_panel<T, NR, false><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
       h->launches += 1;

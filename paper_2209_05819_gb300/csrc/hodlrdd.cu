@@ -166,6 +166,10 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (o.max_nrhs < 1 || o.aca_max_rank < 1) { set_error("hodlrdd_build: max_nrhs and aca_max_rank must be >= 1"); return HODLRDD_ERR_INVALID; }
   if (o.dense_if_cheaper < 0 || o.dense_if_cheaper > 2) { set_error("hodlrdd_build: dense_if_cheaper must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
   if (o.near_mode < 0 || o.near_mode > 2) { set_error("hodlrdd_build: near_mode must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
+  if (o.near_coords < 0 || o.near_coords > 1) {
+    set_error("hodlrdd_build: near_coords must be 0 or 1");
+    return HODLRDD_ERR_INVALID;
+  }
   if (o.admissible_face_dim < -1 || o.admissible_face_dim > d - 1) {
     set_error("hodlrdd_build: admissible_face_dim must be in -1 .. d - 1");
     return HODLRDD_ERR_INVALID;

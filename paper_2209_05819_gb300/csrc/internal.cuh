@@ -354,6 +354,7 @@ struct Plan {
   // (U outputs to a second set of kappa level slices)
   Stream vs2, us2;
   DevBuf<int32_t> vmap2;
+  DevBuf<float> vscl, vscl2;       // per V panel output: su * sv of its t column (16-bit streams)
   int64_t tail_cols = 0;           // columns stored in FP16
   std::vector<int64_t> h_vpanel;   // block -> first whole V panel of its source box (or -1)
   std::vector<int32_t> h_vcol;     // block -> first column within its source box's V panels

@@ -22,8 +22,10 @@ namespace {
 // the entry after the chunk); then threads holding two target rows each sweep
 // the chunk in S source stripes. Result: ynear[i] += scale * sum + diag * x_i
 // (diag is passed as 0 except for the pass that owns the diagonal).
+// HILO = false (option near_coords = 1): the hi parts alone, the lo parts are
+// neither staged nor read.
 
-template <int D, int KID>
+template <int D, int KID, bool HILO>
 __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                       const int4* __restrict__ srcs, const float4* __restrict__ soff,
                                                       const float4* __restrict__ Hi, const float4* __restrict__ Lo,
@@ -46,12 +48,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
     float xa = 0.f, xb = 0.f;
     if (va) {
       tha = Hi[ra];
-      tla = Lo[ra];
+      if (HILO) tla = Lo[ra];
       xa = xt[ra];
     }
     if (vb) {
       thb = Hi[rb];
-      tlb = Lo[rb];
+      if (HILO) tlb = Lo[rb];
       xb = xt[rb];
     }
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
@@ -62,11 +64,16 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
         const int4 sj = srcs[b];
         const float4 of = soff[b];
         for (int k = lane; k < sj.y; k += 32) {
-          const float4 h = Hi[sj.x + k], l = Lo[sj.x + k];
-          float ex, ey, ez;
-          const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
-          shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
-          slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
+          const float4 h = Hi[sj.x + k];
+          if (HILO) {
+            const float4 l = Lo[sj.x + k];
+            float ex, ey, ez;
+            const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
+            shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
+            slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
+          } else {
+            shi[sj.z + k] = make_float4(h.x + of.x, h.y + of.y, h.z + of.z, xt[sj.x + k]);
+          }
         }
       }
       const int4 lastb = srcs[e1 - 1];
@@ -74,16 +81,30 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
       __syncthreads();
       int f = stripe;
       for (; f + S < n; f += 2 * S) {
-        const float4 h0 = shi[f], l0 = slo[f], h1 = shi[f + S], l1 = slo[f + S];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-        a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
-        b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
+        const float4 h0 = shi[f], h1 = shi[f + S];
+        if (HILO) {
+          const float4 l0 = slo[f], l1 = slo[f + S];
+          a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+          b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+          a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
+          b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
+        } else {
+          a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
+          b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
+          a1 = fmaf(f32k<KID>(sqdist1<D>(tha, h1), kc), h1.w, a1);
+          b1 = fmaf(f32k<KID>(sqdist1<D>(thb, h1), kc), h1.w, b1);
+        }
       }
       if (f < n) {
-        const float4 h0 = shi[f], l0 = slo[f];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+        const float4 h0 = shi[f];
+        if (HILO) {
+          const float4 l0 = slo[f];
+          a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+          b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+        } else {
+          a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
+          b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
+        }
       }
       e = e1;
     }
@@ -344,8 +365,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_nr(const int4* __restr
 }
 
 
-template <int D, int KID>
-void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+template <int D, int KID, bool HILO>
+void launch_tiles_kc(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   const Plan& P = h->plan;
   const float kc = (float)kernel_const(h->K);
   const float ks = (float)h->K.scale, kd = (float)h->K.diag;
@@ -353,22 +374,28 @@ void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   // one CTA per task (the hardware scheduler balances tasks of unequal size)
   auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, INT32_MAX)); };
   for (const DenseLevel& DL : P.coarse4) {
-    k_tile<D, KID><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
+    k_tile<D, KID, HILO><<<grid(DL.t1 - DL.t0), kTileThreads, 0, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
                                                                 P.hi4[DL.level].p, P.lo4[DL.level].p, xt, kc, ks,
                                                                 0.f, yn);
     h->launches += 1;
   }
   if (P.excl4.t1 > P.excl4.t0) {
     // low-rank leaf blocks that the parent tiles also evaluate: subtract them
-    k_tile<D, KID><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
+    k_tile<D, KID, HILO><<<grid(P.excl4.t1 - P.excl4.t0), kTileThreads, 0, st>>>(
         P.tasks4.p, P.excl4.t0, P.excl4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.excl4.level].p, P.lo4[P.excl4.level].p, xt,
         kc, -ks, 0.f, yn);
     h->launches += 1;
   }
-  k_tile<D, KID><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
+  k_tile<D, KID, HILO><<<grid(P.leaf4.t1 - P.leaf4.t0), kTileThreads, 0, st>>>(
       P.tasks4.p, P.leaf4.t0, P.leaf4.t1, P.srcs4.p, P.soff4.p, P.hi4[P.leaf4.level].p, P.lo4[P.leaf4.level].p, xt,
       kc, ks, kd, yn);
   h->launches += 1;
+}
+
+template <int D, int KID>
+void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  if (h->opt.near_coords == 1) launch_tiles_kc<D, KID, false>(h, st, xt);
+  else launch_tiles_kc<D, KID, true>(h, st, xt);
 }
 
 template <int D>
