@@ -137,7 +137,16 @@ typedef struct hodlrdd_options {
                            points are. 1: hi only, about 40% fewer operations per pair;
                            a distance r then carries an absolute error of about
                            2^-24 h (h the leaf box size), a relative error 2^-24 h / r */
-  int reserved[4];      /* set to 0 */
+  int fp64_near;        /* near field of FP64 handles for one right-hand side at a
+                           time, d <= 4. 0 (default): FP64 arithmetic. 1: float-float
+                           arithmetic on the FP32 pipes (an unevaluated sum of two
+                           FP32 numbers, about 48 significant bits; coordinates in
+                           box units on a 2^-21 grid plus an FP32 remainder), about
+                           10x the FP64 rate on a GPU whose FP64 rate is 1/64 of its
+                           FP32 rate; kernel values carry a relative error of about
+                           2^-44 (1e-13) instead of 2^-52. Not available for sin r
+                           (HODLRDD_ERR_UNSUPPORTED). Ignored by other precisions. */
+  int reserved[3];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64
@@ -497,6 +506,17 @@ int hodlrdd_debug_expire_wait(hodlrdd_handle h, long long cycles);
  *  n       entries of out to fill (<= 4 used). Synchronous; allocates 16 bytes.
  */
 int hodlrdd_probe_peaks(double* out, int n, void* stream);
+
+/*
+ * Test entry of the float-float kernel evaluation that the FP64 near field uses
+ * with fp64_near = 1: out[i] = F(s[i]) for the kernel (kernel_id, params as in
+ * hodlrdd_build) and squared distances s[i] >= 0, evaluated as the near field
+ * does at box size h (s / h^2 in box units, the box size folded into the
+ * per-level constants). Host arrays of n values; synchronous. Errors:
+ * HODLRDD_ERR_INVALID (NULL, n < 0, h <= 0), HODLRDD_ERR_UNSUPPORTED (sin r or
+ * an unknown kernel).
+ */
+int hodlrdd_debug_ff_eval(int kernel_id, const double* params, double h, const double* s, double* out, int64_t n);
 
 /*
  * Serving: a request loop over models kept resident under a device-memory

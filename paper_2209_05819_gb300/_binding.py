@@ -32,7 +32,8 @@ class HodlrddError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
                 ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("admissible_face_dim", C.c_int),
-                ("lowrank_form", C.c_int), ("near_coords", C.c_int), ("reserved", C.c_int * 4)]
+                ("lowrank_form", C.c_int), ("near_coords", C.c_int), ("fp64_near", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class SolveOptions(C.Structure):
@@ -87,6 +88,7 @@ def load():
         "hodlrdd_forest_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
         "hodlrdd_forest_stats": (i32, [vp, C.POINTER(i64)]),
         "hodlrdd_forest_destroy": (i32, [vp]),
+        "hodlrdd_debug_ff_eval": (i32, [i32, vp, dbl, vp, vp, i64]),
         "hodlrdd_solve_options_default": (i32, [C.POINTER(SolveOptions)]),
         "hodlrdd_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOptions), C.POINTER(SolveStats), vp]),
         "hodlrdd_destroy": (i32, [vp]),
@@ -201,6 +203,7 @@ def _stream_ptr(stream):
 # What a low-rank block keeps: its factors U_b, V_b, or the skeleton (pivots and
 # the LU factors of K(sigma, tau)) with kernel entries evaluated on the fly.
 NEAR_COORDS = {"hilo": 0, "hi": 1}
+FP64_NEAR = {"fp64": 0, "ff": 1}
 LOWRANK_FORM = {"factors": 0, "skeleton": 1}
 
 
@@ -210,7 +213,7 @@ class Handle:
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
                  aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0,
-                 lowrank_form: str = "factors", near_coords: str = "hilo"):
+                 lowrank_form: str = "factors", near_coords: str = "hilo", fp64_near: str = "fp64"):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -232,6 +235,8 @@ class Handle:
         opt.lowrank_form = LOWRANK_FORM[lowrank_form]
         # "hilo": FP32 hi + lo coordinate pairs (exact distances); "hi": hi only
         opt.near_coords = NEAR_COORDS[near_coords]
+        # FP64 handles: near field in FP64 ("fp64") or float-float on the FP32 pipes ("ff")
+        opt.fp64_near = FP64_NEAR[fp64_near]
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:
@@ -639,3 +644,16 @@ def probe_peaks(stream=None) -> dict:
 
 def debug_fail_alloc_after(k: int):
     load().hodlrdd_debug_fail_alloc_after(int(k))
+
+
+def debug_ff_eval(kernel: int, params, h: float, s) -> np.ndarray:
+    """Kernel values F(s) in the float-float arithmetic of the FP64 near field
+    with fp64_near "ff", at box size h (hodlrdd_debug_ff_eval)."""
+    p = np.zeros(4, np.float64)
+    v = np.asarray(params, np.float64).reshape(-1)
+    p[: min(4, v.size)] = v[:4]
+    sa = np.ascontiguousarray(s, np.float64).reshape(-1)
+    out = np.empty_like(sa)
+    _check(load().hodlrdd_debug_ff_eval(int(kernel), p.ctypes.data, float(h), sa.ctypes.data, out.ctypes.data,
+                                        int(sa.size)), "hodlrdd_debug_ff_eval")
+    return out

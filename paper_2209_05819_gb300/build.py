@@ -35,6 +35,7 @@ SOURCES = {
     "tcapply.cu": [],
     "tcnear.cu": [],
     "forest.cu": [],
+    "ffnear.cu": [],
 }
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", os.path.join(ROOT, "include")]

@@ -1388,7 +1388,9 @@ int build_plan(hodlrdd_s* h) {
     for (int64_t t = a; t < b; ++t) t4[t] = w[(size_t)(t - a)].second;
   };
   P.coarse4.clear();
-  if (!f64 && d <= 4) {
+  // packed tasks: the FP32 tiles, and the float-float near field of FP64 handles
+  const bool ffnear = f64 && h->opt.fp64_near == 1;
+  if ((!f64 || ffnear) && d <= 4) {
     for (int l = 1; l < h->kappa; ++l) {
       const Level& L = h->lv[l];
       DenseLevel DL;
@@ -1539,6 +1541,19 @@ int build_plan(hodlrdd_s* h) {
     }
     HD_CUDA(cudaStreamSynchronize(st));
   }
+  if (ffnear && d <= 4) {
+    std::vector<double> hlo(h->lo, h->lo + d);
+    DevBuf<double> dlo;
+    HD_TRY(upload(dlo, hlo, st));
+    P.hq4.clear();
+    P.lq4.clear();
+    for (int l = 0; l <= h->kappa; ++l)
+      if (need4[l]) HD_TRY(build_ffcoords(h, l, dlo.p, st));
+    HD_TRY(upload(P.tasks4, t4, st));
+    HD_TRY(upload(P.srcs4, s4, st));
+    HD_TRY(upload(P.soff4, o4, st));
+    HD_CUDA(cudaStreamSynchronize(st));
+  }
   HD_CUDA(cudaStreamSynchronize(st));
   return HODLRDD_OK;
 }
@@ -1638,8 +1653,11 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   // tiles), else FP32 multi-RHS tiles for d <= 4
   const bool packed1 = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
   const bool packed = !F64 && h->d <= 4 && P.tasks4.n > 0;
+  // FP64, one right-hand side: the float-float near field on the FP32 pipes (option fp64_near)
+  const bool ffn = F64 && NR == 1 && h->opt.fp64_near == 1 && P.tasks4.n > 0 && !P.hq4.empty();
+  double* ynear64 = reinterpret_cast<double*>(h->ynear.p);  // N doubles fit in the N x 8 floats
   if (prof) {
-    HD_TRY(chunk_events(h, ev, packed ? 7 : 5));
+    HD_TRY(chunk_events(h, ev, (packed || ffn) ? 7 : 5));  // 5, 6: the near field on the aux stream
     HD_CUDA(cudaEventRecord(ev[0], st));
   }
   k_gather<Acc, IO, NR><<<(int)std::min<int64_t>((h->N + 255) / 256, sms * 16), 256, 0, st>>>(x, h->perm.p, h->N,
@@ -1650,14 +1668,16 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   // stream beside the low-rank applies (HBM-bound against instruction-bound)
   // and joins before the final sum; it is enqueued after the V-apply so that
   // the persistent panel CTAs are placed first
-  if (packed) HD_CUDA(cudaEventRecord(h->ev_fork, st));
+  if (packed || ffn) HD_CUDA(cudaEventRecord(h->ev_fork, st));
   auto fork_near = [&]() -> int {
-    if (!packed) return HODLRDD_OK;
+    if (!packed && !ffn) return HODLRDD_OK;
     HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
     if constexpr (!F64) {
       if (packed1) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
       else HD_TRY(launch_tiles_nr(h, h->aux, reinterpret_cast<const float*>(xt), NR));
+    } else {
+      HD_TRY(launch_tiles_ff(h, h->aux, reinterpret_cast<const double*>(xt), ynear64));
     }
     if (prof) HD_CUDA(cudaEventRecord(ev[6], h->aux));
     HD_CUDA(cudaEventRecord(h->ev_join, h->aux));
@@ -1743,6 +1763,11 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if constexpr (!F64 && std::is_same<IO, float>::value)
       HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), level_slices(h), y, NR, ldx, c0));
+  } else if (ffn) {
+    HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
+    if constexpr (F64 && std::is_same<IO, double>::value)
+      HD_TRY(launch_finish_ff(h, st, ynear64, reinterpret_cast<const double*>(yl), h->kappa >= 1 ? level_slices(h) : 0,
+                              y, ldx, c0));
   } else if constexpr (NR <= 8) {
     switch (h->d) {
       case 1: HD_TRY((launch_dense<Acc, IO, NR, 1, F64>(h, st, sms, xt, yl, y, ldx, c0))); break;

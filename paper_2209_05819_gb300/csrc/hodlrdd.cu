@@ -133,6 +133,8 @@ void fill_stats(hodlrdd_s* h) {
                      P.sk_boff.bytes() + P.sk_part.bytes() + P.sk_hi.bytes() + P.sk_lo.bytes());
   for (auto& a : P.hi4) bytes += (int64_t)a.bytes();
   for (auto& a : P.lo4) bytes += (int64_t)a.bytes();
+  for (auto& a : P.hq4) bytes += (int64_t)a.bytes();
+  for (auto& a : P.lq4) bytes += (int64_t)a.bytes();
   for (auto& r : P.rel) bytes += (int64_t)r.bytes();
   bytes += tc_device_bytes(h);
   for (auto& L : h->lv)
@@ -169,6 +171,14 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (o.near_coords < 0 || o.near_coords > 1) {
     set_error("hodlrdd_build: near_coords must be 0 or 1");
     return HODLRDD_ERR_INVALID;
+  }
+  if (o.fp64_near < 0 || o.fp64_near > 1) {
+    set_error("hodlrdd_build: fp64_near must be 0 or 1");
+    return HODLRDD_ERR_INVALID;
+  }
+  if (o.fp64_near == 1 && o.precision == HODLRDD_PREC_FP64 && (d > 4 || kernel_id == HODLRDD_K_SIN)) {
+    set_error("hodlrdd_build: the float-float FP64 near field (fp64_near 1) needs d <= 4 and a kernel other than sin r");
+    return HODLRDD_ERR_UNSUPPORTED;
   }
   if (o.admissible_face_dim < -1 || o.admissible_face_dim > d - 1) {
     set_error("hodlrdd_build: admissible_face_dim must be in -1 .. d - 1");

@@ -372,6 +372,7 @@ struct Plan {
   DevBuf<int4> srcs4;              // {J0, n, position in its staging chunk, chunk end on a chunk's first entry}
   DevBuf<float4> soff4;            // per source: (c_J - c_I) h_l, exact in FP32
   std::vector<DevBuf<float4>> hi4, lo4;  // per level (where used)
+  std::vector<DevBuf<float4>> hq4, lq4;  // FP64 float-float near field: box units, 2^-21 grid + remainder
   std::vector<DenseLevel> coarse4; // dense IL blocks above the leaf level
   DenseLevel leaf4;                // final pass: per parent box (tiles) or per leaf box (lists)
   DenseLevel excl4;                // tiles only: low-rank leaf IL blocks to subtract (level kappa)
@@ -531,6 +532,11 @@ void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt);
 int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int ldx = 0, int cx = 0);
 int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0);
 int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
+// float-float near field of FP64 handles (one right-hand side)
+int build_ffcoords(hodlrdd_s* h, int l, const double* dlo, cudaStream_t st);
+int launch_tiles_ff(hodlrdd_s* h, cudaStream_t st, const double* xt, double* ynear);
+int launch_finish_ff(hodlrdd_s* h, cudaStream_t st, const double* ynear, const double* ylev, int slices, double* y,
+                     int ldy, int c0);
 int unpack_block(hodlrdd_s* h, int64_t b, double* U, double* V);
 // Skeleton form (skeleton.cu).
 int build_skeleton(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64,
