@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
-    p.add_argument("--only", default=None, choices=["many_rhs", "batch", "solve"],
+    p.add_argument("--only", default=None, choices=["many_rhs", "batch", "solve", "serve"],
                    help="run only this workload's products (--steps of them after --warmup) and print its line; "
                         "for profiling")
     p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
@@ -560,19 +560,28 @@ def solve_line(args, torch, hd, N=262144):
     w = W.precision_3d(N=N, seed=args.seed, system=True)
     pts = torch.from_numpy(w.points).cuda()
     h64 = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp64")
+    hff = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision="fp64", fp64_near="ff")
     hlo = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision)
     b = torch.from_numpy(np.ascontiguousarray(w.x[:, 0])).cuda()
     out = {"workload": f"(I + K/N) u = b, d=3 N={N} uniform [-1,1]^3, F=1/r, leaf {w.leaf}, tol {w.tol:g}; "
-                       "GMRES(50), x0 = 0, stop at ||b - K x|| <= 1e-10 ||b|| with the FP64 operator"}
-    for name, inner in (("mixed", hlo), ("fp64", h64)):
-        hd.solve(inner, h64, b, tol=1e-10)  # warm-up
+                       "GMRES(50), x0 = 0, stop at ||b - K x|| <= 1e-10 ||b|| with the FP64 operator",
+           "legs": {"mixed_ff": f"inner {args.precision}, refinement FP64 with the float-float near field",
+                    "mixed": f"inner {args.precision}, refinement plain FP64",
+                    "fp64": "FP64-only GMRES (inner and refinement plain FP64)"}}
+    for name, inner, outer in (("mixed_ff", hlo, hff), ("mixed", hlo, h64), ("fp64", h64, h64)):
+        hd.solve(inner, outer, b, tol=1e-10)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, st = hd.solve(inner, h64, b, tol=1e-10)
+        x, st = hd.solve(inner, outer, b, tol=1e-10)
         torch.cuda.synchronize()
         out[name] = {"ms": 1e3 * (time.perf_counter() - t0), **st}
+        # the residual against the plain FP64 operator, whichever operator refined
+        r = b - h64.matvec(x)
+        out[name]["residual_plain_fp64"] = float((torch.linalg.norm(r) / torch.linalg.norm(b)).item())
+    out["speedup_mixed_ff_vs_fp64"] = out["fp64"]["ms"] / out["mixed_ff"]["ms"]
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     hlo.close()
+    hff.close()
     h64.close()
     return out
 
@@ -744,6 +753,17 @@ def solve_only(args):
     print(json.dumps(solve_line(args, torch, hd)))
 
 
+def serve_only(args):
+    """The request-loop line alone, for profiling."""
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import build as cbuild
+
+    cbuild.build()
+    print(json.dumps(serving_line(args, torch, hd)))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -754,6 +774,8 @@ def main():
         return batch_only(args)
     if args.only == "solve":
         return solve_only(args)
+    if args.only == "serve":
+        return serve_only(args)
     import torch
 
     import paper_2209_05819_gb300 as hd

@@ -546,7 +546,10 @@ int hodlrdd_debug_ff_eval(int kernel_id, const double* params, double h, const d
  *  kind = HODLRDD_REQ_SOLVE: K u = b column by column through hodlrdd_solve
  *  with the model as the fast operator and an FP64 twin of it (built on the
  *  first solve, counted in the budget) as the refinement operator; x = b and
- *  y = u are HOST arrays of N x nrhs doubles, original point order.
+ *  y = u are HOST arrays of N x nrhs doubles, original point order. The twin
+ *  evaluates its near field in float-float (fp64_near = 1) where that exists
+ *  (d <= 4, every kernel but sin r): about 1e-13 per kernel value, far below the
+ *  refinement's tolerance, at about 10x the FP64 rate.
  *  Buffers must stay valid until the request is waited for. Asynchronous;
  *  *request_id identifies the request.
  * hodlrdd_server_wait

@@ -165,6 +165,8 @@ int ensure(hodlrdd_server_s* s, Model& m, bool twin) {
     hodlrdd_options o64 = m.opt;
     o64.precision = HODLRDD_PREC_FP64;
     o64.lowrank_form = 0;
+    // the refinement operator: float-float near field where it exists
+    o64.fp64_near = m.d <= 4 && m.kid != HODLRDD_K_SIN ? 1 : 0;
     hodlrdd_s* h = nullptr;
     HD_TRY(hodlrdd_build_ex(m.points.data(), m.d, m.N, m.kid, m.prm, m.leaf, m.tol, &o64, &h));
     std::lock_guard<std::mutex> lk(s->mu);
