@@ -533,7 +533,13 @@ int hodlrdd_debug_ff_eval(int kernel_id, const double* params, double h, const d
  *                short), and at most workers - 1 solves run at once (with more
  *                than one worker) so that one worker stays free for products;
  *                each kind starts in arrival order. Products of different models
- *                run side by side; requests for one model run one at a time.
+ *                run side by side; requests for one model run one at a time,
+ *                except that products of one model queued while another of its
+ *                products waits are batched: a worker that starts a product takes
+ *                the model's other queued products along (up to 64 columns, see
+ *                hodlrdd_server_set_batching) and runs them as one product over
+ *                their columns side by side (FP32-I/O precisions with stored
+ *                factors; FP64 models and the skeleton form run products alone).
  * hodlrdd_server_add
  *  Registers a model (host copy of the points; same arguments as
  *  hodlrdd_build_ex, opt may be NULL). It is built on its first request and
@@ -562,8 +568,17 @@ int hodlrdd_debug_ff_eval(int kernel_id, const double* params, double h, const d
  *  out[3] evictions so far, out[4] queued requests not yet started.
  * hodlrdd_server_destroy
  *  Finishes queued requests, stops the workers, destroys every handle.
+ * hodlrdd_server_set_batching
+ *  max_cols >= 0: columns of one batched product (default 64); 0 or 1 turns
+ *  batching off.
+ * hodlrdd_server_batch_stats
+ *  out[0] batched products run so far (batches of two or more requests),
+ *  out[1] requests served by them.
  * Results equal those of hodlrdd_matvec / hodlrdd_solve on the model's handle
- * alone (bitwise for products).
+ * alone: bitwise for a product that runs alone; a batched product's columns go
+ * through the handle's chunks of several right-hand sides (uncompensated FP32
+ * accumulation, tensor-core chunks for FP16X2), which stay within those forms'
+ * stated bounds of the single-column product.
  */
 enum { HODLRDD_REQ_MATVEC = 0, HODLRDD_REQ_SOLVE = 1 };
 typedef struct hodlrdd_server_s* hodlrdd_server;
@@ -575,6 +590,8 @@ int hodlrdd_server_submit(hodlrdd_server s, int64_t model_id, int kind, const vo
                           int64_t* request_id);
 int hodlrdd_server_wait(hodlrdd_server s, int64_t request_id, double* latency_ms);
 int hodlrdd_server_stats(hodlrdd_server s, int64_t* out);
+int hodlrdd_server_set_batching(hodlrdd_server s, int max_cols);
+int hodlrdd_server_batch_stats(hodlrdd_server s, int64_t* out);
 int hodlrdd_server_destroy(hodlrdd_server s);
 
 #ifdef __cplusplus

@@ -115,6 +115,8 @@ def load():
         "hodlrdd_server_submit": (i32, [vp, i64, i32, vp, vp, i32, C.POINTER(i64)]),
         "hodlrdd_server_wait": (i32, [vp, i64, vp]),
         "hodlrdd_server_stats": (i32, [vp, vp]),
+        "hodlrdd_server_set_batching": (i32, [vp, i32]),
+        "hodlrdd_server_batch_stats": (i32, [vp, C.POINTER(i64)]),
         "hodlrdd_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -618,8 +620,14 @@ class Server:
     def stats(self) -> dict:
         out = np.zeros(5, np.int64)
         _check(self._lib.hodlrdd_server_stats(self._s, out.ctypes.data), "hodlrdd_server_stats")
+        b = (C.c_int64 * 2)()
+        _check(self._lib.hodlrdd_server_batch_stats(self._s, b), "hodlrdd_server_batch_stats")
         return {"resident_bytes": int(out[0]), "resident_models": int(out[1]), "builds": int(out[2]),
-                "evictions": int(out[3]), "queued": int(out[4])}
+                "evictions": int(out[3]), "queued": int(out[4]), "batches": int(b[0]), "batched_requests": int(b[1])}
+
+    def set_batching(self, max_cols: int):
+        """Columns of one batched product (0 or 1: products of a model run alone)."""
+        _check(self._lib.hodlrdd_server_set_batching(self._s, int(max_cols)), "hodlrdd_server_set_batching")
 
     def close(self):
         if getattr(self, "_s", None):

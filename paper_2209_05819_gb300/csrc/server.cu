@@ -85,8 +85,10 @@ struct hodlrdd_server_s {
   std::vector<std::thread> workers;
   bool stop = false;
   int64_t resident = 0, builds = 0, evictions = 0, next_id = 1;
+  int64_t batches = 0, batched = 0;  // products run together: batches of two or more, their requests
   uint64_t tick = 0;
   int nworkers = 1, solves_running = 0;
+  int batch_cols = 64;  // columns of one batched product (<= 1: no batching)
 };
 
 namespace hd {
@@ -198,15 +200,23 @@ int ensure(hodlrdd_server_s* s, Model& m, bool twin) {
   return HODLRDD_ERR_OOM;
 }
 
-// Device staging of one worker for solves (grown on demand).
+// Device staging of one worker for solves and batched products (grown on demand).
 struct Staging {
   DevBuf<double> b, x;
+  DevBuf<float> xc, yc;  // batched products: N x columns, row-major
   int grow(int64_t n) {
     if ((int64_t)b.n < n) HD_TRY(b.alloc(n));
     if ((int64_t)x.n < n) HD_TRY(x.alloc(n));
     return HODLRDD_OK;
   }
+  int grow_batch(int64_t n) {
+    if ((int64_t)xc.n < n) HD_TRY(xc.alloc(n));
+    if ((int64_t)yc.n < n) HD_TRY(yc.alloc(n));
+    return HODLRDD_OK;
+  }
 };
+
+
 
 // The handle's bounded-wait error word after a product on st (already
 // synchronised), read and cleared on st: hodlrdd_sync would synchronise the
@@ -217,6 +227,32 @@ int check_waits(hodlrdd_s* h, cudaStream_t st) {
   if (code == 0) return HODLRDD_OK;
   set_error("a bounded device-side wait expired; the product is invalid");
   return HODLRDD_ERR_TIMEOUT;
+}
+
+// Products of one model that were queued together, as one product over their
+// columns side by side: x_i into columns [c_i, c_i + nrhs_i) of one N x C
+// array, one hodlrdd_matvec, the columns back into y_i (2-D copies, host or
+// device buffers). FP32-I/O forms only (their results stay within the FP32
+// chunk bound of the single products; FP64 models run their products alone).
+int run_batch(Model& m, const std::vector<Request>& rs, cudaStream_t st, Staging& sg) {
+  std::lock_guard<std::mutex> one(m.run);
+  int64_t C = 0;
+  for (const Request& r : rs) C += r.nrhs;
+  HD_TRY(sg.grow_batch(m.N * C));
+  const size_t es = sizeof(float);
+  int64_t c0 = 0;
+  for (const Request& r : rs) {
+    HD_CUDA(cudaMemcpy2DAsync(sg.xc.p + c0, C * es, r.x, r.nrhs * es, r.nrhs * es, m.N, cudaMemcpyDefault, st));
+    c0 += r.nrhs;
+  }
+  HD_TRY(hodlrdd_matvec(m.h, sg.xc.p, sg.yc.p, (int)C, st));
+  c0 = 0;
+  for (const Request& r : rs) {
+    HD_CUDA(cudaMemcpy2DAsync(r.y, r.nrhs * es, sg.yc.p + c0, C * es, r.nrhs * es, m.N, cudaMemcpyDefault, st));
+    c0 += r.nrhs;
+  }
+  HD_CUDA(cudaStreamSynchronize(st));
+  return check_waits(m.h, st);
 }
 
 int run_request(Model& m, const Request& r, cudaStream_t st, Staging& sg) {
@@ -257,6 +293,8 @@ void worker(hodlrdd_server_s* s) {
     int64_t id = 0;
     Model* m = nullptr;
     Request r;
+    std::vector<int64_t> batch;  // further products of the same model, run with r
+    std::vector<Request> rs;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       const int max_solves = s->nworkers > 1 ? s->nworkers - 1 : 1;
@@ -276,19 +314,50 @@ void worker(hodlrdd_server_s* s) {
       r = q;
       m = s->models[(size_t)r.model].get();
       m->last_use = ++s->tick;
+      // continuous batching: products of the same model queued meanwhile join
+      // this one, up to batch_cols columns (FP32-I/O forms with stored factors)
+      if (r.kind == HODLRDD_REQ_MATVEC && s->batch_cols > 1 && m->opt.precision != HODLRDD_PREC_FP64 &&
+          m->opt.lowrank_form == 0) {
+        int64_t cols = r.nrhs;
+        for (auto it = s->queue_mv.begin(); it != s->queue_mv.end();) {
+          Request& q2 = s->reqs[*it];
+          if (q2.model == r.model && cols + q2.nrhs <= s->batch_cols) {
+            cols += q2.nrhs;
+            q2.t_start = q.t_start;
+            batch.push_back(*it);
+            it = s->queue_mv.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        if (!batch.empty()) {
+          rs.push_back(r);
+          for (int64_t b : batch) rs.push_back(s->reqs[b]);
+          s->batches += 1;
+          s->batched += (int64_t)rs.size();
+        }
+      }
     }
     int rc = have_stream ? ensure(s, *m, r.kind == HODLRDD_REQ_SOLVE) : HODLRDD_ERR_CUDA;
     const bool ran = rc == HODLRDD_OK;
-    if (ran) rc = run_request(*m, r, r.kind == HODLRDD_REQ_SOLVE ? st_sv : st_mv, sg);
+    if (ran) {
+      if (!rs.empty()) rc = run_batch(*m, rs, st_mv, sg);
+      else rc = run_request(*m, r, r.kind == HODLRDD_REQ_SOLVE ? st_sv : st_mv, sg);
+    }
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (ran) m->running--;
       m->last_use = ++s->tick;
-      Request& q = s->reqs[id];
-      q.status = rc;
-      if (rc != HODLRDD_OK) q.msg = hodlrdd_last_error();
-      q.done = true;
-      q.t_done = now_ms();
+      const std::string msg = rc != HODLRDD_OK ? std::string(hodlrdd_last_error()) : std::string();
+      batch.push_back(id);
+      const double t_done = now_ms();
+      for (int64_t b : batch) {
+        Request& q = s->reqs[b];
+        q.status = rc;
+        if (rc != HODLRDD_OK) q.msg = msg;
+        q.done = true;
+        q.t_done = t_done;
+      }
       if (r.kind == HODLRDD_REQ_SOLVE) s->solves_running--;
     }
     s->cv_done.notify_all();
@@ -399,6 +468,24 @@ extern "C" int hodlrdd_server_stats(hodlrdd_server s, int64_t* out) {
   out[2] = s->builds;
   out[3] = s->evictions;
   out[4] = (int64_t)(s->queue_mv.size() + s->queue_sv.size());
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_set_batching(hodlrdd_server s, int max_cols) {
+  if (!s || max_cols < 0) {
+    set_error("hodlrdd_server_set_batching: NULL server or max_cols < 0");
+    return HODLRDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->batch_cols = max_cols;
+  return HODLRDD_OK;
+}
+
+extern "C" int hodlrdd_server_batch_stats(hodlrdd_server s, int64_t* out) {
+  if (!s || !out) return HODLRDD_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = s->batches;
+  out[1] = s->batched;
   return HODLRDD_OK;
 }
 

@@ -1,7 +1,8 @@
 """hodlrdd_server: requests over models kept resident under a device-memory
-budget. Every result equals the model's handle alone (bitwise for products);
-a budget below the models' total size evicts and rebuilds without changing a
-result; solves reach the FP64 system's tolerance."""
+budget. A product that runs alone equals the model's handle alone bitwise; a
+batched product (continuous batching of one model's queued products) equals it
+within the chunked FP32 bound; a budget below the models' total size evicts and
+rebuilds without changing a result; solves reach the FP64 system's tolerance."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,7 @@ def test_products_equal_alone_and_in_the_mix(env, tight):
     # tight: room for the largest model and a bit more, far below all of them together
     budget = int(1.5 * max(sizes)) if tight else int(64e9)
     srv = hd.Server(budget, workers=3)
+    srv.set_batching(0)  # every product alone: bitwise equal to the handle's
     ids = [srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision=prec) for w in ws]
     rng = np.random.default_rng(0)
     order = rng.integers(0, len(ws), 40)
@@ -66,6 +68,43 @@ def test_products_equal_alone_and_in_the_mix(env, tight):
         assert st["resident_models"] >= 1
     else:
         assert st["evictions"] == 0 and st["builds"] == len(ws)
+    srv.close()
+
+
+FP32_WIDE_BOUND = 5e-6  # FP32 forms, chunks of 4-16 right-hand sides (uncompensated applies)
+TC_BOUND = 5e-6         # the tensor-core form
+
+
+@pytest.mark.parametrize("prec", ["fp32+fp16", "fp16x2"])
+def test_continuous_batching(env, prec):
+    """Many products of two models submitted at once: a worker that starts one
+    takes the model's other queued products along and runs them as one product
+    over their columns. Every result stays within the form's bound of the
+    handle alone, and the server reports the batches."""
+    torch, oracle, hd = env
+    ws = [models()[1], models()[3]]
+    bound = TC_BOUND if prec == "fp16x2" else FP32_WIDE_BOUND
+    hs = [gpu_handle(hd, w, precision=prec) for w in ws]
+    rng = np.random.default_rng(3)
+    xs = [[np.ascontiguousarray(rng.standard_normal((w.N, k)), dtype=np.float32) for k in (1, 2, 3, 1, 5, 1, 2, 1)]
+          for w in ws]
+    ref = [[np.asarray(h.matvec(x)) for x in xl] for h, xl in zip(hs, xs)]
+    for h in hs:
+        h.close()
+    srv = hd.Server(int(64e9), workers=1)
+    ids = [srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision=prec) for w in ws]
+    # build both models first, then queue everything while the worker is busy
+    for m in range(2):
+        srv.wait(srv.submit(ids[m], xs[m][0]))
+    reqs = []
+    for k in range(len(xs[0])):
+        for m in range(2):
+            reqs.append((m, k, srv.submit(ids[m], xs[m][k])))
+    for m, k, r in reqs:
+        y, _ = srv.wait(r)
+        assert relerr(y, ref[m][k]) <= bound, (m, k)
+    st = srv.stats()
+    assert st["batches"] >= 1 and st["batched_requests"] >= 2
     srv.close()
 
 
@@ -142,6 +181,7 @@ def test_solve_whose_twin_does_not_fit_beside_running_products(env):
     h64.close()
     budget = sizes[0] + twin // 2
     srv = hd.Server(budget, workers=3)
+    srv.set_batching(0)  # products alone: bitwise equal to the model's handle
     mid = srv.add(w.points, w.kernel, w.params, w.leaf, w.tol, precision="fp32")
     x = np.ascontiguousarray(w.x, dtype=np.float32)
     y0, _ = srv.wait(srv.submit(mid, x))  # resident before the mix
