@@ -508,6 +508,25 @@ def serving_line(args, torch, hd, rates=(200.0, 50.0), seconds=3.0, n_models=6, 
                        "p99_ms": pct(lat["matvec"], 0.99), "service_p50_ms": pct(svc["matvec"], 0.5)},
             "solve": {"count": len(lat["solve"]), "p50_ms": pct(lat["solve"], 0.5), "p99_ms": pct(lat["solve"], 0.99),
                       "service_p50_ms": pct(svc["solve"], 0.5)}})
+    # a burst: 64 single-column products per model submitted at once, with the
+    # model's queued products batched into wide products, and with batching off
+    burst = {}
+    for cols in (64, 0):
+        srv.set_batching(cols)
+        b0 = srv.stats()
+        t0 = time.perf_counter()
+        rb = [srv.submit(ids[m], xs32[m]) for _ in range(64) for m in range(n_models)]
+        for r in rb:
+            srv.wait(r)
+        dt = time.perf_counter() - t0
+        b1 = srv.stats()
+        burst["batched" if cols else "alone"] = {
+            "requests": len(rb), "seconds": dt, "rps": len(rb) / dt,
+            "n_rhs_per_s": sum(w.N for w in specs) * 64 / dt,
+            "batches": b1["batches"] - b0["batches"], "batched_requests": b1["batched_requests"] - b0["batched_requests"]}
+    burst["speedup_batched_vs_alone"] = burst["alone"]["seconds"] / burst["batched"]["seconds"]
+    out["burst"] = burst
+    srv.set_batching(64)
     out["server"] = srv.stats()
     srv.close()
     return out
