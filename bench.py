@@ -62,6 +62,7 @@ def parse():
                    help="run only this workload's products (--steps of them after --warmup) and print its line; "
                         "for profiling")
     p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
+    p.add_argument("--solve-n", type=int, default=262144, help="points of the integral-equation solve")
     return p.parse_args()
 
 
@@ -769,7 +770,7 @@ def solve_only(args):
     from paper_2209_05819_gb300 import build as cbuild
 
     cbuild.build()
-    print(json.dumps(solve_line(args, torch, hd)))
+    print(json.dumps(solve_line(args, torch, hd, N=args.solve_n)))
 
 
 def serve_only(args):
