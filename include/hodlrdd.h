@@ -493,6 +493,23 @@ int hodlrdd_import_factors(hodlrdd_handle h, const int32_t* rank, const int32_t*
 int hodlrdd_debug_expire_wait(hodlrdd_handle h, long long cycles);
 
 /*
+ * Test entry for the failure paths of device allocations: the k-th following
+ * device allocation of the library (k >= 0, counted process-wide) fails as if
+ * the device were out of memory, once; k < 0 turns the injection off.
+ * Optional scratch (the ACA's one-pass pool) is not counted. Always HODLRDD_OK.
+ */
+int hodlrdd_debug_fail_alloc_after(int64_t k);
+
+/*
+ * Test entry: caps the device pool in which the ACA keeps each block's factors
+ * during its one pass (bytes; -1 restores the default, half of the free device
+ * memory beyond 2 GB, at most 128 GB; 0 disables it). Blocks that do not fit are
+ * recomputed by a second pass with the same arithmetic, so the factors do not
+ * depend on the cap. Process-wide; always HODLRDD_OK.
+ */
+int hodlrdd_debug_aca_pool_bytes(int64_t bytes);
+
+/*
  * Measurement aid (the paper has no counterpart): throughput of the arithmetic
  * pipes the on-the-fly kernel evaluation and the FP64 form are bound by, on the
  * current device, each timed with CUDA events on `stream` (best of three

@@ -89,6 +89,7 @@ def load():
         "hodlrdd_forest_stats": (i32, [vp, C.POINTER(i64)]),
         "hodlrdd_forest_destroy": (i32, [vp]),
         "hodlrdd_debug_ff_eval": (i32, [i32, vp, dbl, vp, vp, i64]),
+        "hodlrdd_debug_aca_pool_bytes": (i32, [i64]),
         "hodlrdd_solve_options_default": (i32, [C.POINTER(SolveOptions)]),
         "hodlrdd_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOptions), C.POINTER(SolveStats), vp]),
         "hodlrdd_destroy": (i32, [vp]),
@@ -665,3 +666,8 @@ def debug_ff_eval(kernel: int, params, h: float, s) -> np.ndarray:
     _check(load().hodlrdd_debug_ff_eval(int(kernel), p.ctypes.data, float(h), sa.ctypes.data, out.ctypes.data,
                                         int(sa.size)), "hodlrdd_debug_ff_eval")
     return out
+
+
+def debug_aca_pool_bytes(nbytes: int):
+    """Cap the ACA's one-pass factor pool (bytes; -1: default, 0: two passes)."""
+    load().hodlrdd_debug_aca_pool_bytes(int(nbytes))

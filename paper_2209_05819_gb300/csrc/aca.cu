@@ -15,9 +15,13 @@
 // norm update run one per lane, each summed in index order, so a warp rounds
 // exactly like a sequential FP64 evaluation (this file is compiled with FP
 // contraction off). Larger blocks get a whole CTA. Each team keeps its block's
-// u_k, v_k in a private scratch slab. Pass 1 records ranks; after the host has
-// laid out the exact output, pass 2 repeats the same arithmetic and writes the
-// factors (FP64) and pivots. No spin-waits: every loop is bounded by min(m, n).
+// u_k, v_k in a private scratch slab. One pass computes every block: a team that
+// finishes a block reserves room for its factors and pivots in a device pool
+// (an atomic bump pointer) and copies them there; the host then lays out the
+// block-ordered output and a compaction kernel moves each block's factors into
+// it. Blocks that found the pool full (possible only when device memory is
+// short) are recomputed by a second pass over those blocks alone, with the same
+// arithmetic. No spin-waits: every loop is bounded by min(m, n).
 #include <algorithm>
 #include <climits>
 
@@ -54,6 +58,11 @@ struct AcaArgs {
   int32_t* sig_out;
   int32_t* tau_out;
   int32_t* err;  // set when pass 2 disagrees with pass 1 (nothing is written then)
+  // pass 1: the pool (factors k (m + n) doubles, then the 2k pivots as doubles)
+  double* pool;
+  int64_t pool_elems;
+  unsigned long long* pool_top;
+  int64_t* poff;  // per block: its place in the pool, -1 when it did not fit
 };
 
 __device__ __forceinline__ double entry(const AcaArgs& A, const double* xr, int64_t col) {
@@ -69,6 +78,7 @@ struct WarpTeam {
   __device__ int tid() const { return threadIdx.x & 31; }
   __device__ int size() const { return 32; }
   __device__ void sync() const { __syncwarp(); }
+  __device__ long long bcast(long long v) const { return __shfl_sync(0xffffffffu, v, 0); }
   __device__ void argmax(double& v, int& i) const {
     for (int o = 16; o; o >>= 1) {
       double ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -101,9 +111,17 @@ struct WarpTeam {
 struct CtaTeam {
   double* red_v;
   int* red_i;
+  long long* red_ll;
   __device__ int tid() const { return threadIdx.x; }
   __device__ int size() const { return blockDim.x; }
   __device__ void sync() const { __syncthreads(); }
+  __device__ long long bcast(long long v) const {
+    if (threadIdx.x == 0) *red_ll = v;
+    __syncthreads();
+    v = *red_ll;
+    __syncthreads();
+    return v;
+  }
   __device__ void argmax(double& v, int& i) const {
     for (int o = 16; o; o >>= 1) {
       double ov = __shfl_xor_sync(0xffffffffu, v, o);
@@ -283,6 +301,28 @@ __device__ void aca_block(const Team& T, const AcaArgs& A, int32_t b, double* Us
     A.dense[b] = dense ? 1 : 0;
     A.capped[b] = capped ? 1 : 0;
   }
+  if (A.U64 == nullptr && A.pool != nullptr) {
+    // one pass: the factors and pivots into the pool, if there is room
+    long long off = -1;
+    if (rank_out > 0) {
+      const long long need = (long long)k * (m + n) + 2LL * k;
+      if (tid == 0) {
+        const unsigned long long at = atomicAdd(A.pool_top, (unsigned long long)need);
+        off = at + (unsigned long long)need <= (unsigned long long)A.pool_elems ? (long long)at : -1LL;
+      }
+      off = T.bcast(off);
+      if (off >= 0) {
+        double* P = A.pool + off;
+        for (int64_t e = tid; e < (int64_t)k * m; e += TS) P[e] = Us[e];
+        for (int64_t e = tid; e < (int64_t)k * n; e += TS) P[(int64_t)k * m + e] = Vs[e];
+        for (int q = tid; q < k; q += TS) {
+          P[(int64_t)k * (m + n) + q] = (double)S.sig[q];
+          P[(int64_t)k * (m + n) + k + q] = (double)S.tau[q];
+        }
+      }
+    }
+    if (tid == 0) A.poff[b] = off;
+  }
   if (A.U64 != nullptr && !dense && k > 0) {
     double* Uo = A.U64 + A.uoff[b];
     double* Vo = A.V64 + A.voff[b];
@@ -320,10 +360,11 @@ __global__ void k_aca_cta(AcaArgs A, int mcap) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red_v[32];
   __shared__ int red_i[32];
+  __shared__ long long red_ll;
   __shared__ int s_it;
   TeamSmem S = carve(smem, A.rcap, mcap);
   double* slab = A.slab + (size_t)blockIdx.x * A.slab_elems;
-  CtaTeam T{red_v, red_i};
+  CtaTeam T{red_v, red_i, &red_ll};
   while (true) {
     if (threadIdx.x == 0) s_it = atomicAdd(A.counter, 1);
     __syncthreads();
@@ -334,6 +375,28 @@ __global__ void k_aca_cta(AcaArgs A, int mcap) {
     double* Us = slab;
     double* Vs = slab + (size_t)A.rcap * A.m[b];
     aca_block(T, A, b, Us, Vs, S);
+  }
+}
+
+// Block-ordered factors and pivots from the pool: one CTA per block (stride).
+__global__ void k_aca_compact(int64_t nblk, const int64_t* __restrict__ poff, const int32_t* __restrict__ rank,
+                              const int32_t* __restrict__ bm, const int32_t* __restrict__ bn,
+                              const double* __restrict__ pool, const int64_t* __restrict__ uoff,
+                              const int64_t* __restrict__ voff, const int64_t* __restrict__ toff,
+                              double* __restrict__ U64, double* __restrict__ V64, int32_t* __restrict__ sig,
+                              int32_t* __restrict__ tau) {
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int k = rank[b];
+    const int64_t off = poff[b];
+    if (k <= 0 || off < 0) continue;
+    const int64_t m = bm[b], n = bn[b];
+    const double* P = pool + off;
+    for (int64_t e = threadIdx.x; e < k * m; e += blockDim.x) U64[uoff[b] + e] = P[e];
+    for (int64_t e = threadIdx.x; e < k * n; e += blockDim.x) V64[voff[b] + e] = P[k * m + e];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+      sig[toff[b] + q] = (int32_t)P[k * (m + n) + q];
+      tau[toff[b] + q] = (int32_t)P[k * (m + n) + k + q];
+    }
   }
 }
 
@@ -469,12 +532,43 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
   base.rank = h->rank.p;
   base.dense = h->dense.p;
   base.capped = capped.p;
-  int rc = launch_all(base);  // pass 1: ranks
+  // the pool of the one-pass factors: half of the free device memory beyond a
+  // reserve (the block-ordered output needs as much again), at most 128 GB
+  DevBuf<double> pool;
+  DevBuf<unsigned long long> pool_top;
+  DevBuf<int64_t> poff;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    const int64_t reserve = (int64_t)2 << 30;
+    int64_t bytes = std::min<int64_t>(((int64_t)fr - reserve) / 2, (int64_t)128 << 30);
+    if (bytes < ((int64_t)64 << 20)) bytes = 0;
+    const int64_t cap = debug_aca_pool_bytes();  // tests: a small pool sends blocks to the second pass
+    if (cap >= 0) bytes = std::min(bytes, cap);
+    if (bytes >= (int64_t)sizeof(double) && pool.try_alloc((size_t)bytes / sizeof(double)) &&
+        pool_top.try_alloc(1) && poff.try_alloc(nblk) &&
+        cudaMemsetAsync(pool_top.p, 0, sizeof(unsigned long long), h->st) == cudaSuccess &&
+        cudaStreamSynchronize(h->st) == cudaSuccess) {
+      base.pool = pool.p;
+      base.pool_elems = (int64_t)pool.n;
+      base.pool_top = pool_top.p;
+      base.poff = poff.p;
+    } else {
+      cudaGetLastError();
+      pool.release();  // two passes: ranks, then the same arithmetic writing the factors
+    }
+  }
+  int rc = launch_all(base);  // ranks (and, with the pool, the factors)
   if (rc == HODLRDD_OK) {
     std::vector<int32_t> hcap;
+    std::vector<int64_t> hpoff;
     rc = download(h->h_rank, h->rank.p, nblk, h->st);
     if (rc == HODLRDD_OK) rc = download(h->h_dense, h->dense.p, nblk, h->st);
     if (rc == HODLRDD_OK) rc = download(hcap, capped.p, nblk, h->st);
+    if (rc == HODLRDD_OK && base.pool) rc = download(hpoff, poff.p, nblk, h->st);
     if (rc == HODLRDD_OK && cudaStreamSynchronize(h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
     if (rc == HODLRDD_OK) {
       std::vector<int64_t> toff(nblk + 1, 0);
@@ -495,12 +589,34 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
       if (rc == HODLRDD_OK) rc = h->piv_sigma.alloc(std::max<int64_t>(h->total_rank, 1));
       if (rc == HODLRDD_OK) rc = h->piv_tau.alloc(std::max<int64_t>(h->total_rank, 1));
       if (rc == HODLRDD_OK && cudaStreamSynchronize(h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
+      // blocks whose factors are in the pool move to their place; the others
+      // (the pool was full, or there is no pool) are recomputed below
+      bool again = false;
+      for (auto& B : bins) {
+        std::vector<int32_t> rest;
+        for (int32_t b : B.list)
+          if (h->h_rank[b] > 0 && (!base.pool || hpoff[b] < 0)) rest.push_back(b);
+        again |= !rest.empty();
+        B.list.swap(rest);
+        if (rc == HODLRDD_OK && !B.list.empty()) rc = upload(B.dlist, B.list, h->st);
+      }
+      if (rc == HODLRDD_OK && base.pool) {
+        k_aca_compact<<<(int)std::min<int64_t>(nblk, (int64_t)dev_sms * 8), 256, 0, h->st>>>(
+            nblk, poff.p, h->rank.p, h->bm.p, h->bn.p, pool.p, du.p, dv.p, h->toff.p, U64.p, V64.p,
+            h->piv_sigma.p, h->piv_tau.p);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "ACA compaction", __FILE__, __LINE__);
+        if (rc == HODLRDD_OK && cudaStreamSynchronize(h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
+      }
+      pool.release();
       DevBuf<int32_t> err;
-      if (rc == HODLRDD_OK) rc = err.alloc(1);
-      if (rc == HODLRDD_OK && cudaMemsetAsync(err.p, 0, sizeof(int32_t), h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
-      if (rc == HODLRDD_OK && cudaStreamSynchronize(h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
-      if (rc == HODLRDD_OK) {
+      if (rc == HODLRDD_OK && again) rc = err.alloc(1);
+      if (rc == HODLRDD_OK && again && cudaMemsetAsync(err.p, 0, sizeof(int32_t), h->st) != cudaSuccess)
+        rc = HODLRDD_ERR_CUDA;
+      if (rc == HODLRDD_OK && again && cudaStreamSynchronize(h->st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
+      if (rc == HODLRDD_OK && again) {
         AcaArgs p2 = base;
+        p2.pool = nullptr;
         p2.err = err.p;
         p2.U64 = U64.p;
         p2.V64 = V64.p;
@@ -509,7 +625,7 @@ int run_aca(hodlrdd_s* h, DevBuf<double>& U64, DevBuf<double>& V64, std::vector<
         p2.toff = h->toff.p;
         p2.sig_out = h->piv_sigma.p;
         p2.tau_out = h->piv_tau.p;
-        rc = launch_all(p2);  // pass 2: same arithmetic, factors written out
+        rc = launch_all(p2);  // the same arithmetic, factors written out
         int32_t herr = 0;
         if (rc == HODLRDD_OK && cudaMemcpy(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost) != cudaSuccess)
           rc = HODLRDD_ERR_CUDA;

@@ -29,6 +29,11 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
 
 void debug_fail_alloc_after(int64_t k) { g_fail_after.store(k); }
 
+namespace {
+std::atomic<int64_t> g_aca_pool_cap{-1};
+}  // namespace
+int64_t debug_aca_pool_bytes() { return g_aca_pool_cap.load(); }
+
 int dev_alloc(void** p, size_t bytes) {
   int64_t f = g_fail_after.load();
   if (f >= 0) {
@@ -605,8 +610,14 @@ int hodlrdd_get_profile(hodlrdd_handle h, double* ms, int64_t* chunks, int64_t* 
   return HODLRDD_OK;
 }
 
-// Test hook (not part of the public header): make the k-th device allocation
-// from now fail with HODLRDD_ERR_OOM; k < 0 disarms.
+// Test hook: caps the ACA's one-pass factor pool (bytes; -1 default).
+int hodlrdd_debug_aca_pool_bytes(int64_t bytes) {
+  g_aca_pool_cap.store(bytes < 0 ? -1 : bytes);
+  return HODLRDD_OK;
+}
+
+// Test hook: make the k-th device allocation from now fail with
+// HODLRDD_ERR_OOM; k < 0 disarms.
 int hodlrdd_debug_fail_alloc_after(int64_t k) {
   debug_fail_alloc_after(k);
   return HODLRDD_OK;

@@ -54,6 +54,7 @@ struct PerDeviceOnce {
 
 // Test hook: make the k-th device allocation from now fail (k < 0: never).
 void debug_fail_alloc_after(int64_t k);
+int64_t debug_aca_pool_bytes();  // test hook: cap on the one-pass ACA pool (-1: none)
 int dev_alloc(void** p, size_t bytes);
 
 // Owning device buffer. Frees on destruction; never copied.
@@ -88,6 +89,20 @@ struct DevBuf {
     p = static_cast<T*>(q);
     n = count;
     return HODLRDD_OK;
+  }
+  // An optional scratch: cudaMalloc without the allocation-failure hook (its
+  // failure only selects a slower path); false when it could not be had.
+  bool try_alloc(size_t count) {
+    release();
+    if (count == 0) return false;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    p = static_cast<T*>(q);
+    n = count;
+    return true;
   }
   size_t bytes() const { return n * sizeof(T); }
 };

@@ -117,3 +117,42 @@ def test_repeated_builds_are_bitwise_identical():
         assert np.array_equal(ref[0], got[0])
         for (U0, V0), (U1, V1) in zip(ref[1], got[1]):
             assert np.array_equal(U0, U1) and np.array_equal(V0, V1)
+
+
+@pytest.mark.parametrize("pool_bytes", [0, 1 << 16, 1 << 22])
+def test_one_pass_pool_does_not_change_the_factors(pool_bytes):
+    """The ACA keeps each block's factors in a device pool during its one pass;
+    blocks that find the pool full are recomputed by a second pass. A pool of
+    0 (two passes for every block), 64 KB (a few blocks fit) or 4 MB gives the
+    same ranks, pivots, factors and product, bitwise, as the default pool."""
+    torch = require_cuda()
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import _binding as B
+
+    w = W.make("t", 3, 12000, W.K_INV_R, (1.0, 0.0, 0, 0), 32, 1e-8, nrhs=1, seed=77)
+    pts = torch.from_numpy(w.points).cuda()
+    x = torch.from_numpy(np.ascontiguousarray(w.x)).cuda()
+
+    def build():
+        h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol)
+        rec = h.blocks()
+        low = np.flatnonzero(rec[:, 7] > 0)
+        pick = low[:: max(1, len(low) // 40)]
+        fac = [h.factors(b, int(rec[b, 4]), int(rec[b, 6]), int(rec[b, 7])) for b in pick]
+        piv = [h.pivots(b, int(rec[b, 7])) for b in pick]
+        y = h.matvec(x).cpu().numpy()
+        h.close()
+        return rec, fac, piv, y
+
+    ref = build()
+    try:
+        B.debug_aca_pool_bytes(pool_bytes)
+        got = build()
+    finally:
+        B.debug_aca_pool_bytes(-1)
+    assert np.array_equal(ref[0], got[0])
+    for (U0, V0), (U1, V1) in zip(ref[1], got[1]):
+        assert np.array_equal(U0, U1) and np.array_equal(V0, V1)
+    for (s0, t0), (s1, t1) in zip(ref[2], got[2]):
+        assert np.array_equal(s0, s1) and np.array_equal(t0, t1)
+    assert np.array_equal(ref[3], got[3])
