@@ -1338,7 +1338,14 @@ int build_plan(hodlrdd_s* h) {
     };
     while (rows_cap > 64 && leaf_tasks(rows_cap) < 8 * (int64_t)sms) rows_cap /= 2;
   }
-  auto add_task = [&](int32_t I0, int32_t m) {
+  // tensor-core tiles: each task's target box, and after packing per task its
+  // box records and per source entry the boxes of its task that read it
+  std::vector<int64_t> tbox_of;  // parallel to t4 (before packing)
+  std::vector<int2> tb4;         // parallel to t4 (after packing): {first record, records}
+  std::vector<int32_t> brow4;    // record: first row of the box within its task
+  std::vector<float4> boff4;     // record: (c_box - c_frame) h_l, the box's offset in the task's frame
+  std::vector<uint32_t> em4;     // parallel to s4: bit b = box b of the task reads the entry
+  auto add_task = [&](int32_t I0, int32_t m, int64_t box) {
     int64_t nsrc = 0;
     for (auto& so : sl) nsrc += so.first.y;
     for (int32_t r0 = 0; r0 < m; r0 += rows_cap) {
@@ -1354,13 +1361,94 @@ int build_plan(hodlrdd_s* h) {
           }
           s4.push_back(make_int4(so.first.x + p0, np, pos, 0));
           o4.push_back(so.second);
+          em4.push_back(~0u);
           pos += np;
         }
       if ((int32_t)s4.size() > first) s4[first].w = (int32_t)s4.size();
       const int32_t mr = std::min(rows_cap, m - r0);
       t4.push_back(make_int4(I0 + r0, mr, s0, (int32_t)s4.size()));
+      tbox_of.push_back(box);
       P.packed_pairs += (int64_t)mr * nsrc;
     }
+  };
+  // Tensor-core tiles hold 128 target rows whatever a task's size: consecutive
+  // tasks [a, b) of one pass at level l whose boxes share their ancestor two
+  // levels up (so every offset below stays an exact small multiple of h_l) are
+  // packed into one task of at most 128 rows and 32 boxes. Its frame is the
+  // first box's; each box keeps a record (first row, offset into the frame);
+  // its sources are the union of the boxes' sources, moved into the frame, each
+  // with the mask of the boxes that read it (the kernel zeroes the other
+  // entries of the tile). Returns the new end of the pass.
+  auto pack_tasks = [&](int64_t a, int64_t b, int l) -> int64_t {
+    std::vector<int4> mt;
+    std::vector<int2> mtb;
+    const double hl = P.h_box[l];
+    for (int64_t i = a; i < b;) {
+      int64_t j = i + 1;
+      int32_t rows = t4[i].y;
+      const uint64_t anc = l >= 2 ? h->lv[l].h_bkey[tbox_of[i]] >> (2 * d) : 0;
+      while (j < b && j - i < 32 && t4[j].x == t4[j - 1].x + t4[j - 1].y && rows + t4[j].y <= 128 &&
+             (l < 2 || (h->lv[l].h_bkey[tbox_of[j]] >> (2 * d)) == anc)) {
+        rows += t4[j].y;
+        ++j;
+      }
+      const int32_t r0 = (int32_t)brow4.size();
+      if (j == i + 1) {
+        mt.push_back(t4[i]);
+        brow4.push_back(0);
+        boff4.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+        mtb.push_back(make_int2(r0, 1));
+        i = j;
+        continue;
+      }
+      int64_t cf[kMaxDim], cb[kMaxDim];
+      coords(l, tbox_of[i], cf);
+      const int32_t e0 = (int32_t)s4.size();
+      std::vector<std::pair<int32_t, int32_t>> seen;  // (source start, entry index)
+      for (int64_t k = i; k < j; ++k) {
+        coords(l, tbox_of[k], cb);
+        float bo[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < d && q < 4; ++q) bo[q] = (float)((double)(cb[q] - cf[q]) * hl);
+        brow4.push_back(t4[k].x - t4[i].x);
+        boff4.push_back(make_float4(bo[0], bo[1], bo[2], bo[3]));
+        const uint32_t bit = 1u << (uint32_t)(k - i);
+        for (int32_t e = t4[k].z; e < t4[k].w; ++e) {
+          const int4 se = s4[e];
+          int32_t at = -1;
+          for (const auto& sv : seen)
+            if (sv.first == se.x) {
+              at = sv.second;
+              break;
+            }
+          if (at < 0) {
+            // the entry's box offset from box k (an integer times h_l), then from the frame
+            const float4 of = o4[e];
+            const float ov[4] = {of.x, of.y, of.z, of.w};
+            float nv[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < d && q < 4; ++q)
+              nv[q] = (float)((std::nearbyint((double)ov[q] / hl) + (double)(cb[q] - cf[q])) * hl);
+            at = (int32_t)s4.size();
+            s4.push_back(make_int4(se.x, se.y, 0, 0));
+            o4.push_back(make_float4(nv[0], nv[1], nv[2], nv[3]));
+            em4.push_back(0u);
+            seen.push_back({se.x, at});
+          }
+          em4[at] |= bit;
+        }
+      }
+      mt.push_back(make_int4(t4[i].x, rows, e0, (int32_t)s4.size()));
+      mtb.push_back(make_int2(r0, (int32_t)(j - i)));
+      i = j;
+    }
+    t4.resize(a);
+    tbox_of.resize(a);
+    tb4.resize(a);
+    for (size_t q = 0; q < mt.size(); ++q) {
+      t4.push_back(mt[q]);
+      tbox_of.push_back(-1);
+      tb4.push_back(mtb[q]);
+    }
+    return (int64_t)t4.size();
   };
   auto box_src = [&](int l, int64_t I, int64_t J) {  // source box J in target box I's frame
     const Level& L = h->lv[l];
@@ -1377,15 +1465,25 @@ int build_plan(hodlrdd_s* h) {
   // its rows, so the order changes no sum)
   auto sort_tasks = [&](int64_t a, int64_t b) {
     if (!tc_tiles) return;  // the CUDA-core tiles keep tree order (they run beside the applies)
-    std::vector<std::pair<int64_t, int4>> w;
+    // a tensor-core tile costs its 128 rows whatever the task's rows
+    std::vector<std::pair<int64_t, int64_t>> w;
     w.reserve((size_t)(b - a));
     for (int64_t t = a; t < b; ++t) {
       int64_t n = 0;
       for (int32_t e = t4[t].z; e < t4[t].w; ++e) n += s4[e].y;
-      w.push_back({-(int64_t)t4[t].y * n, t4[t]});
+      w.push_back({-(int64_t)((t4[t].y + 127) / 128) * n, t});
     }
     std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    for (int64_t t = a; t < b; ++t) t4[t] = w[(size_t)(t - a)].second;
+    std::vector<int4> ts((size_t)(b - a));
+    std::vector<int2> tbs((size_t)(b - a));
+    for (int64_t t = a; t < b; ++t) {
+      ts[(size_t)(t - a)] = t4[w[(size_t)(t - a)].second];
+      tbs[(size_t)(t - a)] = tb4[w[(size_t)(t - a)].second];
+    }
+    for (int64_t t = a; t < b; ++t) {
+      t4[t] = ts[(size_t)(t - a)];
+      tb4[t] = tbs[(size_t)(t - a)];
+    }
   };
   P.coarse4.clear();
   // packed tasks: the FP32 tiles, and the float-float near field of FP64 handles
@@ -1401,9 +1499,9 @@ int build_plan(hodlrdd_s* h) {
         const int64_t b0 = h->h_blk_off[l] + L.h_iloff[i], b1 = h->h_blk_off[l] + L.h_iloff[i + 1];
         for (int64_t b = b0; b < b1; ++b)
           if (h->h_dense[b]) box_src(l, i, h->h_bsj[b]);
-        if (!sl.empty()) add_task(L.h_bstart[i], L.h_bstart[i + 1] - L.h_bstart[i]);
+        if (!sl.empty()) add_task(L.h_bstart[i], L.h_bstart[i + 1] - L.h_bstart[i], i);
       }
-      DL.t1 = (int64_t)t4.size();
+      DL.t1 = tc_tiles ? pack_tasks(DL.t0, (int64_t)t4.size(), l) : (int64_t)t4.size();
       sort_tasks(DL.t0, DL.t1);
       if (DL.t1 > DL.t0) P.coarse4.push_back(DL);
     }
@@ -1469,9 +1567,9 @@ int build_plan(hodlrdd_s* h) {
         const int64_t b0 = h->h_blk_off[lk] + LK.h_iloff[i], b1 = h->h_blk_off[lk] + LK.h_iloff[i + 1];
         for (int64_t b = b0; b < b1; ++b)
           if (!h->h_dense[b]) box_src(lk, i, h->h_bsj[b]);
-        if (!sl.empty()) add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
+        if (!sl.empty()) add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i], i);
       }
-      P.excl4.t1 = (int64_t)t4.size();
+      P.excl4.t1 = tc_tiles ? pack_tasks(P.excl4.t0, (int64_t)t4.size(), lk) : (int64_t)t4.size();
       sort_tasks(P.excl4.t0, P.excl4.t1);
       const int lp = lk - 1;
       const Level& LP = h->lv[lp];
@@ -1480,9 +1578,9 @@ int build_plan(hodlrdd_s* h) {
       for (int64_t pb = 0; pb < LP.nb; ++pb) {
         sl.clear();
         for (int64_t qb : nbr[pb]) box_src(lp, pb, qb);
-        add_task(LP.h_bstart[pb], LP.h_bstart[pb + 1] - LP.h_bstart[pb]);
+        add_task(LP.h_bstart[pb], LP.h_bstart[pb + 1] - LP.h_bstart[pb], pb);
       }
-      P.leaf4.t1 = (int64_t)t4.size();
+      P.leaf4.t1 = tc_tiles ? pack_tasks(P.leaf4.t0, (int64_t)t4.size(), lp) : (int64_t)t4.size();
       sort_tasks(P.leaf4.t0, P.leaf4.t1);
     } else {
       P.excl4 = DenseLevel{lk, 0, 0};
@@ -1496,9 +1594,9 @@ int build_plan(hodlrdd_s* h) {
           for (int64_t b = b0; b < b1; ++b)
             if (h->h_dense[b]) box_src(lk, i, h->h_bsj[b]);
         }
-        add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i]);
+        add_task(LK.h_bstart[i], LK.h_bstart[i + 1] - LK.h_bstart[i], i);
       }
-      P.leaf4.t1 = (int64_t)t4.size();
+      P.leaf4.t1 = tc_tiles ? pack_tasks(P.leaf4.t0, (int64_t)t4.size(), lk) : (int64_t)t4.size();
       sort_tasks(P.leaf4.t0, P.leaf4.t1);
     }
     if ((int64_t)s4.size() >= INT32_MAX) {
@@ -1538,6 +1636,16 @@ int build_plan(hodlrdd_s* h) {
       HD_TRY(upload(P.tasks4, t4, st));
       HD_TRY(upload(P.srcs4, s4, st));
       HD_TRY(upload(P.soff4, o4, st));
+      P.tbox4.release();
+      P.brow4.release();
+      P.boff4.release();
+      P.emask4.release();
+      if (tc_tiles && !t4.empty()) {
+        HD_TRY(upload(P.tbox4, tb4, st));
+        HD_TRY(upload(P.brow4, brow4, st));
+        HD_TRY(upload(P.boff4, boff4, st));
+        HD_TRY(upload(P.emask4, em4, st));
+      }
     }
     HD_CUDA(cudaStreamSynchronize(st));
   }

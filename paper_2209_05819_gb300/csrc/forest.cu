@@ -96,6 +96,10 @@ struct hodlrdd_forest_s {
   hd::DevBuf<float4> nsoff, nhi, nlo;
   hd::DevBuf<int2> nbase;
   hd::DevBuf<float2> nsd;
+  hd::DevBuf<int2> ntbox;      // per task: its box records (packed small boxes)
+  hd::DevBuf<int32_t> nbrow;
+  hd::DevBuf<float4> nboff;
+  hd::DevBuf<uint32_t> nemask;  // per source entry
   std::vector<std::pair<int64_t, int64_t>> passes;
   cudaStream_t st = nullptr, aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -307,29 +311,56 @@ int forest_near(hodlrdd_forest_s* f) {
   std::vector<int2> base;
   std::vector<float2> sd;
   std::vector<std::vector<int4>> t4(n), s4(n);
-  std::vector<std::vector<float4>> o4(n);
-  std::vector<int64_t> soff_at(n);
+  std::vector<std::vector<float4>> o4(n), bo4(n);
+  std::vector<std::vector<int2>> tb4(n);
+  std::vector<std::vector<int32_t>> br4(n);
+  std::vector<std::vector<uint32_t>> em4(n);
+  std::vector<int64_t> soff_at(n), rec_at(n);
   for (int i = 0; i < n; ++i) {
     const Plan& P = f->h[i]->plan;
     HD_TRY(download_all(t4[i], P.tasks4, st));
     HD_TRY(download_all(s4[i], P.srcs4, st));
     HD_TRY(download_all(o4[i], P.soff4, st));
+    HD_TRY(download_all(tb4[i], P.tbox4, st));
+    HD_TRY(download_all(br4[i], P.brow4, st));
+    HD_TRY(download_all(bo4[i], P.boff4, st));
+    HD_TRY(download_all(em4[i], P.emask4, st));
   }
   HD_CUDA(cudaStreamSynchronize(st));
+  std::vector<uint32_t> emask;
+  std::vector<int32_t> brow;
+  std::vector<float4> boff;
   for (int i = 0; i < n; ++i) {
     soff_at[i] = (int64_t)srcs.size();
     srcs.insert(srcs.end(), s4[i].begin(), s4[i].end());
     soff.insert(soff.end(), o4[i].begin(), o4[i].end());
+    // a tree without packing tables: one box per task, every entry read by it
+    if (tb4[i].size() != t4[i].size()) {
+      tb4[i].clear();
+      br4[i].clear();
+      bo4[i].clear();
+      for (size_t t = 0; t < t4[i].size(); ++t) {
+        tb4[i].push_back(make_int2((int32_t)t, 1));
+        br4[i].push_back(0);
+        bo4[i].push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+      }
+    }
+    if (em4[i].size() != s4[i].size()) em4[i].assign(s4[i].size(), ~0u);
+    emask.insert(emask.end(), em4[i].begin(), em4[i].end());
+    rec_at[i] = (int64_t)brow.size();
+    brow.insert(brow.end(), br4[i].begin(), br4[i].end());
+    boff.insert(boff.end(), bo4[i].begin(), bo4[i].end());
   }
-  if ((int64_t)srcs.size() >= INT32_MAX) {
+  if ((int64_t)srcs.size() >= INT32_MAX || (int64_t)brow.size() >= INT32_MAX) {
     set_error("hodlrdd_forest_create: too many near-field sources");
     return HODLRDD_ERR_UNSUPPORTED;
   }
+  std::vector<int2> tbox;
   f->passes.clear();
   for (size_t k = 0; k < npass; ++k) {
     std::vector<std::pair<int64_t, size_t>> order;  // (-work, index into the pass's entries)
     std::vector<int4> pt;
-    std::vector<int2> pb;
+    std::vector<int2> pb, ptb;
     std::vector<float2> ps;
     for (int i = 0; i < n; ++i) {
       if (k >= ranges[i].size()) continue;
@@ -344,6 +375,7 @@ int forest_near(hodlrdd_forest_s* f) {
         pt.push_back(T);
         pb.push_back(make_int2((int32_t)cbase[i][R.level], (int32_t)f->info[i].off));
         ps.push_back(make_float2(R.scale, R.diag));
+        ptb.push_back(make_int2(tb4[i][t].x + (int32_t)rec_at[i], tb4[i][t].y));
       }
     }
     std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
@@ -352,6 +384,7 @@ int forest_near(hodlrdd_forest_s* f) {
       tasks.push_back(pt[o.second]);
       base.push_back(pb[o.second]);
       sd.push_back(ps[o.second]);
+      tbox.push_back(ptb[o.second]);
     }
     f->passes.push_back({t0, (int64_t)tasks.size()});
   }
@@ -360,6 +393,10 @@ int forest_near(hodlrdd_forest_s* f) {
   HD_TRY(upload(f->nsoff, soff.empty() ? std::vector<float4>{make_float4(0, 0, 0, 0)} : soff, st));
   HD_TRY(upload(f->nbase, base.empty() ? std::vector<int2>{make_int2(0, 0)} : base, st));
   HD_TRY(upload(f->nsd, sd.empty() ? std::vector<float2>{make_float2(0, 0)} : sd, st));
+  HD_TRY(upload(f->ntbox, tbox.empty() ? std::vector<int2>{make_int2(0, 1)} : tbox, st));
+  HD_TRY(upload(f->nbrow, brow.empty() ? std::vector<int32_t>{0} : brow, st));
+  HD_TRY(upload(f->nboff, boff.empty() ? std::vector<float4>{make_float4(0, 0, 0, 0)} : boff, st));
+  HD_TRY(upload(f->nemask, emask.empty() ? std::vector<uint32_t>{~0u} : emask, st));
   return HODLRDD_OK;
 }
 
@@ -396,7 +433,8 @@ int forest_launch(hodlrdd_forest_s* f) {
   for (const auto& ps : f->passes)
     HD_TRY(launch_tc_near_raw(f->d, f->kid, f->aux, ps.second - ps.first, f->ntasks.p + ps.first, f->nsrcs.p,
                               f->nsoff.p, f->nhi.p, f->nlo.p, f->xt.p, colmax, f->kc, f->ynear.p,
-                              f->nbase.p + ps.first, f->nsd.p + ps.first, f->err.p));
+                              f->nbase.p + ps.first, f->nsd.p + ps.first,
+                              TcPack{f->ntbox.p + ps.first, f->nbrow.p, f->nboff.p, f->nemask.p}, f->err.p));
   HD_CUDA(cudaEventRecord(f->ev_join, f->aux));
   TcLaunch lu{&f->u, f->t.p, colmax, f->vmap.p, f->fac.p, f->wbox.p, f->ylev.p, f->pbuf.p, 0};
   HD_TRY(launch_tc_stage(false, lu, f->err.p, st));

@@ -132,7 +132,8 @@ void fill_stats(hodlrdd_s* h) {
                             P.us2.stages.bytes() + P.vs2.splits.bytes() + P.us2.splits.bytes() + P.vmap2.bytes() +
                             h->pbuf.bytes() + P.tasks.bytes() +
                             P.srcs.bytes() + P.soff.bytes() + P.tasks4.bytes() + P.srcs4.bytes() +
-                            P.soff4.bytes());
+                            P.soff4.bytes() + P.tbox4.bytes() + P.brow4.bytes() + P.boff4.bytes() +
+                            P.emask4.bytes());
   bytes += (int64_t)(P.sk_lu.bytes() + P.sk_luoff.bytes() + P.sk_blist.bytes() + P.sk_rtask.bytes() +
                      P.sk_rsum.bytes() + P.sk_rows.bytes() + P.sk_ctask.bytes() + P.sk_cols.bytes() +
                      P.sk_boff.bytes() + P.sk_part.bytes() + P.sk_hi.bytes() + P.sk_lo.bytes());

@@ -386,6 +386,11 @@ struct Plan {
   DevBuf<int4> tasks4;             // {I0, m, src_begin, src_end}, m <= 256
   DevBuf<int4> srcs4;              // {J0, n, position in its staging chunk, chunk end on a chunk's first entry}
   DevBuf<float4> soff4;            // per source: (c_J - c_I) h_l, exact in FP32
+  // tensor-core tiles: small boxes packed into one task (null when not packed)
+  DevBuf<int2> tbox4;              // per task: {first box record, boxes}
+  DevBuf<int32_t> brow4;           // per record: first row of the box within its task
+  DevBuf<float4> boff4;            // per record: the box's offset in the task's frame
+  DevBuf<uint32_t> emask4;         // per source entry: boxes of its task that read it
   std::vector<DevBuf<float4>> hi4, lo4;  // per level (where used)
   std::vector<DevBuf<float4>> hq4, lq4;  // FP64 float-float near field: box units, 2^-21 grid + remainder
   std::vector<DenseLevel> coarse4; // dense IL blocks above the leaf level
@@ -517,10 +522,18 @@ int64_t tc_device_bytes(const hodlrdd_s* h);
 bool tc_near_supported(const hodlrdd_s* h);
 inline bool tc_near_kernel(int kid) { return kid != HODLRDD_K_INV_R && kid != HODLRDD_K_INV_R2_4D; }
 int launch_tc_near(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigned int* colmax);
+// Packed tensor-core tasks (small boxes in one tile): null pointers = one box per task.
+struct TcPack {
+  const int2* tbox;
+  const int32_t* brow;
+  const float4* boff;
+  const uint32_t* emask;
+};
+inline TcPack tc_pack(const Plan& P) { return TcPack{P.tbox4.p, P.brow4.p, P.boff4.p, P.emask4.p}; }
 int launch_tc_near_raw(int d, int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs,
                        const float4* soff, const float4* Hi, const float4* Lo, const float* xt,
                        const unsigned int* colmax, float kc, float* ynear, const int2* tbase, const float2* tsd,
-                       int32_t* err);
+                       TcPack pk, int32_t* err);
 // tensor-core applies and combine over an explicit panel set (tcapply.cu)
 struct TcLaunch {
   const TcStream* S;

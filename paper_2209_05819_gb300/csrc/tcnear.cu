@@ -90,11 +90,18 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
                                                             float kscale, float kdiag, float* __restrict__ ynear,
                                                             const int2* __restrict__ tbase,
                                                             const float2* __restrict__ tsd,
-                                                            int32_t* __restrict__ err) {
+                                                            TcPack pk, int32_t* __restrict__ err) {
+  const int2* __restrict__ tbox = pk.tbox;
+  const int32_t* __restrict__ brow = pk.brow;
+  const float4* __restrict__ boff = pk.boff;
+  const uint32_t* __restrict__ emask = pk.emask;
   extern __shared__ __align__(1024) unsigned char nr_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(nr_raw) + 1023) & ~uintptr_t(1023));
   __shared__ float4 s_hi[2][kNrKC], s_lo[2][kNrKC];
   __shared__ int s_row[2][kNrKC];
+  __shared__ uint32_t s_mask[2][kNrKC];  // boxes of the task that read the source
+  __shared__ int s_brow[32];             // packed task: first row of each box
+  __shared__ float4 s_boff[32];          // packed task: each box's offset into the task's frame
   __shared__ int s_pre[kNrEntWin + 1];
   __shared__ float s_sx[kTcR], s_isx[kTcR];
   __shared__ __align__(8) uint64_t mma_done[2], dready, fin;
@@ -146,17 +153,34 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
     const float4* __restrict__ Lt = Lo + base.x;
     const float* __restrict__ xb = xt + (int64_t)base.y * kTcR;
     float* __restrict__ yb = ynear + (int64_t)base.y * kTcR;
+    // packed tasks: several small boxes, each with its first row and frame offset
+    const int2 tb = tbox ? tbox[it] : make_int2(0, 1);
+    if (tid < tb.y) {
+      s_brow[tid] = tbox ? brow[tb.x + tid] : 0;
+      s_boff[tid] = tbox ? boff[tb.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
     for (int r0 = 0; r0 < T.y && ok; r0 += 128) {
       const int mm = min(128, T.y - r0);
-      // the thread's 8 targets (rows r0 + 8 ac + i of the task)
+      // the thread's 8 targets (rows r0 + 8 ac + i of the task), moved into the
+      // task's frame, and the box each belongs to (5 bits per row)
       float4 th[8], tl[8];
       bool tv[8];
+      uint64_t bidx = 0;
+      int bi = 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = 8 * ac + i;
         tv[i] = r < mm;
-        th[i] = tv[i] ? Ht[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tl[i] = tv[i] && !kSmooth ? Lt[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        while (bi + 1 < tb.y && s_brow[bi + 1] <= r0 + r) ++bi;
+        bidx |= (uint64_t)bi << (5 * i);
+        const float4 ph = tv[i] ? Ht[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pl = tv[i] && !kSmooth ? Lt[T.x + r0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 of = s_boff[bi];
+        float ex, ey, ez, ew;
+        th[i] = make_float4(two_sum(ph.x, of.x, ex), two_sum(ph.y, of.y, ey), two_sum(ph.z, of.z, ez),
+                            two_sum(ph.w, of.w, ew));
+        tl[i] = make_float4(pl.x + ex, pl.y + ey, pl.z + ez, pl.w + ew);
       }
       int c = 0;  // chunks of this tile; chunk c accumulates into D(c & 1), added into the total two chunks later
       for (int w0 = T.z; w0 < T.w && ok; w0 += kNrEntWin) {
@@ -198,11 +222,13 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
           if (tid < kNrKC) {
             const int k = k0 + tid;
             int row = -1;
+            uint32_t msk = 0u;
             float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
             if (k < nsrc) {
               const int e = find_entry(s_pre, nw, k);
               const int4 sj = srcs[w0 + e];
               const float4 of = soff[w0 + e];
+              msk = emask ? emask[w0 + e] : ~0u;
               row = sj.x + (k - s_pre[e]);
               const float4 ph = Ht[row], pl = Lt[row];
               float ex, ey, ez, ew;
@@ -213,6 +239,7 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
             s_hi[st][tid] = h;
             s_lo[st][tid] = l;
             s_row[st][tid] = row;
+            s_mask[st][tid] = msk;
           }
           __syncthreads();
           // B: source row k = tid / 4, columns bq .. bq + 15, scaled by 1 / sigma_x, as hi and lo planes
@@ -248,12 +275,15 @@ __global__ void __launch_bounds__(kNrThreads, 2) k_tc_near(const int4* __restric
           for (int j = 0; j < 4; ++j) {
             const int k = (tid >> 4) + 16 * j;
             const bool sv = s_row[st][k] >= 0;
+            const uint32_t msk = s_mask[st][k];
             const float4 sh = s_hi[st][k], sl = s_lo[st][k];
             __half hh[8], ll[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               float f = 0.f;
-              if (tv[i] && sv) f = f32k<KID>(kSmooth ? sqdist1<D>(th[i], sh) : sqdist2<D>(th[i], tl[i], sh, sl), kc);
+              const bool reads = (msk >> (uint32_t)((bidx >> (5 * i)) & 31u)) & 1u;
+              if (tv[i] && sv && reads)
+                f = f32k<KID>(kSmooth ? sqdist1<D>(th[i], sh) : sqdist2<D>(th[i], tl[i], sh, sl), kc);
               split_plain(f, hh[i], ll[i]);
             }
             const int phys = k * 128 + ((acc8 ^ (k & 7)) << 4);
@@ -376,7 +406,7 @@ int tc_near_dk(hodlrdd_s* h, cudaStream_t st, const float* xt, const unsigned in
     const int grid = (int)std::min<int64_t>(n, INT32_MAX);
     k_tc_near<D, KID><<<grid, kNrThreads, kNrSmem, st>>>(P.tasks4.p, DL.t0, DL.t1, P.srcs4.p, P.soff4.p,
                                                           P.hi4[DL.level].p, P.lo4[DL.level].p, xt, colmax, kc, scale,
-                                                          diag, h->ynear.p, nullptr, nullptr, h->err.p);
+                                                          diag, h->ynear.p, nullptr, nullptr, tc_pack(P), h->err.p);
     h->launches += 1;
   };
   for (const DenseLevel& DL : P.coarse4) run(DL, ks, 0.f);
@@ -424,7 +454,7 @@ namespace {
 template <int D, int KID>
 int tc_near_raw_dk(cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs, const float4* soff,
                    const float4* Hi, const float4* Lo, const float* xt, const unsigned int* colmax, float kc,
-                   float* ynear, const int2* tbase, const float2* tsd, int32_t* err) {
+                   float* ynear, const int2* tbase, const float2* tsd, TcPack pk, int32_t* err) {
   static PerDeviceOnce attr;
   HD_TRY(attr.run([] {
     HD_CUDA(cudaFuncSetAttribute(k_tc_near<D, KID>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNrSmem));
@@ -432,7 +462,7 @@ int tc_near_raw_dk(cudaStream_t st, int64_t ntask, const int4* tasks, const int4
   }));
   if (ntask <= 0) return HODLRDD_OK;
   k_tc_near<D, KID><<<(int)std::min<int64_t>(ntask, INT32_MAX), kNrThreads, kNrSmem, st>>>(
-      tasks, 0, ntask, srcs, soff, Hi, Lo, xt, colmax, kc, 1.f, 0.f, ynear, tbase, tsd, err);
+      tasks, 0, ntask, srcs, soff, Hi, Lo, xt, colmax, kc, 1.f, 0.f, ynear, tbase, tsd, pk, err);
   HD_CUDA(cudaGetLastError());
   return HODLRDD_OK;
 }
@@ -440,8 +470,9 @@ int tc_near_raw_dk(cudaStream_t st, int64_t ntask, const int4* tasks, const int4
 template <int D>
 int tc_near_raw_d(int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs, const float4* soff,
                   const float4* Hi, const float4* Lo, const float* xt, const unsigned int* colmax, float kc,
-                  float* ynear, const int2* tbase, const float2* tsd, int32_t* err) {
-#define HD_NEAR_RAW(K) tc_near_raw_dk<D, K>(st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err)
+                  float* ynear, const int2* tbase, const float2* tsd, TcPack pk, int32_t* err) {
+#define HD_NEAR_RAW(K) \
+  tc_near_raw_dk<D, K>(st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, pk, err)
   switch (kid) {
     case HODLRDD_K_LOG: return HD_NEAR_RAW(HODLRDD_K_LOG);
     case HODLRDD_K_MATERN32: return HD_NEAR_RAW(HODLRDD_K_MATERN32);
@@ -461,12 +492,12 @@ int tc_near_raw_d(int kid, cudaStream_t st, int64_t ntask, const int4* tasks, co
 int launch_tc_near_raw(int d, int kid, cudaStream_t st, int64_t ntask, const int4* tasks, const int4* srcs,
                        const float4* soff, const float4* Hi, const float4* Lo, const float* xt,
                        const unsigned int* colmax, float kc, float* ynear, const int2* tbase, const float2* tsd,
-                       int32_t* err) {
+                       TcPack pk, int32_t* err) {
   switch (d) {
-    case 1: return tc_near_raw_d<1>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
-    case 2: return tc_near_raw_d<2>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
-    case 3: return tc_near_raw_d<3>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
-    default: return tc_near_raw_d<4>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, err);
+    case 1: return tc_near_raw_d<1>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, pk, err);
+    case 2: return tc_near_raw_d<2>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, pk, err);
+    case 3: return tc_near_raw_d<3>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, pk, err);
+    default: return tc_near_raw_d<4>(kid, st, ntask, tasks, srcs, soff, Hi, Lo, xt, colmax, kc, ynear, tbase, tsd, pk, err);
   }
 }
 
