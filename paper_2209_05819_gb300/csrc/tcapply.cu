@@ -344,8 +344,9 @@ __global__ void k_tc_colstats(int64_t ncol, const int64_t* __restrict__ colU, co
 }
 
 // The planes of every panel of one stream from the FP64 ACA output. V panels:
-// row k = source point J0 + k, entry j of half hh = V column out0 + 64 hh + j
-// (its t index through vmap). U panels: row k = t index brow + k, entry j of
+// row k = source point brow + k, entry j of half hh = V column out0 + 64 hh + j
+// (its t index through vmap; zero outside the rows of the column's source box,
+// since a panel may hold the columns of several consecutive small boxes). U panels: row k = t index brow + k, entry j of
 // half hh = point out0 + 64 hh + j. Entries are divided by their column's
 // power-of-two scale and split into the high and the scaled low FP16 part;
 // rows >= kvalid and entries past mvalid are zero. One CTA per panel.
@@ -353,6 +354,7 @@ template <bool VMODE>
 __global__ void __launch_bounds__(256) k_tc_pack(int64_t npan, const TcPanel* __restrict__ panels,
                                                  const int32_t* __restrict__ vmap, const int64_t* __restrict__ colU,
                                                  const int64_t* __restrict__ colV, const int32_t* __restrict__ urow0,
+                                                 const int32_t* __restrict__ vrow0, const int32_t* __restrict__ vrows,
                                                  const double* __restrict__ U64, const double* __restrict__ V64,
                                                  const float* __restrict__ su, const float* __restrict__ sv,
                                                  __half* __restrict__ out) {
@@ -366,8 +368,10 @@ __global__ void __launch_bounds__(256) k_tc_pack(int64_t npan, const TcPanel* __
       double v = 0.0;
       if (k < P.kvalid && m < P.mvalid) {
         if constexpr (VMODE) {
+          // packed panels hold several source boxes: a column is zero outside its own box's rows
           const int32_t t = vmap[P.out0 + m];
-          v = V64[colV[t] + k] / (double)sv[t];
+          const int64_t rr = (int64_t)P.brow + k - vrow0[t];
+          if (rr >= 0 && rr < vrows[t]) v = V64[colV[t] + rr] / (double)sv[t];
         } else {
           const int32_t t = P.brow + k;
           v = U64[colU[t] + (P.out0 - urow0[t]) + m] / (double)su[t];
@@ -480,7 +484,8 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
   }
   // per t column: FP64 data offsets, rows, first output point of its U rows
   std::vector<int64_t> hcolU(std::max<int64_t>(ncol, 1)), hcolV(std::max<int64_t>(ncol, 1));
-  std::vector<int32_t> hru(std::max<int64_t>(ncol, 1)), hrv(std::max<int64_t>(ncol, 1)), hur0(std::max<int64_t>(ncol, 1));
+  std::vector<int32_t> hru(std::max<int64_t>(ncol, 1)), hrv(std::max<int64_t>(ncol, 1)), hur0(std::max<int64_t>(ncol, 1)),
+      hvr0(std::max<int64_t>(ncol, 1));
   for (int64_t b = 0; b < nblk; ++b)
     for (int k = 0; k < h->h_rank[b]; ++k) {
       const int64_t t = h->h_toff[b] + k;
@@ -489,14 +494,16 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
       hru[t] = h->h_bm[b];
       hrv[t] = h->h_bn[b];
       hur0[t] = h->h_bI0[b];
+      hvr0[t] = h->h_bJ0[b];
     }
   DevBuf<int64_t> colU, colV;
-  DevBuf<int32_t> ru, rv, ur0;
+  DevBuf<int32_t> ru, rv, ur0, vr0;
   HD_TRY(upload(colU, hcolU, st));
   HD_TRY(upload(colV, hcolV, st));
   HD_TRY(upload(ru, hru, st));
   HD_TRY(upload(rv, hrv, st));
   HD_TRY(upload(ur0, hur0, st));
+  HD_TRY(upload(vr0, hvr0, st));
   std::vector<double4> stats(std::max<int64_t>(ncol, 1), make_double4(0, 0, 0, 0));
   if (ncol > 0) {
     DevBuf<double4> dstats;
@@ -525,13 +532,27 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
       by_src.assign(L.nb, {});
       for (int64_t b = h->h_blk_off[l]; b < h->h_blk_off[l + 1]; ++b)
         if (!h->h_dense[b] && h->h_rank[b] > 0) by_src[h->h_bsj[b]].push_back(b);
-      for (int64_t J = 0; J < L.nb; ++J) {
-        if (by_src[J].empty()) continue;
+      // consecutive small source boxes share a panel (block-diagonal planes:
+      // each column is zero outside its box's rows) when that streams fewer
+      // bytes than their own panels, counting each panel's fixed cost
+      auto cost = [](int64_t rows, int64_t cols) {
+        return pad16(rows) * ((cols + 63) / 64) * 256 + 8192;
+      };
+      std::vector<int64_t> grp;
+      int64_t grows = 0, gcols = 0;
+      auto box_cols = [&](int64_t J) {
+        int64_t c = 0;
+        for (int64_t b : by_src[J]) c += h->h_rank[b];
+        return c;
+      };
+      auto emit = [&](const std::vector<int64_t>& boxes) {
         const int32_t c0 = (int32_t)hvmap.size();
-        for (int64_t b : by_src[J])
-          for (int k = 0; k < h->h_rank[b]; ++k) hvmap.push_back((int32_t)(h->h_toff[b] + k));
+        for (int64_t J : boxes)
+          for (int64_t b : by_src[J])
+            for (int k = 0; k < h->h_rank[b]; ++k) hvmap.push_back((int32_t)(h->h_toff[b] + k));
         const int32_t cols = (int32_t)hvmap.size() - c0;
-        const int32_t n = L.h_bstart[J + 1] - L.h_bstart[J];
+        const int32_t r0 = L.h_bstart[boxes.front()];
+        const int32_t n = L.h_bstart[boxes.back() + 1] - r0;
         for (int32_t m0 = 0; m0 < cols; m0 += 128) {
           TcPanel Q{};
           Q.mvalid = std::min(128, cols - m0);
@@ -541,7 +562,7 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
           Q.K = Q.kstride;
           Q.koff = 0;
           Q.kvalid = n;
-          Q.brow = L.h_bstart[J];
+          Q.brow = r0;
           Q.out0 = c0 + m0;
           Q.sbox = 0;
           Q.slice = l - 1;
@@ -550,7 +571,36 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
           SV.rows += (int64_t)Q.pieces * Q.halves * Q.kstride;
           SV.h_panels.push_back(Q);
         }
+      };
+      auto flush = [&]() {
+        if (!grp.empty()) emit(grp);
+        grp.clear();
+        grows = gcols = 0;
+      };
+      for (int64_t J = 0; J < L.nb; ++J) {
+        if (by_src[J].empty()) {
+          flush();  // the group's rows must stay contiguous
+          continue;
+        }
+        const int64_t nJ = L.h_bstart[J + 1] - L.h_bstart[J], cJ = box_cols(J);
+        if (nJ > 64 || cJ > 128) {
+          flush();
+          emit({J});
+          continue;
+        }
+        if (!grp.empty() && grows + nJ <= 64 && gcols + cJ <= 128 &&
+            cost(grows + nJ, gcols + cJ) <= cost(grows, gcols) + cost(nJ, cJ)) {
+          grp.push_back(J);
+          grows += nJ;
+          gcols += cJ;
+          continue;
+        }
+        flush();
+        grp.push_back(J);
+        grows = nJ;
+        gcols = cJ;
       }
+      flush();
     }
   }
   // ---- U panels: per level and target box, its rows in tiles of 128, K over its t columns
@@ -610,12 +660,12 @@ int pack_tc(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64, 
     HD_TRY(upload(tmpu, whole, st));
     if (!SV.h_panels.empty())
       k_tc_pack<true><<<(int)std::min<size_t>(SV.h_panels.size(), 65535), 256, 0, st>>>(
-          (int64_t)SV.h_panels.size(), tmpv.p, P.tc_vmap.p, colU.p, colV.p, ur0.p, U64.p, V64.p, dsu.p, dsv.p,
-          SV.data.p);
+          (int64_t)SV.h_panels.size(), tmpv.p, P.tc_vmap.p, colU.p, colV.p, ur0.p, vr0.p, rv.p, U64.p, V64.p,
+          dsu.p, dsv.p, SV.data.p);
     if (!whole.empty())
       k_tc_pack<false><<<(int)std::min<size_t>(whole.size(), 65535), 256, 0, st>>>(
-          (int64_t)whole.size(), tmpu.p, P.tc_vmap.p, colU.p, colV.p, ur0.p, U64.p, V64.p, dsu.p, dsv.p,
-          SU.data.p);
+          (int64_t)whole.size(), tmpu.p, P.tc_vmap.p, colU.p, colV.p, ur0.p, vr0.p, rv.p, U64.p, V64.p,
+          dsu.p, dsv.p, SU.data.p);
     HD_CUDA(cudaGetLastError());
     HD_CUDA(cudaStreamSynchronize(st));
   }
