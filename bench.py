@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-skeleton", action="store_true", help="skip the skeleton-form line")
     p.add_argument("--no-serve", action="store_true", help="skip the request-loop (serving) line")
     p.add_argument("--no-admissibility", action="store_true", help="skip the admissibility comparison line")
-    p.add_argument("--only", default=None, choices=["many_rhs", "batch", "solve", "serve"],
+    p.add_argument("--only", default=None, choices=["many_rhs", "batch", "solve", "serve", "admissibility"],
                    help="run only this workload's products (--steps of them after --warmup) and print its line; "
                         "for profiling")
     p.add_argument("--many-n", type=int, default=65536, help="points of the many-right-hand-side workload")
@@ -783,6 +783,17 @@ def serve_only(args):
     print(json.dumps(serving_line(args, torch, hd)))
 
 
+def admissibility_only(args):
+    """The admissibility comparison alone (d=2, N=65536, log r), for profiling."""
+    import torch
+
+    import paper_2209_05819_gb300 as hd
+    from paper_2209_05819_gb300 import build as cbuild
+
+    cbuild.build()
+    print(json.dumps(admissibility_line(args, torch, torch.cuda.current_stream(), hd)))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -795,6 +806,8 @@ def main():
         return solve_only(args)
     if args.only == "serve":
         return serve_only(args)
+    if args.only == "admissibility":
+        return admissibility_only(args)
     import torch
 
     import paper_2209_05819_gb300 as hd
