@@ -909,13 +909,20 @@ void schedule_stream(Stream& S, const std::vector<int32_t>& vfirst, const std::v
   S.h_cwork.clear();
   for (size_t i = 0; i < S.h_splits.size(); ++i)
     for (int w0 = 0; w0 < S.h_splits[i].R; w0 += kCombineRows) S.h_cwork.push_back(make_int2((int)i, w0));
+  // CTA ranges balanced by time, not bytes: a stage costs its bytes plus a
+  // fixed hand-over (the ring round trip, the end-of-panel reduction and the
+  // output indices a one-stage panel waits for), about what 32 KB take to
+  // stream; trees whose finest boxes hold a few points have thousands of
+  // one-stage panels, and a bytes-only split gave some CTAs twenty times the
+  // others' time
+  const int64_t stage_cost = std::max<int64_t>(1, 32768 / esize);
   int64_t total = 0;
-  for (const Stage& st : S.h_stages) total += st.nelem;
+  for (const Stage& st : S.h_stages) total += st.nelem + stage_cost;
   S.h_cta.assign(1, 0);
   int64_t acc = 0;
   const int64_t target = std::max<int64_t>(1, (total + ctas - 1) / ctas);
   for (size_t q = 0; q < S.h_stages.size(); ++q) {
-    acc += S.h_stages[q].nelem;
+    acc += S.h_stages[q].nelem + stage_cost;
     if (S.h_stages[q].last && acc >= target * (int64_t)S.h_cta.size() && (int)S.h_cta.size() < ctas)
       S.h_cta.push_back((int32_t)(q + 1));
   }
