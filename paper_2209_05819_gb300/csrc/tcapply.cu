@@ -388,13 +388,17 @@ __global__ void __launch_bounds__(256) k_tc_pack(int64_t npan, const TcPanel* __
 
 int64_t pad16(int64_t v) { return (v + 15) / 16 * 16; }
 
-// Ranges of consecutive panels per CTA, balanced by the bytes they stream.
+// Ranges of consecutive panels per CTA, balanced by the bytes they move (the
+// factor planes, the B rows, the kTcR-wide output rows) plus a fixed cost per
+// panel (the ring round trip and the epilogue): trees of many small boxes have
+// many one-step panels whose output outweighs their planes.
 void tc_schedule(TcStream& S, int ctas) {
   std::vector<double> w(S.h_panels.size());
   double tot = 0.0;
   for (size_t i = 0; i < w.size(); ++i) {
     const TcPanel& P = S.h_panels[i];
-    w[i] = (double)P.pieces * P.halves * P.K * 128.0 + (double)P.K * kTcR * 4.0 + 16384.0;
+    w[i] = (double)P.pieces * P.halves * P.K * 128.0 + (double)P.K * kTcR * 4.0 + (double)P.mvalid * kTcR * 4.0 +
+           32768.0;
     tot += w[i];
   }
   ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)w.size()));
