@@ -673,6 +673,8 @@ def batch_line(args, torch, hd):
     out["forest_fp16x2"] = {"value": units / (statistics.median(lat) / 1e3), "unit": UNIT,
                             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[-1], "build_s": t_forest,
                             "launches_per_run": fs["launches_per_run"], "near_passes": fs["near_passes"],
+                            "graph_launches_per_run": 1,
+                            "autotuned_panel_cost_bytes": {"vapply": fs["tuned_fixed_v"], "uapply": fs["tuned_fixed_u"]},
                             "rel_err_vs_fp64_max": max(errs), "err_sets": len(errs),
                             "speedup_vs_batch_graph": out["batch_graph"]["p50_ms"] / lat[len(lat) // 2]}
     f.close()

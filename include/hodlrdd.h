@@ -385,8 +385,13 @@ int hodlrdd_batch_destroy(hodlrdd_batch b);
  *              FP32 additions (the same arithmetic on the same data).
  *  HODLRDD_ERR_TIMEOUT when a bounded device-side wait expired (y invalid).
  * hodlrdd_forest_stats
- *  out[5] = total points, bytes of the factor planes (both stages), apply
- *  panels, near-field passes, kernel launches per run.
+ *  out[7] = total points, bytes of the factor planes (both stages), apply
+ *  panels, near-field passes, kernel launches per run (one CUDA graph launch
+ *  replays them), and the fixed cost per panel (bytes' worth) that the
+ *  autotuner picked for the V-apply's and the U-apply's panel schedule.
+ * Creation also tunes: each apply stage's persistent-CTA panel ranges are
+ *  rebuilt for a few fixed costs per panel, timed, and the fastest kept; then
+ *  one run's launches are captured into a CUDA graph that every run replays.
  */
 typedef struct hodlrdd_forest_s* hodlrdd_forest;
 int hodlrdd_forest_create(const hodlrdd_handle* handles, const int* nrhs, int count, hodlrdd_forest* out);

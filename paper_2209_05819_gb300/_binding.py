@@ -532,9 +532,10 @@ class Forest:
         return ys
 
     def stats(self):
-        out = (C.c_int64 * 5)()
+        out = (C.c_int64 * 7)()
         _check(self._lib.hodlrdd_forest_stats(self._f, out), "hodlrdd_forest_stats")
-        keys = ("points", "plane_bytes", "panels", "near_passes", "launches_per_run")
+        keys = ("points", "plane_bytes", "panels", "near_passes", "launches_per_run", "tuned_fixed_v",
+                "tuned_fixed_u")
         return {k: int(v) for k, v in zip(keys, out)}
 
     def close(self):

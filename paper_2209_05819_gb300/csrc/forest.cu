@@ -104,6 +104,9 @@ struct hodlrdd_forest_s {
   cudaStream_t st = nullptr, aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t launches = 0;
+  // the schedules' fixed cost per panel, picked by timing at creation
+  double fixed_v = 32768.0, fixed_u = 32768.0;
+  cudaGraphExec_t graph = nullptr;  // one run's launches, captured once
 };
 
 namespace hd {
@@ -115,6 +118,7 @@ void forest_free(hodlrdd_forest_s* f) {
   if (f->aux) cudaStreamSynchronize(f->aux);
   if (f->ev_fork) cudaEventDestroy(f->ev_fork);
   if (f->ev_join) cudaEventDestroy(f->ev_join);
+  if (f->graph) cudaGraphExecDestroy(f->graph);
   cudaStream_t st = f->st, aux = f->aux;
   delete f;
   if (st) cudaStreamDestroy(st);
@@ -446,6 +450,90 @@ int forest_launch(hodlrdd_forest_s* f) {
   return HODLRDD_OK;
 }
 
+// The autotuner: each apply stage's panel ranges are rebuilt for a few fixed
+// costs per panel (the weight of a panel's hand-over against its bytes), each
+// timed on the forest's own data layout (zero inputs: the arithmetic does not
+// depend on the values), and the fastest kept.
+int forest_tune(hodlrdd_forest_s* f) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
+  cudaStream_t st = f->st;
+  unsigned int* colmax = reinterpret_cast<unsigned int*>(f->pbuf.p + (size_t)std::max<int64_t>(f->parts, 1) * 128 * kTcR);
+  HD_CUDA(cudaMemsetAsync(f->xt.p, 0, (size_t)f->Ntot * kTcR * sizeof(float), st));
+  HD_CUDA(cudaMemsetAsync(f->t.p, 0, (size_t)std::max<int64_t>(f->trank, 1) * kTcR * sizeof(float), st));
+  HD_CUDA(cudaMemsetAsync(colmax, 0, kTcR * sizeof(unsigned int), st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HD_CUDA(cudaEventCreate(&e0));
+  HD_CUDA(cudaEventCreate(&e1));
+  const double cand[4] = {8192.0, 32768.0, 131072.0, 524288.0};
+  int rc = HODLRDD_OK;
+  for (int stage = 0; stage < 2 && rc == HODLRDD_OK; ++stage) {
+    const bool vmode = stage == 0;
+    TcStream& S = vmode ? f->v : f->u;
+    if (S.h_panels.empty()) continue;
+    double best_ms = 1e30, best = 32768.0;
+    for (double c : cand) {
+      tc_schedule_stream(S, sms, c);
+      rc = upload(S.cta, S.h_cta, st);
+      if (rc != HODLRDD_OK) break;
+      TcLaunch L = vmode ? TcLaunch{&f->v, f->xt.p, colmax, f->vmap.p, f->fac.p, f->wbox.p, f->t.p, nullptr, f->Ntot}
+                         : TcLaunch{&f->u, f->t.p, colmax, f->vmap.p, f->fac.p, f->wbox.p, f->ylev.p, f->pbuf.p, 0};
+      rc = launch_tc_stage(vmode, L, f->err.p, st);  // warm
+      if (rc != HODLRDD_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e0, st) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
+      for (int rep = 0; rep < 2 && rc == HODLRDD_OK; ++rep) rc = launch_tc_stage(vmode, L, f->err.p, st);
+      if (rc == HODLRDD_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = cuda_fail(cudaGetLastError(), "forest autotuning", __FILE__, __LINE__);
+      if (rc != HODLRDD_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (rc != HODLRDD_OK) break;
+    (vmode ? f->fixed_v : f->fixed_u) = best;
+    tc_schedule_stream(S, sms, best);
+    rc = upload(S.cta, S.h_cta, st);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HD_TRY(rc);
+  HD_CUDA(cudaStreamSynchronize(st));
+  int32_t code = 0;
+  HD_CUDA(cudaMemcpy(&code, f->err.p, sizeof code, cudaMemcpyDeviceToHost));
+  if (code != 0) {
+    cudaMemset(f->err.p, 0, sizeof code);
+    set_error("hodlrdd_forest_create: a bounded device-side wait expired while tuning");
+    return HODLRDD_ERR_TIMEOUT;
+  }
+  return HODLRDD_OK;
+}
+
+// One run's launches captured into a CUDA graph (after one eager run, which
+// also sets the kernels' attributes outside the capture).
+int forest_capture(hodlrdd_forest_s* f) {
+  HD_TRY(forest_launch(f));
+  HD_CUDA(cudaStreamSynchronize(f->st));
+  cudaGraph_t g = nullptr;
+  HD_CUDA(cudaStreamBeginCapture(f->st, cudaStreamCaptureModeRelaxed));
+  const int rc = forest_launch(f);
+  const cudaError_t e = cudaStreamEndCapture(f->st, &g);
+  if (rc != HODLRDD_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "forest capture", __FILE__, __LINE__);
+  const cudaError_t e2 = cudaGraphInstantiate(&f->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    f->graph = nullptr;
+    return cuda_fail(e2, "forest graph", __FILE__, __LINE__);
+  }
+  return HODLRDD_OK;
+}
+
 }  // namespace
 }  // namespace hd
 
@@ -503,6 +591,8 @@ extern "C" int hodlrdd_forest_create(const hodlrdd_handle* handles, const int* n
     if (rc == HODLRDD_OK) rc = forest_build(f);
     if (rc == HODLRDD_OK) rc = forest_near(f);
     if (rc == HODLRDD_OK) rc = forest_workspace(f);
+    if (rc == HODLRDD_OK) rc = forest_tune(f);
+    if (rc == HODLRDD_OK) rc = forest_capture(f);
   } catch (const std::bad_alloc&) {
     set_error("hodlrdd_forest_create: host allocation failed");
     rc = HODLRDD_ERR_OOM;
@@ -541,7 +631,14 @@ extern "C" int hodlrdd_forest_run(hodlrdd_forest f, const void* const* x, void* 
   for (int i = 0; i < n && e == cudaSuccess; ++i)
     e = cudaMemcpyAsync(f->xin.p + f->info[i].xoff, x[i], (size_t)f->h[i]->N * f->nrhs[i] * sizeof(float),
                         cudaMemcpyDefault, f->st);
-  int rc = e == cudaSuccess ? forest_launch(f) : cuda_fail(e, "hodlrdd_forest_run: inputs", __FILE__, __LINE__);
+  int rc = HODLRDD_OK;
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "hodlrdd_forest_run: inputs", __FILE__, __LINE__);
+  } else {
+    e = cudaGraphLaunch(f->graph, f->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hodlrdd_forest_run", __FILE__, __LINE__);
+    f->launches += 4 + (int64_t)f->passes.size() + (f->nsplit > 0 ? 1 : 0);
+  }
   for (int i = 0; i < n && rc == HODLRDD_OK; ++i) {
     e = cudaMemcpyAsync(y[i], f->yout.p + f->info[i].xoff, (size_t)f->h[i]->N * f->nrhs[i] * sizeof(float),
                         cudaMemcpyDefault, f->st);
@@ -577,5 +674,7 @@ extern "C" int hodlrdd_forest_stats(hodlrdd_forest f, int64_t* out) {
   out[2] = (int64_t)f->v.h_panels.size() + (int64_t)f->u.h_panels.size();
   out[3] = (int64_t)f->passes.size();
   out[4] = 4 + (int64_t)f->passes.size() + (f->nsplit > 0 ? 1 : 0);
+  out[5] = (int64_t)f->fixed_v;
+  out[6] = (int64_t)f->fixed_u;
   return HODLRDD_OK;
 }

@@ -549,7 +549,8 @@ struct TcLaunch {
 int launch_tc_stage(bool vmode, const TcLaunch& L, int32_t* err, cudaStream_t st);
 int launch_tc_combine(int64_t nsplit, const int2* split, const int32_t* splitp, const TcPanel* panels,
                       const float* part, int64_t N, float* ylev, cudaStream_t st);
-void tc_schedule_stream(TcStream& S, int ctas);
+// Panel ranges per CTA, each panel weighed by its bytes plus `fixed` bytes' worth
+void tc_schedule_stream(TcStream& S, int ctas, double fixed = 32768.0);
 int tc_encode_tmap(TcStream& S);
 // Near field (near.cu).
 constexpr int kGuard = 16;        // zero elements around xt and t (per right-hand side)

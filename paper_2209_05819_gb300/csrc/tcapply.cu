@@ -392,13 +392,13 @@ int64_t pad16(int64_t v) { return (v + 15) / 16 * 16; }
 // factor planes, the B rows, the kTcR-wide output rows) plus a fixed cost per
 // panel (the ring round trip and the epilogue): trees of many small boxes have
 // many one-step panels whose output outweighs their planes.
-void tc_schedule(TcStream& S, int ctas) {
+void tc_schedule(TcStream& S, int ctas, double fixed = 32768.0) {
   std::vector<double> w(S.h_panels.size());
   double tot = 0.0;
   for (size_t i = 0; i < w.size(); ++i) {
     const TcPanel& P = S.h_panels[i];
     w[i] = (double)P.pieces * P.halves * P.K * 128.0 + (double)P.K * kTcR * 4.0 + (double)P.mvalid * kTcR * 4.0 +
-           32768.0;
+           fixed;
     tot += w[i];
   }
   ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)w.size()));
@@ -891,7 +891,7 @@ int launch_tc_combine(int64_t nsplit, const int2* split, const int32_t* splitp, 
   return HODLRDD_OK;
 }
 
-void tc_schedule_stream(TcStream& S, int ctas) { tc_schedule(S, ctas); }
+void tc_schedule_stream(TcStream& S, int ctas, double fixed) { tc_schedule(S, ctas, fixed); }
 
 int tc_encode_tmap(TcStream& S) { return encode_tmap(S); }
 
