@@ -627,11 +627,15 @@ __global__ void __launch_bounds__(256) k_combine(const Split* __restrict__ split
 }
 
 // ------------------------------------------------------------- dense ----
-// One warp per task (target rows [I0, I0+m) at one level). Rows are handled G
-// at a time with 32 / G source stripes. Box-relative FP32 coordinates:
-// x_i - x_j = (rel_i - rel_j) + (c_I - c_J) h, where the box offset is exact in
-// FP32, so differences keep full FP32 accuracy at the box scale. The FP64 form
-// uses the global FP64 coordinates.
+// One CTA (256 threads) per task (target rows [I0, I0+m) at one level). Rows
+// are handled G at a time (G a power of two up to 256) with 256 / G source
+// stripes; each stripe's partial sums meet in shared memory and are added in
+// stripe order (fixed, so products are bitwise reproducible). A CTA, not a
+// warp, per task: small trees (C1: 256 leaf tasks) would otherwise leave most
+// SMs idle while each warp walks its task's sources alone. Box-relative FP32
+// coordinates: x_i - x_j = (rel_i - rel_j) + (c_I - c_J) h, where the box
+// offset is exact in FP32, so differences keep full FP32 accuracy at the box
+// scale. The FP64 form uses the global FP64 coordinates.
 template <class Acc, class IO, int NR, int D, bool F64, bool FINAL>
 __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                const int2* __restrict__ srcs, const float* __restrict__ soff,
@@ -641,63 +645,71 @@ __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, i
                                                const Acc* __restrict__ ylev, int kappa,
                                                const int32_t* __restrict__ perm, IO* __restrict__ y, int ldy,
                                                int c0) {
+  constexpr int NT = 256;
+  __shared__ Acc red[NT * NR];
   const int d = D > 0 ? D : d_rt;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int tid = threadIdx.x;
   const float kcf = (float)kc;
-  for (int64_t it = t0 + warp; it < t1; it += nwarps) {
+  for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
     const int4 task = tasks[it];
     const int I0 = task.x, m = task.y;
     int G = 1;
-    while (G < m && G < 32) G <<= 1;
-    const int S = 32 / G;
-    const int gi = lane % G, stripe = lane / G;
+    while (G < m && G < NT) G <<= 1;
+    const int S = NT / G;
+    const int gi = tid % G, stripe = tid / G;
     for (int g0 = 0; g0 < m; g0 += G) {
       const int row = I0 + g0 + gi;
       const bool valid = g0 + gi < m;
       Acc acc[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
-      if constexpr (F64) {
-        double xr[D > 0 ? D : kMaxDim];
-        for (int k = 0; k < d; ++k) xr[k] = valid ? p64[(int64_t)k * N + row] : 0.0;
-        for (int e = task.z; e < task.w; ++e) {
-          const int2 sj = srcs[e];
-          for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
-            double s = 0.0;
-            for (int k = 0; k < d; ++k) {
-              double t = xr[k] - p64[(int64_t)k * N + j];
-              s = fma(t, t, s);
-            }
-            const double f = f64fast_of_s(kid, s, kc);
+      if (valid) {
+        if constexpr (F64) {
+          double xr[D > 0 ? D : kMaxDim];
+          for (int k = 0; k < d; ++k) xr[k] = p64[(int64_t)k * N + row];
+          for (int e = task.z; e < task.w; ++e) {
+            const int2 sj = srcs[e];
+            for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
+              double s = 0.0;
+              for (int k = 0; k < d; ++k) {
+                double t = xr[k] - p64[(int64_t)k * N + j];
+                s = fma(t, t, s);
+              }
+              const double f = f64fast_of_s(kid, s, kc);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
+              for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
+            }
           }
-        }
-      } else {
-        float xr[D > 0 ? D : kMaxDim];
-        for (int k = 0; k < d; ++k) xr[k] = valid ? rel[(int64_t)k * N + row] : 0.f;
-        for (int e = task.z; e < task.w; ++e) {
-          const int2 sj = srcs[e];
-          float off[D > 0 ? D : kMaxDim];
-          for (int k = 0; k < d; ++k) off[k] = soff[(int64_t)e * d + k];
-          for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
-            float s = 0.f;
-            for (int k = 0; k < d; ++k) {
-              float t = (xr[k] - rel[(int64_t)k * N + j]) + off[k];
-              s = fmaf(t, t, s);
-            }
-            const float f = f32_of_s(kid, s, kcf);
+        } else {
+          float xr[D > 0 ? D : kMaxDim];
+          for (int k = 0; k < d; ++k) xr[k] = rel[(int64_t)k * N + row];
+          for (int e = task.z; e < task.w; ++e) {
+            const int2 sj = srcs[e];
+            float off[D > 0 ? D : kMaxDim];
+            for (int k = 0; k < d; ++k) off[k] = soff[(int64_t)e * d + k];
+            for (int j = sj.x + stripe; j < sj.x + sj.y; j += S) {
+              float s = 0.f;
+              for (int k = 0; k < d; ++k) {
+                float t = (xr[k] - rel[(int64_t)k * N + j]) + off[k];
+                s = fmaf(t, t, s);
+              }
+              const float f = f32_of_s(kid, s, kcf);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
+              for (int r = 0; r < NR; ++r) acc[r] += (Acc)f * xt[(int64_t)j * NR + r];
+            }
           }
         }
       }
 #pragma unroll
-      for (int r = 0; r < NR; ++r)
-        for (int o = G; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+      for (int r = 0; r < NR; ++r) red[tid * NR + r] = acc[r];
+      __syncthreads();
       if (stripe == 0 && valid) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          Acc a = Acc(0);
+          for (int q = 0; q < S; ++q) a += red[(q * G + gi) * NR + r];
+          acc[r] = a;
+        }
         if constexpr (FINAL) {
           const int64_t orow = perm[row];
 #pragma unroll
@@ -711,6 +723,7 @@ __global__ void __launch_bounds__(256) k_dense(const int4* __restrict__ tasks, i
           for (int r = 0; r < NR; ++r) ylev_l[(int64_t)row * NR + r] += (Acc)kscale * acc[r];
         }
       }
+      __syncthreads();  // red is reused by the next rows
     }
   }
 }
@@ -1735,16 +1748,19 @@ int chunk_events(hodlrdd_s* h, cudaEvent_t* ev, int n) {
 template <class Acc, class IO, int NR, int D, bool F64>
 int launch_dense(hodlrdd_s* h, cudaStream_t st, int sms, const Acc* xt, Acc* yl, IO* y, int ldy, int c0) {
   const Plan& P = h->plan;
+  (void)sms;
+  // one CTA per task (the hardware scheduler balances tasks of unequal size)
+  auto grid_tasks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(n, 1 << 30)); };
   const double kc = kernel_const(h->K);
   for (const DenseLevel& DL : P.coarse) {
     const float* rel = F64 ? nullptr : P.rel[DL.level].p;
-    k_dense<Acc, IO, NR, D, F64, false><<<grid_warps(DL.t1 - DL.t0, sms), 256, 0, st>>>(
+    k_dense<Acc, IO, NR, D, F64, false><<<grid_tasks(DL.t1 - DL.t0), 256, 0, st>>>(
         P.tasks.p, DL.t0, DL.t1, P.srcs.p, P.soff.p, rel, h->pts64.p, h->N, h->d, h->K.id, kc, h->K.scale,
         h->K.diag, xt, yl + (int64_t)(DL.level - 1) * h->N * NR, yl, h->kappa, h->perm.p, y, ldy, c0);
     h->launches += 1;
   }
   const float* rel = F64 ? nullptr : P.rel[h->kappa].p;
-  k_dense<Acc, IO, NR, D, F64, true><<<grid_warps(P.leaf.t1 - P.leaf.t0, sms), 256, 0, st>>>(
+  k_dense<Acc, IO, NR, D, F64, true><<<grid_tasks(P.leaf.t1 - P.leaf.t0), 256, 0, st>>>(
       P.tasks.p, P.leaf.t0, P.leaf.t1, P.srcs.p, P.soff.p, rel, h->pts64.p, h->N, h->d, h->K.id, kc, h->K.scale,
       h->K.diag, xt, nullptr, yl, level_slices(h), h->perm.p, y, ldy, c0);
   h->launches += 1;
