@@ -670,13 +670,25 @@ def batch_line(args, torch, hd):
         errs.append(float(e.max().item()))
         h64.close()
     fs = f.stats()
+    pr = f.profile()
+    hst = [h.stats() for h in ht]
+    hbm, _ = measured_peaks()
+    # the V-apply stage: its factor planes as streamed (FP16 pairs, panels padded to 16 rows and 64
+    # columns), t written and x_t read, 64 columns of 4 bytes
+    vbytes = (sum(s_["factor_bytes_v"] for s_ in hst) + sum(s_["total_rank"] for s_ in hst) * 256
+              + sum(w.N for w in ws) * 256)
+    roof = {"kernel": "forest V-apply (k_tc_apply<V>, 152 persistent CTAs)", "bound": "hbm",
+            "bytes": vbytes, "stage_ms": pr["vapply_ms"], "achieved": vbytes / (pr["vapply_ms"] / 1e3) / 1e9,
+            "peak": hbm, "unit": "GB/s", "frac": vbytes / (pr["vapply_ms"] / 1e3) / 1e9 / hbm,
+            "stage_ms_all": {k: round(v, 3) for k, v in pr.items()}}
     out["forest_fp16x2"] = {"value": units / (statistics.median(lat) / 1e3), "unit": UNIT,
                             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[-1], "build_s": t_forest,
                             "launches_per_run": fs["launches_per_run"], "near_passes": fs["near_passes"],
                             "graph_launches_per_run": 1,
                             "autotuned_panel_cost_bytes": {"vapply": fs["tuned_fixed_v"], "uapply": fs["tuned_fixed_u"]},
                             "rel_err_vs_fp64_max": max(errs), "err_sets": len(errs),
-                            "speedup_vs_batch_graph": out["batch_graph"]["p50_ms"] / lat[len(lat) // 2]}
+                            "speedup_vs_batch_graph": out["batch_graph"]["p50_ms"] / lat[len(lat) // 2],
+                            "roofline": roof}
     f.close()
     for h in ht:
         h.close()

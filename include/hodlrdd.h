@@ -397,6 +397,10 @@ typedef struct hodlrdd_forest_s* hodlrdd_forest;
 int hodlrdd_forest_create(const hodlrdd_handle* handles, const int* nrhs, int count, hodlrdd_forest* out);
 int hodlrdd_forest_run(hodlrdd_forest f, const void* const* x, void* const* y, void* stream);
 int hodlrdd_forest_stats(hodlrdd_forest f, int64_t* out);
+/* Stage times of one extra run of the forest on the inputs of its last run
+ * (CUDA events; synchronous): ms[5] = gather, V-apply, U-apply with the sums of
+ * cut panels, near field (second stream), whole run. */
+int hodlrdd_forest_profile(hodlrdd_forest f, double* ms);
 int hodlrdd_forest_destroy(hodlrdd_forest f);
 
 /*

@@ -87,6 +87,7 @@ def load():
         "hodlrdd_forest_create": (i32, [C.POINTER(vp), C.POINTER(C.c_int), i32, C.POINTER(vp)]),
         "hodlrdd_forest_run": (i32, [vp, C.POINTER(vp), C.POINTER(vp), vp]),
         "hodlrdd_forest_stats": (i32, [vp, C.POINTER(i64)]),
+        "hodlrdd_forest_profile": (i32, [vp, vp]),
         "hodlrdd_forest_destroy": (i32, [vp]),
         "hodlrdd_debug_ff_eval": (i32, [i32, vp, dbl, vp, vp, i64]),
         "hodlrdd_debug_aca_pool_bytes": (i32, [i64]),
@@ -537,6 +538,12 @@ class Forest:
         keys = ("points", "plane_bytes", "panels", "near_passes", "launches_per_run", "tuned_fixed_v",
                 "tuned_fixed_u")
         return {k: int(v) for k, v in zip(keys, out)}
+
+    def profile(self):
+        """Stage times (ms) of one extra run on the last run's inputs."""
+        ms = np.zeros(5, np.float64)
+        _check(self._lib.hodlrdd_forest_profile(self._f, ms.ctypes.data), "hodlrdd_forest_profile")
+        return dict(zip(("gather_ms", "vapply_ms", "uapply_ms", "near_ms", "run_ms"), (float(v) for v in ms)))
 
     def close(self):
         if getattr(self, "_f", None):

@@ -419,33 +419,40 @@ int forest_workspace(hodlrdd_forest_s* f) {
 }
 
 // One product of every tree on f->st (the near field on f->aux).
-int forest_launch(hodlrdd_forest_s* f) {
+int forest_launch(hodlrdd_forest_s* f, cudaEvent_t* ev = nullptr) {
   cudaStream_t st = f->st;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->device);
   unsigned int* colmax = reinterpret_cast<unsigned int*>(f->pbuf.p + (size_t)std::max<int64_t>(f->parts, 1) * 128 * kTcR);
   const int grid = (int)std::min<int64_t>((f->Ntot * kTcR + 255) / 256, (int64_t)sms * 16);
+  if (ev) HD_CUDA(cudaEventRecord(ev[0], st));
   HD_CUDA(cudaMemsetAsync(colmax, 0, kTcR * sizeof(unsigned int), st));
   k_forest_gather<<<grid, 256, 0, st>>>(f->Ntot, f->tp.p, f->dinfo.p, f->perm.p, f->xin.p, f->xt.p, colmax);
   HD_CUDA(cudaGetLastError());
+  if (ev) HD_CUDA(cudaEventRecord(ev[1], st));
   HD_CUDA(cudaEventRecord(f->ev_fork, st));
   HD_CUDA(cudaMemsetAsync(f->ylev.p, 0, (size_t)std::max<int64_t>(f->ylev_rows, 1) * kTcR * sizeof(float), st));
   TcLaunch lv{&f->v, f->xt.p, colmax, f->vmap.p, f->fac.p, f->wbox.p, f->t.p, nullptr, f->Ntot};
   HD_TRY(launch_tc_stage(true, lv, f->err.p, st));
+  if (ev) HD_CUDA(cudaEventRecord(ev[2], st));
   HD_CUDA(cudaStreamWaitEvent(f->aux, f->ev_fork, 0));
+  if (ev) HD_CUDA(cudaEventRecord(ev[4], f->aux));
   HD_CUDA(cudaMemsetAsync(f->ynear.p, 0, (size_t)f->Ntot * kTcR * sizeof(float), f->aux));
   for (const auto& ps : f->passes)
     HD_TRY(launch_tc_near_raw(f->d, f->kid, f->aux, ps.second - ps.first, f->ntasks.p + ps.first, f->nsrcs.p,
                               f->nsoff.p, f->nhi.p, f->nlo.p, f->xt.p, colmax, f->kc, f->ynear.p,
                               f->nbase.p + ps.first, f->nsd.p + ps.first,
                               TcPack{f->ntbox.p + ps.first, f->nbrow.p, f->nboff.p, f->nemask.p}, f->err.p));
+  if (ev) HD_CUDA(cudaEventRecord(ev[5], f->aux));
   HD_CUDA(cudaEventRecord(f->ev_join, f->aux));
   TcLaunch lu{&f->u, f->t.p, colmax, f->vmap.p, f->fac.p, f->wbox.p, f->ylev.p, f->pbuf.p, 0};
   HD_TRY(launch_tc_stage(false, lu, f->err.p, st));
   HD_TRY(launch_tc_combine(f->nsplit, f->split.p, f->splitp.p, f->u.panels.p, f->pbuf.p, 0, f->ylev.p, st));
+  if (ev) HD_CUDA(cudaEventRecord(ev[3], st));
   HD_CUDA(cudaStreamWaitEvent(st, f->ev_join, 0));
   k_forest_finish<<<grid, 256, 0, st>>>(f->Ntot, f->tp.p, f->dinfo.p, f->perm.p, f->ynear.p, f->ylev.p, f->yout.p);
   HD_CUDA(cudaGetLastError());
+  if (ev) HD_CUDA(cudaEventRecord(ev[6], st));
   f->launches += 4 + (int64_t)f->passes.size() + (f->nsplit > 0 ? 1 : 0);
   return HODLRDD_OK;
 }
@@ -659,6 +666,33 @@ extern "C" int hodlrdd_forest_run(hodlrdd_forest f, const void* const* x, void* 
       return HODLRDD_ERR_TIMEOUT;
     }
   }
+  return rc;
+}
+
+extern "C" int hodlrdd_forest_profile(hodlrdd_forest f, double* ms) {
+  if (!f || !ms) {
+    set_error("hodlrdd_forest_profile: NULL argument");
+    return HODLRDD_ERR_INVALID;
+  }
+  cudaEvent_t ev[7] = {};
+  int rc = HODLRDD_OK;
+  for (int i = 0; i < 7 && rc == HODLRDD_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "forest events", __FILE__, __LINE__);
+  if (rc == HODLRDD_OK) rc = forest_launch(f, ev);
+  if (rc == HODLRDD_OK) {
+    const cudaError_t e = cudaStreamSynchronize(f->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hodlrdd_forest_profile", __FILE__, __LINE__);
+  }
+  if (rc == HODLRDD_OK) {
+    const int pairs[5][2] = {{0, 1}, {1, 2}, {2, 3}, {4, 5}, {0, 6}};
+    for (int k = 0; k < 5; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[pairs[k][0]], ev[pairs[k][1]]);
+      ms[k] = t;
+    }
+  }
+  for (int i = 0; i < 7; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   return rc;
 }
 
