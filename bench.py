@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--near-coords", default="hi", choices=["hi", "hilo"],
                    help="near-field tile coordinates of the headline product: hi only (default; distances carry "
                         "2^-24 h absolute error) or hi + lo pairs (exact distances)")
+    p.add_argument("--near-sms", default="auto",
+                   help="SMs given to the headline product's near field: auto (default; the build times the "
+                        "settings and keeps the fastest), 0 (shared with the applies on every SM) or a count")
     p.add_argument("--n", type=int, default=262144)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--seed", type=int, default=0)
@@ -213,15 +216,19 @@ def scaled_traffic(kernel, algo_bytes, precision, nrhs):
 # one rsqrt evaluates F (a MUFU operation in FP32), and one FMA per right-hand
 # side adds F x_j. FP32 pipe operations per pair: 2d + nrhs; MUFU: 1. As FP64
 # flops (for the FP64 form): d + 2d - 1 for the distance, 1 for F, 2 nrhs.
-def near_roofline(s, d, nrhs, seconds, peaks):
+def near_roofline(s, d, nrhs, seconds, peaks, near_sms=0, sms=None):
+    """near_sms > 0: the near field ran on near_sms of the sms SMs (k_tile_split), so its peak is that share."""
     pairs = int(s["dense_pairs"])
     if seconds <= 0 or pairs == 0:
         return None
     ops = 2 * d + nrhs
-    fp32_ops_peak = peaks["fp32_tflops"] * 1e12 / 2  # FMA lane-operations per second
-    mufu_peak = peaks["mufu_rsqrt_gops"] * 1e9
+    share = near_sms / sms if near_sms and sms else 1.0
+    fp32_ops_peak = peaks["fp32_tflops"] * 1e12 / 2 * share  # FMA lane-operations per second
+    mufu_peak = peaks["mufu_rsqrt_gops"] * 1e9 * share
     achieved = pairs * ops / seconds
-    return {"kernel": "near field (k_tile, second stream)", "bound": "alu", "unit": "G FP32 ops/s",
+    kernel = (f"near field (k_tile_split on {near_sms} of {sms} SMs, second stream)" if near_sms
+              else "near field (k_tile, second stream, sharing the SMs with the applies)")
+    return {"kernel": kernel, "bound": "alu", "unit": "G FP32 ops/s",
             "pairs": pairs, "ops_per_pair": ops, "achieved": achieved / 1e9, "peak": fp32_ops_peak / 1e9,
             "frac": achieved / fp32_ops_peak, "mufu_frac": pairs / seconds / mufu_peak,
             "stage_ms": 1e3 * seconds, "peak_source": "measured (hodlrdd_probe_peaks)", "traffic": None}
@@ -837,7 +844,8 @@ def main():
     nrhs = w.nrhs
     units = w.N * nrhs
 
-    h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision, near_coords=args.near_coords)
+    h = hd.Handle(pts, w.kernel, w.params, w.leaf, w.tol, precision=args.precision, near_coords=args.near_coords,
+                  near_sms=args.near_sms if args.near_sms == "auto" else int(args.near_sms))
     s = h.stats()
     io = torch.float64 if args.precision == "fp64" else torch.float32
     x = torch.from_numpy(np.ascontiguousarray(w.x.reshape(w.N, nrhs))).to(io).cuda()
@@ -952,7 +960,8 @@ def main():
             "stage_ms": {k: round(v, 4) for k, v in stage.items()},
             "stage_share": {k: round(v / sum(stage.values()), 4) for k, v in stage.items()}}
 
-    roof["near"] = near_roofline(s, w.d, nrhs, stage["near"] / 1e3, peaks)
+    roof["near"] = near_roofline(s, w.d, nrhs, stage["near"] / 1e3, peaks, s["near_sms"],
+                                 torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
     roof["fp64"] = fp64["roofline"] if fp64 else None
 
     # the plain FP64 configuration (d=2, N=4096, log r)
@@ -1002,6 +1011,7 @@ def main():
                                            "fp32+fp16": "f32 (factors f32 + f16)"}[
                 args.precision], "data": "synthetic",
             "config": {"workload": workload_name(w), "precision": args.precision, "near_coords": args.near_coords,
+                       "near_sms": s["near_sms"],
                        "factors": ("leading ACA terms FP32, trailing terms FP16 with FP32 column scales, FP32 "
                                    "arithmetic" if args.precision == "fp32+fp16" else
                                    f"{args.precision} U,V with FP32 accumulation" if args.precision != "fp64"

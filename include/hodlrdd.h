@@ -146,7 +146,21 @@ typedef struct hodlrdd_options {
                            FP32 rate; kernel values carry a relative error of about
                            2^-44 (1e-13) instead of 2^-52. Not available for sin r
                            (HODLRDD_ERR_UNSUPPORTED). Ignored by other precisions. */
-  int reserved[3];      /* set to 0 */
+  int near_sms;         /* streaming multiprocessors given to the near field of the
+                           single-right-hand-side FP32 tiles (FP32/FP16/BF16/FP32_FP16
+                           forms, d <= 3), -1 or 0 .. SMs - 1. 0 (default): the near field
+                           runs beside the low-rank applies on every SM. R > 0: the
+                           persistent apply kernels run on SMs - R CTAs that reserve a
+                           whole SM's shared memory each, and the near field runs as R
+                           persistent CTAs of the same size (all its passes in one
+                           launch, tasks taken from a counter), so that neither shares
+                           an SM with the other. Products are the same in both
+                           settings (each pass sums into a buffer of its own; the
+                           buffers are added in pass order, the order in which the
+                           shared setting accumulates them). -1: the build times
+                           products with 0 and with R from about SMs / 8 to 9 SMs / 32
+                           and keeps the fastest (hodlrdd_stats.near_sms). */
+  int reserved[2];      /* set to 0 */
 } hodlrdd_options;
 
 #define HODLRDD_MAX_LEVELS 64
@@ -188,6 +202,7 @@ typedef struct hodlrdd_stats {
   int64_t skeleton_terms;    /* skeleton form: sum of the kept ranks p'. FP64 keeps every ACA
                                 term (p' = p); FP32 keeps the leading terms whose pivot is at
                                 least 2^-23 of the largest pivot before it */
+  int near_sms;              /* the option near_sms in use (-1 resolved by the build) */
 } hodlrdd_stats;
 
 /* Fills *opt with the defaults described above. */

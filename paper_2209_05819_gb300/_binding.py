@@ -33,7 +33,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("dense_if_cheaper", C.c_int), ("max_nrhs", C.c_int),
                 ("aca_max_rank", C.c_int), ("near_mode", C.c_int), ("admissible_face_dim", C.c_int),
                 ("lowrank_form", C.c_int), ("near_coords", C.c_int), ("fp64_near", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("near_sms", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class SolveOptions(C.Structure):
@@ -57,7 +57,7 @@ class Stats(C.Structure):
         ("t_pack_ms", C.c_double), ("t_build_ms", C.c_double), ("device_bytes", C.c_int64),
         ("factor_bytes_u", C.c_int64), ("factor_bytes_v", C.c_int64), ("total_rank", C.c_int64),
         ("lowrank_form", C.c_int), ("skeleton_bytes", C.c_int64), ("skeleton_pairs", C.c_int64),
-        ("tail_cols", C.c_int64), ("skeleton_terms", C.c_int64),
+        ("tail_cols", C.c_int64), ("skeleton_terms", C.c_int64), ("near_sms", C.c_int),
     ]
 
 
@@ -217,7 +217,8 @@ class Handle:
     def __init__(self, points, kernel: int, params=None, leaf: int = 64, tol: float = 1e-8,
                  precision: str = "fp64", dense_if_cheaper: bool = True, max_nrhs: int = 8,
                  aca_max_rank: int = 1024, near_mode: int = 0, admissible_face_dim: int = 0,
-                 lowrank_form: str = "factors", near_coords: str = "hilo", fp64_near: str = "fp64"):
+                 lowrank_form: str = "factors", near_coords: str = "hilo", fp64_near: str = "fp64",
+                 near_sms: int = 0):
         lib = load()
         if isinstance(points, np.ndarray):
             points = np.ascontiguousarray(points, dtype=np.float64)
@@ -241,6 +242,9 @@ class Handle:
         opt.near_coords = NEAR_COORDS[near_coords]
         # FP64 handles: near field in FP64 ("fp64") or float-float on the FP32 pipes ("ff")
         opt.fp64_near = FP64_NEAR[fp64_near]
+        # SMs given to the single-RHS FP32 near field (0: it shares every SM with the
+        # applies; "auto" or -1: chosen by the build from timed products)
+        opt.near_sms = -1 if near_sms == "auto" else int(near_sms)
         p = np.zeros(4, np.float64)
         p[0] = 1.0
         if params is not None:

@@ -243,7 +243,18 @@ struct PanelCfg {
   static constexpr int kStagesN = kFit < 3 ? kFit : 3;
   static constexpr size_t kSmem = (size_t)kStagesN * kSlot + kRed;
   static_assert(kStagesN >= 3, "panel ring needs at least three slots");
+  // a CTA that reserves the whole SM (the near field on SMs of its own) has
+  // room for a fourth slot: 192 KB in flight, for fewer CTAs streaming the
+  // same bytes
+  static constexpr int kStagesWide = kFit < 4 ? kFit : 4;
+  static constexpr size_t smem(int ns) { return (size_t)ns * kSlot + kRed; }
 };
+
+// A panel CTA's dynamic shared memory when it reserves a whole SM: the
+// per-block limit less 512 bytes for its static shared memory (the mbarriers,
+// 128 bytes as compiled); what stays free of the SM's 228 KB is less than the
+// 1 KB every CTA reserves, so no other CTA fits beside it
+constexpr size_t panel_smem_full() { return (size_t)232448 - 512; }
 
 struct PanelMeta {
   Stage st;
@@ -274,12 +285,11 @@ struct PanelArgs {
 // and eight ahead (L2). `issued` counts every stage the ring has taken, over
 // the streams one launch applies. False when a bounded wait expired (the
 // copies already issued have then landed).
-template <class T, int NR>
+template <class T, int NR, int NS>
 __device__ __forceinline__ bool panel_produce(const PanelArgs<T>& a, char* smem, uint64_t* full, uint64_t* empty,
                                               int& issued, int32_t* err, uint64_t once) {
   using Acc = typename Fac<T>::acc;
   using C = PanelCfg<T, NR>;
-  constexpr int NS = C::kStagesN;
   constexpr int A1 = 16 / (int)sizeof(Acc);  // vector elements per 16 bytes
   {
     const int lane = threadIdx.x & 31;
@@ -348,13 +358,12 @@ __device__ __forceinline__ bool panel_produce(const PanelArgs<T>& a, char* smem,
 
 // Consumer warps: apply this CTA's stages of one stream; ibase = the ring index
 // of its first stage. False when a bounded wait expired.
-template <class T, int NR, bool VMODE>
+template <class T, int NR, bool VMODE, int NS>
 __device__ __forceinline__ bool panel_consume(const PanelArgs<T>& a, char* smem, uint64_t* full, uint64_t* empty,
                                               typename Fac<T>::acc* red, int ibase, int32_t* err) {
   using Acc = typename Fac<T>::acc;
   using C = PanelCfg<T, NR>;
   constexpr int E = Fac<T>::E;
-  constexpr int NS = C::kStagesN;
   constexpr int NT = kConsumerWarps * 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q0 = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x] : 0;
@@ -557,32 +566,32 @@ __device__ __forceinline__ void panel_ring_init(uint64_t* full, uint64_t* empty,
   __syncthreads();
 }
 
-template <class T, int NR, bool VMODE>
+// NS: ring slots (PanelCfg::kStagesN, or kStagesWide when the CTA holds a whole SM)
+template <class T, int NR, bool VMODE, int NS>
 __global__ void __launch_bounds__(kSegThreads, 1) k_panel(PanelArgs<T> a, int32_t* __restrict__ err) {
   using C = PanelCfg<T, NR>;
-  constexpr int NS = C::kStagesN;
   extern __shared__ __align__(128) char smem[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS];
   auto* red = reinterpret_cast<typename Fac<T>::acc*>(smem + (size_t)NS * C::kSlot);  // NT * 8
   panel_ring_init<NR>(full, empty, NS);
   if ((threadIdx.x >> 5) == 0) {
     int issued = 0;
-    panel_produce<T, NR>(a, smem, full, empty, issued, err, l2_evict_first());
+    panel_produce<T, NR, NS>(a, smem, full, empty, issued, err, l2_evict_first());
     return;
   }
-  panel_consume<T, NR, VMODE>(a, smem, full, empty, red, 0, err);
+  panel_consume<T, NR, VMODE, NS>(a, smem, full, empty, red, 0, err);
 }
 
 // Mixed storage: one launch applies the FP32 stream and then the FP16 stream of
 // the same stage through one ring (both have the same slot layout), so that the
 // two parts share one persistent CTA per SM instead of following each other.
-template <int NR, bool VMODE>
+template <int NR, bool VMODE, int NS>
 __global__ void __launch_bounds__(kSegThreads, 1) k_panel_mix(PanelArgs<float> a, PanelArgs<__half> b,
                                                               int32_t* __restrict__ err) {
   using C = PanelCfg<float, NR>;
-  static_assert(C::kSlot == PanelCfg<__half, NR>::kSlot && C::kStagesN == PanelCfg<__half, NR>::kStagesN,
+  static_assert(C::kSlot == PanelCfg<__half, NR>::kSlot && C::kStagesN == PanelCfg<__half, NR>::kStagesN &&
+                    C::kStagesWide == PanelCfg<__half, NR>::kStagesWide,
                 "the two element types must share the ring layout");
-  constexpr int NS = C::kStagesN;
   extern __shared__ __align__(128) char smem[];
   __shared__ __align__(8) uint64_t full[NS], empty[NS];
   float* red = reinterpret_cast<float*>(smem + (size_t)NS * C::kSlot);
@@ -590,13 +599,13 @@ __global__ void __launch_bounds__(kSegThreads, 1) k_panel_mix(PanelArgs<float> a
   if ((threadIdx.x >> 5) == 0) {
     const uint64_t once = l2_evict_first();
     int issued = 0;
-    if (!panel_produce<float, NR>(a, smem, full, empty, issued, err, once)) return;
-    panel_produce<__half, NR>(b, smem, full, empty, issued, err, once);
+    if (!panel_produce<float, NR, NS>(a, smem, full, empty, issued, err, once)) return;
+    panel_produce<__half, NR, NS>(b, smem, full, empty, issued, err, once);
     return;
   }
   const int na = blockIdx.x < a.ctas ? a.cta_first[blockIdx.x + 1] - a.cta_first[blockIdx.x] : 0;
-  if (!panel_consume<float, NR, VMODE>(a, smem, full, empty, red, 0, err)) return;
-  panel_consume<__half, NR, VMODE>(b, smem, full, empty, red, na, err);
+  if (!panel_consume<float, NR, VMODE, NS>(a, smem, full, empty, red, 0, err)) return;
+  panel_consume<__half, NR, VMODE, NS>(b, smem, full, empty, red, na, err);
 }
 
 // Sums of cut panels: out = sum over the sub-panels' partials, in sub-panel
@@ -888,6 +897,17 @@ int grid_warps(int64_t items, int sms) {
 // are balanced by bytes and cut only between sub-panels.
 constexpr int64_t kSplitBytes = 1 << 20;
 
+// SMs the persistent apply kernels are scheduled on: all of them, or all but
+// near_sms when the single-right-hand-side FP32 near field has SMs of its own
+int apply_sms(const hodlrdd_s* h, int sms) {
+  const int pr = h->opt.precision;
+  const bool own = h->opt.near_sms > 0 && h->opt.lowrank_form == 0 && h->d <= 3 && pr != HODLRDD_PREC_FP64 &&
+                   pr != HODLRDD_PREC_FP16X2;
+  return own ? std::max(1, sms - h->opt.near_sms) : sms;
+}
+
+void balance_ctas(Stream& S, size_t esize, int ctas);
+
 void schedule_stream(Stream& S, const std::vector<int32_t>& vfirst, const std::vector<int32_t>& out0,
                      size_t esize, int ctas) {
   S.h_panels.clear();
@@ -922,12 +942,16 @@ void schedule_stream(Stream& S, const std::vector<int32_t>& vfirst, const std::v
   S.h_cwork.clear();
   for (size_t i = 0; i < S.h_splits.size(); ++i)
     for (int w0 = 0; w0 < S.h_splits[i].R; w0 += kCombineRows) S.h_cwork.push_back(make_int2((int)i, w0));
-  // CTA ranges balanced by time, not bytes: a stage costs its bytes plus a
-  // fixed hand-over (the ring round trip, the end-of-panel reduction and the
-  // output indices a one-stage panel waits for), about what 32 KB take to
-  // stream; trees whose finest boxes hold a few points have thousands of
-  // one-stage panels, and a bytes-only split gave some CTAs twenty times the
-  // others' time
+  balance_ctas(S, esize, ctas);
+}
+
+// CTA ranges of a stream's stages, balanced by time, not bytes: a stage costs
+// its bytes plus a fixed hand-over (the ring round trip, the end-of-panel
+// reduction and the output indices a one-stage panel waits for), about what
+// 32 KB take to stream; trees whose finest boxes hold a few points have
+// thousands of one-stage panels, and a bytes-only split gave some CTAs twenty
+// times the others' time. Ranges end only where a sub-panel ends.
+void balance_ctas(Stream& S, size_t esize, int ctas) {
   const int64_t stage_cost = std::max<int64_t>(1, 32768 / esize);
   int64_t total = 0;
   for (const Stage& st : S.h_stages) total += st.nelem + stage_cost;
@@ -1054,8 +1078,8 @@ int pack_part(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& V64
     }
   }
   us.elems = off;
-  schedule_stream(vs, vfirst_v, out0_v, sizeof(T), sms);
-  schedule_stream(us, vfirst_u, out0_u, sizeof(T), sms);
+  schedule_stream(vs, vfirst_v, out0_v, sizeof(T), apply_sms(h, sms));
+  schedule_stream(us, vfirst_u, out0_u, sizeof(T), apply_sms(h, sms));
 
   DevBuf<int32_t> dprow0, dpcol0, dvm0;
   DevBuf<LPanel> dvlp, dulp;
@@ -1719,7 +1743,10 @@ int alloc_workspace(hodlrdd_s* h) {
   const int64_t prows = std::max<int64_t>({h->plan.vs.part_rows, h->plan.us.part_rows, 1}) +
                         std::max<int64_t>(h->plan.vs2.part_rows, h->plan.us2.part_rows);
   HD_TRY(h->pbuf.alloc((size_t)prows * nr * acc));
-  if (h->plan.tasks4.n > 0) HD_TRY(h->ynear.alloc((size_t)h->N * nr));
+  if (h->plan.tasks4.n > 0) {
+    HD_TRY(h->ynear.alloc((size_t)h->N * nr));
+    HD_TRY(h->nctr.alloc(1));
+  }
   HD_TRY(h->err.alloc(1));
   HD_CUDA(cudaMemsetAsync(h->xt.p, 0, h->xt.bytes(), h->st));
   HD_CUDA(cudaMemsetAsync(h->tbuf.p, 0, h->tbuf.bytes(), h->st));
@@ -1783,6 +1810,10 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   // packed near field: one right-hand side in d <= 3 (kernel-specialised
   // tiles), else FP32 multi-RHS tiles for d <= 4
   const bool packed1 = !F64 && NR == 1 && ldx == 1 && c0 == 0 && h->d <= 3 && P.tasks4.n > 0;
+  // the near field on SMs of its own (option near_sms): apply CTAs and near
+  // CTAs each reserve a whole SM's shared memory, so neither shares an SM
+  const int nsplit = packed1 && apply_sms(h, sms) < sms ? split_passes(h) : 0;
+  const bool split = nsplit > 0 && nsplit <= std::min(kSplitMaxPass, h->wnr);
   const bool packed = !F64 && h->d <= 4 && P.tasks4.n > 0;
   // FP64, one right-hand side: the float-float near field on the FP32 pipes (option fp64_near)
   const bool ffn = F64 && NR == 1 && h->opt.fp64_near == 1 && P.tasks4.n > 0 && !P.hq4.empty();
@@ -1805,7 +1836,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
     HD_CUDA(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     if (prof) HD_CUDA(cudaEventRecord(ev[5], h->aux));
     if constexpr (!F64) {
-      if (packed1) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
+      if (split) HD_TRY(launch_tiles_split(h, h->aux, reinterpret_cast<const float*>(xt)));
+      else if (packed1) launch_tiles(h, h->aux, reinterpret_cast<const float*>(xt));
       else HD_TRY(launch_tiles_nr(h, h->aux, reinterpret_cast<const float*>(xt), NR));
     } else {
       HD_TRY(launch_tiles_ff(h, h->aux, reinterpret_cast<const double*>(xt), ynear64));
@@ -1848,16 +1880,38 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
         const int grid = std::max(S1.ctas, S2.ctas);
         const PanelArgs<float> A = args(S1, vec, out, m1, nullptr, pb);
         const PanelArgs<__half> B = args16(S2, vec, out, m2, vmode ? P.vscl2.p : nullptr, pb2);
-        if (vmode) k_panel_mix<NR, true><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
-        else k_panel_mix<NR, false><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
+        constexpr int NW = C::kStagesWide, N3 = C::kStagesN;
+        bool wide = false;
+        if constexpr (NR == 1) {
+          if (split) {  // the whole SM's shared memory (near field on SMs of its own), four ring slots
+            if (vmode) k_panel_mix<NR, true, NW><<<grid, kSegThreads, panel_smem_full(), st>>>(A, B, h->err.p);
+            else k_panel_mix<NR, false, NW><<<grid, kSegThreads, panel_smem_full(), st>>>(A, B, h->err.p);
+            wide = true;
+          }
+        }
+        if (!wide) {
+          if (vmode) k_panel_mix<NR, true, N3><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
+          else k_panel_mix<NR, false, N3><<<grid, kSegThreads, C::kSmem, st>>>(A, B, h->err.p);
+        }
         h->launches += 1;
         launched = true;
       }
     }
     if (!launched && S1.ctas > 0 && !S1.h_stages.empty()) {
       const PanelArgs<T> A = args(S1, vec, out, m1, vmode && Fac<T>::scaled ? P.vscl.p : nullptr, pb);
-      if (vmode) k_panel<T, NR, true><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
-      else k_panel<T, NR, false><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
+      constexpr int NW = C::kStagesWide, N3 = C::kStagesN;
+      bool wide = false;
+      if constexpr (NR == 1) {
+        if (split) {
+          if (vmode) k_panel<T, NR, true, NW><<<S1.ctas, kSegThreads, panel_smem_full(), st>>>(A, h->err.p);
+          else k_panel<T, NR, false, NW><<<S1.ctas, kSegThreads, panel_smem_full(), st>>>(A, h->err.p);
+          wide = true;
+        }
+      }
+      if (!wide) {
+        if (vmode) k_panel<T, NR, true, N3><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
+        else k_panel<T, NR, false, N3><<<S1.ctas, kSegThreads, C::kSmem, st>>>(A, h->err.p);
+      }
       h->launches += 1;
     }
     // sums of cut panels, each part from its own partial-sum area
@@ -1893,7 +1947,8 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   if (packed) {
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if constexpr (!F64 && std::is_same<IO, float>::value)
-      HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), level_slices(h), y, NR, ldx, c0));
+      HD_TRY(launch_finish(h, st, reinterpret_cast<const float*>(yl), level_slices(h), y, NR, ldx, c0,
+                           split ? nsplit : 1));
   } else if (ffn) {
     HD_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     if constexpr (F64 && std::is_same<IO, double>::value)
@@ -1916,15 +1971,24 @@ int matvec_chunk(hodlrdd_s* h, const IO* x, IO* y, int ldx, int c0, cudaStream_t
   return HODLRDD_OK;
 }
 
+// dynamic shared memory up to the whole per-block limit, less the rings'
+// mbarriers (launches with the near field on SMs of its own reserve it all)
+template <class T, int NR, int NS>
+int set_smem_attr_ns() {
+  const int smem = (int)panel_smem_full();
+  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, true, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, false, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if constexpr (std::is_same<T, float>::value && NR <= 8) {
+    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, true, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, false, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
+  return HODLRDD_OK;
+}
+
 template <class T, int NR>
 int set_smem_attr_nr() {
-  const int smem = (int)PanelCfg<T, NR>::kSmem;
-  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  HD_CUDA(cudaFuncSetAttribute(k_panel<T, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  if constexpr (std::is_same<T, float>::value && NR <= 8) {
-    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    HD_CUDA(cudaFuncSetAttribute(k_panel_mix<NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  }
+  HD_TRY((set_smem_attr_ns<T, NR, PanelCfg<T, NR>::kStagesN>()));
+  if constexpr (NR == 1) HD_TRY((set_smem_attr_ns<T, NR, PanelCfg<T, NR>::kStagesWide>()));
   return HODLRDD_OK;
 }
 
@@ -1980,6 +2044,80 @@ int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t s
     default:
       return matvec_typed<__nv_bfloat16, float>(h, static_cast<const float*>(x), static_cast<float*>(y), nrhs, st);
   }
+}
+
+// The apply kernels' CTA ranges over apply_sms CTAs, after near_sms changed.
+// No product of the handle may be in flight.
+int rebalance_applies(hodlrdd_s* h) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int ctas = apply_sms(h, sms);
+  Plan& P = h->plan;
+  const size_t e1 = elem_size(h->opt.precision);
+  Stream* streams[4] = {&P.vs, &P.us, &P.vs2, &P.us2};
+  for (int i = 0; i < 4; ++i) {
+    Stream& S = *streams[i];
+    if (S.h_stages.empty()) continue;
+    balance_ctas(S, i < 2 ? e1 : 2, ctas);
+    HD_TRY(upload(S.cta, S.h_cta, h->st));
+  }
+  HD_CUDA(cudaStreamSynchronize(h->st));
+  return HODLRDD_OK;
+}
+
+// Option near_sms = -1: products of a zero vector (the work does not depend on
+// the values) timed with the near field beside the applies and on R SMs of its
+// own, R from 1/8 to 9/32 of the SMs (the near field's share of the product's
+// work on the single-right-hand-side forms); the fastest setting is kept, the
+// shared one unless a split is at least 1% faster.
+int tune_near_sms(hodlrdd_s* h) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->opt.near_sms = 1;
+  const bool can = apply_sms(h, sms) < sms && h->plan.tasks4.n > 0 && h->kappa >= 1 &&
+                   split_passes(h) <= std::min(kSplitMaxPass, h->wnr);
+  h->opt.near_sms = 0;
+  if (!can) return rebalance_applies(h);
+  DevBuf<float> x, y;
+  HD_TRY(x.alloc((size_t)h->N));
+  HD_TRY(y.alloc((size_t)h->N));
+  HD_CUDA(cudaMemsetAsync(x.p, 0, x.bytes(), h->st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HD_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    HD_CUDA(ce);
+  }
+  const int64_t launches = h->launches;
+  std::vector<int> cand = {0};
+  for (int f : {8, 12, 13, 14, 15, 16, 18})  // R = f sms / 64
+    cand.push_back(std::max(1, std::min(sms - 1, (f * sms + 32) / 64)));
+  double best_ms = 0.0;
+  int best = 0;
+  int rc = HODLRDD_OK;
+  for (size_t c = 0; c < cand.size() && rc == HODLRDD_OK; ++c) {
+    h->opt.near_sms = cand[c];
+    rc = rebalance_applies(h);
+    for (int it = 0; it < 2 && rc == HODLRDD_OK; ++it) rc = launch_matvec(h, x.p, y.p, 1, h->st);
+    if (rc != HODLRDD_OK) break;
+    cudaEventRecord(e0, h->st);
+    for (int it = 0; it < 5 && rc == HODLRDD_OK; ++it) rc = launch_matvec(h, x.p, y.p, 1, h->st);
+    cudaEventRecord(e1, h->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = HODLRDD_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c == 0 || ms < best_ms * (best == 0 ? 0.99 : 1.0)) {
+      best_ms = ms;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->launches = launches;
+  HD_TRY(rc);
+  h->opt.near_sms = best;
+  return rebalance_applies(h);
 }
 
 namespace {

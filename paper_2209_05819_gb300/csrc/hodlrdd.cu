@@ -130,7 +130,7 @@ void fill_stats(hodlrdd_s* h) {
                             P.us.splits.bytes() + P.vmap.bytes() + P.vs2.data.bytes() + P.us2.data.bytes() +
                             P.vs2.panels.bytes() + P.us2.panels.bytes() + P.vs2.stages.bytes() +
                             P.us2.stages.bytes() + P.vs2.splits.bytes() + P.us2.splits.bytes() + P.vmap2.bytes() +
-                            h->pbuf.bytes() + P.tasks.bytes() +
+                            h->pbuf.bytes() + h->ynear.bytes() + h->nctr.bytes() + h->err.bytes() + P.tasks.bytes() +
                             P.srcs.bytes() + P.soff.bytes() + P.tasks4.bytes() + P.srcs4.bytes() +
                             P.soff4.bytes() + P.tbox4.bytes() + P.brow4.bytes() + P.boff4.bytes() +
                             P.emask4.bytes());
@@ -155,6 +155,7 @@ void fill_stats(hodlrdd_s* h) {
   s.skeleton_bytes = P.sk_bytes;
   s.skeleton_pairs = P.sk_pairs;
   s.skeleton_terms = P.sk_terms;
+  s.near_sms = h->opt.near_sms;
 }
 
 int validate_build(const double* points, int d, int64_t N, int kernel_id, const double* prm, int leaf, double tol,
@@ -176,6 +177,10 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
   if (o.near_mode < 0 || o.near_mode > 2) { set_error("hodlrdd_build: near_mode must be 0, 1 or 2"); return HODLRDD_ERR_INVALID; }
   if (o.near_coords < 0 || o.near_coords > 1) {
     set_error("hodlrdd_build: near_coords must be 0 or 1");
+    return HODLRDD_ERR_INVALID;
+  }
+  if (o.near_sms < -1 || o.near_sms > 4096) {
+    set_error("hodlrdd_build: near_sms must be -1 or 0 .. SMs - 1");
     return HODLRDD_ERR_INVALID;
   }
   if (o.fp64_near < 0 || o.fp64_near > 1) {
@@ -208,6 +213,14 @@ int validate_build(const double* points, int d, int64_t N, int kernel_id, const 
 int do_build(hodlrdd_s* h, const double* points) {
   auto t0 = std::chrono::steady_clock::now();
   HD_CUDA(cudaGetDevice(&h->device));
+  {
+    int sms = 0;
+    HD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (h->opt.near_sms >= sms) {
+      set_error("hodlrdd_build: near_sms must be -1 or 0 .. SMs - 1");
+      return HODLRDD_ERR_INVALID;
+    }
+  }
   HD_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   HD_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
   HD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -246,6 +259,7 @@ int do_build(hodlrdd_s* h, const double* points) {
   HD_TRY(build_plan(h));
   if (h->opt.lowrank_form == 1) HD_TRY(build_skeleton_plan(h));
   HD_TRY(alloc_workspace(h));
+  if (h->opt.near_sms < 0) HD_TRY(tune_near_sms(h));
   HD_CUDA(cudaStreamSynchronize(h->st));
   h->stats.t_pack_ms = ms_since(t);
   h->stats.t_build_ms = ms_since(t0);

@@ -484,6 +484,7 @@ struct hodlrdd_s {
   int wnr = 8;                 // right-hand sides per chunk the workspace holds (8 or 16)
   hd::DevBuf<char> pbuf;       // partial sums of cut panels
   hd::DevBuf<float> ynear;     // packed near-field sums (tree order)
+  hd::DevBuf<int32_t> nctr;    // task counter of the near field on its own SMs (option near_sms)
   hd::DevBuf<int32_t> err;     // device error word of bounded waits
   std::shared_ptr<void> solve_scratch;  // hodlrdd_solve's buffers when this handle is the inner operator
   bool solve_scratch_f64 = false;
@@ -512,6 +513,10 @@ int pack_factors(hodlrdd_s* h, const DevBuf<double>& U64, const DevBuf<double>& 
 int build_plan(hodlrdd_s* h);
 int alloc_workspace(hodlrdd_s* h);
 int launch_matvec(hodlrdd_s* h, const void* x, void* y, int nrhs, cudaStream_t st);
+// The apply kernels' CTA ranges after near_sms changed; near_sms = -1 resolved
+// by timed products at the end of the build (apply.cu).
+int rebalance_applies(hodlrdd_s* h);
+int tune_near_sms(hodlrdd_s* h);
 int launch_direct(hodlrdd_s* h, const float* x, float* y, cudaStream_t st);
 // Tensor-core form (tcapply.cu).
 constexpr int kTcR = 64;          // right-hand sides per chunk (the MMA N)
@@ -558,8 +563,30 @@ constexpr int kTileThreads = 256; // threads of a near-field tile CTA
 constexpr int kTileRows = 256;    // target rows per tile task
 constexpr int kTileCap = 1024;    // staged source points per chunk
 void launch_tiles(hodlrdd_s* h, cudaStream_t st, const float* xt);
+// The packed single-RHS near field on near_sms SMs of their own (k_tile_split):
+// kSplitGroups tile groups per CTA, at most kSplitMaxPass passes, pass p
+// summing into ynear + p N.
+constexpr int kSplitGroups = 3;
+constexpr int kSplitMaxPass = 8;
+constexpr int kSplitGroupBytes = 2 * kTileCap * 16 + 2 * kTileThreads * 4 + 16;
+struct SplitPass {
+  int64_t t0, n;  // the pass's tasks [t0, t0 + n) of the packed plan
+  const float4* Hi;
+  const float4* Lo;
+  float scale, diag;
+  float* out;
+};
+struct SplitArgs {
+  SplitPass pass[kSplitMaxPass];
+  int npass;
+  int64_t total;
+  int* ctr;
+};
+int split_passes(const hodlrdd_s* h);
+int launch_tiles_split(hodlrdd_s* h, cudaStream_t st, const float* xt);
 int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int ldx = 0, int cx = 0);
-int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0);
+int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0,
+                  int nnear = 1);
 int launch_relhilo(hodlrdd_s* h, int l, float4* Hi, float4* Lo, const double* dlo, cudaStream_t st);
 // float-float near field of FP64 handles (one right-hand side)
 int build_ffcoords(hodlrdd_s* h, int l, const double* dlo, cudaStream_t st);

@@ -25,6 +25,121 @@ namespace {
 // HILO = false (option near_coords = 1): the hi parts alone, the lo parts are
 // neither staged nor read.
 
+// Barriers of the tile body: the whole CTA, or one 256-thread group of a
+// larger CTA (named barrier `id`, the group's threads only).
+struct SyncCta {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncGroup {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kTileThreads) : "memory");
+  }
+};
+
+// One task of the packed near field on kTileThreads threads (tid = the thread's
+// index among them), staging through shi / slo (kTileCap entries each) and
+// red / red2 (kTileThreads each); ends with a barrier, after which the staging
+// arrays may be reused.
+template <int D, int KID, bool HILO, class Sync>
+__device__ __forceinline__ void tile_task(const int4 T, const int4* __restrict__ srcs,
+                                          const float4* __restrict__ soff, const float4* __restrict__ Hi,
+                                          const float4* __restrict__ Lo, const float* __restrict__ xt, float kc,
+                                          float kscale, float kdiag, float* __restrict__ ynear, float4* shi,
+                                          float4* slo, float* red, float* red2, int tid, Sync sync) {
+  const int warp = tid >> 5, lane = tid & 31;
+  // each thread holds two target rows, gi and gi + G
+  int G = 1;
+  while (2 * G < T.y) G <<= 1;
+  const int S = kTileThreads / G;
+  const int gi = tid % G, stripe = tid / G;
+  const bool va = gi < T.y, vb = gi + G < T.y;
+  const int ra = T.x + gi, rb = T.x + gi + G;
+  float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
+  float xa = 0.f, xb = 0.f;
+  if (va) {
+    tha = Hi[ra];
+    if (HILO) tla = Lo[ra];
+    xa = xt[ra];
+  }
+  if (vb) {
+    thb = Hi[rb];
+    if (HILO) tlb = Lo[rb];
+    xb = xt[rb];
+  }
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  for (int e = T.z; e < T.w;) {
+    const int e1 = srcs[e].w;
+    sync();  // the previous chunk has been consumed
+    for (int b = e + warp; b < e1; b += kTileThreads / 32) {
+      const int4 sj = srcs[b];
+      const float4 of = soff[b];
+      for (int k = lane; k < sj.y; k += 32) {
+        const float4 h = Hi[sj.x + k];
+        if (HILO) {
+          const float4 l = Lo[sj.x + k];
+          float ex, ey, ez;
+          const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
+          shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
+          slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
+        } else {
+          shi[sj.z + k] = make_float4(h.x + of.x, h.y + of.y, h.z + of.z, xt[sj.x + k]);
+        }
+      }
+    }
+    const int4 lastb = srcs[e1 - 1];
+    const int n = lastb.z + lastb.y;
+    sync();
+    int f = stripe;
+    for (; f + S < n; f += 2 * S) {
+      const float4 h0 = shi[f], h1 = shi[f + S];
+      if (HILO) {
+        const float4 l0 = slo[f], l1 = slo[f + S];
+        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+        a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
+        b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
+      } else {
+        a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
+        a1 = fmaf(f32k<KID>(sqdist1<D>(tha, h1), kc), h1.w, a1);
+        b1 = fmaf(f32k<KID>(sqdist1<D>(thb, h1), kc), h1.w, b1);
+      }
+    }
+    if (f < n) {
+      const float4 h0 = shi[f];
+      if (HILO) {
+        const float4 l0 = slo[f];
+        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+      } else {
+        a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
+        b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
+      }
+    }
+    e = e1;
+  }
+  red[tid] = a0 + a1;
+  red2[tid] = b0 + b1;
+  sync();
+  if (stripe == 0) {
+    float acc_a = 0.f, acc_b = 0.f;
+    for (int s = 0; s < S; ++s) {
+      acc_a += red[s * G + gi];
+      acc_b += red2[s * G + gi];
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool v = q == 0 ? va : vb;
+      if (!v) continue;
+      const int row = q == 0 ? ra : rb;
+      const float acc = q == 0 ? acc_a : acc_b;
+      ynear[row] += kscale * acc + kdiag * (q == 0 ? xa : xb);
+    }
+  }
+  sync();  // red and the staging arrays are reused by the next task
+}
+
 template <int D, int KID, bool HILO>
 __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict__ tasks, int64_t t0, int64_t t1,
                                                       const int4* __restrict__ srcs, const float4* __restrict__ soff,
@@ -34,99 +149,40 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_tile(const int4* __restrict
   __shared__ float4 shi[kTileCap];  // hi coordinates in the task's frame, x_j in .w
   __shared__ float4 slo[kTileCap];  // lo coordinates
   __shared__ float red[kTileThreads], red2[kTileThreads];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
-    const int4 T = tasks[it];
-    // each thread holds two target rows, gi and gi + G
-    int G = 1;
-    while (2 * G < T.y) G <<= 1;
-    const int S = kTileThreads / G;
-    const int gi = tid % G, stripe = tid / G;
-    const bool va = gi < T.y, vb = gi + G < T.y;
-    const int ra = T.x + gi, rb = T.x + gi + G;
-    float4 tha = make_float4(0.f, 0.f, 0.f, 0.f), tla = tha, thb = tha, tlb = tha;
-    float xa = 0.f, xb = 0.f;
-    if (va) {
-      tha = Hi[ra];
-      if (HILO) tla = Lo[ra];
-      xa = xt[ra];
-    }
-    if (vb) {
-      thb = Hi[rb];
-      if (HILO) tlb = Lo[rb];
-      xb = xt[rb];
-    }
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-    for (int e = T.z; e < T.w;) {
-      const int e1 = srcs[e].w;
-      __syncthreads();  // the previous chunk has been consumed
-      for (int b = e + warp; b < e1; b += kTileThreads / 32) {
-        const int4 sj = srcs[b];
-        const float4 of = soff[b];
-        for (int k = lane; k < sj.y; k += 32) {
-          const float4 h = Hi[sj.x + k];
-          if (HILO) {
-            const float4 l = Lo[sj.x + k];
-            float ex, ey, ez;
-            const float hx = two_sum(h.x, of.x, ex), hy = two_sum(h.y, of.y, ey), hz = two_sum(h.z, of.z, ez);
-            shi[sj.z + k] = make_float4(hx, hy, hz, xt[sj.x + k]);
-            slo[sj.z + k] = make_float4(l.x + ex, l.y + ey, l.z + ez, 0.f);
-          } else {
-            shi[sj.z + k] = make_float4(h.x + of.x, h.y + of.y, h.z + of.z, xt[sj.x + k]);
-          }
-        }
-      }
-      const int4 lastb = srcs[e1 - 1];
-      const int n = lastb.z + lastb.y;
-      __syncthreads();
-      int f = stripe;
-      for (; f + S < n; f += 2 * S) {
-        const float4 h0 = shi[f], h1 = shi[f + S];
-        if (HILO) {
-          const float4 l0 = slo[f], l1 = slo[f + S];
-          a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-          b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-          a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
-          b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
-        } else {
-          a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
-          b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
-          a1 = fmaf(f32k<KID>(sqdist1<D>(tha, h1), kc), h1.w, a1);
-          b1 = fmaf(f32k<KID>(sqdist1<D>(thb, h1), kc), h1.w, b1);
-        }
-      }
-      if (f < n) {
-        const float4 h0 = shi[f];
-        if (HILO) {
-          const float4 l0 = slo[f];
-          a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-          b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-        } else {
-          a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
-          b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
-        }
-      }
-      e = e1;
-    }
-    red[tid] = a0 + a1;
-    red2[tid] = b0 + b1;
-    __syncthreads();
-    if (stripe == 0) {
-      float acc_a = 0.f, acc_b = 0.f;
-      for (int s = 0; s < S; ++s) {
-        acc_a += red[s * G + gi];
-        acc_b += red2[s * G + gi];
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const bool v = q == 0 ? va : vb;
-        if (!v) continue;
-        const int row = q == 0 ? ra : rb;
-        const float acc = q == 0 ? acc_a : acc_b;
-        ynear[row] += kscale * acc + kdiag * (q == 0 ? xa : xb);
-      }
-    }
-    __syncthreads();  // red and the staging arrays are reused by the next task
+  for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x)
+    tile_task<D, KID, HILO>(tasks[it], srcs, soff, Hi, Lo, xt, kc, kscale, kdiag, ynear, shi, slo, red, red2,
+                            (int)threadIdx.x, SyncCta{});
+}
+
+// The same passes on a fixed set of SMs (option near_sms): one CTA per SM of
+// kSplitGroups groups of kTileThreads threads, launched with a whole SM's
+// shared memory so that no other CTA shares its SM. All passes are one launch:
+// a group takes the next task from a counter (tasks of all passes numbered in
+// pass order) and adds its sums into its pass's own buffer, so passes never
+// write the same row at the same time; the final sum adds the buffers in pass
+// order.
+template <int D, int KID, bool HILO>
+__global__ void __launch_bounds__(kSplitGroups* kTileThreads, 1)
+    k_tile_split(const __grid_constant__ SplitArgs a, const int4* __restrict__ tasks, const int4* __restrict__ srcs,
+                 const float4* __restrict__ soff, const float* __restrict__ xt, float kc) {
+  extern __shared__ __align__(16) unsigned char split_sm[];
+  const int g = (int)threadIdx.x / kTileThreads, tid = (int)threadIdx.x % kTileThreads;
+  float4* shi = reinterpret_cast<float4*>(split_sm + (size_t)g * kSplitGroupBytes);
+  float4* slo = shi + kTileCap;
+  float* red = reinterpret_cast<float*>(slo + kTileCap);
+  float* red2 = red + kTileThreads;
+  int* slot = reinterpret_cast<int*>(red2 + kTileThreads);
+  const SyncGroup sync{1 + g};
+  for (;;) {
+    if (tid == 0) *slot = atomicAdd(a.ctr, 1);
+    sync();
+    int64_t k = *slot;
+    if (k >= a.total) break;  // every thread of the group read the same value
+    int p = 0;
+    while (p + 1 < a.npass && k >= a.pass[p].n) k -= a.pass[p++].n;
+    const SplitPass& P = a.pass[p];
+    tile_task<D, KID, HILO>(tasks[P.t0 + k], srcs, soff, P.Hi, P.Lo, xt, kc, P.scale, P.diag, P.out, shi, slo, red,
+                            red2, tid, sync);
   }
 }
 
@@ -225,12 +281,15 @@ __global__ void k_relhilo(const double* __restrict__ p64, int64_t N, int d, int 
 // y_l(i, r) (one per level, two with the mixed storage's FP16 tail), for NR
 // right-hand sides stored NR per point.
 template <int NR>
-__global__ void k_finish(const float* __restrict__ ynear, const float* __restrict__ ylev, int slices, int64_t N,
-                         const int32_t* __restrict__ perm, float* __restrict__ y, int ldy, int c0) {
+__global__ void k_finish(const float* __restrict__ ynear, int nnear, const float* __restrict__ ylev, int slices,
+                         int64_t N, const int32_t* __restrict__ perm, float* __restrict__ y, int ldy, int c0) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     float tot[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) tot[r] = ynear[i * NR + r];
+    for (int p = 1; p < nnear; ++p)  // near-field passes summed into buffers of their own
+#pragma unroll
+      for (int r = 0; r < NR; ++r) tot[r] += ynear[((int64_t)p * N + i) * NR + r];
     for (int l = 0; l < slices; ++l)
 #pragma unroll
       for (int r = 0; r < NR; ++r) tot[r] += ylev[((int64_t)l * N + i) * NR + r];
@@ -398,6 +457,67 @@ void launch_tiles_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   else launch_tiles_kc<D, KID, true>(h, st, xt);
 }
 
+// The passes of launch_tiles_kc as one k_tile_split launch on near_sms CTAs,
+// pass p summing into ynear + p N (zeroed here with the task counter).
+template <int D, int KID, bool HILO>
+int launch_split_kc(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  static PerDeviceOnce attr;
+  HD_TRY(attr.run([] {
+    int dev = 0, optin = 0;
+    HD_CUDA(cudaGetDevice(&dev));
+    HD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    HD_CUDA(cudaFuncSetAttribute(k_tile_split<D, KID, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - 512));
+    return (int)HODLRDD_OK;
+  }));
+  const Plan& P = h->plan;
+  SplitArgs a{};
+  int np = 0;
+  auto add = [&](int64_t t0, int64_t t1, int level, float scale, float diag) {
+    if (t1 <= t0) return;
+    a.pass[np] = SplitPass{t0, t1 - t0, P.hi4[level].p, P.lo4[level].p, scale, diag, h->ynear.p + (size_t)np * h->N};
+    a.total += t1 - t0;
+    ++np;
+  };
+  const float ks = (float)h->K.scale, kd = (float)h->K.diag;
+  for (const DenseLevel& DL : P.coarse4) add(DL.t0, DL.t1, DL.level, ks, 0.f);
+  add(P.excl4.t0, P.excl4.t1, P.excl4.level, -ks, 0.f);
+  add(P.leaf4.t0, P.leaf4.t1, P.leaf4.level, ks, kd);
+  a.npass = np;
+  a.ctr = h->nctr.p;
+  HD_CUDA(cudaMemsetAsync(h->ynear.p, 0, (size_t)np * h->N * sizeof(float), st));
+  HD_CUDA(cudaMemsetAsync(h->nctr.p, 0, sizeof(int32_t), st));
+  int dev = 0, optin = 0;
+  HD_CUDA(cudaGetDevice(&dev));
+  HD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // the per-block limit less 512 bytes: less than the 1 KB a CTA reserves stays free on the SM
+  k_tile_split<D, KID, HILO><<<h->opt.near_sms, kSplitGroups * kTileThreads, optin - 512, st>>>(
+      a, P.tasks4.p, P.srcs4.p, P.soff4.p, xt, (float)kernel_const(h->K));
+  h->launches += 1;
+  HD_CUDA(cudaGetLastError());
+  return HODLRDD_OK;
+}
+
+template <int D, int KID>
+int launch_split_k(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  return h->opt.near_coords == 1 ? launch_split_kc<D, KID, false>(h, st, xt) : launch_split_kc<D, KID, true>(h, st, xt);
+}
+
+template <int D>
+int launch_split_d(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  switch (h->K.id) {
+    case HODLRDD_K_LOG: return launch_split_k<D, HODLRDD_K_LOG>(h, st, xt);
+    case HODLRDD_K_INV_R: return launch_split_k<D, HODLRDD_K_INV_R>(h, st, xt);
+    case HODLRDD_K_MATERN32: return launch_split_k<D, HODLRDD_K_MATERN32>(h, st, xt);
+    case HODLRDD_K_GAUSS: return launch_split_k<D, HODLRDD_K_GAUSS>(h, st, xt);
+    case HODLRDD_K_EXP: return launch_split_k<D, HODLRDD_K_EXP>(h, st, xt);
+    case HODLRDD_K_INV_R2_4D: return launch_split_k<D, HODLRDD_K_INV_R2_4D>(h, st, xt);
+    case HODLRDD_K_R: return launch_split_k<D, HODLRDD_K_R>(h, st, xt);
+    case HODLRDD_K_SIN: return launch_split_k<D, HODLRDD_K_SIN>(h, st, xt);
+    default: return launch_split_k<D, HODLRDD_K_INV_SQRT1P>(h, st, xt);
+  }
+}
+
 template <int D>
 void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, const float* xt) {
   switch (h->K.id) {
@@ -414,6 +534,23 @@ void launch_tiles_d(hodlrdd_s* h, cudaStream_t st, const float* xt) {
 }
 
 }  // namespace
+
+int split_passes(const hodlrdd_s* h) {
+  const Plan& P = h->plan;
+  int np = 0;
+  for (const DenseLevel& DL : P.coarse4) np += DL.t1 > DL.t0;
+  np += P.excl4.t1 > P.excl4.t0;
+  np += P.leaf4.t1 > P.leaf4.t0;
+  return np;
+}
+
+int launch_tiles_split(hodlrdd_s* h, cudaStream_t st, const float* xt) {
+  switch (h->d) {
+    case 1: return launch_split_d<1>(h, st, xt);
+    case 2: return launch_split_d<2>(h, st, xt);
+    default: return launch_split_d<3>(h, st, xt);
+  }
+}
 
 // Packed near-field launches (FP32, d <= 3, one right-hand side) on stream st,
 // accumulating into ynear (zeroed here).
@@ -514,16 +651,18 @@ int launch_tiles_nr(hodlrdd_s* h, cudaStream_t st, const float* xt, int nr, int 
 }
 
 // y = near + sum of the level slices, scattered to the original order.
-int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0) {
+int launch_finish(hodlrdd_s* h, cudaStream_t st, const float* ylev, int slices, float* y, int nr, int ldy, int c0,
+                  int nnear) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   const int grid = (int)std::min<int64_t>((h->N + 255) / 256, sms * 16);
+  const float* yn = h->ynear.p;
   switch (nr) {
-    case 1: k_finish<1><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
-    case 2: k_finish<2><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
-    case 4: k_finish<4><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
-    case 8: k_finish<8><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
-    default: k_finish<16><<<grid, 256, 0, st>>>(h->ynear.p, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 1: k_finish<1><<<grid, 256, 0, st>>>(yn, nnear, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 2: k_finish<2><<<grid, 256, 0, st>>>(yn, nnear, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 4: k_finish<4><<<grid, 256, 0, st>>>(yn, nnear, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    case 8: k_finish<8><<<grid, 256, 0, st>>>(yn, nnear, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
+    default: k_finish<16><<<grid, 256, 0, st>>>(yn, nnear, ylev, slices, h->N, h->perm.p, y, ldy, c0); break;
   }
   h->launches += 1;
   HD_CUDA(cudaGetLastError());

@@ -32,6 +32,7 @@ def test_option_defaults(lib):
     assert lib.hodlrdd_options_default(C.byref(o)) == hd.OK
     assert (o.precision, o.dense_if_cheaper, o.max_nrhs, o.aca_max_rank) == (0, 1, 8, 1024)
     assert (o.near_mode, o.admissible_face_dim, o.lowrank_form, o.near_coords) == (0, 0, 0, 0)
+    assert (o.fp64_near, o.near_sms) == (0, 0)
     assert C.sizeof(B.Options) == 12 * 4
     assert lib.hodlrdd_options_default(None) == hd.ERR_INVALID
 
@@ -88,6 +89,10 @@ def test_build_ex_rejects_bad_options(lib):
     lib.hodlrdd_options_default(C.byref(o))
     o.near_coords = 2
     assert lib.hodlrdd_build_ex(pts.ctypes.data, 2, 10, 0, None, 8, 1e-8, C.byref(o), C.byref(h)) == hd.ERR_INVALID
+    lib.hodlrdd_options_default(C.byref(o))
+    o.near_sms = -2
+    assert lib.hodlrdd_build_ex(pts.ctypes.data, 2, 10, 0, None, 8, 1e-8, C.byref(o), C.byref(h)) == hd.ERR_INVALID
+    assert b"near_sms" in lib.hodlrdd_last_error()
 
 
 def test_null_handle_calls(lib):
