@@ -91,30 +91,31 @@ __device__ __forceinline__ void tile_task(const int4 T, const int4* __restrict__
     const int n = lastb.z + lastb.y;
     sync();
     int f = stripe;
+#pragma unroll(HILO ? 1 : 2)
     for (; f + S < n; f += 2 * S) {
       const float4 h0 = shi[f], h1 = shi[f + S];
       if (HILO) {
         const float4 l0 = slo[f], l1 = slo[f + S];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
-        a1 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h1, l1), kc), h1.w, a1);
-        b1 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h1, l1), kc), h1.w, b1);
+        acc_pair<KID>(sqdist2<D>(tha, tla, h0, l0), kc, h0.w, a0);
+        acc_pair<KID>(sqdist2<D>(thb, tlb, h0, l0), kc, h0.w, b0);
+        acc_pair<KID>(sqdist2<D>(tha, tla, h1, l1), kc, h1.w, a1);
+        acc_pair<KID>(sqdist2<D>(thb, tlb, h1, l1), kc, h1.w, b1);
       } else {
-        a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
-        a1 = fmaf(f32k<KID>(sqdist1<D>(tha, h1), kc), h1.w, a1);
-        b1 = fmaf(f32k<KID>(sqdist1<D>(thb, h1), kc), h1.w, b1);
+        acc_pair<KID>(sqdist1<D>(tha, h0), kc, h0.w, a0);
+        acc_pair<KID>(sqdist1<D>(thb, h0), kc, h0.w, b0);
+        acc_pair<KID>(sqdist1<D>(tha, h1), kc, h1.w, a1);
+        acc_pair<KID>(sqdist1<D>(thb, h1), kc, h1.w, b1);
       }
     }
     if (f < n) {
       const float4 h0 = shi[f];
       if (HILO) {
         const float4 l0 = slo[f];
-        a0 = fmaf(f32k<KID>(sqdist2<D>(tha, tla, h0, l0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist2<D>(thb, tlb, h0, l0), kc), h0.w, b0);
+        acc_pair<KID>(sqdist2<D>(tha, tla, h0, l0), kc, h0.w, a0);
+        acc_pair<KID>(sqdist2<D>(thb, tlb, h0, l0), kc, h0.w, b0);
       } else {
-        a0 = fmaf(f32k<KID>(sqdist1<D>(tha, h0), kc), h0.w, a0);
-        b0 = fmaf(f32k<KID>(sqdist1<D>(thb, h0), kc), h0.w, b0);
+        acc_pair<KID>(sqdist1<D>(tha, h0), kc, h0.w, a0);
+        acc_pair<KID>(sqdist1<D>(thb, h0), kc, h0.w, b0);
       }
     }
     e = e1;

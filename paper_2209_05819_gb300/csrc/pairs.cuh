@@ -47,6 +47,29 @@ __device__ __forceinline__ float f32k(float s, float c) {
   else return rsqrt_hw(1.0f + sqrt_hw(s));
 }
 
+// a += F(s) w with F = f32k<KID>. For the kernels that are zero at r = 0 the
+// value is left out by a predicated multiply-add (s below the smallest normal
+// number: a coincident point) instead of a select of zero: one instruction less
+// per pair, the same sums (a + 0 w = a).
+template <int KID>
+__device__ __forceinline__ void acc_pair(float s, float c, float w, float& a) {
+  if constexpr (KID == HODLRDD_K_INV_R || KID == HODLRDD_K_INV_R2_4D || KID == HODLRDD_K_LOG) {
+    float f;
+    if constexpr (KID == HODLRDD_K_INV_R) f = rsqrt_hw(s);
+    else if constexpr (KID == HODLRDD_K_INV_R2_4D) f = c * rcp_hw(s);
+    else f = 0.5f * logf(s);
+    const float lim = KID == HODLRDD_K_LOG ? 0.0f : kTinySq;
+    if constexpr (KID == HODLRDD_K_LOG)
+      asm("{\n\t.reg .pred p;\n\tsetp.gt.f32 p, %1, %2;\n\t@p fma.rn.f32 %0, %3, %4, %0;\n\t}"
+          : "+f"(a) : "f"(s), "f"(lim), "f"(f), "f"(w));
+    else
+      asm("{\n\t.reg .pred p;\n\tsetp.ge.f32 p, %1, %2;\n\t@p fma.rn.f32 %0, %3, %4, %0;\n\t}"
+          : "+f"(a) : "f"(s), "f"(lim), "f"(f), "f"(w));
+  } else {
+    a = fmaf(f32k<KID>(s, c), w, a);
+  }
+}
+
 // 1/sqrt(s) to about one ulp: the hardware approximation refined by one Newton
 // step, y1 = y0 + y0 (1 - s y0^2) / 2, with the residual formed by an FMA.
 __device__ __forceinline__ float rsqrt_nt(float s) {
