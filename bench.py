@@ -186,13 +186,16 @@ def measured_peaks():
 # DRAM traffic of each apply stage (its panel and combine launches) per
 # algorithmic byte, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum per launch) of the d=3 N=65536 case of this workload
-# with one right-hand side, per storage precision; scaled to a full launch by
-# the bytes processed (traffic grows with the factor bytes). It is reported
-# only while the apply source is the one that was captured.
+# with one right-hand side, per storage precision, with the near field on SMs
+# of its own (near_sms 32: the apply kernels' four-slot ring on 120 CTAs);
+# scaled to a full launch by the bytes processed (traffic grows with the factor
+# bytes). It is reported only while the apply source is the one that was
+# captured and the product ran in that configuration (near_sms > 0).
 TRAFFIC_CAPTURE = {
-    "apply_sha256": "610da9c2ee1ec2a2780ee704f6663d03ec7740e9af51b24b2f8660847b365f16",
+    "apply_sha256": "e7170237b287aade596668c107215e67a821197b5eed3005fd1d810d2e8595ff",
     "nrhs": 1,
-    "ratio": {"fp32+fp16": {"vapply": 1.0033, "uapply": 1.0012}},  # mean over the two captured matvecs
+    "near_sms_split": True,
+    "ratio": {"fp32+fp16": {"vapply": 1.0046, "uapply": 1.0014}},  # mean over the two captured matvecs
 }
 
 
@@ -203,10 +206,11 @@ def apply_source_sha256():
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def scaled_traffic(kernel, algo_bytes, precision, nrhs):
+def scaled_traffic(kernel, algo_bytes, precision, nrhs, near_sms):
     c = TRAFFIC_CAPTURE
     r = c["ratio"].get(precision, {})
-    if c["apply_sha256"] is None or kernel not in r or nrhs != c["nrhs"] or apply_source_sha256() != c["apply_sha256"]:
+    if (c["apply_sha256"] is None or kernel not in r or nrhs != c["nrhs"] or (near_sms > 0) != c["near_sms_split"]
+            or apply_source_sha256() != c["apply_sha256"]):
         return None
     return r[kernel] * algo_bytes
 
@@ -954,7 +958,7 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = algo[dom] / (stage[dom] / 1e3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": scaled_traffic(dom, algo[dom], args.precision, nrhs),
+            "frac": achieved / peak, "traffic": scaled_traffic(dom, algo[dom], args.precision, nrhs, s["near_sms"]),
             "peak_source": peak_kind, "algorithmic_bytes": algo[dom],
             "algorithmic_bytes_per_kernel": algo,
             "stage_ms": {k: round(v, 4) for k, v in stage.items()},
