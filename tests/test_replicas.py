@@ -105,10 +105,12 @@ def test_traffic_is_scaled_only_for_the_captured_source_and_storage():
     try:
         cap["apply_sha256"] = bench.apply_source_sha256()
         r = cap["ratio"]["fp32+fp16"]["vapply"]
-        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1) == r * 1e9
-        assert bench.scaled_traffic("vapply", 1e9, "bf16", 1) is None      # no capture for that storage
-        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 4) is None  # nor for other chunk widths
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1, 33) == r * 1e9
+        assert bench.scaled_traffic("vapply", 1e9, "bf16", 1, 33) is None      # no capture for that storage
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 4, 33) is None  # nor for other chunk widths
+        # captured with the near field on SMs of its own: not for the shared setting's kernels
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1, 0) is None
         cap["apply_sha256"] = "0" * 64  # the apply source changed since the capture
-        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1) is None
+        assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1, 33) is None
     finally:
         cap["apply_sha256"] = saved
