@@ -48,9 +48,11 @@ __device__ __forceinline__ void tile_task(const int4 T, const int4* __restrict__
                                           float kscale, float kdiag, float* __restrict__ ynear, float4* shi,
                                           float4* slo, float* red, float* red2, int tid, Sync sync) {
   const int warp = tid >> 5, lane = tid & 31;
-  // each thread holds two target rows, gi and gi + G
-  int G = 1;
-  while (2 * G < T.y) G <<= 1;
+  // each thread holds two target rows, gi and gi + G with G = ceil(m / 2), and
+  // sweeps one of S = 256 / G source stripes; the 256 - S G threads left over
+  // sweep nothing (a power-of-two G would leave up to half the row slots empty
+  // for boxes just above a power of two)
+  const int G = max(1, (T.y + 1) / 2);
   const int S = kTileThreads / G;
   const int gi = tid % G, stripe = tid / G;
   const bool va = gi < T.y, vb = gi + G < T.y;
@@ -90,7 +92,7 @@ __device__ __forceinline__ void tile_task(const int4 T, const int4* __restrict__
     const int4 lastb = srcs[e1 - 1];
     const int n = lastb.z + lastb.y;
     sync();
-    int f = stripe;
+    int f = stripe < S ? stripe : n;  // threads past the S stripes sweep nothing
 #pragma unroll(HILO ? 1 : 2)
     for (; f + S < n; f += 2 * S) {
       const float4 h0 = shi[f], h1 = shi[f + S];
