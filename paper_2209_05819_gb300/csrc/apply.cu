@@ -2091,7 +2091,7 @@ int tune_near_sms(hodlrdd_s* h) {
   }
   const int64_t launches = h->launches;
   std::vector<int> cand = {0};
-  for (int f : {8, 11, 12, 13, 14, 15, 16, 18})  // R = f sms / 64
+  for (int f : {8, 12, 13, 14, 15, 16, 18})  // R = f sms / 64
     cand.push_back(std::max(1, std::min(sms - 1, (f * sms + 32) / 64)));
   double best_ms = 0.0;
   int best = 0;
