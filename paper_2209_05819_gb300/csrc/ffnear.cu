@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(kFfThreads, 2) k_tile_ff(const int4* __restric
   const FfExp E{K.c0, K.c1, K.c2, K.inv, tab};
   for (int64_t it = t0 + blockIdx.x; it < t1; it += gridDim.x) {
     const int4 T = tasks[it];
-    int G = 1;
-    while (2 * G < T.y) G <<= 1;
+    // two rows per thread, G = ceil(m / 2) row pairs and S = kFfThreads / G
+    // source stripes; the kFfThreads - S G threads left over sweep nothing
+    const int G = max(1, (T.y + 1) / 2);
     const int S = kFfThreads / G;
     const int gi = tid % G, stripe = tid / G;
     const bool va = gi < T.y, vb = gi + G < T.y;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kFfThreads, 2) k_tile_ff(const int4* __restric
       const int n = lastb.z + lastb.y;
       __syncthreads();
       ff acc_a = {0.f, 0.f}, acc_b = {0.f, 0.f};
-      for (int f = stripe; f < n; f += S) {
+      for (int f = stripe < S ? stripe : n; f < n; f += S) {
         const float4 q = sq[f], r = sr[f];
         const float2 x2 = sx[f];
         const ff xv = {x2.x, x2.y};
