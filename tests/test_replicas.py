@@ -114,3 +114,17 @@ def test_traffic_is_scaled_only_for_the_captured_source_and_storage():
         assert bench.scaled_traffic("vapply", 1e9, "fp32+fp16", 1, 33) is None
     finally:
         cap["apply_sha256"] = saved
+
+
+def test_near_roofline_takes_the_share_of_its_sms():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    peaks = {"fp32_tflops": 78.0, "mufu_rsqrt_gops": 5000.0}
+    s = {"dense_pairs": 1e9}
+    whole = bench.near_roofline(s, 3, 1, 1e-3, peaks)
+    part = bench.near_roofline(s, 3, 1, 1e-3, peaks, near_sms=38, sms=152)
+    assert whole["achieved"] == part["achieved"]
+    assert abs(part["peak"] - whole["peak"] / 4) < 1e-9 * whole["peak"]
+    assert abs(part["frac"] - 4 * whole["frac"]) < 1e-12
+    assert "38 of 152" in part["kernel"] and bench.near_roofline({"dense_pairs": 0}, 3, 1, 1e-3, peaks) is None
